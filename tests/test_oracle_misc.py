@@ -1,0 +1,51 @@
+"""Pins for the oracle's Adam step (against torch.optim.Adam on CPU, the library
+special case), loss and PSNR (closed forms), and the input generators."""
+
+import math
+
+import numpy as np
+import pytest
+
+from gs2d_inputs import conferencing_frame, random_gaussians, smooth_noise_target
+
+
+def test_adam_matches_torch_cpu(oracle):
+    torch = pytest.importorskip("torch")
+    g = np.random.Generator(np.random.PCG64(5))
+    p0 = g.normal(size=(9, 17))
+    tp = torch.tensor(p0, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([tp], lr=1e-2, betas=(0.9, 0.999), eps=1e-8)
+    p, m, v = p0.copy(), np.zeros_like(p0), np.zeros_like(p0)
+    for step in range(1, 8):
+        grad = g.normal(size=p0.shape) * (10.0 ** g.uniform(-4, 1))
+        opt.zero_grad()
+        tp.grad = torch.tensor(grad, dtype=torch.float64)
+        opt.step()
+        p, m, v = oracle.adam_step(p, grad, m, v, step)
+        np.testing.assert_allclose(p, tp.detach().numpy(), rtol=1e-12, atol=1e-14)
+
+
+def test_loss_and_psnr_closed_forms(oracle):
+    t = np.full((3, 8, 8), 0.5)
+    img = t + 0.1
+    loss, g = oracle.l2_loss(img, t)
+    assert loss == pytest.approx(0.01, rel=1e-12)
+    np.testing.assert_allclose(g, 2 * 0.1 / img.size)
+    assert oracle.psnr(img, t) == pytest.approx(20.0, rel=1e-12)
+    # PSNR clamps the rendered image to [0, 1]; the loss does not
+    assert oracle.psnr(np.full_like(t, 7.0), np.ones_like(t)) == math.inf
+    assert oracle.l2_loss(np.full_like(t, 7.0), np.ones_like(t))[0] == pytest.approx(36.0)
+
+
+def test_generators_are_seeded_and_shaped():
+    a = random_gaussians(100, 256, 256, seed=0)
+    b = random_gaussians(100, 256, 256, seed=0)
+    assert a.shape == (9, 100) and a.dtype == np.float32
+    np.testing.assert_array_equal(a, b)
+    assert np.all((a[0] >= 0) & (a[0] < 256))
+    assert np.all((a[2] >= 1) & (a[2] <= 8)) and np.all((a[8] >= 0.2) & (a[8] <= 1))
+    t = smooth_noise_target(64, 48, seed=1)
+    assert t.shape == (3, 48, 64) and t.min() >= 0 and t.max() <= 1
+    f, m = conferencing_frame(320, 180, seed=1)
+    assert f.shape == (3, 180, 320) and m.shape == (180, 320)
+    assert abs(m.mean() - 0.3) < 0.01
