@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Benchmark: rasterizer fwd+bwd ms/iter at 1080p with 20k Gaussians, and encode
+seconds per frame to 35 dB PSNR.
+
+Workload: one 1920x1080 RGB FP32 synthetic video-conferencing frame (smooth
+background, centred elliptical subject of 30 % area with band-limited texture)
+and 20,000 Gaussians, 70 % inside the subject (seeded stand-in for the paper's
+VCD talking-head data).  A timed step is one fitting iteration through the C
+ABI: project -> bin_sort -> render_l2 (fused forward + L2 loss + backward +
+per-Gaussian reduction) -> adam_step, inputs resident in HBM; L2 is flushed
+(256 MiB write) before every timed step and each step is timed with CUDA events
+on the launching stream.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs N independent replicas (one frame per GPU, launched by torchrun);
+value = max-over-ranks time / (N * K) ms per frame-iteration.  The reference
+arm times the CPU oracle (brute-force renderer with analytic gradients, exact
+bounding-box mode) on the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+W, H, N_GAUSS, SEED = 1920, 1080, 20000, 1
+METRIC = "fwd+bwd ms/iter @1080p,20k Gaussians; encode s/frame to 35 dB PSNR vs plain"
+UNIT = "ms/iter"
+WORKLOAD = ("1920x1080 RGB FP32 synthetic conferencing frame (seed 1), 20000 Gaussians "
+            "(70% inside the subject ellipse), L2 loss, Adam lr 1e-2")
+# FP32-pipe operations and MUFU ex2 per contributing (pixel, Gaussian) pair of the
+# fused fit kernel: forward 8 (sigma + predicate) + 3 (accumulate); backward 8
+# (recompute) + 3 (colour sums) + 4 (dL/dsigma) + 7 (quadratic-form moments).
+OPS_PER_HIT = 33
+MUFU_PER_HIT = 2
+SMS, FP32_LANES, MUFU_LANES, SM_MAX_MHZ = 152, 128, 32, 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--encode-iters", type=int, default=2000)
+    ap.add_argument("--target-psnr", type=float, default=35.0)
+    ap.add_argument("--no-encode", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def workload(seed):
+    from gs2d_inputs import conferencing_frame, conferencing_gaussians
+    frame, mask = conferencing_frame(W, H, seed=seed)
+    params = conferencing_gaussians(frame, mask, N_GAUSS, seed=seed)
+    return frame, params
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+
+def oracle_iteration(orc, p, m, v, step, frame):
+    res = orc.loss_and_grad(p, frame, fast=True)
+    return orc.adam_step(p, res["grad"], m, v, step)
+
+
+def time_oracle(frame, params, min_seconds, max_iters=None, warmup=1):
+    import numpy as np
+    import oracle as orc
+    cores = orc.set_threads(0)
+    p = params.astype(np.float64)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    for s in range(1, warmup + 1):
+        p, m, v = oracle_iteration(orc, p, m, v, s, frame)
+    times = []
+    t_all = time.perf_counter()
+    step = warmup
+    while True:
+        step += 1
+        t0 = time.perf_counter()
+        p, m, v = oracle_iteration(orc, p, m, v, step, frame)
+        times.append(time.perf_counter() - t0)
+        if max_iters is not None and len(times) >= max_iters:
+            break
+        if max_iters is None and time.perf_counter() - t_all >= min_seconds and len(times) >= 3:
+            break
+    return times, cores
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    frame, params = workload(SEED)
+    times, cores = time_oracle(frame, params, 0.0, max_iters=args.steps, warmup=args.warmup)
+    ms = 1e3 * statistics.fmean(times)
+    sample = (f"{args.steps} full oracle fit iterations (fwd+bwd in exact bounding-box mode + "
+              f"Adam, double precision) on the benchmark workload")
+    line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "cpu"},
+            "cpu_baseline": {"value": ms, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": ms, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for row in out.strip().splitlines():
+            f = [x.strip() for x in row.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2505_09324_gb300 import GaussianRasterizer, _native as nat, build
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    nat.load()
+    dev = torch.device("cuda", local)
+    frame_np, params_np = workload(SEED + rank)
+    frame = torch.from_numpy(frame_np).to(dev)
+    params0 = torch.from_numpy(params_np).to(dev)
+    rast = GaussianRasterizer(W, H, N_GAUSS, device=dev)
+    plan, ws = rast.plan, rast.ws_ptr
+    params = params0.clone()
+    grads = torch.empty_like(params)
+    m = torch.zeros_like(params)
+    v = torch.zeros_like(params)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = int(stream.cuda_stream)
+    step_no = [0]
+
+    def fit_step(p_t):
+        step_no[0] += 1
+        nat.project(plan, ws, p_t.data_ptr(), sp)
+        nat.bin_sort(plan, ws, sp)
+        nat.render_l2(plan, ws, p_t.data_ptr(), frame.data_ptr(), grads.data_ptr(), 0, 0, sp)
+        nat.adam_step(p_t.data_ptr(), grads.data_ptr(), m.data_ptr(), v.data_ptr(), p_t.numel(),
+                      step_no[0], 0, None, sp)
+
+    launches_per_step = 1 + (3 if N_GAUSS > 0 else 1) + 1 + 3 * plan.sort_passes + 1 + 2 + 1
+
+    # pair statistics at the start of the timed region (roofline work count)
+    rast.prepare(params)
+    pairs0, hits0 = rast.count_pairs()
+
+    for _ in range(args.warmup):
+        fit_step(params)
+    torch.cuda.synchronize(dev)
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    wall0 = time.perf_counter()
+    for k in range(K):
+        flush.zero_()
+        e = ev[k]
+        step_no[0] += 1
+        e[0].record(stream)
+        nat.project(plan, ws, params.data_ptr(), sp)
+        e[1].record(stream)
+        nat.bin_sort(plan, ws, sp)
+        e[2].record(stream)
+        nat.render_l2(plan, ws, params.data_ptr(), frame.data_ptr(), grads.data_ptr(), 0, 0, sp)
+        e[3].record(stream)
+        nat.adam_step(params.data_ptr(), grads.data_ptr(), m.data_ptr(), v.data_ptr(),
+                      params.numel(), step_no[0], 0, None, sp)
+        e[4].record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    st = rast.status()
+    if st != 0:
+        raise RuntimeError(f"device status {nat.STATUS_NAMES.get(st, st)} during the benchmark")
+    rast.prepare(params)
+    pairs1, hits1 = rast.count_pairs()
+
+    per = {"project": [], "bin_sort": [], "render_l2": [], "adam": [], "step": []}
+    for e in ev:
+        per["project"].append(e[0].elapsed_time(e[1]))
+        per["bin_sort"].append(e[1].elapsed_time(e[2]))
+        per["render_l2"].append(e[2].elapsed_time(e[3]))
+        per["adam"].append(e[3].elapsed_time(e[4]))
+        per["step"].append(e[0].elapsed_time(e[4]))
+    total_ms = sum(per["step"])
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / K
+    value = total_ms / (K * world)
+
+    # roofline of the dominant call (fused forward + loss + backward + reduction)
+    t_render = statistics.fmean(per["render_l2"]) * 1e-3
+    hits = 0.5 * (hits0 + hits1)
+    f_hz = SM_MAX_MHZ * 1e6
+    peak_fp32 = SMS * FP32_LANES * f_hz / 1e12
+    peak_mufu = SMS * MUFU_LANES * f_hz / 1e12
+    achieved = OPS_PER_HIT * hits / t_render / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_fp32,
+                "unit": "Top/s (FP32 pipe)", "frac": achieved / peak_fp32, "traffic": None,
+                "kernel": "render_l2 (k_render_l2 + k_reduce_chain)",
+                "mufu_frac": MUFU_PER_HIT * hits / t_render / 1e12 / peak_mufu,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz; MUFU 32/SM/clk"}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if K > 0:
+        h_frame = torch.from_numpy(frame_np).pin_memory()
+        h_params = torch.from_numpy(params_np).clone().pin_memory()
+        h_loss = torch.empty(2).pin_memory()
+        d_loss = torch.empty(2, device=dev)
+        d_frame = torch.empty_like(frame)
+        d_params = torch.empty_like(params)
+        e2e_steps = max(5, min(K, 50))
+        m.zero_()
+        v.zero_()
+        torch.cuda.synchronize(dev)
+        tot = 0.0
+        for k in range(e2e_steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            d_frame.copy_(h_frame, non_blocking=True)
+            d_params.copy_(h_params, non_blocking=True)
+            nat.project(plan, ws, d_params.data_ptr(), sp)
+            nat.bin_sort(plan, ws, sp)
+            nat.render_l2(plan, ws, d_params.data_ptr(), d_frame.data_ptr(), grads.data_ptr(), 0,
+                          d_loss.data_ptr(), sp)
+            nat.adam_step(d_params.data_ptr(), grads.data_ptr(), m.data_ptr(), v.data_ptr(),
+                          d_params.numel(), k + 1, 0, None, sp)
+            h_loss.copy_(d_loss, non_blocking=True)
+            h_params.copy_(d_params, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        e2e = {"value": tot / e2e_steps / world, "unit": UNIT,
+               "h2d_bytes_per_step": frame.numel() * 4 + params.numel() * 4,
+               "d2h_bytes_per_step": 8 + params.numel() * 4, "steps": e2e_steps}
+
+    # encode to the PSNR target with the captured-graph fit loop
+    encode = None
+    if not args.no_encode:
+        side = torch.cuda.Stream(dev)
+        p_enc = params0.clone()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        with torch.cuda.stream(side):
+            out = rast.encode_frame(frame, p_enc, args.encode_iters, target_psnr=args.target_psnr,
+                                    check_every=25, stream=side)
+        side.synchronize()
+        secs = time.perf_counter() - t0
+        encode = {"seconds": secs, "iters": out["iters"], "psnr": out["psnr"],
+                  "target_psnr": args.target_psnr, "reached": out["psnr"] >= args.target_psnr,
+                  "ms_per_iter_graph": 1e3 * secs / max(out["iters"], 1),
+                  "init": "synthetic ROI-shaped Gaussian set (gs2d_inputs.conferencing_gaussians)",
+                  "status": out["status"]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        times, cores = time_oracle(frame_np, params_np, args.cpu_seconds)
+        cpu = {"value": 1e3 * statistics.fmean(times), "unit": UNIT, "cores": cores,
+               "kind": "oracle",
+               "sample": f"{len(times)} full oracle fit iterations on this workload "
+                         f"(exact bounding-box mode, double precision), ~{sum(times):.0f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "global_batch": world, "image": [W, H],
+                           "gaussians": N_GAUSS, "l2": "flushed before each timed step",
+                           "parallelism": f"replicas{world}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches_per_step * K, "clocks": clocks,
+                "wall_s_timed_region": wall,
+                "kernels_ms": {k: statistics.fmean(vv) for k, vv in per.items()},
+                "pairs": {"listed": pairs0, "hits": hits0, "listed_end": pairs1,
+                          "hits_end": hits1},
+                "encode": encode}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -40,6 +40,7 @@ __all__ = [
     "smooth_noise_target",
     "SubjectMotion",
     "conferencing_frame",
+    "conferencing_gaussians",
     "conferencing_sequence",
     "random_motion",
     "clip_table",
@@ -181,6 +182,40 @@ def conferencing_frame(width: int, height: int, seed: int, t: int = 0,
         frame[ch] = alpha * fg + (1.0 - alpha) * bgc
     mask = rho <= 1.0
     return frame.astype(np.float32), mask
+
+
+def conferencing_gaussians(frame: np.ndarray, mask: np.ndarray, n: int, seed: int,
+                           roi_frac: float = 0.7) -> np.ndarray:
+    """Seeded Gaussian set shaped like an ROI-initialised fit of a conferencing
+    frame: ``roi_frac`` of the means uniform inside the mask, the rest outside;
+    isotropic-ish footprints sized so each Gaussian covers its share of its
+    region (variance area / (4 pi), the variance of a disk of that area);
+    colour sampled from the frame at the mean; weight 1.  A synthetic stand-in
+    for timing and parity work (the initialiser itself is not here)."""
+    g = rng(seed)
+    _, h, w = frame.shape
+    n_roi = int(round(roi_frac * n))
+    out = np.empty((9, n), dtype=np.float64)
+    ys, xs = np.nonzero(mask)
+    yb, xb = np.nonzero(~mask)
+    for sl, (py, px) in ((slice(0, n_roi), (ys, xs)), (slice(n_roi, n), (yb, xb))):
+        k = sl.stop - sl.start
+        if k <= 0:
+            continue
+        if len(px) == 0:
+            py, px = np.nonzero(np.ones_like(mask))
+        pick = g.integers(0, len(px), k)
+        out[0, sl] = px[pick] + g.uniform(0.0, 1.0, k)
+        out[1, sl] = py[pick] + g.uniform(0.0, 1.0, k)
+        s = math.sqrt(len(px) / k / (4.0 * math.pi))
+        out[2, sl] = s * g.uniform(0.8, 1.25, k)
+        out[4, sl] = s * g.uniform(0.8, 1.25, k)
+        out[3, sl] = g.normal(0.0, 0.2 * s, k)
+    xi = np.clip(out[0].astype(np.int64), 0, w - 1)
+    yi = np.clip(out[1].astype(np.int64), 0, h - 1)
+    out[5:8] = frame[:, yi, xi]
+    out[8] = 1.0
+    return out.astype(np.float32)
 
 
 def conferencing_sequence(width: int, height: int, seed: int, frames: int,

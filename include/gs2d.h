@@ -1,0 +1,196 @@
+/*
+ * gs2d.h -- C ABI of the GB300 (sm_103a) 2D Gaussian-splatting frame encoder.
+ *
+ * The library implements the hot path of the video encoder of "Neural Video
+ * Compression using 2D Gaussian Splatting" (arXiv 2505.09324): fitting N 2D
+ * Gaussians to a frame by gradient steps (Sec. 3.2 A), through a
+ * differentiable tile-based rasterizer (Sec. 3) that blends by the
+ * accumulated-sum rule of Eq. 2 over Gaussians parametrised by mean, Cholesky
+ * factor (Eq. 1) and colour (Sec. 3.1).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Parameters: one float32 array of 9*n values, structure-of-arrays, row r at
+ *   params + r*n, rows (mu_x, mu_y, l1, l2, l3, c_r, c_g, c_b, w).  mu is in
+ *   pixels; L = [[l1, 0], [l2, l3]] and Sigma = L L^T (Eq. 1); the colour
+ *   coefficient c'_n of Eq. 2 is w_n * c_n.
+ * Images: float32 [3][H][W] planar, pixel (x, y) centred at (x + 0.5, y + 0.5).
+ * Blending (Eq. 2): C(p) = sum_n w_n c_n exp(-sigma_n(p)) with
+ *   sigma_n(p) = 1/2 (p - mu_n)^T Sigma_n^{-1} (p - mu_n), over the Gaussians
+ *   with finite parameters, det Sigma > det_eps and sigma_n(p) <= tau_n,
+ *   tau_n = min(sigma_cut, ln(|w_n| / alpha_min)); ascending n, FP32.
+ * Memory: the caller allocates and owns every buffer.  Pointers marked
+ *   "device" must be CUDA device (or managed) memory on the current device;
+ *   "host" pointers are ordinary host memory.  The library allocates no device
+ *   memory.  `ws` is a device workspace of gs2d_plan.ws_bytes bytes, 256-byte
+ *   aligned, laid out by gs2d_plan_init, and zero-filled by the caller before
+ *   its first use (its status word must start at GS2D_OK); one workspace serves
+ *   one plan and one stream at a time.
+ * Streams: every device call is asynchronous and ordered on `stream`
+ *   (a cudaStream_t passed as void*; NULL is the legacy default stream).
+ * Errors: argument errors are detected on the host and returned at once
+ *   (GS2D_ERR_INVALID_ARG).  Launch failures return GS2D_ERR_CUDA.  Errors
+ *   found by kernels (entry capacity exceeded) are recorded in a status word in
+ *   the workspace; gs2d_ws_status() reads it (synchronising the stream).
+ *   gs2d_last_error() returns a message for the calling thread's last error.
+ */
+#ifndef GS2D_H
+#define GS2D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GS2D_OK = 0,
+  GS2D_ERR_INVALID_ARG = 1, /* bad size, pointer, plan or alignment        */
+  GS2D_ERR_CUDA = 2,        /* a CUDA call or kernel launch failed          */
+  GS2D_ERR_CAPACITY = 3,    /* more (tile, Gaussian) pairs than max_entries */
+  GS2D_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up           */
+  GS2D_ERR_BOUNDS = 5       /* a device-side bounds check failed            */
+} gs2d_status;
+
+/* Rasterizer and optimiser constants.  The paper fixes none of them; these
+ * are the project's readings (gs2d_config_default): tile 16, sigma_cut 4.5 (the
+ * 3-sigma ellipse), alpha_min 1/255, det_eps 1e-8, Adam lr 1e-2, betas
+ * (0.9, 0.999), eps 1e-8. */
+typedef struct {
+  int32_t tile;      /* tile edge in pixels; 16 is the supported value */
+  float sigma_cut;   /* sigma cut-off, > 0 */
+  float alpha_min;   /* minimum |w| exp(-sigma), > 0 */
+  float det_eps;     /* minimum det Sigma, >= 0 */
+  float lr, beta1, beta2, eps; /* Adam */
+} gs2d_config;
+
+/* Host-side plan: image size, Gaussian count, capacity and the workspace
+ * layout.  Filled by gs2d_plan_init; treat as read-only afterwards. */
+typedef struct {
+  int32_t width, height, n;
+  int32_t tile, tiles_x, tiles_y, num_tiles;
+  int32_t tile_bits;   /* bits of a tile id (radix-sort key width) */
+  int32_t sort_passes; /* 8-bit digit passes over tile_bits */
+  int32_t sort_blocks; /* CTAs of each radix pass */
+  int64_t max_entries; /* capacity for (tile, Gaussian) pairs */
+  gs2d_config cfg;
+  uint64_t ws_bytes;   /* device workspace size the caller must allocate */
+  uint64_t off[20];    /* internal: byte offsets of workspace sections */
+  uint64_t magic;      /* internal: set by gs2d_plan_init */
+} gs2d_plan;
+
+/* Fills *cfg with the defaults listed above. */
+void gs2d_config_default(gs2d_config* cfg);
+
+/* sizeof(gs2d_plan) and sizeof(gs2d_config) as compiled into the library, so
+ * that foreign-language bindings can verify their struct layouts. */
+size_t gs2d_sizeof_plan(void);
+size_t gs2d_sizeof_config(void);
+
+/* Lays out a workspace for a W x H frame and n Gaussians with room for
+ * max_entries (tile, Gaussian) pairs (0 picks max(2^20, 16 n)).
+ * cfg may be NULL (defaults).  Host only; no CUDA call.
+ * Errors: W, H < 1, n < 0, tile != 16, non-positive constants. */
+gs2d_status gs2d_plan_init(gs2d_plan* plan, int32_t width, int32_t height, int32_t n,
+                           int64_t max_entries, const gs2d_config* cfg);
+
+/* Projection (Sec. 3: the per-Gaussian step of tile-based rasterization).
+ * Reads params (device, 9n floats) and writes, into ws, each Gaussian's
+ * screen-space record (conic in Cholesky form, cut-off, weighted colour), its
+ * tile rectangle and tile count; culls non-finite, degenerate (det <= det_eps),
+ * invisible (|w| < alpha_min) and off-image Gaussians (count 0). */
+gs2d_status gs2d_project(const gs2d_plan* plan, void* ws, const float* params, void* stream);
+
+/* Binning and sort (Sec. 3 tile-based rasterization; 2D has no depth, so the
+ * order inside a tile is the Gaussian index): exclusive scan of the tile
+ * counts, emission of one (tile, n) entry per covered tile, a stable LSD radix
+ * sort by tile id, and per-tile ranges [start, end) into the sorted list.
+ * Needs gs2d_project on the same ws first.  If the entries exceed
+ * max_entries, the status word is set to GS2D_ERR_CAPACITY and the sorted list
+ * is empty (renders then produce zero). */
+gs2d_status gs2d_bin_sort(const gs2d_plan* plan, void* ws, void* stream);
+
+/* Forward render, Eq. 2.  img: device [3][H][W] output (every pixel written).
+ * Needs gs2d_bin_sort first. */
+gs2d_status gs2d_render_fwd(const gs2d_plan* plan, void* ws, float* img, void* stream);
+
+/* Backward render: given dimg = dL/dC (device [3][H][W]), writes grads
+ * (device, 9n floats, same layout as params) = dL/dparams through Eq. 2 and
+ * Eq. 1.  Recomputes the blend from the saved per-tile lists (no per-pixel
+ * state is stored by the forward pass).  params must be the values given to
+ * gs2d_project.  Culled Gaussians get zero gradient. */
+gs2d_status gs2d_render_bwd(const gs2d_plan* plan, void* ws, const float* params,
+                            const float* dimg, float* grads, void* stream);
+
+/* Fused forward + L2 loss + backward for fitting: L = mean over 3HW of
+ * (C - target)^2.  target: device [3][H][W].  grads: device 9n floats
+ * (dL/dparams).  img: device [3][H][W] or NULL (the rendered image is then not
+ * stored).  loss: device, 2 floats or NULL: {L, mean squared error of C
+ * clamped to [0, 1]} (the latter gives PSNR = -10 log10).  Needs
+ * gs2d_bin_sort first. */
+gs2d_status gs2d_render_l2(const gs2d_plan* plan, void* ws, const float* params,
+                           const float* target, float* grads, float* img, float* loss,
+                           void* stream);
+
+/* One Adam step (the "optimization steps" of Sec. 4.1; Adam with bias
+ * correction is a project reading) over count floats: m = b1 m + (1-b1) g,
+ * v = b2 v + (1-b2) g^2, p -= lr (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps).
+ * params, grads, m, v: device, count floats each.  step >= 1.  mask: device
+ * uint8 per Gaussian (count / 9 entries, parameter k belongs to Gaussian
+ * k % (count / 9)) or NULL; masked-out Gaussians keep params, m and v.
+ * cfg NULL means defaults. */
+gs2d_status gs2d_adam_step(float* params, const float* grads, float* m, float* v, int64_t count,
+                           int32_t step, const uint8_t* mask, const gs2d_config* cfg, void* stream);
+
+/* Fits the plan's n Gaussians to a frame (Sec. 3.2 A: optimise N Gaussians
+ * to the frame; I-frames start from an initialiser's output, P-frames from the
+ * previous frame's Gaussians).  Runs up to `iters` iterations of
+ * project -> bin_sort -> render_l2 -> adam_step, replayed as a captured CUDA
+ * graph on non-default streams (plain launches on the legacy default stream).
+ * Every check_every iterations (>= 1) the PSNR of the clamped render is read
+ * back; the loop stops once it reaches target_psnr (<= 0 disables the test).
+ * target: device [3][H][W].  params: device 9n floats, in: start, out: fitted.
+ * adam_m, adam_v: device 9n floats each, zeroed by this call (the optimiser
+ * state restarts per frame).  psnr_trace: host, NULL or room for
+ * iters / check_every + 1 floats (PSNR after each check).  iters_done,
+ * final_psnr: host, may be NULL.  Synchronises the stream before returning.
+ * Returns GS2D_ERR_CAPACITY if the entry capacity was exceeded (iters_done
+ * tells where; re-plan with more max_entries and continue from params). */
+gs2d_status gs2d_encode_frame(const gs2d_plan* plan, void* ws, const float* target, float* params,
+                              float* adam_m, float* adam_v, int32_t iters, float target_psnr,
+                              int32_t check_every, float* psnr_trace, int32_t* iters_done,
+                              float* final_psnr, void* stream);
+
+/* Copies the sorted list state to host memory for inspection (tests and
+ * tools): n_entries (host, int64), keys (host, may be NULL: tile ids of the
+ * sorted list, max_keys entries at most), values (host, may be NULL: Gaussian
+ * index of each sorted entry), ranges (host, may be NULL: [num_tiles][2]
+ * int32), counts (host, may be NULL: per-Gaussian tile count, n int32).
+ * Synchronises the stream. */
+gs2d_status gs2d_read_bins(const gs2d_plan* plan, const void* ws, int64_t* n_entries,
+                           uint32_t* keys, uint32_t* values, int64_t max_keys, int32_t* ranges,
+                           int32_t* counts, void* stream);
+
+/* Work statistics of the current sorted list (diagnostics, autotuning and
+ * roofline accounting): pairs = sum over tiles of (pixels of the tile inside
+ * the image) x (list length), i.e. the (pixel, Gaussian) pairs a tile
+ * rasterizer visits; hits = the pairs that contribute to Eq. 2 (the cut-off
+ * predicate holds).  Writes host int64 values (either may be NULL).  Launches
+ * one counting kernel and synchronises the stream. */
+gs2d_status gs2d_count_pairs(const gs2d_plan* plan, void* ws, int64_t* pairs, int64_t* hits,
+                             void* stream);
+
+/* Synchronises the stream and returns the workspace status word
+ * (GS2D_OK or the first device-detected error); reset != 0 clears it. */
+gs2d_status gs2d_ws_status(const gs2d_plan* plan, void* ws, int32_t reset, void* stream);
+
+/* Message for the calling thread's last error ("" if none).  Copies at most
+ * len - 1 characters and a terminating NUL into buf (host). */
+gs2d_status gs2d_last_error(char* buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS2D_H */

@@ -1,0 +1,12 @@
+"""GB300-native (sm_103a) 2D Gaussian-splatting frame encoder: the hot path of
+"Neural Video Compression using 2D Gaussian Splatting" (arXiv 2505.09324).
+
+The differentiable tile rasterizer (projection, tile binning + radix sort,
+accumulated-sum blending of Eq. 2, backward pass), the Adam fitting step and
+the frame-fitting loop are hand-written CUDA kernels in ``libgs2d.so`` behind
+the C ABI of ``include/gs2d.h``; this package is a thin binding over it.
+"""
+
+from .raster import GaussianRasterizer, RasterConfig, adam_step  # noqa: F401
+
+__all__ = ["GaussianRasterizer", "RasterConfig", "adam_step"]

@@ -1,0 +1,218 @@
+"""ctypes binding of libgs2d (include/gs2d.h).  Argument marshalling only: every
+step of the rasterizer runs in the library's CUDA kernels.  Importing this
+module does not touch the GPU; the first call loads the library and raises if
+it is missing (there is no fallback implementation)."""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+GS2D_OK = 0
+GS2D_ERR_INVALID_ARG = 1
+GS2D_ERR_CUDA = 2
+GS2D_ERR_CAPACITY = 3
+GS2D_ERR_TIMEOUT = 4
+GS2D_ERR_BOUNDS = 5
+STATUS_NAMES = {0: "GS2D_OK", 1: "GS2D_ERR_INVALID_ARG", 2: "GS2D_ERR_CUDA",
+                3: "GS2D_ERR_CAPACITY", 4: "GS2D_ERR_TIMEOUT", 5: "GS2D_ERR_BOUNDS"}
+
+# every function declared in include/gs2d.h
+EXPORTS = (
+    "gs2d_config_default", "gs2d_sizeof_plan", "gs2d_sizeof_config", "gs2d_plan_init",
+    "gs2d_project", "gs2d_bin_sort", "gs2d_render_fwd", "gs2d_render_bwd", "gs2d_render_l2",
+    "gs2d_adam_step", "gs2d_encode_frame", "gs2d_read_bins", "gs2d_count_pairs", "gs2d_ws_status",
+    "gs2d_last_error",
+)
+
+
+class Gs2dError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int32), ("sigma_cut", ctypes.c_float),
+                ("alpha_min", ctypes.c_float), ("det_eps", ctypes.c_float),
+                ("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float)]
+
+
+class Plan(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("n", ctypes.c_int32),
+                ("tile", ctypes.c_int32), ("tiles_x", ctypes.c_int32),
+                ("tiles_y", ctypes.c_int32), ("num_tiles", ctypes.c_int32),
+                ("tile_bits", ctypes.c_int32), ("sort_passes", ctypes.c_int32),
+                ("sort_blocks", ctypes.c_int32), ("max_entries", ctypes.c_int64),
+                ("cfg", Config), ("ws_bytes", ctypes.c_uint64), ("off", ctypes.c_uint64 * 20),
+                ("magic", ctypes.c_uint64)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Loads libgs2d.so (building it first only if asked)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(
+                    f"libgs2d.so not found at {path}; build it with "
+                    "paper_2505_09324_gb300.build.build() (the CUDA library is required)")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        P, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+        pp = ctypes.POINTER(Plan)
+        sig = {
+            "gs2d_config_default": (None, [ctypes.POINTER(Config)]),
+            "gs2d_sizeof_plan": (ctypes.c_size_t, []),
+            "gs2d_sizeof_config": (ctypes.c_size_t, []),
+            "gs2d_plan_init": (i32, [pp, i32, i32, i32, i64, ctypes.POINTER(Config)]),
+            "gs2d_project": (i32, [pp, P, P, P]),
+            "gs2d_bin_sort": (i32, [pp, P, P]),
+            "gs2d_render_fwd": (i32, [pp, P, P, P]),
+            "gs2d_render_bwd": (i32, [pp, P, P, P, P, P]),
+            "gs2d_render_l2": (i32, [pp, P, P, P, P, P, P, P]),
+            "gs2d_adam_step": (i32, [P, P, P, P, i64, i32, P, ctypes.POINTER(Config), P]),
+            "gs2d_encode_frame": (i32, [pp, P, P, P, P, P, i32, f32, i32, P, P, P, P]),
+            "gs2d_read_bins": (i32, [pp, P, P, P, P, i64, P, P, P]),
+            "gs2d_count_pairs": (i32, [pp, P, ctypes.POINTER(i64), ctypes.POINTER(i64), P]),
+            "gs2d_ws_status": (i32, [pp, P, i32, P]),
+            "gs2d_last_error": (i32, [ctypes.c_char_p, ctypes.c_size_t]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        if lib.gs2d_sizeof_plan() != ctypes.sizeof(Plan):
+            raise RuntimeError("gs2d_plan layout mismatch between library and binding")
+        if lib.gs2d_sizeof_config() != ctypes.sizeof(Config):
+            raise RuntimeError("gs2d_config layout mismatch between library and binding")
+        _lib = lib
+        return lib
+
+
+def last_error() -> str:
+    buf = ctypes.create_string_buffer(512)
+    load().gs2d_last_error(buf, 512)
+    return buf.value.decode(errors="replace")
+
+
+def check(status: int, what: str = ""):
+    if status != GS2D_OK:
+        raise Gs2dError(status, f"{what}: {last_error()}")
+
+
+def default_config() -> Config:
+    c = Config()
+    load().gs2d_config_default(ctypes.byref(c))
+    return c
+
+
+def plan_init(width: int, height: int, n: int, max_entries: int = 0,
+              config: Config | None = None) -> Plan:
+    p = Plan()
+    cfg = ctypes.byref(config) if config is not None else None
+    check(load().gs2d_plan_init(ctypes.byref(p), width, height, n, max_entries, cfg),
+          "gs2d_plan_init")
+    return p
+
+
+def _p(x):
+    return None if x is None or x == 0 else ctypes.c_void_p(x)
+
+
+def project(plan: Plan, ws: int, params: int, stream: int):
+    check(load().gs2d_project(ctypes.byref(plan), _p(ws), _p(params), _p(stream)), "gs2d_project")
+
+
+def bin_sort(plan: Plan, ws: int, stream: int):
+    check(load().gs2d_bin_sort(ctypes.byref(plan), _p(ws), _p(stream)), "gs2d_bin_sort")
+
+
+def render_fwd(plan: Plan, ws: int, img: int, stream: int):
+    check(load().gs2d_render_fwd(ctypes.byref(plan), _p(ws), _p(img), _p(stream)),
+          "gs2d_render_fwd")
+
+
+def render_bwd(plan: Plan, ws: int, params: int, dimg: int, grads: int, stream: int):
+    check(load().gs2d_render_bwd(ctypes.byref(plan), _p(ws), _p(params), _p(dimg), _p(grads),
+                                 _p(stream)), "gs2d_render_bwd")
+
+
+def render_l2(plan: Plan, ws: int, params: int, target: int, grads: int, img: int, loss: int,
+              stream: int):
+    check(load().gs2d_render_l2(ctypes.byref(plan), _p(ws), _p(params), _p(target), _p(grads),
+                                _p(img), _p(loss), _p(stream)), "gs2d_render_l2")
+
+
+def adam_step(params: int, grads: int, m: int, v: int, count: int, step: int, mask: int,
+              config: Config | None, stream: int):
+    cfg = ctypes.byref(config) if config is not None else None
+    check(load().gs2d_adam_step(_p(params), _p(grads), _p(m), _p(v), count, step, _p(mask), cfg,
+                                _p(stream)), "gs2d_adam_step")
+
+
+def encode_frame(plan: Plan, ws: int, target: int, params: int, m: int, v: int, iters: int,
+                 target_psnr: float, check_every: int, stream: int):
+    """Returns (status, iters_done, final_psnr, psnr_trace list)."""
+    nchk = iters // max(check_every, 1) + 2
+    trace = (ctypes.c_float * nchk)()
+    done = ctypes.c_int32(0)
+    final = ctypes.c_float(0.0)
+    st = load().gs2d_encode_frame(ctypes.byref(plan), _p(ws), _p(target), _p(params), _p(m), _p(v),
+                                  iters, target_psnr, check_every, trace, ctypes.byref(done),
+                                  ctypes.byref(final), _p(stream))
+    checks = -(-done.value // max(check_every, 1)) if done.value else 0
+    return st, done.value, final.value, [trace[i] for i in range(min(checks, nchk))]
+
+
+def read_bins(plan: Plan, ws: int, stream: int, max_keys: int = -1, want_keys=True,
+              want_ranges=True, want_counts=True):
+    import numpy as np
+    n_entries = ctypes.c_int64(0)
+    lib = load()
+    check(lib.gs2d_read_bins(ctypes.byref(plan), _p(ws), ctypes.byref(n_entries), None, None, 0,
+                             None, None, _p(stream)), "gs2d_read_bins")
+    e = n_entries.value if max_keys < 0 else min(n_entries.value, max_keys)
+    keys = np.zeros(max(e, 1), np.uint32) if want_keys else None
+    vals = np.zeros(max(e, 1), np.uint32) if want_keys else None
+    ranges = np.zeros((plan.num_tiles, 2), np.int32) if want_ranges else None
+    counts = np.zeros(max(plan.n, 1), np.int32) if want_counts else None
+
+    def ptr(a):
+        return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+    check(lib.gs2d_read_bins(ctypes.byref(plan), _p(ws), ctypes.byref(n_entries), ptr(keys),
+                             ptr(vals), e, ptr(ranges), ptr(counts), _p(stream)),
+          "gs2d_read_bins")
+    return {"n_entries": n_entries.value,
+            "keys": None if keys is None else keys[:e],
+            "values": None if vals is None else vals[:e],
+            "ranges": ranges,
+            "counts": None if counts is None else counts[:plan.n]}
+
+
+def count_pairs(plan: Plan, ws: int, stream: int):
+    """(pairs, hits) of the current sorted list."""
+    a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+    check(load().gs2d_count_pairs(ctypes.byref(plan), _p(ws), ctypes.byref(a), ctypes.byref(b),
+                                  _p(stream)), "gs2d_count_pairs")
+    return a.value, b.value
+
+
+def ws_status(plan: Plan, ws: int, reset: bool, stream: int) -> int:
+    return int(load().gs2d_ws_status(ctypes.byref(plan), _p(ws), int(reset), _p(stream)))

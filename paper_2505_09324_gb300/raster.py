@@ -1,0 +1,161 @@
+"""Torch-facing wrapper of libgs2d: PyTorch provides device memory and streams,
+the library's kernels do all the work.
+
+``GaussianRasterizer`` owns one workspace (a plan for a W x H frame and n
+Gaussians).  Parameters are float32 CUDA tensors of shape ``[9, n]`` with rows
+``mu_x, mu_y, l1, l2, l3, c_r, c_g, c_b, w`` (Sec. 3.1: mean, Cholesky vector of
+Eq. 1, colour; w weights the colour, c' = w c in Eq. 2).  Images are float32
+``[3, H, W]``.
+"""
+
+from __future__ import annotations
+
+import dataclasses
+
+import torch
+
+from . import _native as nat
+
+
+@dataclasses.dataclass
+class RasterConfig:
+    """Constants of the rasterizer and the optimiser (project readings; the paper
+    fixes none): tile 16, sigma <= 4.5, |alpha| >= 1/255, det Sigma > 1e-8,
+    Adam lr 1e-2, betas (0.9, 0.999), eps 1e-8."""
+
+    tile: int = 16
+    sigma_cut: float = 4.5
+    alpha_min: float = 1.0 / 255.0
+    det_eps: float = 1e-8
+    lr: float = 1e-2
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-8
+
+    def to_c(self) -> nat.Config:
+        return nat.Config(self.tile, self.sigma_cut, self.alpha_min, self.det_eps, self.lr,
+                          self.beta1, self.beta2, self.eps)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _check(t: torch.Tensor, name: str, shape=None, dtype=torch.float32):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t.data_ptr()
+
+
+class GaussianRasterizer:
+    """One plan + workspace: project -> bin_sort -> render_fwd / render_bwd /
+    render_l2 on a W x H frame with n Gaussians."""
+
+    def __init__(self, width: int, height: int, n: int, max_entries: int = 0,
+                 config: RasterConfig | None = None, device=None):
+        self.config = config or RasterConfig()
+        self.plan = nat.plan_init(width, height, n, max_entries, self.config.to_c())
+        self.width, self.height, self.n = width, height, n
+        self.device = torch.device(device) if device is not None else torch.device("cuda")
+        # zero-filled: the workspace status word must start at GS2D_OK
+        self.ws = torch.zeros(int(self.plan.ws_bytes), dtype=torch.uint8, device=self.device)
+        if self.ws.data_ptr() % 256:
+            raise RuntimeError("workspace allocation is not 256-byte aligned")
+
+    @property
+    def ws_ptr(self) -> int:
+        return self.ws.data_ptr()
+
+    def image_shape(self):
+        return (3, self.height, self.width)
+
+    def project(self, params: torch.Tensor, stream=None):
+        p = _check(params, "params", (9, self.n))
+        nat.project(self.plan, self.ws_ptr, p, _stream(stream))
+
+    def bin_sort(self, stream=None):
+        nat.bin_sort(self.plan, self.ws_ptr, _stream(stream))
+
+    def prepare(self, params: torch.Tensor, stream=None):
+        """project + bin_sort."""
+        self.project(params, stream)
+        self.bin_sort(stream)
+
+    def render_fwd(self, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        img = out if out is not None else torch.empty(self.image_shape(), device=self.device)
+        nat.render_fwd(self.plan, self.ws_ptr, _check(img, "img", self.image_shape()),
+                       _stream(stream))
+        return img
+
+    def render_bwd(self, params: torch.Tensor, dimg: torch.Tensor, out: torch.Tensor | None = None,
+                   stream=None) -> torch.Tensor:
+        grads = out if out is not None else torch.empty((9, self.n), device=self.device)
+        nat.render_bwd(self.plan, self.ws_ptr, _check(params, "params", (9, self.n)),
+                       _check(dimg, "dimg", self.image_shape()),
+                       _check(grads, "grads", (9, self.n)), _stream(stream))
+        return grads
+
+    def render_l2(self, params: torch.Tensor, target: torch.Tensor, want_image: bool = False,
+                  stream=None):
+        """Fused forward + L2 loss + backward.  Returns (grads, loss[2], img|None)
+        where loss = (mean squared error, mean squared error of the clamped image)."""
+        grads = torch.empty((9, self.n), device=self.device)
+        loss = torch.empty(2, device=self.device)
+        img = torch.empty(self.image_shape(), device=self.device) if want_image else None
+        nat.render_l2(self.plan, self.ws_ptr, _check(params, "params", (9, self.n)),
+                      _check(target, "target", self.image_shape()),
+                      _check(grads, "grads", (9, self.n)),
+                      0 if img is None else img.data_ptr(), loss.data_ptr(), _stream(stream))
+        return grads, loss, img
+
+    def read_bins(self, stream=None, max_keys: int = -1):
+        return nat.read_bins(self.plan, self.ws_ptr, _stream(stream), max_keys)
+
+    def count_pairs(self, stream=None):
+        """(listed pairs, contributing pairs) of the current sorted list."""
+        return nat.count_pairs(self.plan, self.ws_ptr, _stream(stream))
+
+    def status(self, reset: bool = False, stream=None) -> int:
+        return nat.ws_status(self.plan, self.ws_ptr, reset, _stream(stream))
+
+    def encode_frame(self, target: torch.Tensor, params: torch.Tensor, iters: int,
+                     target_psnr: float = 0.0, check_every: int = 50, adam_state=None,
+                     stream=None):
+        """Fits ``params`` (in place) to ``target``; see gs2d_encode_frame."""
+        if adam_state is None:
+            adam_state = (torch.empty_like(params), torch.empty_like(params))
+        m, v = adam_state
+        st, done, final, trace = nat.encode_frame(
+            self.plan, self.ws_ptr, _check(target, "target", self.image_shape()),
+            _check(params, "params", (9, self.n)), _check(m, "adam_m", (9, self.n)),
+            _check(v, "adam_v", (9, self.n)), iters, float(target_psnr), check_every,
+            _stream(stream))
+        if st not in (nat.GS2D_OK, nat.GS2D_ERR_CAPACITY):
+            nat.check(st, "gs2d_encode_frame")
+        return {"status": st, "iters": done, "psnr": final, "trace": trace}
+
+
+def adam_step(params: torch.Tensor, grads: torch.Tensor, m: torch.Tensor, v: torch.Tensor,
+              step: int, mask: torch.Tensor | None = None, config: RasterConfig | None = None,
+              stream=None):
+    """One Adam step in place over equally shaped float32 CUDA tensors."""
+    shape = tuple(params.shape)
+    ptrs = [_check(t, n, shape) for t, n in ((params, "params"), (grads, "grads"), (m, "m"),
+                                              (v, "v"))]
+    mp = 0
+    if mask is not None:
+        if params.numel() % 9:
+            raise ValueError("mask needs params with 9 rows")
+        mp = _check(mask, "mask", (params.numel() // 9,), dtype=torch.uint8)
+    cfg = (config or RasterConfig()).to_c()
+    nat.adam_step(*ptrs, params.numel(), step, mp, cfg, _stream(stream))
