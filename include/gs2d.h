@@ -115,6 +115,32 @@ gs2d_status gs2d_bin_sort(const gs2d_plan* plan, void* ws, void* stream);
  * Needs gs2d_bin_sort first. */
 gs2d_status gs2d_render_fwd(const gs2d_plan* plan, void* ws, float* img, void* stream);
 
+/* Forward render that allocates nothing (the paper has no counterpart; this
+ * is an integration convenience).  For callers that cannot allocate device
+ * memory when they render: a real-time pipeline that must not stall on the
+ * allocator, a host application or plugin that forbids libraries to allocate
+ * from its memory budget, or code that must not call allocation routines while
+ * a CUDA graph is being captured.  Runs projection, binning and the forward
+ * render of params (device, 9n floats, layout as above) into img (device
+ * [3][H][W], every pixel written) with cfg (NULL: defaults), using as scratch
+ * a fixed 16 MiB array that the library reserves on every GPU that loads it,
+ * held until the process exits.  Frames and Gaussian counts whose workspace
+ * (with room for at least 1024 tile entries) exceeds 16 MiB are rejected with
+ * GS2D_ERR_INVALID_ARG and a message; the entry capacity is whatever the rest
+ * of the array holds (about 3e5 entries at 1920x1080 with 20 000 Gaussians),
+ * and an overflow renders zero and reports GS2D_ERR_CAPACITY through status
+ * (device int32, may be NULL), written on the stream after the render.
+ * Makes no cudaMalloc, cudaFree or other allocating call.  The first call on
+ * each device, with that device current, looks up the array's device address
+ * (a CUDA runtime query) and caches it: make that first call before any
+ * stream capture.  Every call shares the one array and it keeps the previous
+ * call's contents (the call clears what must start at zero): calls that may
+ * overlap on the GPU (different streams, or host threads without ordering)
+ * race and must be serialised by the caller. */
+gs2d_status gs2d_render_fwd_noalloc(const float* params, int32_t n, int32_t width, int32_t height,
+                                    const gs2d_config* cfg, float* img, int32_t* status,
+                                    void* stream);
+
 /* Backward render: given dimg = dL/dC (device [3][H][W]), writes grads
  * (device, 9n floats, same layout as params) = dL/dparams through Eq. 2 and
  * Eq. 1.  Recomputes the blend from the saved per-tile lists (no per-pixel

@@ -23,7 +23,8 @@ STATUS_NAMES = {0: "GS2D_OK", 1: "GS2D_ERR_INVALID_ARG", 2: "GS2D_ERR_CUDA",
 # every function declared in include/gs2d.h
 EXPORTS = (
     "gs2d_config_default", "gs2d_sizeof_plan", "gs2d_sizeof_config", "gs2d_plan_init",
-    "gs2d_project", "gs2d_bin_sort", "gs2d_render_fwd", "gs2d_render_bwd", "gs2d_render_l2",
+    "gs2d_project", "gs2d_bin_sort", "gs2d_render_fwd", "gs2d_render_fwd_noalloc",
+    "gs2d_render_bwd", "gs2d_render_l2",
     "gs2d_adam_step", "gs2d_encode_frame", "gs2d_read_bins", "gs2d_count_pairs", "gs2d_ws_status",
     "gs2d_last_error",
 )
@@ -84,6 +85,8 @@ def load(build_if_missing: bool = False):
             "gs2d_project": (i32, [pp, P, P, P]),
             "gs2d_bin_sort": (i32, [pp, P, P]),
             "gs2d_render_fwd": (i32, [pp, P, P, P]),
+            "gs2d_render_fwd_noalloc": (i32, [P, i32, i32, i32, ctypes.POINTER(Config), P, P,
+                                              P]),
             "gs2d_render_bwd": (i32, [pp, P, P, P, P, P]),
             "gs2d_render_l2": (i32, [pp, P, P, P, P, P, P, P]),
             "gs2d_adam_step": (i32, [P, P, P, P, i64, i32, P, ctypes.POINTER(Config), P]),

@@ -52,6 +52,13 @@ bool cfg_valid(const gs2d_config& c) {
 
 }  // namespace
 
+namespace gs2d {
+gs2d_status set_error(gs2d_status st, const char* msg) {
+  snprintf(g_err, sizeof(g_err), "%s", msg);
+  return st;
+}
+}  // namespace gs2d
+
 extern "C" {
 
 void gs2d_config_default(gs2d_config* cfg) {

@@ -106,4 +106,7 @@ cudaError_t launch_loss_reduce(const gs2d_plan& p, void* ws, float* loss, cudaSt
 cudaError_t launch_adam_tick(const gs2d_plan& p, void* ws, cudaStream_t s);
 cudaError_t launch_count_pairs(const gs2d_plan& p, void* ws, cudaStream_t s);
 
+// Records msg as the calling thread's last error (gs2d_last_error); returns st.
+gs2d_status set_error(gs2d_status st, const char* msg);
+
 }  // namespace gs2d
