@@ -111,6 +111,10 @@ gs2d_status gs2d_project(const gs2d_plan* plan, void* ws, const float* params, v
  * is empty (renders then produce zero). */
 gs2d_status gs2d_bin_sort(const gs2d_plan* plan, void* ws, void* stream);
 
+/* gs2d_project followed by gs2d_bin_sort, with the same results, in as few
+ * launches as the device allows (one thread-block cluster launch on GB300). */
+gs2d_status gs2d_prepare(const gs2d_plan* plan, void* ws, const float* params, void* stream);
+
 /* Forward render, Eq. 2.  img: device [3][H][W] output (every pixel written).
  * Needs gs2d_bin_sort first. */
 gs2d_status gs2d_render_fwd(const gs2d_plan* plan, void* ws, float* img, void* stream);

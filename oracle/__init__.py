@@ -69,7 +69,8 @@ def _load():
             lib.orc_render_grad.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P,
                                             ctypes.c_int, P, P, P, ctypes.c_int, P, P]
             lib.orc_tile_rects.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                           P, ctypes.c_float, ctypes.c_float, P, P, P]
+                                           P, ctypes.c_float, ctypes.c_float, ctypes.c_float, P,
+                                           P, P]
             lib.orc_sorted_keys.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             P, i64, P, P]
             lib.orc_set_threads.argtypes = [ctypes.c_int]
@@ -227,9 +228,9 @@ def tile_rects(params, width: int, height: int, cfg: Config = Config()):
     rect = np.zeros((n, 4), np.int32)
     count = np.zeros(n, np.int32)
     total = ctypes.c_int64(0)
-    rc = _load().orc_tile_rects(width, height, cfg.tile, n, _ptr(p), np.float32(cfg.alpha_min),
-                                np.float32(cfg.det_eps), _ptr(rect), _ptr(count),
-                                ctypes.byref(total))
+    rc = _load().orc_tile_rects(width, height, cfg.tile, n, _ptr(p), np.float32(cfg.sigma_cut),
+                                np.float32(cfg.alpha_min), np.float32(cfg.det_eps), _ptr(rect),
+                                _ptr(count), ctypes.byref(total))
     if rc != 0:
         raise RuntimeError(f"orc_tile_rects failed ({rc})")
     return rect, count, int(total.value)

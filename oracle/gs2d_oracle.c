@@ -37,7 +37,8 @@
  *   (the file is compiled with -ffp-contract=off so no FMA is formed):
  *        Sxx = l1*l1, Syy = l2*l2 + l3*l3, a = l1*l3, det = a*a,
  *        mid = 0.5*(Sxx + Syy), disc = max(0.1, mid*mid - det),
- *        lam = mid + sqrt(disc), r = ceil(3 * sqrt(lam)),
+ *        lam = mid + sqrt(disc), r = ceil(sqrt(2*sigma_cut) * sqrt(lam))
+ *        (the sigma <= sigma_cut ellipse; 3*sqrt(lam) at sigma_cut = 4.5),
  *        px0 = floor(mx - r), px1 = floor(mx + r)  (same in y),
  *   clipped to the image; tiles tx0 = xlo / T .. xhi / T inclusive.  A Gaussian
  *   is culled when a parameter is non-finite, det <= det_eps, |w| < alpha_min
@@ -358,10 +359,11 @@ int orc_render_grad(int W, int H, int n, const double* p, const orc_cfg* cfg, in
 
 /* Per-Gaussian tile rectangle [tx0, tx1) x [ty0, ty1) and tile count. */
 static int orc_rect32(int W, int H, int T, float mx, float my, float l1, float l2, float l3,
-                      float w, float alpha_min, float det_eps, int32_t rect[4]) {
+                      float cr, float cg, float cb, float w, float sigma_cut, float alpha_min,
+                      float det_eps, int32_t rect[4]) {
   rect[0] = rect[1] = rect[2] = rect[3] = 0;
   if (!(isfinite(mx) && isfinite(my) && isfinite(l1) && isfinite(l2) && isfinite(l3) &&
-        isfinite(w)))
+        isfinite(cr) && isfinite(cg) && isfinite(cb) && isfinite(w)))
     return 0;
   float sxx = l1 * l1;
   float t1 = l2 * l2;
@@ -375,7 +377,10 @@ static int orc_rect32(int W, int H, int T, float mx, float my, float l1, float l
   float disc = mid * mid - det;
   if (!(disc > 0.1f)) disc = 0.1f;
   float lam = mid + sqrtf(disc);
-  float r = ceilf(3.0f * sqrtf(lam));
+  /* the sigma <= sigma_cut ellipse reaches sqrt(2 sigma_cut lam) along its
+   * major axis; at sigma_cut = 4.5 the factor is exactly 3 */
+  float kc = sqrtf(2.0f * sigma_cut);
+  float r = ceilf(kc * sqrtf(lam));
   float fx0 = floorf(mx - r), fx1 = floorf(mx + r);
   float fy0 = floorf(my - r), fy1 = floorf(my + r);
   /* clip to the image (as floats first so huge values cannot overflow int) */
@@ -393,13 +398,14 @@ static int orc_rect32(int W, int H, int T, float mx, float my, float l1, float l
 }
 
 /* rect: [n][4] (tx0, ty0, tx1, ty1), count: [n]; returns total entries via *total */
-int orc_tile_rects(int W, int H, int T, int n, const float* p, float alpha_min, float det_eps,
-                   int32_t* rect, int32_t* count, int64_t* total) {
+int orc_tile_rects(int W, int H, int T, int n, const float* p, float sigma_cut, float alpha_min,
+                   float det_eps, int32_t* rect, int32_t* count, int64_t* total) {
   if (W <= 0 || H <= 0 || T <= 0 || n < 0 || !rect || !count || !total) return ORC_EINVAL;
   int64_t tot = 0;
   for (int i = 0; i < n; i++) {
-    count[i] = orc_rect32(W, H, T, p[i], p[(size_t)n + i], p[2 * (size_t)n + i],
-                          p[3 * (size_t)n + i], p[4 * (size_t)n + i], p[8 * (size_t)n + i],
+    const size_t m = (size_t)n;
+    count[i] = orc_rect32(W, H, T, p[i], p[m + i], p[2 * m + i], p[3 * m + i], p[4 * m + i],
+                          p[5 * m + i], p[6 * m + i], p[7 * m + i], p[8 * m + i], sigma_cut,
                           alpha_min, det_eps, &rect[4 * (size_t)i]);
     tot += count[i];
   }

@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "GS2D_OK", 1: "GS2D_ERR_INVALID_ARG", 2: "GS2D_ERR_CUDA",
 # every function declared in include/gs2d.h
 EXPORTS = (
     "gs2d_config_default", "gs2d_sizeof_plan", "gs2d_sizeof_config", "gs2d_plan_init",
-    "gs2d_project", "gs2d_bin_sort", "gs2d_render_fwd", "gs2d_render_fwd_noalloc",
+    "gs2d_project", "gs2d_bin_sort", "gs2d_prepare", "gs2d_render_fwd", "gs2d_render_fwd_noalloc",
     "gs2d_render_bwd", "gs2d_render_l2",
     "gs2d_adam_step", "gs2d_encode_frame", "gs2d_read_bins", "gs2d_count_pairs", "gs2d_ws_status",
     "gs2d_last_error",
@@ -84,6 +84,7 @@ def load(build_if_missing: bool = False):
             "gs2d_plan_init": (i32, [pp, i32, i32, i32, i64, ctypes.POINTER(Config)]),
             "gs2d_project": (i32, [pp, P, P, P]),
             "gs2d_bin_sort": (i32, [pp, P, P]),
+            "gs2d_prepare": (i32, [pp, P, P, P]),
             "gs2d_render_fwd": (i32, [pp, P, P, P]),
             "gs2d_render_fwd_noalloc": (i32, [P, i32, i32, i32, ctypes.POINTER(Config), P, P,
                                               P]),
@@ -144,6 +145,10 @@ def project(plan: Plan, ws: int, params: int, stream: int):
 
 def bin_sort(plan: Plan, ws: int, stream: int):
     check(load().gs2d_bin_sort(ctypes.byref(plan), _p(ws), _p(stream)), "gs2d_bin_sort")
+
+
+def prepare(plan: Plan, ws: int, params: int, stream: int):
+    check(load().gs2d_prepare(ctypes.byref(plan), _p(ws), _p(params), _p(stream)), "gs2d_prepare")
 
 
 def render_fwd(plan: Plan, ws: int, img: int, stream: int):

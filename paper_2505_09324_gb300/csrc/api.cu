@@ -101,20 +101,20 @@ gs2d_status gs2d_plan_init(gs2d_plan* plan, int32_t width, int32_t height, int32
   int bits = 0;
   while ((int64_t(1) << bits) < plan->num_tiles) bits++;
   plan->tile_bits = bits;
-  plan->sort_passes = (bits + kRadixBits - 1) / kRadixBits;
-  plan->sort_blocks = 128;
+  plan->sort_passes = 1;  // one counting pass over the whole tile id
+  plan->sort_blocks = 0;
   plan->max_entries = max_entries;
   plan->cfg = c;
   const uint64_t nn = (uint64_t)n, me = (uint64_t)max_entries, nt = (uint64_t)plan->num_tiles;
-  const uint64_t scan_blocks = (nn + kScanThreads * kScanItems - 1) / (kScanThreads * kScanItems);
   uint64_t sz[kNumSections];
   sz[kOffHeader] = sizeof(WsHeader);
   sz[kOffRec] = 3 * nn * sizeof(float4);
   sz[kOffRect] = nn * sizeof(int4);
   sz[kOffCount] = (nn + 1) * sizeof(int);
-  sz[kOffBlockSum] = (scan_blocks + 1) * sizeof(long long);
-  sz[kOffKeysA] = sz[kOffKeysB] = sz[kOffValsA] = sz[kOffValsB] = me * sizeof(uint32_t);
-  sz[kOffHist] = (uint64_t)kRadixBuckets * plan->sort_blocks * sizeof(uint32_t);
+  sz[kOffTileCnt] = nt * sizeof(int);
+  sz[kOffCursor] = nt * sizeof(int);
+  sz[kOffLong] = (nt + 1) * sizeof(int);
+  sz[kOffList] = me * sizeof(uint32_t);
   sz[kOffRanges] = nt * sizeof(int2);
   sz[kOffPartial] = me * kPartials * sizeof(float);
   sz[kOffLossPart] = nt * sizeof(float2);
@@ -140,6 +140,14 @@ gs2d_status gs2d_bin_sort(const gs2d_plan* plan, void* ws, void* stream) {
   gs2d_status st = check_plan(plan, ws);
   if (st) return st;
   return cuda_check(launch_bin_sort(*plan, ws, (cudaStream_t)stream), "gs2d_bin_sort");
+}
+
+gs2d_status gs2d_prepare(const gs2d_plan* plan, void* ws, const float* params, void* stream) {
+  gs2d_status st = check_plan(plan, ws);
+  if (st) return st;
+  if (!params && plan->n > 0) return fail(GS2D_ERR_INVALID_ARG, "params is NULL");
+  return cuda_check(launch_prepare(*plan, ws, params, false, (cudaStream_t)stream),
+                    "gs2d_prepare");
 }
 
 gs2d_status gs2d_render_fwd(const gs2d_plan* plan, void* ws, float* img, void* stream) {
@@ -192,8 +200,7 @@ gs2d_status gs2d_adam_step(float* params, const float* grads, float* m, float* v
 
 static cudaError_t fit_iteration(const gs2d_plan& p, void* ws, const float* target, float* params,
                                  float* m, float* v, cudaStream_t s) {
-  cudaError_t e = launch_project(p, ws, params, s);
-  if (e == cudaSuccess) e = launch_bin_sort(p, ws, s);
+  cudaError_t e = launch_prepare(p, ws, params, true, s);
   if (e == cudaSuccess) e = launch_fit_step(p, ws, target, params, m, v, s);
   return e;
 }
@@ -279,15 +286,12 @@ gs2d_status gs2d_read_bins(const gs2d_plan* plan, const void* ws, int64_t* n_ent
   if (e != cudaSuccess) return cuda_check(e, "gs2d_read_bins");
   if (n_entries) *n_entries = h.n_entries;
   const int64_t k = std::min<int64_t>(h.n_entries, std::max<int64_t>(max_keys, 0));
-  const bool odd = p.sort_passes & 1;
-  if (keys && k > 0)
-    e = cudaMemcpyAsync(keys, ws_ptr<uint32_t>(ws, p, odd ? kOffKeysB : kOffKeysA),
-                        k * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && values && k > 0)
-    e = cudaMemcpyAsync(values, ws_ptr<uint32_t>(ws, p, odd ? kOffValsB : kOffValsA),
-                        k * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && ranges)
-    e = cudaMemcpyAsync(ranges, ws_ptr<int2>(ws, p, kOffRanges), (size_t)p.num_tiles * sizeof(int2),
+  if (values && k > 0)
+    e = cudaMemcpyAsync(values, ws_ptr<uint32_t>(ws, p, kOffList), k * sizeof(uint32_t),
+                        cudaMemcpyDeviceToHost, s);
+  std::vector<int2> rg((size_t)p.num_tiles);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(rg.data(), ws_ptr<int2>(ws, p, kOffRanges), rg.size() * sizeof(int2),
                         cudaMemcpyDeviceToHost, s);
   std::vector<int> offs;
   if (e == cudaSuccess && counts && p.n > 0) {
@@ -299,6 +303,15 @@ gs2d_status gs2d_read_bins(const gs2d_plan* plan, const void* ws, int64_t* n_ent
   if (e != cudaSuccess) return cuda_check(e, "gs2d_read_bins");
   if (counts)
     for (int i = 0; i < p.n; i++) counts[i] = offs[i + 1] - offs[i];
+  if (ranges)
+    for (int t = 0; t < p.num_tiles; t++) {
+      ranges[2 * t] = rg[t].x;
+      ranges[2 * t + 1] = rg[t].y;
+    }
+  // the key of a list position is the tile whose range holds it
+  if (keys)
+    for (int t = 0; t < p.num_tiles; t++)
+      for (int64_t i = rg[t].x; i < rg[t].y && i < k; i++) keys[i] = (uint32_t)t;
   return ok();
 }
 

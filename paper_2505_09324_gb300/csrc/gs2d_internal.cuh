@@ -13,12 +13,8 @@ namespace gs2d {
 constexpr uint64_t kPlanMagic = 0x67733264706c616eull;  // "gs2dplan"
 constexpr int kTile = 16;                               // tile edge (pixels)
 constexpr int kTilePix = kTile * kTile;                 // 256 pixels per tile
-constexpr int kBatch = 256;                             // Gaussians staged per smem batch
-constexpr int kRadixBits = 8;
-constexpr int kRadixBuckets = 1 << kRadixBits;
-constexpr int kSortThreads = 256;
 constexpr int kScanThreads = 1024;
-constexpr int kScanItems = 8;  // per thread in the count scan
+constexpr int kScanItems = 8;  // per thread in the count scans
 constexpr int kPartials = 8;   // backward accumulators per (tile, Gaussian)
 
 // log2(e) / 2: scales the Cholesky-form coordinates so that
@@ -31,15 +27,13 @@ enum WsSection {
   kOffHeader = 0,   // WsHeader
   kOffRec,          // float4[3][n]  render records (SoA of float4 rows)
   kOffRect,         // int4[n]       tile rectangle [tx0, ty0, tx1, ty1)
-  kOffCount,        // int32[n + 1]  tile counts, then exclusive offsets
-  kOffBlockSum,     // int32[...]    scan block sums
-  kOffKeysA,        // uint32[max_entries]
-  kOffKeysB,        // uint32[max_entries]
-  kOffValsA,        // uint32[max_entries]
-  kOffValsB,        // uint32[max_entries]
-  kOffHist,         // uint32[kRadixBuckets * sort_blocks]
+  kOffCount,        // int32[n + 1]  per-Gaussian tile counts, then exclusive offsets
+  kOffTileCnt,      // int32[num_tiles]  entries per tile (zero between calls)
+  kOffCursor,       // int32[num_tiles]  next free slot of each tile's list
+  kOffLong,         // int32[num_tiles + 1]  tiles whose list needs the CTA sort
+  kOffList,         // uint32[max_entries]  Gaussian indices, tile-major
   kOffRanges,       // int2[num_tiles]
-  kOffPartial,      // float[kPartials][max_entries] (SoA rows) backward partials
+  kOffPartial,      // float[max_entries][kPartials] backward sums per (tile, Gaussian)
   kOffLossPart,     // float2[num_tiles]  per-tile (sum sq err, sum sq err clamped)
   kOffGrad,         // float[9 n] gradient scratch of the fit loop
   kNumSections
@@ -54,7 +48,8 @@ struct WsHeader {
   int32_t pad0;
   float loss[2];        // last reduced {loss, clamped mse}
   unsigned long long pairs, hits;  // gs2d_count_pairs results
-  int32_t pad[50];
+  int32_t long_count;              // tiles queued for the long-list sort
+  int32_t pad[49];
 };
 static_assert(sizeof(WsHeader) == 256, "header is one 256-byte block");
 
@@ -88,6 +83,71 @@ __device__ __forceinline__ void set_status(WsHeader* h, int code) {
   atomicCAS(&h->status, 0, code);
 }
 
+// Projection of Gaussian i (Sec. 3.1 parameters -> screen-space record, tile
+// rectangle and tile count).  The rectangle uses only single-rounded operations
+// (no FMA contraction) so it is reproducible on the host; the rest of the
+// record is ordinary FP32.  Culled Gaussians (non-finite, det <= det_eps,
+// |w| < alpha_min, off-image) get count 0.
+__device__ __forceinline__ void project_one(int i, int n, int W, int H, float sigma_cut,
+                                            float alpha_min, float det_eps,
+                                            const float* __restrict__ params,
+                                            float4* __restrict__ rec, int4* __restrict__ rect,
+                                            int* __restrict__ count) {
+  const float mx = params[i], my = params[n + i];
+  const float l1 = params[2 * n + i], l2 = params[3 * n + i], l3 = params[4 * n + i];
+  const float cr = params[5 * n + i], cg = params[6 * n + i], cb = params[7 * n + i];
+  const float w = params[8 * n + i];
+  int4 rc = make_int4(0, 0, 0, 0);
+  int cnt = 0;
+  const bool finite = isfinite(mx) && isfinite(my) && isfinite(l1) && isfinite(l2) &&
+                      isfinite(l3) && isfinite(cr) && isfinite(cg) && isfinite(cb) && isfinite(w);
+  const float sxx = __fmul_rn(l1, l1);
+  const float syy = __fadd_rn(__fmul_rn(l2, l2), __fmul_rn(l3, l3));
+  const float a = __fmul_rn(l1, l3);
+  const float det = __fmul_rn(a, a);
+  if (finite && (det > det_eps) && (fabsf(w) >= alpha_min)) {
+    const float mid = __fmul_rn(0.5f, __fadd_rn(sxx, syy));
+    float disc = __fsub_rn(__fmul_rn(mid, mid), det);
+    if (!(disc > 0.1f)) disc = 0.1f;
+    const float lam = __fadd_rn(mid, __fsqrt_rn(disc));
+    // sigma <= sigma_cut reaches sqrt(2 sigma_cut lam) along the major axis
+    // (3 sqrt(lam), the 3-sigma ellipse, at sigma_cut = 4.5)
+    const float kc = __fsqrt_rn(__fmul_rn(2.0f, sigma_cut));
+    const float r = ceilf(__fmul_rn(kc, __fsqrt_rn(lam)));
+    float fx0 = floorf(__fsub_rn(mx, r)), fx1 = floorf(__fadd_rn(mx, r));
+    float fy0 = floorf(__fsub_rn(my, r)), fy1 = floorf(__fadd_rn(my, r));
+    fx0 = fx0 < 0.0f ? 0.0f : fx0;
+    fy0 = fy0 < 0.0f ? 0.0f : fy0;
+    fx1 = fx1 > (float)(W - 1) ? (float)(W - 1) : fx1;
+    fy1 = fy1 > (float)(H - 1) ? (float)(H - 1) : fy1;
+    if (fx0 <= fx1 && fy0 <= fy1) {
+      rc = make_int4((int)fx0 / kTile, (int)fy0 / kTile, (int)fx1 / kTile + 1,
+                     (int)fy1 / kTile + 1);
+      cnt = (rc.z - rc.x) * (rc.w - rc.y);
+    }
+  }
+  rect[i] = rc;
+  count[i] = cnt;
+  float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
+  if (cnt > 0) {
+    const float s = 0.84932180028801904272f;  // sqrt(log2(e) / 2)
+    const float log2e = 1.44269504088896340736f;
+    float tau2 = fminf(sigma_cut * log2e, log2f(fabsf(w) / alpha_min));
+    tau2 = fmaxf(tau2, 0.0f);
+    const float tau = tau2 * kLn2;
+    // half extents of {sigma <= tau}: sqrt(2 tau Sxx), sqrt(2 tau Syy), padded so
+    // the box stays conservative under FP32 rounding
+    const float hx = sqrtf(2.0f * tau * sxx) * 1.001f + 0.0039f;
+    const float hy = sqrtf(2.0f * tau * syy) * 1.001f + 0.0039f;
+    r0 = make_float4(mx, my, s / l1, s / l3);
+    r1 = make_float4(-l2 / l3, tau2, w * cr, w * cg);
+    r2 = make_float4(w * cb, hx, hy, 0.0f);
+  }
+  rec[i] = r0;
+  rec[n + i] = r1;
+  rec[2 * n + i] = r2;
+}
+
 // ---- launchers implemented in the .cu files (return cudaGetLastError) ----
 cudaError_t launch_project(const gs2d_plan& p, void* ws, const float* params, cudaStream_t s);
 cudaError_t launch_bin_sort(const gs2d_plan& p, void* ws, cudaStream_t s);
@@ -105,6 +165,10 @@ cudaError_t launch_adam(float* params, const float* grads, float* m, float* v, i
 cudaError_t launch_loss_reduce(const gs2d_plan& p, void* ws, float* loss, cudaStream_t s);
 cudaError_t launch_adam_tick(const gs2d_plan& p, void* ws, cudaStream_t s);
 cudaError_t launch_count_pairs(const gs2d_plan& p, void* ws, cudaStream_t s);
+// project + bin_sort; with adam_tick the fit loop's Adam step counter and bias
+// corrections advance in the same launch.
+cudaError_t launch_prepare(const gs2d_plan& p, void* ws, const float* params, bool adam_tick,
+                           cudaStream_t s);
 
 // Records msg as the calling thread's last error (gs2d_last_error); returns st.
 gs2d_status set_error(gs2d_status st, const char* msg);

@@ -71,6 +71,7 @@ class GaussianRasterizer:
         self.ws = torch.zeros(int(self.plan.ws_bytes), dtype=torch.uint8, device=self.device)
         if self.ws.data_ptr() % 256:
             raise RuntimeError("workspace allocation is not 256-byte aligned")
+        self.version = 0  # bumped whenever the binned lists in the workspace change
 
     @property
     def ws_ptr(self) -> int:
@@ -82,14 +83,17 @@ class GaussianRasterizer:
     def project(self, params: torch.Tensor, stream=None):
         p = _check(params, "params", (9, self.n))
         nat.project(self.plan, self.ws_ptr, p, _stream(stream))
+        self.version += 1
 
     def bin_sort(self, stream=None):
         nat.bin_sort(self.plan, self.ws_ptr, _stream(stream))
+        self.version += 1
 
     def prepare(self, params: torch.Tensor, stream=None):
-        """project + bin_sort."""
-        self.project(params, stream)
-        self.bin_sort(stream)
+        """project + bin_sort (fused into one launch where the device allows)."""
+        p = _check(params, "params", (9, self.n))
+        nat.prepare(self.plan, self.ws_ptr, p, _stream(stream))
+        self.version += 1
 
     def render_fwd(self, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         img = out if out is not None else torch.empty(self.image_shape(), device=self.device)

@@ -49,13 +49,13 @@ def test_default_config(nat):
 def test_plan_layout(nat):
     p = nat.plan_init(1920, 1080, 20000)
     assert (p.tiles_x, p.tiles_y, p.num_tiles) == (120, 68, 8160)
-    assert p.tile_bits == 13 and p.sort_passes == 2
+    assert p.tile_bits == 13 and p.sort_passes == 1
     assert p.max_entries == max(1 << 20, 16 * 20000)
-    offs = list(p.off)[:14]
+    offs = list(p.off)[:12]
     assert all(o % 256 == 0 for o in offs)
     assert offs == sorted(offs) and p.ws_bytes > offs[-1]
     q = nat.plan_init(16, 16, 5)
-    assert q.num_tiles == 1 and q.sort_passes == 0
+    assert q.num_tiles == 1 and q.tile_bits == 0
 
 
 @pytest.mark.parametrize("args", [(0, 10, 5, 0), (10, -1, 5, 0), (10, 10, -1, 0),

@@ -38,12 +38,19 @@ def to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
 
 
-def check_bins(gs, oracle, p, W, H, max_entries=0):
-    r = gs.GaussianRasterizer(W, H, p.shape[1], max_entries=max_entries)
-    r.prepare(to_dev(p))
+def check_bins(gs, oracle, p, W, H, max_entries=0, separate=False, sigma_cut=4.5,
+               alpha_min=1 / 255):
+    cfg = gs.RasterConfig(sigma_cut=sigma_cut, alpha_min=alpha_min)
+    r = gs.GaussianRasterizer(W, H, p.shape[1], max_entries=max_entries, config=cfg)
+    if separate:
+        r.project(to_dev(p))
+        r.bin_sort()
+    else:
+        r.prepare(to_dev(p))
     got = r.read_bins()
-    keys, ranges = oracle.sorted_keys(p, W, H)
-    _, count, total = oracle.tile_rects(p, W, H)
+    ocfg = oracle.Config(sigma_cut=sigma_cut, alpha_min=alpha_min)
+    keys, ranges = oracle.sorted_keys(p, W, H, ocfg)
+    _, count, total = oracle.tile_rects(p, W, H, ocfg)
     assert got["n_entries"] == total
     np.testing.assert_array_equal(got["keys"].astype(np.uint64), keys >> np.uint64(32))
     np.testing.assert_array_equal(got["values"].astype(np.uint64), keys & np.uint64(0xFFFFFFFF))
@@ -95,10 +102,26 @@ def test_bins_bit_exact(gs, oracle, name, W, H, n, seed):
     check_bins(gs, oracle, random_gaussians(n, W, H, seed=seed), W, H)
 
 
+@pytest.mark.parametrize("name,W,H,n,seed", CASES)
+def test_bins_bit_exact_separate_calls(gs, oracle, name, W, H, n, seed):
+    check_bins(gs, oracle, random_gaussians(n, W, H, seed=seed), W, H, separate=True)
+
+
 def test_bins_bit_exact_full_size_1080p(gs, oracle):
     frame, mask = conferencing_frame(1920, 1080, seed=1)
     p = conferencing_gaussians(frame, mask, 20000, seed=1)
     check_bins(gs, oracle, p, 1920, 1080)
+    check_bins(gs, oracle, p, 1920, 1080, separate=True)
+
+
+@pytest.mark.parametrize("n", [20, 50, 100, 200, 400, 700])
+def test_bins_every_list_length_path(gs, oracle, n):
+    """Every Gaussian covers all four tiles of a 32 x 32 frame, so each tile's
+    list holds all n: exercises the register sorts for <= 32 .. 512 entries and
+    the shared-memory sort beyond."""
+    p = random_gaussians(n, 32, 32, seed=n, l_range=(6.0, 8.0))
+    p[0:2] = 16.0 + np.random.Generator(np.random.PCG64(n)).uniform(-2, 2, (2, n))
+    check_bins(gs, oracle, p, 32, 32)
 
 
 def test_bins_edge_cases(gs, oracle):
@@ -110,8 +133,14 @@ def test_bins_edge_cases(gs, oracle):
     p[0, 3] = -500.0              # off-image
     p[2, 4] = p[4, 4] = 400.0     # covers every tile
     p[3, 5] = 1e30                # huge shear (finite)
+    p[6, 6] = np.nan              # non-finite colour
     check_bins(gs, oracle, p, W, H)
     check_bins(gs, oracle, np.zeros((9, 0), np.float32), W, H)
+    # a single-tile frame (no radix pass) and a wider cut-off
+    check_bins(gs, oracle, random_gaussians(5, 16, 16, seed=2), 16, 16)
+    check_bins(gs, oracle, random_gaussians(5, 1, 1, seed=2), 1, 1, separate=True)
+    check_bins(gs, oracle, random_gaussians(200, 100, 70, seed=9), 100, 70, sigma_cut=8.0,
+               alpha_min=1e-6)
 
 
 @pytest.mark.parametrize("name,W,H,n,seed", CASES)

@@ -62,19 +62,29 @@ def test_sorted_keys_and_ranges_are_consistent(oracle):
     assert total == len(keys) == count.sum()
 
 
-def test_coverage_every_contributing_pair_is_listed(oracle):
+def test_nonfinite_colour_is_culled(oracle):
+    p = one32(50, 50, 2, 0, 2)
+    p[6, 0] = np.nan
+    _, c, total = oracle.tile_rects(p, 256, 256)
+    assert c[0] == 0 and total == 0
+
+
+@pytest.mark.parametrize("sigma_cut", [4.5, 8.0])
+def test_coverage_every_contributing_pair_is_listed(oracle, sigma_cut):
     """Tiling is exact: each pixel where Gaussian n contributes (brute force,
-    double precision, including the ambiguity band) lies in a tile of n's list."""
+    double precision, including the ambiguity band) lies in a tile of n's list,
+    for the default cut-off and a wider one (radius sqrt(2 sigma_cut lambda))."""
     W, H, T = 100, 70, 16
+    cfg = oracle.Config(sigma_cut=sigma_cut, alpha_min=1e-6)
     p = random_gaussians(120, W, H, seed=37)
     p[2:5] *= 1.7  # larger footprints, more tile crossings
-    keys, _ = oracle.sorted_keys(p, W, H)
+    keys, _ = oracle.sorted_keys(p, W, H, cfg)
     listed = {}
     for k in keys:
         listed.setdefault(int(k & np.uint64(0xFFFFFFFF)), set()).add(int(k >> np.uint64(32)))
     TX = (W + T - 1) // T
     for i in range(p.shape[1]):
-        img, lo, hi = oracle.render(p[:, i:i + 1], W, H, ambiguity=True)
+        img, lo, hi = oracle.render(p[:, i:i + 1], W, H, cfg, ambiguity=True)
         touched = np.nonzero(np.abs(img[0]) + np.abs(lo[0]) + np.abs(hi[0]) + np.abs(img[1]))
         tiles = set((touched[0] // T) * TX + touched[1] // T)
         assert tiles <= listed.get(i, set()), f"Gaussian {i} not covered"
