@@ -111,6 +111,7 @@ gs2d_status gs2d_plan_init(gs2d_plan* plan, int32_t width, int32_t height, int32
   sz[kOffRec] = 3 * nn * sizeof(float4);
   sz[kOffRect] = nn * sizeof(int4);
   sz[kOffCount] = (nn + 1) * sizeof(int);
+  sz[kOffBlockSum] = (nn / 256 + 1) * sizeof(long long);
   sz[kOffTileCnt] = nt * sizeof(int);
   sz[kOffCursor] = nt * sizeof(int);
   sz[kOffLong] = (nt + 1) * sizeof(int);

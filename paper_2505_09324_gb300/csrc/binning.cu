@@ -6,12 +6,13 @@
 // ordered by index: the sorted list is the (tile, index) key order.
 //
 // The sort is a single-digit radix (counting) sort by tile id over all SMs:
-//   1. per-tile entry counts (atomic increments from each Gaussian's tiles);
-//   2. exclusive scans: per-Gaussian offsets (backward slots) and per-tile
-//      list ranges; capacity check;
-//   3. scatter: each entry claims the next slot of its tile's list;
+//   1. per-tile entry counts (atomic increments from each Gaussian's tiles)
+//      and per-block sums of the per-Gaussian counts;
+//   2. exclusive scans: one CTA per block of 256 Gaussians for the offsets
+//      (backward slots), one CTA for the per-tile list ranges; capacity check;
+//   3. scatter: every entry claims the next slot of its tile's list;
 //   4. segment sort: each tile's list is sorted by Gaussian index (a warp
-//      bitonic network in registers for lists of up to 32, a CTA bitonic
+//      bitonic network in registers for lists of up to 512, a CTA bitonic
 //      network in shared memory for longer ones), restoring exactly the order
 //      a stable sort of the index-ordered entries would give.
 #include "gs2d_internal.cuh"
@@ -19,27 +20,30 @@
 namespace gs2d {
 
 constexpr int kLongMax = 1 << 15;  // longest list the CTA sort holds (128 KB)
+constexpr int kGB = 256;           // Gaussians per counting / scan block
 
 // ---------------------------------------------------------------------------
 // Projection (gs2d_project): records, rectangles, per-Gaussian counts.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kGB)
 k_project(int n, int W, int H, float sigma_cut, float alpha_min, float det_eps,
           const float* __restrict__ params, float4* __restrict__ rec, int4* __restrict__ rect,
           int* __restrict__ count) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) count[n] = 0;
   if (i >= n) return;
   project_one(i, n, W, H, sigma_cut, alpha_min, det_eps, params, rec, rect, count);
 }
 
-// Per-tile entry counts from the rectangles (warp-cooperative: lanes share
-// the tiles of one Gaussian at a time).
-__device__ __forceinline__ void count_tiles_warp(int g_base, int n, int TX,
-                                                 const int4* __restrict__ rect,
-                                                 int* __restrict__ tile_cnt) {
+// Per-tile entry counts from the rectangles (warp-cooperative: lanes share the
+// tiles of one Gaussian at a time; fire-and-forget atomics) and the block's
+// sum of per-Gaussian counts.
+__device__ __forceinline__ void count_block(int n, int TX, const int4* __restrict__ rect,
+                                           const int* __restrict__ count,
+                                           int* __restrict__ tile_cnt,
+                                           long long* __restrict__ block_sum) {
+  __shared__ int s_warp[kGB / 32];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  const int g = g_base + lane;
-  const int4 rc = g < n ? rect[g] : make_int4(0, 0, 0, 0);
+  const int4 rc = i < n ? rect[i] : make_int4(0, 0, 0, 0);
   for (int l = 0; l < 32; l++) {
     const int x0 = __shfl_sync(0xffffffffu, rc.x, l);
     const int y0 = __shfl_sync(0xffffffffu, rc.y, l);
@@ -50,44 +54,57 @@ __device__ __forceinline__ void count_tiles_warp(int g_base, int n, int TX,
       atomicAdd(&tile_cnt[(y0 + dy) * TX + x0 + (j - dy * w)], 1);
     }
   }
+  int c = i < n ? count[i] : 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) s_warp[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long s = 0;
+    for (int w = 0; w < kGB / 32; w++) s += s_warp[w];
+    block_sum[blockIdx.x] = s;
+  }
 }
 
-__global__ void __launch_bounds__(256)
-k_count_tiles(int n, int TX, const int4* __restrict__ rect, int* __restrict__ tile_cnt) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  count_tiles_warp(warp * 32, n, TX, rect, tile_cnt);
+__global__ void __launch_bounds__(kGB)
+k_count_tiles(int n, int TX, const int4* __restrict__ rect, const int* __restrict__ count,
+              int* __restrict__ tile_cnt, long long* __restrict__ block_sum) {
+  count_block(n, TX, rect, count, tile_cnt, block_sum);
 }
 
-// Fused projection + tile counts for gs2d_prepare and the fit loop; with
-// adam_tick, the Adam step counter and bias corrections advance here (the
-// first kernel of a fit iteration).
-__global__ void __launch_bounds__(256)
+// Fused projection + counts for gs2d_prepare and the fit loop; with adam_tick
+// the Adam step counter and the powers beta^step advance here (the first
+// kernel of a fit iteration).
+__global__ void __launch_bounds__(kGB)
 k_project_count(int n, int W, int H, int TX, float sigma_cut, float alpha_min, float det_eps,
                 const float* __restrict__ params, float4* __restrict__ rec,
                 int4* __restrict__ rect, int* __restrict__ count, int* __restrict__ tile_cnt,
-                WsHeader* __restrict__ hdr, int adam_tick, float b1, float b2) {
+                long long* __restrict__ block_sum, WsHeader* __restrict__ hdr, int adam_tick,
+                float b1, float b2) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) {
-    count[n] = 0;
-    if (adam_tick) {
-      const int t = ++hdr->step;
-      hdr->bc1 = (float)(1.0 - pow((double)b1, (double)t));
-      hdr->bc2 = (float)(1.0 - pow((double)b2, (double)t));
-    }
+  if (i == 0 && adam_tick) {
+    const int t = ++hdr->step;
+    const double p1 = t == 1 ? (double)b1 : hdr->pw1 * b1;
+    const double p2 = t == 1 ? (double)b2 : hdr->pw2 * b2;
+    hdr->pw1 = p1;
+    hdr->pw2 = p2;
+    hdr->bc1 = (float)(1.0 - p1);
+    hdr->bc2 = (float)(1.0 - p2);
   }
   if (i < n) project_one(i, n, W, H, sigma_cut, alpha_min, det_eps, params, rec, rect, count);
   __syncwarp();
-  count_tiles_warp(i & ~31, n, TX, rect, tile_cnt);
+  count_block(n, TX, rect, count, tile_cnt, block_sum);
 }
 
 // ---------------------------------------------------------------------------
-// Scans.  Block 0: per-Gaussian exclusive offsets (backward slots) and the
-// capacity decision; block 1: per-tile ranges and cursors, and the reset of the
-// tile counts for the next call.  Sums are 64-bit so that a pathological input
-// is reported as over capacity instead of wrapping around.
+// Scans.  CTAs 0 .. nbg-1: offsets of their 256 Gaussians (prefix of the block
+// sums + in-block exclusive scan).  CTA nbg: per-tile ranges and cursors, the
+// reset of the tile counts, the entry total and the capacity decision.  Sums
+// are 64-bit so that a pathological input is reported as over capacity
+// instead of wrapping around.
 __device__ __forceinline__ long long block_scan64(long long v, long long* warp_sum,
                                                   long long* total) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   long long x = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -97,98 +114,139 @@ __device__ __forceinline__ long long block_scan64(long long v, long long* warp_s
   if (lane == 31) warp_sum[wid] = x;
   __syncthreads();
   if (wid == 0) {
-    long long t = warp_sum[lane];
+    long long t = lane < nw ? warp_sum[lane] : 0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const long long y = __shfl_up_sync(0xffffffffu, t, o);
       if (lane >= o) t += y;
     }
-    warp_sum[lane] = t;
+    if (lane < nw) warp_sum[lane] = t;
   }
   __syncthreads();
   const long long ex = (wid > 0 ? warp_sum[wid - 1] : 0) + x - v;
-  *total = warp_sum[31];
+  *total = warp_sum[nw - 1];
   __syncthreads();
   return ex;
 }
 
-__global__ void __launch_bounds__(kScanThreads)
-k_bin_scan(int n, int num_tiles, int64_t max_entries, int* __restrict__ count,
-           int* __restrict__ tile_cnt, int* __restrict__ cursor, int2* __restrict__ ranges,
-           WsHeader* __restrict__ hdr) {
+constexpr int kTileItems = 8;
+
+__global__ void __launch_bounds__(kGB)
+k_bin_scan(int n, int nbg, int num_tiles, int64_t max_entries, int* __restrict__ count,
+           const long long* __restrict__ block_sum, int* __restrict__ tile_cnt,
+           int* __restrict__ cursor, int2* __restrict__ ranges, WsHeader* __restrict__ hdr) {
   __shared__ long long warp_sum[32];
   const int t = threadIdx.x;
-  const bool gauss = blockIdx.x == 0;
-  const int len = gauss ? n : num_tiles;
-  int* src = gauss ? count : tile_cnt;
-  // pass 1: total (decides capacity before anything is written)
+  if ((int)blockIdx.x < nbg) {
+    // total and this block's prefix from the block sums
+    long long tot = 0, pre = 0;
+    for (int b = t; b < nbg; b += kGB) {
+      const long long v = block_sum[b];
+      tot += v;
+      pre += b < (int)blockIdx.x ? v : 0;
+    }
+    long long total, prefix;
+    block_scan64(tot, warp_sum, &total);
+    block_scan64(pre, warp_sum, &prefix);
+    const bool over = total > max_entries;
+    const int i = blockIdx.x * kGB + t;
+    const int c = i < n ? count[i] : 0;
+    long long dummy;
+    const long long ex = block_scan64(c, warp_sum, &dummy);
+    if (i < n) count[i] = over ? 0 : (int)(prefix + ex);
+    return;
+  }
+  // the tile CTA
   long long tot = 0;
-  for (int i = t; i < len; i += kScanThreads) tot += src[i];
+  for (int i = t; i < num_tiles; i += kGB) tot += tile_cnt[i];
   long long total;
   block_scan64(tot, warp_sum, &total);
   const bool over = total > max_entries;
-  // pass 2: exclusive scan in chunks of kScanThreads * kScanItems
   long long carry = 0;
-  for (int b = 0; b < len; b += kScanThreads * kScanItems) {
-    const int base = b + t * kScanItems;
-    int c[kScanItems];
+  for (int b = 0; b < num_tiles; b += kGB * kTileItems) {
+    const int base = b + t * kTileItems;
+    int c[kTileItems];
     long long v = 0;
 #pragma unroll
-    for (int k = 0; k < kScanItems; k++) {
-      c[k] = base + k < len ? src[base + k] : 0;
+    for (int k = 0; k < kTileItems; k++) {
+      c[k] = base + k < num_tiles ? tile_cnt[base + k] : 0;
       v += c[k];
     }
     long long chunk;
     long long run = carry + block_scan64(v, warp_sum, &chunk);
 #pragma unroll
-    for (int k = 0; k < kScanItems; k++) {
+    for (int k = 0; k < kTileItems; k++) {
       const int i = base + k;
-      if (i < len) {
-        if (gauss) {
-          count[i] = over ? 0 : (int)run;
-        } else {
-          const int s = over ? 0 : (int)run;
-          // an empty tile's range is (0, 0) wherever it sits in the list
-          ranges[i] = (over || c[k] == 0) ? make_int2(0, 0) : make_int2(s, s + c[k]);
-          cursor[i] = s;
-          tile_cnt[i] = 0;
-        }
+      if (i < num_tiles) {
+        const int s = over ? 0 : (int)run;
+        // an empty tile's range is (0, 0) wherever it sits in the list
+        ranges[i] = (over || c[k] == 0) ? make_int2(0, 0) : make_int2(s, s + c[k]);
+        cursor[i] = s;
+        tile_cnt[i] = 0;
       }
       run += c[k];
     }
     carry += chunk;
   }
   if (t == 0) {
-    if (gauss) {
-      hdr->entries_raw = total;
-      hdr->n_entries = over ? 0 : (int)total;
-      if (over) atomicCAS(&hdr->status, 0, (int)GS2D_ERR_CAPACITY);
-      count[n] = over ? 0 : (int)total;
-    } else {
-      hdr->long_count = 0;
-    }
+    hdr->entries_raw = total;
+    hdr->n_entries = over ? 0 : (int)total;
+    if (over) atomicCAS(&hdr->status, 0, (int)GS2D_ERR_CAPACITY);
+    count[n] = over ? 0 : (int)total;
+    hdr->long_count = 0;
   }
 }
 
-// Scatter: every entry claims the next slot of its tile's list.
-__global__ void __launch_bounds__(256)
+// Scatter: every entry claims the next slot of its tile's list.  A warp takes
+// 32 Gaussians, flattens their entries, and each lane keeps kInFlight atomics
+// in flight before it stores the claimed slots.
+constexpr int kInFlight = 4;
+
+__global__ void __launch_bounds__(kGB)
 k_bin_scatter(int n, int TX, const int4* __restrict__ rect, const WsHeader* __restrict__ hdr,
               int* __restrict__ cursor, uint32_t* __restrict__ list) {
+  __shared__ int s_start[kGB / 32][33];
   if (hdr->entries_raw != (int64_t)hdr->n_entries) return;  // over capacity
-  const int lane = threadIdx.x & 31;
-  const int g_base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int g_base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31;
   const int g = g_base + lane;
   const int4 rc = g < n ? rect[g] : make_int4(0, 0, 0, 0);
-  for (int l = 0; l < 32; l++) {
-    const int x0 = __shfl_sync(0xffffffffu, rc.x, l);
-    const int y0 = __shfl_sync(0xffffffffu, rc.y, l);
-    const int w = __shfl_sync(0xffffffffu, rc.z, l) - x0;
-    const int cnt = w * (__shfl_sync(0xffffffffu, rc.w, l) - y0);
-    for (int j = lane; j < cnt; j += 32) {
-      const int dy = j / w;
-      const int tile = (y0 + dy) * TX + x0 + (j - dy * w);
-      list[atomicAdd(&cursor[tile], 1)] = (uint32_t)(g_base + l);
+  const int cnt = (rc.z - rc.x) * (rc.w - rc.y);
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  int* start = s_start[wid];
+  start[lane] = incl - cnt;
+  const int T = __shfl_sync(0xffffffffu, incl, 31);
+  __syncwarp();
+  for (int e0 = 0; e0 < T; e0 += 32 * kInFlight) {
+    int pos[kInFlight];
+    uint32_t gi[kInFlight];
+#pragma unroll
+    for (int u = 0; u < kInFlight; u++) {
+      const int e = e0 + u * 32 + lane;
+      pos[u] = -1;
+      if (e < T) {
+        // owner: the last lane whose start is <= e (binary search over 32)
+        // (starts are non-decreasing; 16 + 8 + 4 + 2 + 1 keeps lo + step <= 31)
+        int lo = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+          if (start[lo + step] <= e) lo += step;
+        gi[u] = (uint32_t)(g_base + lo);
+        const int4 ro = rect[g_base + lo];
+        const int w = ro.z - ro.x;
+        const int j = e - start[lo];
+        const int dy = j / w;
+        pos[u] = atomicAdd(&cursor[(ro.y + dy) * TX + ro.x + (j - dy * w)], 1);
+      }
     }
+#pragma unroll
+    for (int u = 0; u < kInFlight; u++)
+      if (pos[u] >= 0) list[pos[u]] = gi[u];
   }
 }
 
@@ -319,8 +377,8 @@ k_sort_long(int2* __restrict__ ranges, uint32_t* __restrict__ list,
 
 // ---------------------------------------------------------------------------
 cudaError_t launch_project(const gs2d_plan& p, void* ws, const float* params, cudaStream_t s) {
-  const int blocks = (p.n + 255) / 256;
-  k_project<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(
+  if (p.n == 0) return cudaSuccess;
+  k_project<<<(p.n + kGB - 1) / kGB, kGB, 0, s>>>(
       p.n, p.width, p.height, p.cfg.sigma_cut, p.cfg.alpha_min, p.cfg.det_eps, params,
       ws_ptr<float4>(ws, p, kOffRec), ws_ptr<int4>(ws, p, kOffRect), ws_ptr<int>(ws, p, kOffCount));
   return cudaGetLastError();
@@ -328,7 +386,7 @@ cudaError_t launch_project(const gs2d_plan& p, void* ws, const float* params, cu
 
 static bool g_long_attr_set = false;
 
-// Scans, scatter and segment sorts (everything after the tile counts).
+// Scans, scatter and segment sorts (everything after the counts).
 static cudaError_t launch_bin_rest(const gs2d_plan& p, void* ws, cudaStream_t s) {
   WsHeader* hdr = ws_ptr<WsHeader>(ws, p, kOffHeader);
   int* count = ws_ptr<int>(ws, p, kOffCount);
@@ -337,11 +395,13 @@ static cudaError_t launch_bin_rest(const gs2d_plan& p, void* ws, cudaStream_t s)
   int* long_tiles = ws_ptr<int>(ws, p, kOffLong);
   uint32_t* list = ws_ptr<uint32_t>(ws, p, kOffList);
   int2* ranges = ws_ptr<int2>(ws, p, kOffRanges);
-  k_bin_scan<<<2, kScanThreads, 0, s>>>(p.n, p.num_tiles, p.max_entries, count, tile_cnt, cursor,
-                                        ranges, hdr);
+  const int nbg = (p.n + kGB - 1) / kGB;
+  k_bin_scan<<<nbg + 1, kGB, 0, s>>>(p.n, nbg, p.num_tiles, p.max_entries, count,
+                                     ws_ptr<long long>(ws, p, kOffBlockSum), tile_cnt, cursor,
+                                     ranges, hdr);
   if (p.n > 0)
-    k_bin_scatter<<<(p.n + 255) / 256, 256, 0, s>>>(p.n, p.tiles_x, ws_ptr<int4>(ws, p, kOffRect),
-                                                    hdr, cursor, list);
+    k_bin_scatter<<<nbg, kGB, 0, s>>>(p.n, p.tiles_x, ws_ptr<int4>(ws, p, kOffRect), hdr, cursor,
+                                      list);
   k_sort_short<<<(p.num_tiles + 7) / 8, 256, 0, s>>>(p.num_tiles, ranges, list, long_tiles, hdr);
   const int smem = kLongMax * (int)sizeof(uint32_t);
   if (!g_long_attr_set) {
@@ -356,8 +416,9 @@ static cudaError_t launch_bin_rest(const gs2d_plan& p, void* ws, cudaStream_t s)
 
 cudaError_t launch_bin_sort(const gs2d_plan& p, void* ws, cudaStream_t s) {
   if (p.n > 0)
-    k_count_tiles<<<(p.n + 255) / 256, 256, 0, s>>>(p.n, p.tiles_x, ws_ptr<int4>(ws, p, kOffRect),
-                                                    ws_ptr<int>(ws, p, kOffTileCnt));
+    k_count_tiles<<<(p.n + kGB - 1) / kGB, kGB, 0, s>>>(
+        p.n, p.tiles_x, ws_ptr<int4>(ws, p, kOffRect), ws_ptr<int>(ws, p, kOffCount),
+        ws_ptr<int>(ws, p, kOffTileCnt), ws_ptr<long long>(ws, p, kOffBlockSum));
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_bin_rest(p, ws, s);
@@ -365,12 +426,12 @@ cudaError_t launch_bin_sort(const gs2d_plan& p, void* ws, cudaStream_t s) {
 
 cudaError_t launch_prepare(const gs2d_plan& p, void* ws, const float* params, bool adam_tick,
                            cudaStream_t s) {
-  const int blocks = (p.n + 255) / 256;
-  k_project_count<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(
+  const int blocks = (p.n + kGB - 1) / kGB;
+  k_project_count<<<blocks > 0 ? blocks : 1, kGB, 0, s>>>(
       p.n, p.width, p.height, p.tiles_x, p.cfg.sigma_cut, p.cfg.alpha_min, p.cfg.det_eps, params,
       ws_ptr<float4>(ws, p, kOffRec), ws_ptr<int4>(ws, p, kOffRect), ws_ptr<int>(ws, p, kOffCount),
-      ws_ptr<int>(ws, p, kOffTileCnt), ws_ptr<WsHeader>(ws, p, kOffHeader), adam_tick ? 1 : 0,
-      p.cfg.beta1, p.cfg.beta2);
+      ws_ptr<int>(ws, p, kOffTileCnt), ws_ptr<long long>(ws, p, kOffBlockSum),
+      ws_ptr<WsHeader>(ws, p, kOffHeader), adam_tick ? 1 : 0, p.cfg.beta1, p.cfg.beta2);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_bin_rest(p, ws, s);

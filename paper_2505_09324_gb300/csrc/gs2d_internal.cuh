@@ -28,6 +28,7 @@ enum WsSection {
   kOffRec,          // float4[3][n]  render records (SoA of float4 rows)
   kOffRect,         // int4[n]       tile rectangle [tx0, ty0, tx1, ty1)
   kOffCount,        // int32[n + 1]  per-Gaussian tile counts, then exclusive offsets
+  kOffBlockSum,     // int64[n / 256 + 1]  entry counts per block of 256 Gaussians
   kOffTileCnt,      // int32[num_tiles]  entries per tile (zero between calls)
   kOffCursor,       // int32[num_tiles]  next free slot of each tile's list
   kOffLong,         // int32[num_tiles + 1]  tiles whose list needs the CTA sort
@@ -45,11 +46,11 @@ struct WsHeader {
   int64_t entries_raw;  // total entries requested by the tile counts
   int32_t step;         // Adam step counter of the fit loop
   float bc1, bc2;       // Adam bias corrections for that step
-  int32_t pad0;
+  int32_t long_count;   // tiles queued for the long-list sort
   float loss[2];        // last reduced {loss, clamped mse}
   unsigned long long pairs, hits;  // gs2d_count_pairs results
-  int32_t long_count;              // tiles queued for the long-list sort
-  int32_t pad[49];
+  double pw1, pw2;      // beta1^step, beta2^step
+  int32_t pad[46];
 };
 static_assert(sizeof(WsHeader) == 256, "header is one 256-byte block");
 
@@ -163,7 +164,6 @@ cudaError_t launch_adam(float* params, const float* grads, float* m, float* v, i
                         int32_t step, const uint8_t* mask, const gs2d_config& cfg,
                         cudaStream_t s);
 cudaError_t launch_loss_reduce(const gs2d_plan& p, void* ws, float* loss, cudaStream_t s);
-cudaError_t launch_adam_tick(const gs2d_plan& p, void* ws, cudaStream_t s);
 cudaError_t launch_count_pairs(const gs2d_plan& p, void* ws, cudaStream_t s);
 // project + bin_sort; with adam_tick the fit loop's Adam step counter and bias
 // corrections advance in the same launch.

@@ -352,13 +352,21 @@ __device__ __forceinline__ void chain_grads(const float* __restrict__ params, in
   gr[8] = fmaf(cr, a[0], fmaf(cg, a[1], cb * a[2]));
 }
 
+// kRL lanes share one Gaussian: lane `sub` sums slots s0 + sub, s0 + sub + kRL,
+// ..., then the group adds its kRL partial sums (a fixed order: deterministic).
+constexpr int kRL = 4;
+
 __device__ __forceinline__ bool gather_partials(const float4* __restrict__ partial,
-                                                const int* __restrict__ offs, int i,
-                                                float a[kPartials]) {
-  const int s0 = offs[i], s1 = offs[i + 1];
+                                                const int* __restrict__ offs, int i, bool valid,
+                                                int sub, float a[kPartials]) {
+  int s0 = 0, s1 = 0;
+  if (valid) {
+    s0 = offs[i];
+    s1 = offs[i + 1];
+  }
 #pragma unroll
   for (int k = 0; k < kPartials; k++) a[k] = 0.0f;
-  for (int sl = s0; sl < s1; sl++) {
+  for (int sl = s0 + sub; sl < s1; sl += kRL) {
     const float4 p = partial[2 * sl], q = partial[2 * sl + 1];
     a[0] += p.x;
     a[1] += p.y;
@@ -369,6 +377,10 @@ __device__ __forceinline__ bool gather_partials(const float4* __restrict__ parti
     a[6] += q.z;
     a[7] += q.w;
   }
+#pragma unroll
+  for (int o = 1; o < kRL; o <<= 1)
+#pragma unroll
+    for (int k = 0; k < kPartials; k++) a[k] += __shfl_xor_sync(0xffffffffu, a[k], o);
   return s1 > s0;
 }
 
@@ -376,34 +388,40 @@ __global__ void __launch_bounds__(256)
 k_reduce_chain(int n, const float* __restrict__ params, const int* __restrict__ offs,
                const float4* __restrict__ partial, const WsHeader* __restrict__ hdr,
                float* __restrict__ grads) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const bool ok = hdr->entries_raw == (int64_t)hdr->n_entries;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = gt / kRL, sub = gt % kRL;
+  const bool valid = i < n && hdr->entries_raw == (int64_t)hdr->n_entries;
   float a[kPartials], gr[9];
-  const bool any = ok && gather_partials(partial, offs, i, a);
+  const bool any = gather_partials(partial, offs, i, valid, sub, a);
+  if (i >= n) return;
   if (any) chain_grads(params, n, i, a, gr);
 #pragma unroll
-  for (int r = 0; r < 9; r++) grads[(size_t)r * n + i] = any ? gr[r] : 0.0f;
+  for (int r = sub; r < 9; r += kRL) grads[(size_t)r * n + i] = any ? gr[r] : 0.0f;
 }
 
-// Fit loop: reduction + chain + Adam on the Gaussian's nine parameters.
+// Fit loop: reduction + chain + Adam on the Gaussian's nine parameters (lane
+// `sub` of the group updates rows sub, sub + kRL, ...).
 __global__ void __launch_bounds__(256)
 k_reduce_chain_adam(int n, float* __restrict__ params, const int* __restrict__ offs,
                     const float4* __restrict__ partial, const WsHeader* __restrict__ hdr,
                     float* __restrict__ m, float* __restrict__ v, float lr, float b1, float b2,
                     float eps) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  if (hdr->entries_raw != (int64_t)hdr->n_entries) return;  // over capacity: no update
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = gt / kRL, sub = gt % kRL;
+  const bool ok = hdr->entries_raw == (int64_t)hdr->n_entries;  // else over capacity
   float a[kPartials], gr[9];
-  const bool any = gather_partials(partial, offs, i, a);
-  if (any)
+  const bool any = gather_partials(partial, offs, i, i < n && ok, sub, a);
+  if (!ok) return;  // the same for every thread of the grid
+  const bool act = i < n;
+  if (act && any)
     chain_grads(params, n, i, a, gr);
   else
     for (int r = 0; r < 9; r++) gr[r] = 0.0f;
+  __syncwarp();  // every lane of the group has read the parameters
+  if (!act) return;
   const float ibc1 = 1.0f / hdr->bc1, ibc2 = 1.0f / hdr->bc2;
 #pragma unroll
-  for (int r = 0; r < 9; r++) {
+  for (int r = sub; r < 9; r += kRL) {
     const size_t k = (size_t)r * n + i;
     const float g = gr[r];
     const float mm = fmaf(b1, m[k], (1.0f - b1) * g);
@@ -488,12 +506,6 @@ k_count_pairs(TileCtx c, WsHeader* __restrict__ hdr) {
   }
 }
 
-__global__ void k_adam_tick(WsHeader* __restrict__ hdr, float b1, float b2) {
-  const int t = ++hdr->step;
-  hdr->bc1 = (float)(1.0 - pow((double)b1, (double)t));
-  hdr->bc2 = (float)(1.0 - pow((double)b2, (double)t));
-}
-
 // ---------------------------------------------------------------------------
 static TileCtx make_ctx(const gs2d_plan& p, void* ws) {
   TileCtx c;
@@ -519,7 +531,7 @@ cudaError_t launch_render_bwd(const gs2d_plan& p, void* ws, const float* params,
   float* partial = ws_ptr<float>(ws, p, kOffPartial);
   k_render_bwd<<<p.num_tiles, kRT, 0, s>>>(make_ctx(p, ws), dimg, partial);
   if (p.n > 0)
-    k_reduce_chain<<<(p.n + 255) / 256, 256, 0, s>>>(
+    k_reduce_chain<<<(p.n * kRL + 255) / 256, 256, 0, s>>>(
         p.n, params, ws_ptr<int>(ws, p, kOffCount), reinterpret_cast<const float4*>(partial),
         ws_ptr<WsHeader>(ws, p, kOffHeader), grads);
   return cudaGetLastError();
@@ -543,15 +555,10 @@ cudaError_t launch_render_l2(const gs2d_plan& p, void* ws, const float* params,
   k_render_l2<<<p.num_tiles, kRT, 0, s>>>(make_ctx(p, ws), target, grad_scale(p), img, partial,
                                           ws_ptr<float2>(ws, p, kOffLossPart));
   if (p.n > 0)
-    k_reduce_chain<<<(p.n + 255) / 256, 256, 0, s>>>(
+    k_reduce_chain<<<(p.n * kRL + 255) / 256, 256, 0, s>>>(
         p.n, params, ws_ptr<int>(ws, p, kOffCount), reinterpret_cast<const float4*>(partial),
         ws_ptr<WsHeader>(ws, p, kOffHeader), grads);
   if (loss) return launch_loss_reduce(p, ws, loss, s);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_adam_tick(const gs2d_plan& p, void* ws, cudaStream_t s) {
-  k_adam_tick<<<1, 1, 0, s>>>(ws_ptr<WsHeader>(ws, p, kOffHeader), p.cfg.beta1, p.cfg.beta2);
   return cudaGetLastError();
 }
 
@@ -571,7 +578,7 @@ cudaError_t launch_fit_step(const gs2d_plan& p, void* ws, const float* target, f
   k_render_l2<<<p.num_tiles, kRT, 0, s>>>(make_ctx(p, ws), target, grad_scale(p), nullptr,
                                           partial, ws_ptr<float2>(ws, p, kOffLossPart));
   if (p.n > 0)
-    k_reduce_chain_adam<<<(p.n + 255) / 256, 256, 0, s>>>(
+    k_reduce_chain_adam<<<(p.n * kRL + 255) / 256, 256, 0, s>>>(
         p.n, params, ws_ptr<int>(ws, p, kOffCount), reinterpret_cast<const float4*>(partial),
         ws_ptr<WsHeader>(ws, p, kOffHeader), m, v, p.cfg.lr, p.cfg.beta1, p.cfg.beta2, p.cfg.eps);
   return cudaGetLastError();

@@ -51,7 +51,7 @@ def test_plan_layout(nat):
     assert (p.tiles_x, p.tiles_y, p.num_tiles) == (120, 68, 8160)
     assert p.tile_bits == 13 and p.sort_passes == 1
     assert p.max_entries == max(1 << 20, 16 * 20000)
-    offs = list(p.off)[:12]
+    offs = list(p.off)[:13]
     assert all(o % 256 == 0 for o in offs)
     assert offs == sorted(offs) and p.ws_bytes > offs[-1]
     q = nat.plan_init(16, 16, 5)
