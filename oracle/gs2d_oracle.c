@@ -36,10 +36,10 @@
  *   computed in single precision with exactly these single-rounded operations
  *   (the file is compiled with -ffp-contract=off so no FMA is formed):
  *        Sxx = l1*l1, Syy = l2*l2 + l3*l3, a = l1*l3, det = a*a,
- *        mid = 0.5*(Sxx + Syy), disc = max(0.1, mid*mid - det),
- *        lam = mid + sqrt(disc), r = ceil(sqrt(2*sigma_cut) * sqrt(lam))
- *        (the sigma <= sigma_cut ellipse; 3*sqrt(lam) at sigma_cut = 4.5),
- *        px0 = floor(mx - r), px1 = floor(mx + r)  (same in y),
+ *        k = sqrt(2*sigma_cut), rx = ceil(k * sqrt(Sxx)), ry = ceil(k * sqrt(Syy))
+ *        (the axis-aligned box of the sigma <= sigma_cut ellipse; k = 3 at
+ *        sigma_cut = 4.5),
+ *        px0 = floor(mx - rx), px1 = floor(mx + rx)  (same in y with ry),
  *   clipped to the image; tiles tx0 = xlo / T .. xhi / T inclusive.  A Gaussian
  *   is culled when a parameter is non-finite, det <= det_eps, |w| < alpha_min
  *   or its clipped rectangle is empty.  The key of a (tile, n) pair is
@@ -373,16 +373,14 @@ static int orc_rect32(int W, int H, int T, float mx, float my, float l1, float l
   float det = a * a;
   if (!(det > det_eps)) return 0;
   if (!(fabsf(w) >= alpha_min)) return 0;
-  float mid = 0.5f * (sxx + syy);
-  float disc = mid * mid - det;
-  if (!(disc > 0.1f)) disc = 0.1f;
-  float lam = mid + sqrtf(disc);
-  /* the sigma <= sigma_cut ellipse reaches sqrt(2 sigma_cut lam) along its
-   * major axis; at sigma_cut = 4.5 the factor is exactly 3 */
+  /* the sigma <= sigma_cut ellipse {d : d^T Sigma^-1 d <= 2 sigma_cut} reaches
+   * sqrt(2 sigma_cut Sxx) along x and sqrt(2 sigma_cut Syy) along y; at
+   * sigma_cut = 4.5 the factor is exactly 3 */
   float kc = sqrtf(2.0f * sigma_cut);
-  float r = ceilf(kc * sqrtf(lam));
-  float fx0 = floorf(mx - r), fx1 = floorf(mx + r);
-  float fy0 = floorf(my - r), fy1 = floorf(my + r);
+  float rx = ceilf(kc * sqrtf(sxx));
+  float ry = ceilf(kc * sqrtf(syy));
+  float fx0 = floorf(mx - rx), fx1 = floorf(mx + rx);
+  float fy0 = floorf(my - ry), fy1 = floorf(my + ry);
   /* clip to the image (as floats first so huge values cannot overflow int) */
   if (fx0 < 0.0f) fx0 = 0.0f;
   if (fy0 < 0.0f) fy0 = 0.0f;

@@ -9,7 +9,7 @@
 //   1. per-tile entry counts (atomic increments from each Gaussian's tiles)
 //      and per-block sums of the per-Gaussian counts;
 //   2. exclusive scans: one CTA per block of 256 Gaussians for the offsets
-//      (backward slots), one CTA for the per-tile list ranges; capacity check;
+//      (backward slots), one CTA per 1024 tiles for the list ranges; capacity;
 //   3. scatter: every entry claims the next slot of its tile's list;
 //   4. segment sort: each tile's list is sorted by Gaussian index (a warp
 //      bitonic network in registers for lists of up to 512, a CTA bitonic
@@ -98,10 +98,10 @@ k_project_count(int n, int W, int H, int TX, float sigma_cut, float alpha_min, f
 
 // ---------------------------------------------------------------------------
 // Scans.  CTAs 0 .. nbg-1: offsets of their 256 Gaussians (prefix of the block
-// sums + in-block exclusive scan).  CTA nbg: per-tile ranges and cursors, the
-// reset of the tile counts, the entry total and the capacity decision.  Sums
-// are 64-bit so that a pathological input is reported as over capacity
-// instead of wrapping around.
+// sums + in-block exclusive scan).  CTAs nbg ..: per-tile ranges and cursors of
+// a chunk of 1024 tiles; the first of them also records the entry total and
+// the capacity decision.  Sums are 64-bit so that a pathological input is
+// reported as over capacity instead of wrapping around.
 __device__ __forceinline__ long long block_scan64(long long v, long long* warp_sum,
                                                   long long* total) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -129,7 +129,7 @@ __device__ __forceinline__ long long block_scan64(long long v, long long* warp_s
   return ex;
 }
 
-constexpr int kTileItems = 8;
+constexpr int kTileItems = 4;  // tiles per thread of a tile-scan CTA
 
 __global__ void __launch_bounds__(kGB)
 k_bin_scan(int n, int nbg, int num_tiles, int64_t max_entries, int* __restrict__ count,
@@ -156,15 +156,23 @@ k_bin_scan(int n, int nbg, int num_tiles, int64_t max_entries, int* __restrict__
     if (i < n) count[i] = over ? 0 : (int)(prefix + ex);
     return;
   }
-  // the tile CTA
-  long long tot = 0;
-  for (int i = t; i < num_tiles; i += kGB) tot += tile_cnt[i];
-  long long total;
+  // tile CTAs: chunk [c0, c0 + kGB * kTileItems) of the tiles; the prefix of the
+  // chunk and the total come from a strided pass over all tile counts (the
+  // counts are reset later, by k_sort_short, once nothing reads them)
+  const int tb = (int)blockIdx.x - nbg;
+  const int c0 = tb * kGB * kTileItems;
+  long long tot = 0, pre = 0;
+  for (int i = t; i < num_tiles; i += kGB) {
+    const int v = tile_cnt[i];
+    tot += v;
+    pre += i < c0 ? v : 0;
+  }
+  long long total, prefix;
   block_scan64(tot, warp_sum, &total);
+  block_scan64(pre, warp_sum, &prefix);
   const bool over = total > max_entries;
-  long long carry = 0;
-  for (int b = 0; b < num_tiles; b += kGB * kTileItems) {
-    const int base = b + t * kTileItems;
+  {
+    const int base = c0 + t * kTileItems;
     int c[kTileItems];
     long long v = 0;
 #pragma unroll
@@ -173,7 +181,7 @@ k_bin_scan(int n, int nbg, int num_tiles, int64_t max_entries, int* __restrict__
       v += c[k];
     }
     long long chunk;
-    long long run = carry + block_scan64(v, warp_sum, &chunk);
+    long long run = prefix + block_scan64(v, warp_sum, &chunk);
 #pragma unroll
     for (int k = 0; k < kTileItems; k++) {
       const int i = base + k;
@@ -182,13 +190,11 @@ k_bin_scan(int n, int nbg, int num_tiles, int64_t max_entries, int* __restrict__
         // an empty tile's range is (0, 0) wherever it sits in the list
         ranges[i] = (over || c[k] == 0) ? make_int2(0, 0) : make_int2(s, s + c[k]);
         cursor[i] = s;
-        tile_cnt[i] = 0;
       }
       run += c[k];
     }
-    carry += chunk;
   }
-  if (t == 0) {
+  if (tb == 0 && t == 0) {
     hdr->entries_raw = total;
     hdr->n_entries = over ? 0 : (int)total;
     if (over) atomicCAS(&hdr->status, 0, (int)GS2D_ERR_CAPACITY);
@@ -303,13 +309,16 @@ __device__ __forceinline__ void warp_sort_list(uint32_t* __restrict__ seg, int l
 }
 
 // Segment sort: one warp per tile, bitonic network in registers for lists of
-// up to 512; longer lists are queued for k_sort_long.
+// up to 512; longer lists are queued for k_sort_long.  Also resets the tile's
+// entry counter for the next binning (its last reader, the scan, is done).
 __global__ void __launch_bounds__(256)
 k_sort_short(int num_tiles, const int2* __restrict__ ranges, uint32_t* __restrict__ list,
-             int* __restrict__ long_tiles, WsHeader* __restrict__ hdr) {
+             int* __restrict__ long_tiles, int* __restrict__ tile_cnt,
+             WsHeader* __restrict__ hdr) {
   const int lane = threadIdx.x & 31;
   const int tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (tile >= num_tiles) return;
+  if (lane == 0) tile_cnt[tile] = 0;
   const int2 rg = ranges[tile];
   const int len = rg.y - rg.x;
   uint32_t* seg = list + rg.x;
@@ -396,13 +405,15 @@ static cudaError_t launch_bin_rest(const gs2d_plan& p, void* ws, cudaStream_t s)
   uint32_t* list = ws_ptr<uint32_t>(ws, p, kOffList);
   int2* ranges = ws_ptr<int2>(ws, p, kOffRanges);
   const int nbg = (p.n + kGB - 1) / kGB;
-  k_bin_scan<<<nbg + 1, kGB, 0, s>>>(p.n, nbg, p.num_tiles, p.max_entries, count,
+  const int nbt = (p.num_tiles + kGB * kTileItems - 1) / (kGB * kTileItems);
+  k_bin_scan<<<nbg + nbt, kGB, 0, s>>>(p.n, nbg, p.num_tiles, p.max_entries, count,
                                      ws_ptr<long long>(ws, p, kOffBlockSum), tile_cnt, cursor,
                                      ranges, hdr);
   if (p.n > 0)
     k_bin_scatter<<<nbg, kGB, 0, s>>>(p.n, p.tiles_x, ws_ptr<int4>(ws, p, kOffRect), hdr, cursor,
                                       list);
-  k_sort_short<<<(p.num_tiles + 7) / 8, 256, 0, s>>>(p.num_tiles, ranges, list, long_tiles, hdr);
+  k_sort_short<<<(p.num_tiles + 7) / 8, 256, 0, s>>>(p.num_tiles, ranges, list, long_tiles,
+                                                    tile_cnt, hdr);
   const int smem = kLongMax * (int)sizeof(uint32_t);
   if (!g_long_attr_set) {
     const cudaError_t e =

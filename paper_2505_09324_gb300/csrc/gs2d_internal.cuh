@@ -107,16 +107,13 @@ __device__ __forceinline__ void project_one(int i, int n, int W, int H, float si
   const float a = __fmul_rn(l1, l3);
   const float det = __fmul_rn(a, a);
   if (finite && (det > det_eps) && (fabsf(w) >= alpha_min)) {
-    const float mid = __fmul_rn(0.5f, __fadd_rn(sxx, syy));
-    float disc = __fsub_rn(__fmul_rn(mid, mid), det);
-    if (!(disc > 0.1f)) disc = 0.1f;
-    const float lam = __fadd_rn(mid, __fsqrt_rn(disc));
-    // sigma <= sigma_cut reaches sqrt(2 sigma_cut lam) along the major axis
-    // (3 sqrt(lam), the 3-sigma ellipse, at sigma_cut = 4.5)
+    // the ellipse sigma <= sigma_cut reaches sqrt(2 sigma_cut Sxx) along x and
+    // sqrt(2 sigma_cut Syy) along y (3 sqrt(Sxx), 3 sqrt(Syy) at 4.5)
     const float kc = __fsqrt_rn(__fmul_rn(2.0f, sigma_cut));
-    const float r = ceilf(__fmul_rn(kc, __fsqrt_rn(lam)));
-    float fx0 = floorf(__fsub_rn(mx, r)), fx1 = floorf(__fadd_rn(mx, r));
-    float fy0 = floorf(__fsub_rn(my, r)), fy1 = floorf(__fadd_rn(my, r));
+    const float rx = ceilf(__fmul_rn(kc, __fsqrt_rn(sxx)));
+    const float ry = ceilf(__fmul_rn(kc, __fsqrt_rn(syy)));
+    float fx0 = floorf(__fsub_rn(mx, rx)), fx1 = floorf(__fadd_rn(mx, rx));
+    float fy0 = floorf(__fsub_rn(my, ry)), fy1 = floorf(__fadd_rn(my, ry));
     fx0 = fx0 < 0.0f ? 0.0f : fx0;
     fy0 = fy0 < 0.0f ? 0.0f : fy0;
     fx1 = fx1 > (float)(W - 1) ? (float)(W - 1) : fx1;

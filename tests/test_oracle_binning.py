@@ -12,20 +12,19 @@ def one32(mx, my, l1, l2, l3, w=0.7):
     return np.array([[mx], [my], [l1], [l2], [l3], [0.5], [0.5], [0.5], [w]], np.float32)
 
 
-# Hand-worked examples of the rule (radius r = ceil(3 sqrt(lambda_max)) with
-# lambda_max = mid + sqrt(max(0.1, mid^2 - det)), pixel span floor(mu -+ r)
-# clipped to the image, tiles of 16 px):
-#  A: mu=(100.3, 50.7), l=(2,0,2): mid=4, disc=0.1, lam=4.316, 3 sqrt=6.23 -> r=7;
-#     x 93..107 -> tiles 5..6, y 43..57 -> tiles 2..3.
-#  B: mu=(3, 250), l=(1,0,1): lam=1.316, r=4; x -1..7 -> 0..7 -> tile 0;
-#     y 246..254 -> tile 15.
-#  C: mu=(128, 128), l=(4,3,2): Sxx=16, Syy=13, det=64, mid=14.5,
-#     disc=146.25, lam=26.59, 3 sqrt=15.47 -> r=16; 112..144 -> tiles 7..9.
+# Hand-worked examples of the rule (half-extents rx = ceil(3 sqrt(Sxx)),
+# ry = ceil(3 sqrt(Syy)) of the sigma <= 4.5 ellipse, pixel span
+# floor(mu -+ r) clipped to the image, tiles of 16 px):
+#  A: mu=(100.3, 50.7), l=(2,0,2): Sxx=Syy=4 -> rx=ry=6;
+#     x 94..106 -> tiles 5..6, y 44..56 -> tiles 2..3.
+#  B: mu=(3, 250), l=(1,0,1): rx=ry=3; x 0..6 -> tile 0; y 247..253 -> tile 15.
+#  C: mu=(128, 128), l=(4,3,2): Sxx=16 -> rx=12, Syy=13 -> 3 sqrt=10.82 -> ry=11;
+#     x 116..140 -> tiles 7..8, y 117..139 -> tiles 7..8.
 #  D: |w| < 1/255, det <= 1e-8, NaN, entirely left of the image -> culled.
 CASES = [
     (one32(100.3, 50.7, 2, 0, 2), (5, 2, 7, 4), 4),
     (one32(3.0, 250.0, 1, 0, 1), (0, 15, 1, 16), 1),
-    (one32(128.0, 128.0, 4, 3, 2), (7, 7, 10, 10), 9),
+    (one32(128.0, 128.0, 4, 3, 2), (7, 7, 9, 9), 4),
     (one32(50, 50, 2, 0, 2, w=0.001), (0, 0, 0, 0), 0),
     (one32(50, 50, 1e-5, 0, 1e-5), (0, 0, 0, 0), 0),
     (one32(np.nan, 50, 2, 0, 2), (0, 0, 0, 0), 0),
