@@ -41,6 +41,8 @@ __all__ = [
     "SubjectMotion",
     "conferencing_frame",
     "conferencing_gaussians",
+    "background_positions",
+    "block_image",
     "conferencing_sequence",
     "random_motion",
     "clip_table",
@@ -215,6 +217,38 @@ def conferencing_gaussians(frame: np.ndarray, mask: np.ndarray, n: int, seed: in
     yi = np.clip(out[1].astype(np.int64), 0, h - 1)
     out[5:8] = frame[:, yi, xi]
     out[8] = 1.0
+    return out.astype(np.float32)
+
+
+def block_image(bx: int, by: int, b: int, seed: int = 0):
+    """``bx`` x ``by`` blocks of ``b`` x ``b`` constant colours (distinct colours
+    from a 4-level lattice per channel, pairwise distance >= 0.3); returns
+    ``(image[3, by b, bx b] float32, colours[bx by, 3])``."""
+    g = rng(seed)
+    levels = (0.1, 0.4, 0.7, 1.0)
+    lattice = np.array([(r, gg, bb) for r in levels for gg in levels for bb in levels])
+    if bx * by > len(lattice):
+        raise ValueError("at most 64 blocks")
+    cols = lattice[g.permutation(len(lattice))[:bx * by]]
+    img = np.zeros((3, by * b, bx * b), np.float32)
+    for j in range(by):
+        for i in range(bx):
+            img[:, j * b:(j + 1) * b, i * b:(i + 1) * b] = cols[j * bx + i][:, None, None]
+    return img, cols
+
+
+def background_positions(mask: np.ndarray, n: int, seed: int) -> np.ndarray:
+    """``[2, n]`` float32 positions uniform over the pixels outside ``mask``
+    (a uniformly chosen background pixel plus a uniform offset inside it): the
+    random draws of an initialiser's background Gaussians, passed in as input."""
+    g = rng(seed)
+    ys, xs = np.nonzero(~np.asarray(mask, bool))
+    if len(xs) == 0:
+        ys, xs = np.nonzero(np.ones_like(mask, bool))
+    pick = g.integers(0, len(xs), n)
+    out = np.empty((2, n), np.float64)
+    out[0] = xs[pick] + g.uniform(0.0, 1.0, n)
+    out[1] = ys[pick] + g.uniform(0.0, 1.0, n)
     return out.astype(np.float32)
 
 

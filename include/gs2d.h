@@ -173,6 +173,31 @@ gs2d_status gs2d_render_l2(const gs2d_plan* plan, void* ws, const float* params,
 gs2d_status gs2d_adam_step(float* params, const float* grads, float* m, float* v, int64_t count,
                            int32_t step, const uint8_t* mask, const gs2d_config* cfg, void* stream);
 
+/* Device scratch (bytes, 256-byte aligned start) that gs2d_roi_init needs for
+ * a W x H frame and n Gaussians. */
+uint64_t gs2d_roi_init_scratch_bytes(int32_t width, int32_t height, int32_t n);
+
+/* Region-of-interest superpixel initialiser (Sec. 3.2 A: the region is cut
+ * into superpixels by K-means; each segment's centre, covariance and mean
+ * colour give one Gaussian's mean, Cholesky factor and colour).  Readings:
+ * about roi_frac * n segments from seeds on a square grid of step
+ * S = sqrt(A / (roi_frac n)) over the mask (A = mask pixels), 10 K-means
+ * iterations in (r, g, b, x, y) with distance
+ * |dcol|^2 + (0.2 / S)^2 |dxy|^2 among centres within S of the pixel (centres
+ * held within S of their seeds), Sigma = pixel covariance + I/12, weight =
+ * area / (2 pi sqrt(det Sigma)).  The other n - n_roi Gaussians are isotropic
+ * (variance = background area per Gaussian / (2 pi), weight 1, colour of the
+ * frame) at bg_xy (random positions are inputs).
+ * frame: device [3][H][W] float32.  mask: device [H][W] uint8 (non-zero = in
+ * the region).  bg_xy: device [2][n] float32 (row x, row y); the first
+ * n - n_roi columns are used.  params: device, 9n floats out (region
+ * Gaussians first, in seed raster order).  n_roi: host int32 out, may be NULL.
+ * scratch: device, gs2d_roi_init_scratch_bytes bytes.  Synchronises the
+ * stream (seed placement reads the mask on the host). */
+gs2d_status gs2d_roi_init(const float* frame, const uint8_t* mask, int32_t width, int32_t height,
+                          int32_t n, float roi_frac, const float* bg_xy, float* params,
+                          int32_t* n_roi, void* scratch, uint64_t scratch_bytes, void* stream);
+
 /* Fits the plan's n Gaussians to a frame (Sec. 3.2 A: optimise N Gaussians
  * to the frame; I-frames start from an initialiser's output, P-frames from the
  * previous frame's Gaussians).  Runs up to `iters` iterations of

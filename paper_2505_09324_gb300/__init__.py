@@ -7,6 +7,6 @@ the frame-fitting loop are hand-written CUDA kernels in ``libgs2d.so`` behind
 the C ABI of ``include/gs2d.h``; this package is a thin binding over it.
 """
 
-from .raster import GaussianRasterizer, RasterConfig, adam_step  # noqa: F401
+from .raster import GaussianRasterizer, RasterConfig, adam_step, roi_init  # noqa: F401
 
-__all__ = ["GaussianRasterizer", "RasterConfig", "adam_step"]
+__all__ = ["GaussianRasterizer", "RasterConfig", "adam_step", "roi_init"]

@@ -26,6 +26,7 @@ EXPORTS = (
     "gs2d_project", "gs2d_bin_sort", "gs2d_prepare", "gs2d_render_fwd", "gs2d_render_fwd_noalloc",
     "gs2d_render_bwd", "gs2d_render_l2",
     "gs2d_adam_step", "gs2d_encode_frame", "gs2d_read_bins", "gs2d_count_pairs", "gs2d_ws_status",
+    "gs2d_roi_init_scratch_bytes", "gs2d_roi_init",
     "gs2d_last_error",
 )
 
@@ -95,6 +96,9 @@ def load(build_if_missing: bool = False):
             "gs2d_read_bins": (i32, [pp, P, P, P, P, i64, P, P, P]),
             "gs2d_count_pairs": (i32, [pp, P, ctypes.POINTER(i64), ctypes.POINTER(i64), P]),
             "gs2d_ws_status": (i32, [pp, P, i32, P]),
+            "gs2d_roi_init_scratch_bytes": (ctypes.c_uint64, [i32, i32, i32]),
+            "gs2d_roi_init": (i32, [P, P, i32, i32, i32, f32, P, P, ctypes.POINTER(i32), P,
+                                    ctypes.c_uint64, P]),
             "gs2d_last_error": (i32, [ctypes.c_char_p, ctypes.c_size_t]),
         }
         for name, (res, args) in sig.items():

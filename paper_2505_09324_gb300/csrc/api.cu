@@ -199,6 +199,28 @@ gs2d_status gs2d_adam_step(float* params, const float* grads, float* m, float* v
                     "gs2d_adam_step");
 }
 
+uint64_t gs2d_roi_init_scratch_bytes(int32_t width, int32_t height, int32_t n) {
+  if (width < 1 || height < 1 || n < 0) return 0;
+  return roi_init_scratch_bytes(width, height, n);
+}
+
+gs2d_status gs2d_roi_init(const float* frame, const uint8_t* mask, int32_t width, int32_t height,
+                          int32_t n, float roi_frac, const float* bg_xy, float* params,
+                          int32_t* n_roi, void* scratch, uint64_t scratch_bytes, void* stream) {
+  if (width < 1 || height < 1 || width > 65536 || height > 65536 || n < 0 || n > (1 << 28))
+    return fail(GS2D_ERR_INVALID_ARG, "gs2d_roi_init: sizes out of range");
+  if (!(roi_frac >= 0.0f && roi_frac <= 1.0f))
+    return fail(GS2D_ERR_INVALID_ARG, "gs2d_roi_init: roi_frac must be in [0, 1]");
+  if (!frame || !mask || (n > 0 && (!params || !bg_xy)) || !scratch)
+    return fail(GS2D_ERR_INVALID_ARG, "gs2d_roi_init: NULL pointer");
+  if ((uintptr_t)scratch % 256) return fail(GS2D_ERR_INVALID_ARG, "scratch not 256-byte aligned");
+  char msg[256] = "";
+  const gs2d_status st = roi_init(frame, mask, width, height, n, roi_frac, bg_xy, params, n_roi,
+                                  scratch, scratch_bytes, (cudaStream_t)stream, msg, sizeof(msg));
+  if (st != GS2D_OK) return fail(st, "%s", msg);
+  return ok();
+}
+
 static cudaError_t fit_iteration(const gs2d_plan& p, void* ws, const float* target, float* params,
                                  float* m, float* v, cudaStream_t s) {
   cudaError_t e = launch_prepare(p, ws, params, true, s);

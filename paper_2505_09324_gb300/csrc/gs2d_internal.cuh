@@ -167,6 +167,11 @@ cudaError_t launch_count_pairs(const gs2d_plan& p, void* ws, cudaStream_t s);
 cudaError_t launch_prepare(const gs2d_plan& p, void* ws, const float* params, bool adam_tick,
                            cudaStream_t s);
 
+uint64_t roi_init_scratch_bytes(int W, int H, int n);
+gs2d_status roi_init(const float* frame, const uint8_t* mask, int W, int H, int n, float roi_frac,
+                     const float* bg_xy, float* params, int32_t* n_roi, void* scratch,
+                     uint64_t scratch_bytes, cudaStream_t s, char* err, size_t err_len);
+
 // Records msg as the calling thread's last error (gs2d_last_error); returns st.
 gs2d_status set_error(gs2d_status st, const char* msg);
 

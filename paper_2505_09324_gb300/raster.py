@@ -149,6 +149,28 @@ class GaussianRasterizer:
         return {"status": st, "iters": done, "psnr": final, "trace": trace}
 
 
+def roi_init(frame: torch.Tensor, mask: torch.Tensor, n: int, roi_frac: float,
+             bg_xy: torch.Tensor, stream=None):
+    """Region-of-interest superpixel initialiser (gs2d_roi_init).  frame:
+    [3, H, W] float32, mask: [H, W] uint8/bool, bg_xy: [2, n] float32 random
+    background positions.  Returns (params [9, n], n_roi)."""
+    _, h, w = frame.shape
+    f = _check(frame, "frame", (3, h, w))
+    if mask.dtype == torch.bool:
+        mask = mask.to(torch.uint8)
+    mk = _check(mask.contiguous(), "mask", (h, w), dtype=torch.uint8)
+    bg = _check(bg_xy, "bg_xy", (2, n))
+    params = torch.empty((9, n), device=frame.device)
+    nbytes = int(nat.load().gs2d_roi_init_scratch_bytes(w, h, n))
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device=frame.device)
+    n_roi = nat.ctypes.c_int32(0)
+    nat.check(nat.load().gs2d_roi_init(
+        nat._p(f), nat._p(mk), w, h, n, float(roi_frac), nat._p(bg), nat._p(params.data_ptr()),
+        nat.ctypes.byref(n_roi), nat._p(scratch.data_ptr()), nbytes, nat._p(_stream(stream))),
+        "gs2d_roi_init")
+    return params, int(n_roi.value)
+
+
 def adam_step(params: torch.Tensor, grads: torch.Tensor, m: torch.Tensor, v: torch.Tensor,
               step: int, mask: torch.Tensor | None = None, config: RasterConfig | None = None,
               stream=None):
