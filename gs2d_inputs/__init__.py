@@ -75,16 +75,19 @@ def random_gaussians(n: int, width: int, height: int, seed: int,
 def _plane_wave_sum(width, height, kx, ky, phase, amp):
     """sum_j amp_j * sin(kx_j * x + ky_j * y + phase_j) at pixel centres.
 
-    Evaluated separably: sin(a + b) = sin a cos b + cos a sin b.
+    Evaluated separably as one matrix product: with
+    sin(a + b) = sin a cos b + cos a sin b, the sum is
+    [cos B | sin B] (H x 2J) times [amp sin A ; amp cos A] (2J x W).
     """
     xs = np.arange(width, dtype=np.float64) + 0.5
     ys = np.arange(height, dtype=np.float64) + 0.5
-    out = np.zeros((height, width), dtype=np.float64)
-    for j in range(len(kx)):
-        a = kx[j] * xs
-        b = ky[j] * ys + phase[j]
-        out += amp[j] * (np.outer(np.cos(b), np.sin(a)) + np.outer(np.sin(b), np.cos(a)))
-    return out
+    kx, ky = np.asarray(kx, np.float64), np.asarray(ky, np.float64)
+    amp, phase = np.asarray(amp, np.float64), np.asarray(phase, np.float64)
+    A = np.outer(kx, xs)                       # [J, W]
+    B = np.outer(ys, ky) + phase[None, :]      # [H, J]
+    left = np.concatenate([np.cos(B), np.sin(B)], axis=1)                        # [H, 2J]
+    right = np.concatenate([amp[:, None] * np.sin(A), amp[:, None] * np.cos(A)])  # [2J, W]
+    return left @ right
 
 
 def smooth_noise_target(width: int, height: int, seed: int, terms: int = 16,

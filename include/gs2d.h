@@ -54,30 +54,61 @@ typedef enum {
 } gs2d_status;
 
 /* Rasterizer and optimiser constants.  The paper fixes none of them; these
- * are the project's readings (gs2d_config_default): tile 16, sigma_cut 4.5 (the
- * 3-sigma ellipse), alpha_min 1/255, det_eps 1e-8, Adam lr 1e-2, betas
- * (0.9, 0.999), eps 1e-8. */
+ * are the project's readings (gs2d_config_default): tile 16, stage 64,
+ * launch GS2D_LAUNCH_GRID,
+ * sigma_cut 4.5 (the 3-sigma ellipse), alpha_min 1/255, det_eps 1e-8, Adam
+ * lr 1e-2, betas (0.9, 0.999), eps 1e-8.  Tile, stage and launch change only the
+ * schedule (which pixels and Gaussians a thread block handles together), never
+ * a result: the image, loss and gradients are identical for every choice up to
+ * the order of FP32 additions inside a tile (tests hold each against the same
+ * oracle). */
 typedef struct {
-  int32_t tile;      /* tile edge in pixels; 16 is the supported value */
+  int32_t tile;      /* tile edge in pixels: 8, 16 or 32 */
   float sigma_cut;   /* sigma cut-off, > 0 */
   float alpha_min;   /* minimum |w| exp(-sigma), > 0 */
   float det_eps;     /* minimum det Sigma, >= 0 */
   float lr, beta1, beta2, eps; /* Adam */
+  int32_t stage;     /* Gaussians staged per shared-memory batch: 32, 64 or 128
+                        (0 means 64) */
+  int32_t launch;    /* render launch form: GS2D_LAUNCH_PERSISTENT (one wave of
+                        blocks taking tiles from a queue) or GS2D_LAUNCH_GRID
+                        (one block per tile, in queue order) */
 } gs2d_config;
 
-/* Host-side plan: image size, Gaussian count, capacity and the workspace
- * layout.  Filled by gs2d_plan_init; treat as read-only afterwards. */
+enum { GS2D_LAUNCH_PERSISTENT = 0, GS2D_LAUNCH_GRID = 1 };
+
+/* One clip of a batch: a W x H frame fitted by n Gaussians.  The caller sets
+ * width, height and n; gs2d_plan_init_batch fills the rest.  A batch stores
+ * the clips' parameters side by side (clip c owns columns [g_off, g_off + n) of
+ * every parameter row of the batch's 9 x n_total array) and their images one
+ * after another (clip c's planar [3][H][W] image starts pix_off floats into the
+ * batch's image buffer). */
 typedef struct {
   int32_t width, height, n;
-  int32_t tile, tiles_x, tiles_y, num_tiles;
-  int32_t tile_bits;   /* bits of a tile id (radix-sort key width) */
-  int32_t sort_passes; /* 8-bit digit passes over tile_bits */
-  int32_t sort_blocks; /* CTAs of each radix pass */
-  int64_t max_entries; /* capacity for (tile, Gaussian) pairs */
+  int32_t tiles_x, tiles_y;
+  int32_t g_off;     /* first Gaussian (column) of the clip */
+  int32_t tile_off;  /* first tile of the clip in the batch's tile numbering */
+  int32_t reserved;
+  int64_t pix_off;   /* first float of the clip's image */
+} gs2d_clip;
+
+/* Host-side plan: image size(s), Gaussian count, capacity and the workspace
+ * layout.  Filled by gs2d_plan_init (one frame) or gs2d_plan_init_batch;
+ * treat as read-only afterwards. */
+typedef struct {
+  int32_t width, height; /* the frame of a one-clip plan; 0, 0 for several clips */
+  int32_t n;             /* Gaussians (all clips) */
+  int32_t tile, tiles_x, tiles_y; /* tile edge; tile grid of a one-clip plan */
+  int32_t num_tiles;     /* tiles of all clips */
+  int32_t tile_bits;     /* bits of a tile id */
+  int32_t num_clips;     /* 1 for gs2d_plan_init */
+  int32_t stage;         /* Gaussians per shared-memory batch of the render */
+  int64_t max_entries;   /* capacity for (tile, Gaussian) pairs */
+  int64_t pixels;        /* sum of W H over the clips */
   gs2d_config cfg;
-  uint64_t ws_bytes;   /* device workspace size the caller must allocate */
-  uint64_t off[20];    /* internal: byte offsets of workspace sections */
-  uint64_t magic;      /* internal: set by gs2d_plan_init */
+  uint64_t ws_bytes;     /* device workspace size the caller must allocate */
+  uint64_t off[24];      /* internal: byte offsets of workspace sections */
+  uint64_t magic;        /* internal: set by the plan_init calls */
 } gs2d_plan;
 
 /* Fills *cfg with the defaults listed above. */
@@ -89,11 +120,32 @@ size_t gs2d_sizeof_plan(void);
 size_t gs2d_sizeof_config(void);
 
 /* Lays out a workspace for a W x H frame and n Gaussians with room for
- * max_entries (tile, Gaussian) pairs (0 picks max(2^20, 16 n)).
+ * max_entries (tile, Gaussian) pairs (0 picks max(2^20, 16 n), 64 n for tile 8).
  * cfg may be NULL (defaults).  Host only; no CUDA call.
- * Errors: W, H < 1, n < 0, tile != 16, non-positive constants. */
+ * Errors: W, H < 1, n < 0, tile not 8, 16 or 32, stage not 0, 32, 64 or 128,
+ * unknown launch form, non-positive constants. */
 gs2d_status gs2d_plan_init(gs2d_plan* plan, int32_t width, int32_t height, int32_t n,
                            int64_t max_entries, const gs2d_config* cfg);
+
+/* Lays out one workspace for a batch of independent clips (frames of
+ * different sizes and Gaussian counts fitted together: every step of the path
+ * runs once over all clips, each clip keeping its own loss).  clips: host
+ * array of num_clips (1 ... 65536) entries whose width, height and n the caller
+ * set; the call fills their other fields.  max_entries 0 picks
+ * max(2^20, 16 n_total), 64 n_total for tile 8.  Host only; no CUDA call.  After
+ * zero-filling the workspace, the caller uploads the clip table once with
+ * gs2d_ws_set_clips.  Every call taking a plan accepts a batch plan, with
+ * images in the batch layout of gs2d_clip; gs2d_render_l2's loss is then the
+ * sum over clips of each clip's mean squared error (so each clip's gradient is
+ * that of its own loss). */
+gs2d_status gs2d_plan_init_batch(gs2d_plan* plan, gs2d_clip* clips, int32_t num_clips,
+                                 int64_t max_entries, const gs2d_config* cfg);
+
+/* Copies the clip table of a batch plan (host, as filled by
+ * gs2d_plan_init_batch) into the workspace.  Synchronises the stream.  A
+ * one-clip plan from gs2d_plan_init needs no table. */
+gs2d_status gs2d_ws_set_clips(const gs2d_plan* plan, void* ws, const gs2d_clip* clips,
+                              void* stream);
 
 /* Projection (Sec. 3: the per-Gaussian step of tile-based rasterization).
  * Reads params (device, 9n floats) and writes, into ws, each Gaussian's
@@ -103,20 +155,23 @@ gs2d_status gs2d_plan_init(gs2d_plan* plan, int32_t width, int32_t height, int32
 gs2d_status gs2d_project(const gs2d_plan* plan, void* ws, const float* params, void* stream);
 
 /* Binning and sort (Sec. 3 tile-based rasterization; 2D has no depth, so the
- * order inside a tile is the Gaussian index): exclusive scan of the tile
- * counts, emission of one (tile, n) entry per covered tile, a stable LSD radix
- * sort by tile id, and per-tile ranges [start, end) into the sorted list.
- * Needs gs2d_project on the same ws first.  If the entries exceed
+ * order inside a tile is the Gaussian index): per-tile entry counts, exclusive
+ * scans (per-Gaussian offsets and per-tile ranges [start, end) into the sorted
+ * list), one (tile, n) entry per covered tile placed in its tile's range, and
+ * a per-tile sort by Gaussian index -- the (tile, index) key order.  Also
+ * orders the tiles by list length (longest first) for the render's work
+ * queue.  Needs gs2d_project on the same ws first.  If the entries exceed
  * max_entries, the status word is set to GS2D_ERR_CAPACITY and the sorted list
  * is empty (renders then produce zero). */
 gs2d_status gs2d_bin_sort(const gs2d_plan* plan, void* ws, void* stream);
 
-/* gs2d_project followed by gs2d_bin_sort, with the same results, in as few
- * launches as the device allows (one thread-block cluster launch on GB300). */
+/* gs2d_project followed by gs2d_bin_sort, with the same results, with the
+ * projection and the tile counts fused into one launch. */
 gs2d_status gs2d_prepare(const gs2d_plan* plan, void* ws, const float* params, void* stream);
 
 /* Forward render, Eq. 2.  img: device [3][H][W] output (every pixel written).
- * Needs gs2d_bin_sort first. */
+ * Needs gs2d_bin_sort first.  The render kernels are persistent: one wave of
+ * thread blocks takes tiles from a queue in the order of gs2d_bin_sort. */
 gs2d_status gs2d_render_fwd(const gs2d_plan* plan, void* ws, float* img, void* stream);
 
 /* Forward render that allocates nothing (the paper has no counterpart; this
@@ -154,7 +209,7 @@ gs2d_status gs2d_render_bwd(const gs2d_plan* plan, void* ws, const float* params
                             const float* dimg, float* grads, void* stream);
 
 /* Fused forward + L2 loss + backward for fitting: L = mean over 3HW of
- * (C - target)^2.  target: device [3][H][W].  grads: device 9n floats
+ * (C - target)^2 (a batch plan: the sum of that over the clips).  target: device [3][H][W].  grads: device 9n floats
  * (dL/dparams).  img: device [3][H][W] or NULL (the rendered image is then not
  * stored).  loss: device, 2 floats or NULL: {L, mean squared error of C
  * clamped to [0, 1]} (the latter gives PSNR = -10 log10).  Needs
@@ -184,10 +239,11 @@ uint64_t gs2d_roi_init_scratch_bytes(int32_t width, int32_t height, int32_t n);
  * S = sqrt(A / (roi_frac n)) over the mask (A = mask pixels), 10 K-means
  * iterations in (r, g, b, x, y) with distance
  * |dcol|^2 + (0.2 / S)^2 |dxy|^2 among centres within S of the pixel (centres
- * held within S of their seeds), Sigma = pixel covariance + I/12, weight =
+ * held within S of their seeds), Sigma = 4 (pixel covariance + I/12) (the
+ * factor 4 keeps the additive blend of the segments flat), weight =
  * area / (2 pi sqrt(det Sigma)).  The other n - n_roi Gaussians are isotropic
- * (variance = background area per Gaussian / (2 pi), weight 1, colour of the
- * frame) at bg_xy (random positions are inputs).
+ * (variance = 4 x background area per Gaussian / (2 pi), weight 1/4, colour
+ * of the frame) at bg_xy (random positions are inputs).
  * frame: device [3][H][W] float32.  mask: device [H][W] uint8 (non-zero = in
  * the region).  bg_xy: device [2][n] float32 (row x, row y); the first
  * n - n_roi columns are used.  params: device, 9n floats out (region
@@ -216,6 +272,47 @@ gs2d_status gs2d_encode_frame(const gs2d_plan* plan, void* ws, const float* targ
                               float* adam_m, float* adam_v, int32_t iters, float target_psnr,
                               int32_t check_every, float* psnr_trace, int32_t* iters_done,
                               float* final_psnr, void* stream);
+
+/* Per-clip losses of the last gs2d_render_l2 on this workspace: out (host,
+ * 2 num_clips floats) gets, per clip,
+ * {mean squared error, mean squared error of the render clamped to [0, 1]}.
+ * Synchronises the stream. */
+gs2d_status gs2d_clip_losses(const gs2d_plan* plan, void* ws, float* out, void* stream);
+
+/* Fits every clip of a batch plan for `iters` iterations (Sec. 3.2 A applied
+ * to many independent frames at once: one launch per step of the path covers
+ * all clips), replayed as one captured CUDA graph.  Each clip's Gaussians get
+ * exactly the updates a gs2d_encode_frame of that clip alone would give them.
+ * targets: device, the batch image layout.  params, adam_m, adam_v: device
+ * 9 n_total floats each (moments zeroed by this call).  clip_psnr: host,
+ * num_clips floats or NULL: PSNR of each clip's fitted Gaussians (one more
+ * evaluation after the last update).  Synchronises the stream. */
+gs2d_status gs2d_encode_batch(const gs2d_plan* plan, void* ws, const float* targets,
+                              float* params, float* adam_m, float* adam_v, int32_t iters,
+                              float* clip_psnr, void* stream);
+
+/* Autotuner of the render schedule: times one fit iteration (projection,
+ * binning, fused render + L2 + backward, reduction) of the given batch for
+ * every (tile, stage, launch) candidate and reports the fastest.  clips:
+ * host, widths, heights and n set (the other fields are overwritten).
+ * params: device 9 n_total floats; targets: device, batch image layout.
+ * tiles, stages, launches: host candidate lists (tile 8, 16 or 32; stage 32,
+ * 64 or 128; launch GS2D_LAUNCH_*).  ws: device scratch of
+ * gs2d_autotune_ws_bytes bytes (contents are overwritten).  reps timed
+ * iterations per candidate after two warm-up iterations.  ms: host,
+ * num_tiles_c x num_stages x num_launches floats out (row-major: tile, then
+ * stage, then launch; -1 if the candidate overflowed max_entries).
+ * best_tile, best_stage, best_launch: host out.  params are not modified.
+ * Synchronises the stream. */
+uint64_t gs2d_autotune_ws_bytes(const gs2d_clip* clips, int32_t num_clips, int64_t max_entries,
+                                const gs2d_config* cfg, const int32_t* tiles,
+                                int32_t num_tiles_c);
+gs2d_status gs2d_autotune(gs2d_clip* clips, int32_t num_clips, int64_t max_entries,
+                          const gs2d_config* cfg, const float* params, const float* targets,
+                          void* ws, uint64_t ws_bytes, const int32_t* tiles, int32_t num_tiles_c,
+                          const int32_t* stages, int32_t num_stages, const int32_t* launches,
+                          int32_t num_launches, int32_t reps, float* ms, int32_t* best_tile,
+                          int32_t* best_stage, int32_t* best_launch, void* stream);
 
 /* Copies the sorted list state to host memory for inspection (tests and
  * tools): n_entries (host, int64), keys (host, may be NULL: tile ids of the

@@ -7,6 +7,8 @@ the frame-fitting loop are hand-written CUDA kernels in ``libgs2d.so`` behind
 the C ABI of ``include/gs2d.h``; this package is a thin binding over it.
 """
 
-from .raster import GaussianRasterizer, RasterConfig, adam_step, roi_init  # noqa: F401
+from .raster import (BatchRasterizer, GaussianRasterizer, RasterConfig, adam_step,  # noqa: F401
+                     autotune, roi_init)
 
-__all__ = ["GaussianRasterizer", "RasterConfig", "adam_step", "roi_init"]
+__all__ = ["BatchRasterizer", "GaussianRasterizer", "RasterConfig", "adam_step", "autotune",
+           "roi_init"]

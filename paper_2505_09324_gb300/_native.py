@@ -23,9 +23,12 @@ STATUS_NAMES = {0: "GS2D_OK", 1: "GS2D_ERR_INVALID_ARG", 2: "GS2D_ERR_CUDA",
 # every function declared in include/gs2d.h
 EXPORTS = (
     "gs2d_config_default", "gs2d_sizeof_plan", "gs2d_sizeof_config", "gs2d_plan_init",
+    "gs2d_plan_init_batch", "gs2d_ws_set_clips",
     "gs2d_project", "gs2d_bin_sort", "gs2d_prepare", "gs2d_render_fwd", "gs2d_render_fwd_noalloc",
     "gs2d_render_bwd", "gs2d_render_l2",
-    "gs2d_adam_step", "gs2d_encode_frame", "gs2d_read_bins", "gs2d_count_pairs", "gs2d_ws_status",
+    "gs2d_adam_step", "gs2d_encode_frame", "gs2d_clip_losses", "gs2d_encode_batch",
+    "gs2d_autotune_ws_bytes", "gs2d_autotune",
+    "gs2d_read_bins", "gs2d_count_pairs", "gs2d_ws_status",
     "gs2d_roi_init_scratch_bytes", "gs2d_roi_init",
     "gs2d_last_error",
 )
@@ -41,16 +44,28 @@ class Config(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("sigma_cut", ctypes.c_float),
                 ("alpha_min", ctypes.c_float), ("det_eps", ctypes.c_float),
                 ("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
-                ("eps", ctypes.c_float)]
+                ("eps", ctypes.c_float), ("stage", ctypes.c_int32), ("launch", ctypes.c_int32)]
+
+
+LAUNCH_PERSISTENT = 0
+LAUNCH_GRID = 1
+
+
+class Clip(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("n", ctypes.c_int32),
+                ("tiles_x", ctypes.c_int32), ("tiles_y", ctypes.c_int32),
+                ("g_off", ctypes.c_int32), ("tile_off", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("pix_off", ctypes.c_int64)]
 
 
 class Plan(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("n", ctypes.c_int32),
                 ("tile", ctypes.c_int32), ("tiles_x", ctypes.c_int32),
                 ("tiles_y", ctypes.c_int32), ("num_tiles", ctypes.c_int32),
-                ("tile_bits", ctypes.c_int32), ("sort_passes", ctypes.c_int32),
-                ("sort_blocks", ctypes.c_int32), ("max_entries", ctypes.c_int64),
-                ("cfg", Config), ("ws_bytes", ctypes.c_uint64), ("off", ctypes.c_uint64 * 20),
+                ("tile_bits", ctypes.c_int32), ("num_clips", ctypes.c_int32),
+                ("stage", ctypes.c_int32), ("max_entries", ctypes.c_int64),
+                ("pixels", ctypes.c_int64),
+                ("cfg", Config), ("ws_bytes", ctypes.c_uint64), ("off", ctypes.c_uint64 * 24),
                 ("magic", ctypes.c_uint64)]
 
 
@@ -78,11 +93,21 @@ def load(build_if_missing: bool = False):
         lib = ctypes.CDLL(path)
         P, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
         pp = ctypes.POINTER(Plan)
+        pc = ctypes.POINTER(Clip)
+        pcfg = ctypes.POINTER(Config)
         sig = {
             "gs2d_config_default": (None, [ctypes.POINTER(Config)]),
             "gs2d_sizeof_plan": (ctypes.c_size_t, []),
             "gs2d_sizeof_config": (ctypes.c_size_t, []),
             "gs2d_plan_init": (i32, [pp, i32, i32, i32, i64, ctypes.POINTER(Config)]),
+            "gs2d_plan_init_batch": (i32, [pp, pc, i32, i64, pcfg]),
+            "gs2d_ws_set_clips": (i32, [pp, P, pc, P]),
+            "gs2d_clip_losses": (i32, [pp, P, P, P]),
+            "gs2d_encode_batch": (i32, [pp, P, P, P, P, P, i32, P, P]),
+            "gs2d_autotune_ws_bytes": (ctypes.c_uint64, [pc, i32, i64, pcfg, P, i32]),
+            "gs2d_autotune": (i32, [pc, i32, i64, pcfg, P, P, P, ctypes.c_uint64, P, i32, P, i32,
+                                    P, i32, i32, P, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                    ctypes.POINTER(i32), P]),
             "gs2d_project": (i32, [pp, P, P, P]),
             "gs2d_bin_sort": (i32, [pp, P, P]),
             "gs2d_prepare": (i32, [pp, P, P, P]),
@@ -137,6 +162,75 @@ def plan_init(width: int, height: int, n: int, max_entries: int = 0,
     check(load().gs2d_plan_init(ctypes.byref(p), width, height, n, max_entries, cfg),
           "gs2d_plan_init")
     return p
+
+
+def plan_init_batch(sizes, max_entries: int = 0, config: Config | None = None):
+    """sizes: sequence of (width, height, n).  Returns (plan, clips array)."""
+    clips = (Clip * len(sizes))()
+    for k, (w, h, n) in enumerate(sizes):
+        clips[k].width, clips[k].height, clips[k].n = int(w), int(h), int(n)
+    p = Plan()
+    cfg = ctypes.byref(config) if config is not None else None
+    check(load().gs2d_plan_init_batch(ctypes.byref(p), clips, len(sizes), max_entries, cfg),
+          "gs2d_plan_init_batch")
+    return p, clips
+
+
+def ws_set_clips(plan: Plan, ws: int, clips, stream: int):
+    check(load().gs2d_ws_set_clips(ctypes.byref(plan), _p(ws), clips, _p(stream)),
+          "gs2d_ws_set_clips")
+
+
+def clip_losses(plan: Plan, ws: int, stream: int):
+    """[(mse, clamped mse)] per clip of the last render_l2."""
+    out = (ctypes.c_float * (2 * plan.num_clips))()
+    check(load().gs2d_clip_losses(ctypes.byref(plan), _p(ws), out, _p(stream)),
+          "gs2d_clip_losses")
+    return [(out[2 * k], out[2 * k + 1]) for k in range(plan.num_clips)]
+
+
+def encode_batch(plan: Plan, ws: int, targets: int, params: int, m: int, v: int, iters: int,
+                 stream: int):
+    """Returns the per-clip PSNR list after `iters` iterations."""
+    out = (ctypes.c_float * plan.num_clips)()
+    check(load().gs2d_encode_batch(ctypes.byref(plan), _p(ws), _p(targets), _p(params), _p(m),
+                                   _p(v), iters, out, _p(stream)), "gs2d_encode_batch")
+    return [out[k] for k in range(plan.num_clips)]
+
+
+def autotune_ws_bytes(sizes, tiles, max_entries: int = 0, config: Config | None = None) -> int:
+    clips = (Clip * len(sizes))()
+    for k, (w, h, n) in enumerate(sizes):
+        clips[k].width, clips[k].height, clips[k].n = int(w), int(h), int(n)
+    t = (ctypes.c_int32 * len(tiles))(*tiles)
+    cfg = ctypes.byref(config) if config is not None else None
+    return int(load().gs2d_autotune_ws_bytes(clips, len(sizes), max_entries, cfg, t, len(tiles)))
+
+
+def autotune(sizes, params: int, targets: int, ws: int, ws_bytes: int, tiles, stages, launches,
+             reps: int, stream: int, max_entries: int = 0, config: Config | None = None):
+    """Returns ({(tile, stage, launch): ms}, best_tile, best_stage, best_launch)."""
+    clips = (Clip * len(sizes))()
+    for k, (w, h, n) in enumerate(sizes):
+        clips[k].width, clips[k].height, clips[k].n = int(w), int(h), int(n)
+    t = (ctypes.c_int32 * len(tiles))(*tiles)
+    st = (ctypes.c_int32 * len(stages))(*stages)
+    la = (ctypes.c_int32 * len(launches))(*launches)
+    ms = (ctypes.c_float * (len(tiles) * len(stages) * len(launches)))()
+    bt, bs, bl = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    cfg = ctypes.byref(config) if config is not None else None
+    check(load().gs2d_autotune(clips, len(sizes), max_entries, cfg, _p(params), _p(targets),
+                               _p(ws), ws_bytes, t, len(tiles), st, len(stages), la,
+                               len(launches), reps, ms, ctypes.byref(bt), ctypes.byref(bs),
+                               ctypes.byref(bl), _p(stream)), "gs2d_autotune")
+    table = {}
+    k = 0
+    for a in tiles:
+        for b in stages:
+            for c in launches:
+                table[(a, b, c)] = ms[k]
+                k += 1
+    return table, bt.value, bs.value, bl.value
 
 
 def _p(x):

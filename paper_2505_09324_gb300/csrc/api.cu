@@ -44,7 +44,9 @@ gs2d_status check_plan(const gs2d_plan* p, const void* ws) {
 }
 
 bool cfg_valid(const gs2d_config& c) {
-  return c.tile == kTile && c.sigma_cut > 0.0f && isfinite(c.sigma_cut) && c.alpha_min > 0.0f &&
+  return (c.tile == 8 || c.tile == 16 || c.tile == 32) &&
+         (c.stage == 0 || c.stage == 32 || c.stage == 64 || c.stage == 128) &&
+         (c.launch == GS2D_LAUNCH_PERSISTENT || c.launch == GS2D_LAUNCH_GRID) && c.sigma_cut > 0.0f && isfinite(c.sigma_cut) && c.alpha_min > 0.0f &&
          isfinite(c.alpha_min) && c.det_eps >= 0.0f && isfinite(c.det_eps) && c.lr > 0.0f &&
          isfinite(c.lr) && c.beta1 >= 0.0f && c.beta1 < 1.0f && c.beta2 >= 0.0f &&
          c.beta2 < 1.0f && c.eps > 0.0f && isfinite(c.eps);
@@ -63,7 +65,7 @@ extern "C" {
 
 void gs2d_config_default(gs2d_config* cfg) {
   if (!cfg) return;
-  cfg->tile = kTile;
+  cfg->tile = kTileDefault;
   cfg->sigma_cut = 4.5f;
   cfg->alpha_min = 1.0f / 255.0f;
   cfg->det_eps = 1e-8f;
@@ -71,6 +73,8 @@ void gs2d_config_default(gs2d_config* cfg) {
   cfg->beta1 = 0.9f;
   cfg->beta2 = 0.999f;
   cfg->eps = 1e-8f;
+  cfg->stage = kStageDefault;
+  cfg->launch = GS2D_LAUNCH_GRID;
 }
 
 size_t gs2d_sizeof_plan(void) { return sizeof(gs2d_plan); }
@@ -79,35 +83,71 @@ size_t gs2d_sizeof_config(void) { return sizeof(gs2d_config); }
 gs2d_status gs2d_plan_init(gs2d_plan* plan, int32_t width, int32_t height, int32_t n,
                            int64_t max_entries, const gs2d_config* cfg) {
   if (!plan) return fail(GS2D_ERR_INVALID_ARG, "plan is NULL");
+  gs2d_clip clip;
+  memset(&clip, 0, sizeof(clip));
+  clip.width = width;
+  clip.height = height;
+  clip.n = n;
+  return gs2d_plan_init_batch(plan, &clip, 1, max_entries, cfg);
+}
+
+gs2d_status gs2d_plan_init_batch(gs2d_plan* plan, gs2d_clip* clips, int32_t num_clips,
+                                 int64_t max_entries, const gs2d_config* cfg) {
+  if (!plan) return fail(GS2D_ERR_INVALID_ARG, "plan is NULL");
   memset(plan, 0, sizeof(*plan));
+  if (!clips || num_clips < 1 || num_clips > 65536)
+    return fail(GS2D_ERR_INVALID_ARG, "num_clips = %d out of range (or clips is NULL)", num_clips);
   gs2d_config c;
   gs2d_config_default(&c);
   if (cfg) c = *cfg;
-  if (!cfg_valid(c)) return fail(GS2D_ERR_INVALID_ARG, "invalid config (tile must be 16)");
-  if (width < 1 || height < 1 || width > 65536 || height > 65536)
-    return fail(GS2D_ERR_INVALID_ARG, "image size %d x %d out of range", width, height);
-  if (n < 0 || n > (1 << 28)) return fail(GS2D_ERR_INVALID_ARG, "n = %d out of range", n);
-  if (max_entries == 0) max_entries = std::max<int64_t>(1 << 20, 16 * (int64_t)n);
+  if (!cfg_valid(c))
+    return fail(GS2D_ERR_INVALID_ARG, "invalid config (tile 8, 16 or 32; stage 0, 32, 64 or 128)");
+  if (c.stage == 0) c.stage = kStageDefault;
+  const int T = c.tile;
+  int64_t n_total = 0, tiles = 0, pixels = 0;
+  for (int k = 0; k < num_clips; k++) {
+    gs2d_clip& cl = clips[k];
+    if (cl.width < 1 || cl.height < 1 || cl.width > 65536 || cl.height > 65536)
+      return fail(GS2D_ERR_INVALID_ARG, "clip %d: image size %d x %d out of range", k, cl.width,
+                  cl.height);
+    if (cl.n < 0) return fail(GS2D_ERR_INVALID_ARG, "clip %d: n = %d < 0", k, cl.n);
+    cl.tiles_x = (cl.width + T - 1) / T;
+    cl.tiles_y = (cl.height + T - 1) / T;
+    cl.g_off = (int32_t)n_total;
+    cl.tile_off = (int32_t)tiles;
+    cl.reserved = 0;
+    cl.pix_off = 3 * pixels;
+    n_total += cl.n;
+    tiles += (int64_t)cl.tiles_x * cl.tiles_y;
+    pixels += (int64_t)cl.width * cl.height;
+    if (n_total > (1 << 28) || tiles > (1 << 28))
+      return fail(GS2D_ERR_INVALID_ARG, "batch too large (%lld Gaussians, %lld tiles)",
+                  (long long)n_total, (long long)tiles);
+  }
+  if (max_entries == 0)
+    max_entries = std::max<int64_t>(1 << 20, 16 * n_total * (T == 8 ? 4 : 1));
   if (max_entries < 1 || max_entries > (int64_t(1) << 30))
     return fail(GS2D_ERR_INVALID_ARG, "max_entries = %lld out of range", (long long)max_entries);
-  const int tx = (width + kTile - 1) / kTile, ty = (height + kTile - 1) / kTile;
-  plan->width = width;
-  plan->height = height;
-  plan->n = n;
-  plan->tile = kTile;
-  plan->tiles_x = tx;
-  plan->tiles_y = ty;
-  plan->num_tiles = tx * ty;
+  // a one-clip plan is a single frame: its kernels take the clip from these
+  plan->width = num_clips == 1 ? clips[0].width : 0;
+  plan->height = num_clips == 1 ? clips[0].height : 0;
+  plan->n = (int32_t)n_total;
+  plan->tile = T;
+  plan->tiles_x = num_clips == 1 ? clips[0].tiles_x : 0;
+  plan->tiles_y = num_clips == 1 ? clips[0].tiles_y : 0;
+  plan->num_tiles = (int32_t)tiles;
   int bits = 0;
-  while ((int64_t(1) << bits) < plan->num_tiles) bits++;
+  while ((int64_t(1) << bits) < tiles) bits++;
   plan->tile_bits = bits;
-  plan->sort_passes = 1;  // one counting pass over the whole tile id
-  plan->sort_blocks = 0;
+  plan->num_clips = num_clips;
+  plan->stage = c.stage;
   plan->max_entries = max_entries;
+  plan->pixels = pixels;
   plan->cfg = c;
-  const uint64_t nn = (uint64_t)n, me = (uint64_t)max_entries, nt = (uint64_t)plan->num_tiles;
+  const uint64_t nn = (uint64_t)n_total, me = (uint64_t)max_entries, nt = (uint64_t)tiles;
   uint64_t sz[kNumSections];
   sz[kOffHeader] = sizeof(WsHeader);
+  sz[kOffClips] = (uint64_t)num_clips * sizeof(gs2d_clip);
   sz[kOffRec] = 3 * nn * sizeof(float4);
   sz[kOffRect] = nn * sizeof(int4);
   sz[kOffCount] = (nn + 1) * sizeof(int);
@@ -117,17 +157,47 @@ gs2d_status gs2d_plan_init(gs2d_plan* plan, int32_t width, int32_t height, int32
   sz[kOffLong] = (nt + 1) * sizeof(int);
   sz[kOffList] = me * sizeof(uint32_t);
   sz[kOffRanges] = nt * sizeof(int2);
+  sz[kOffOrder] = nt * sizeof(int);
+  sz[kOffRank] = nt * sizeof(uint32_t);
+  sz[kOffBucket] = 2 * kBuckets * sizeof(int);
   sz[kOffPartial] = me * kPartials * sizeof(float);
   sz[kOffLossPart] = nt * sizeof(float2);
+  sz[kOffClipLoss] = (uint64_t)num_clips * sizeof(float2);
   sz[kOffGrad] = 9 * nn * sizeof(float);
   uint64_t off = 0;
-  for (int s = 0; s < kNumSections; s++) {
-    plan->off[s] = off;
-    off = align256(off + sz[s]);
+  for (int sec = 0; sec < kNumSections; sec++) {
+    plan->off[sec] = off;
+    off = align256(off + sz[sec]);
   }
   plan->ws_bytes = off;
   plan->magic = kPlanMagic;
   return ok();
+}
+
+gs2d_status gs2d_ws_set_clips(const gs2d_plan* plan, void* ws, const gs2d_clip* clips,
+                              void* stream) {
+  gs2d_status st = check_plan(plan, ws);
+  if (st) return st;
+  if (!clips) return fail(GS2D_ERR_INVALID_ARG, "clips is NULL");
+  // the table must be the one this plan was laid out from
+  int64_t tiles = 0, n = 0;
+  for (int k = 0; k < plan->num_clips; k++) {
+    const gs2d_clip& cl = clips[k];
+    if (cl.tile_off != tiles || cl.g_off != n ||
+        cl.tiles_x != (cl.width + plan->tile - 1) / plan->tile ||
+        cl.tiles_y != (cl.height + plan->tile - 1) / plan->tile)
+      return fail(GS2D_ERR_INVALID_ARG, "clip %d does not match the plan", k);
+    tiles += (int64_t)cl.tiles_x * cl.tiles_y;
+    n += cl.n;
+  }
+  if (tiles != plan->num_tiles || n != plan->n)
+    return fail(GS2D_ERR_INVALID_ARG, "clip table does not match the plan");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(ws_ptr<gs2d_clip>(ws, *plan, kOffClips), clips,
+                                  (size_t)plan->num_clips * sizeof(gs2d_clip),
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return cuda_check(e, "gs2d_ws_set_clips");
 }
 
 gs2d_status gs2d_project(const gs2d_plan* plan, void* ws, const float* params, void* stream) {
@@ -228,6 +298,39 @@ static cudaError_t fit_iteration(const gs2d_plan& p, void* ws, const float* targ
   return e;
 }
 
+// Zeroes the Adam moments and the workspace header (step counter, status,
+// render queue): the optimiser restarts for every frame.
+static cudaError_t reset_fit(const gs2d_plan& p, void* ws, float* m, float* v, cudaStream_t s) {
+  const size_t pbytes = (size_t)9 * p.n * sizeof(float);
+  cudaError_t e = cudaSuccess;
+  if (pbytes) e = cudaMemsetAsync(m, 0, pbytes, s);
+  if (e == cudaSuccess && pbytes) e = cudaMemsetAsync(v, 0, pbytes, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws_ptr<WsHeader>(ws, p, kOffHeader), 0, sizeof(WsHeader), s);
+  return e;
+}
+
+// One fit iteration captured as a CUDA graph (non-default streams), or NULL:
+// the caller then launches the iterations directly.
+static cudaGraphExec_t capture_fit(const gs2d_plan& p, void* ws, const float* target,
+                                   float* params, float* m, float* v, int iters, cudaStream_t s) {
+  cudaGraphExec_t exec = nullptr;
+  if (s == nullptr || iters <= 0 || prime_fit_launches(p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    cudaError_t ce = fit_iteration(p, ws, target, params, m, v, s);
+    cudaError_t ee = cudaStreamEndCapture(s, &graph);
+    if (ce == cudaSuccess && ee == cudaSuccess && graph) {
+      if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
+    }
+    if (graph) cudaGraphDestroy(graph);
+  }
+  cudaGetLastError();  // a failed capture falls back to plain launches
+  return exec;
+}
+
 gs2d_status gs2d_encode_frame(const gs2d_plan* plan, void* ws, const float* target, float* params,
                               float* adam_m, float* adam_v, int32_t iters, float target_psnr,
                               int32_t check_every, float* psnr_trace, int32_t* iters_done,
@@ -238,29 +341,14 @@ gs2d_status gs2d_encode_frame(const gs2d_plan* plan, void* ws, const float* targ
   if (plan->n > 0 && (!params || !adam_m || !adam_v))
     return fail(GS2D_ERR_INVALID_ARG, "params or Adam state is NULL");
   if (iters < 0 || check_every < 1) return fail(GS2D_ERR_INVALID_ARG, "iters / check_every");
+  if (plan->num_clips != 1)
+    return fail(GS2D_ERR_INVALID_ARG, "gs2d_encode_frame takes a one-clip plan (gs2d_encode_batch)");
   const gs2d_plan& p = *plan;
   cudaStream_t s = (cudaStream_t)stream;
-  WsHeader* hdr = ws_ptr<WsHeader>(ws, p, kOffHeader);
-  const size_t pbytes = (size_t)9 * p.n * sizeof(float);
-  cudaError_t e = cudaSuccess;
-  if (pbytes) e = cudaMemsetAsync(adam_m, 0, pbytes, s);
-  if (e == cudaSuccess && pbytes) e = cudaMemsetAsync(adam_v, 0, pbytes, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), s);
+  cudaError_t e = reset_fit(p, ws, adam_m, adam_v, s);
   if (e != cudaSuccess) return cuda_check(e, "gs2d_encode_frame: reset");
-
-  cudaGraphExec_t exec = nullptr;
-  if (s != nullptr && iters > 0) {
-    cudaGraph_t graph = nullptr;
-    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-      cudaError_t ce = fit_iteration(p, ws, target, params, adam_m, adam_v, s);
-      cudaError_t ee = cudaStreamEndCapture(s, &graph);
-      if (ce == cudaSuccess && ee == cudaSuccess && graph) {
-        if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
-      }
-      if (graph) cudaGraphDestroy(graph);
-    }
-    cudaGetLastError();  // a failed capture falls back to plain launches
-  }
+  WsHeader* hdr = ws_ptr<WsHeader>(ws, p, kOffHeader);
+  cudaGraphExec_t exec = capture_fit(p, ws, target, params, adam_m, adam_v, iters, s);
 
   int done = 0, checks = 0;
   float psnr = 0.0f;
@@ -292,6 +380,63 @@ gs2d_status gs2d_encode_frame(const gs2d_plan* plan, void* ws, const float* targ
   if (final_psnr) *final_psnr = psnr;
   if (e != cudaSuccess) return cuda_check(e, "gs2d_encode_frame");
   if (result != GS2D_OK) return result;
+  return ok();
+}
+
+gs2d_status gs2d_clip_losses(const gs2d_plan* plan, void* ws, float* out, void* stream) {
+  gs2d_status st = check_plan(plan, ws);
+  if (st) return st;
+  if (!out) return fail(GS2D_ERR_INVALID_ARG, "out is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = launch_clip_losses(*plan, ws, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, ws_ptr<float2>(ws, *plan, kOffClipLoss),
+                        (size_t)plan->num_clips * sizeof(float2), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return cuda_check(e, "gs2d_clip_losses");
+}
+
+gs2d_status gs2d_encode_batch(const gs2d_plan* plan, void* ws, const float* targets,
+                              float* params, float* adam_m, float* adam_v, int32_t iters,
+                              float* clip_psnr, void* stream) {
+  gs2d_status st = check_plan(plan, ws);
+  if (st) return st;
+  if (!targets) return fail(GS2D_ERR_INVALID_ARG, "targets is NULL");
+  if (plan->n > 0 && (!params || !adam_m || !adam_v))
+    return fail(GS2D_ERR_INVALID_ARG, "params or Adam state is NULL");
+  if (iters < 0) return fail(GS2D_ERR_INVALID_ARG, "iters < 0");
+  const gs2d_plan& p = *plan;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = reset_fit(p, ws, adam_m, adam_v, s);
+  cudaGraphExec_t exec = e == cudaSuccess ? capture_fit(p, ws, targets, params, adam_m, adam_v,
+                                                        iters, s)
+                                          : nullptr;
+  for (int it = 0; it < iters && e == cudaSuccess; it++)
+    e = exec ? cudaGraphLaunch(exec, s)
+             : fit_iteration(p, ws, targets, params, adam_m, adam_v, s);
+  if (exec) cudaGraphExecDestroy(exec);
+  // evaluate the fitted Gaussians (gradients into the scratch section)
+  if (e == cudaSuccess) e = launch_prepare(p, ws, params, false, s);
+  if (e == cudaSuccess)
+    e = launch_render_l2(p, ws, params, targets, ws_ptr<float>(ws, p, kOffGrad), nullptr,
+                         nullptr, s);
+  if (e == cudaSuccess) e = launch_clip_losses(p, ws, s);
+  std::vector<float2> cl((size_t)p.num_clips);
+  WsHeader h;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(cl.data(), ws_ptr<float2>(ws, p, kOffClipLoss), cl.size() * sizeof(float2),
+                        cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&h, ws_ptr<WsHeader>(ws, p, kOffHeader), sizeof(h),
+                        cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_check(e, "gs2d_encode_batch");
+  if (clip_psnr)
+    for (int k = 0; k < p.num_clips; k++) {
+      const double mse = cl[k].y;
+      clip_psnr[k] = mse > 0.0 ? (float)(10.0 * log10(1.0 / mse)) : INFINITY;
+    }
+  if (h.status != 0) return fail((gs2d_status)h.status, "device status %d", h.status);
   return ok();
 }
 

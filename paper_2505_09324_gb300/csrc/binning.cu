@@ -15,6 +15,13 @@
 //      bitonic network in registers for lists of up to 512, a CTA bitonic
 //      network in shared memory for longer ones), restoring exactly the order
 //      a stable sort of the index-ordered entries would give.
+// Steps 2 and 4 also build the render queue: tiles grouped by list-length
+// class (floor(log2(len)) + 1, 0 for empty tiles), longest class first.  The
+// scan gives each tile its rank inside its class (one atomic per class and
+// block), the segment sort turns (class, rank) into the queue position once
+// every class size is known.
+// A batch of clips is binned in one pass: tiles are numbered clip after clip
+// and each Gaussian's rectangle is stored in that numbering.
 #include "gs2d_internal.cuh"
 
 namespace gs2d {
@@ -25,18 +32,19 @@ constexpr int kGB = 256;           // Gaussians per counting / scan block
 // ---------------------------------------------------------------------------
 // Projection (gs2d_project): records, rectangles, per-Gaussian counts.
 __global__ void __launch_bounds__(kGB)
-k_project(int n, int W, int H, float sigma_cut, float alpha_min, float det_eps,
+k_project(int n, ClipSet cs, int tile_shift, float sigma_cut, float alpha_min, float det_eps,
           const float* __restrict__ params, float4* __restrict__ rec, int4* __restrict__ rect,
           int* __restrict__ count) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  project_one(i, n, W, H, sigma_cut, alpha_min, det_eps, params, rec, rect, count);
+  project_one(i, n, clip_of_gaussian(cs, i), tile_shift, sigma_cut, alpha_min, det_eps, params,
+              rec, rect, count);
 }
 
 // Per-tile entry counts from the rectangles (warp-cooperative: lanes share the
 // tiles of one Gaussian at a time; fire-and-forget atomics) and the block's
 // sum of per-Gaussian counts.
-__device__ __forceinline__ void count_block(int n, int TX, const int4* __restrict__ rect,
+__device__ __forceinline__ void count_block(int n, const int4* __restrict__ rect,
                                            const int* __restrict__ count,
                                            int* __restrict__ tile_cnt,
                                            long long* __restrict__ block_sum) {
@@ -45,13 +53,13 @@ __device__ __forceinline__ void count_block(int n, int TX, const int4* __restric
   const int lane = threadIdx.x & 31;
   const int4 rc = i < n ? rect[i] : make_int4(0, 0, 0, 0);
   for (int l = 0; l < 32; l++) {
-    const int x0 = __shfl_sync(0xffffffffu, rc.x, l);
-    const int y0 = __shfl_sync(0xffffffffu, rc.y, l);
-    const int w = __shfl_sync(0xffffffffu, rc.z, l) - x0;
-    const int cnt = w * (__shfl_sync(0xffffffffu, rc.w, l) - y0);
+    const int t0 = __shfl_sync(0xffffffffu, rc.x, l);
+    const int stride = __shfl_sync(0xffffffffu, rc.y, l);
+    const int w = __shfl_sync(0xffffffffu, rc.z, l);
+    const int cnt = w * __shfl_sync(0xffffffffu, rc.w, l);
     for (int j = lane; j < cnt; j += 32) {
       const int dy = j / w;
-      atomicAdd(&tile_cnt[(y0 + dy) * TX + x0 + (j - dy * w)], 1);
+      atomicAdd(&tile_cnt[t0 + dy * stride + (j - dy * w)], 1);
     }
   }
   int c = i < n ? count[i] : 0;
@@ -67,16 +75,17 @@ __device__ __forceinline__ void count_block(int n, int TX, const int4* __restric
 }
 
 __global__ void __launch_bounds__(kGB)
-k_count_tiles(int n, int TX, const int4* __restrict__ rect, const int* __restrict__ count,
+k_count_tiles(int n, const int4* __restrict__ rect, const int* __restrict__ count,
               int* __restrict__ tile_cnt, long long* __restrict__ block_sum) {
-  count_block(n, TX, rect, count, tile_cnt, block_sum);
+  count_block(n, rect, count, tile_cnt, block_sum);
 }
 
 // Fused projection + counts for gs2d_prepare and the fit loop; with adam_tick
 // the Adam step counter and the powers beta^step advance here (the first
 // kernel of a fit iteration).
 __global__ void __launch_bounds__(kGB)
-k_project_count(int n, int W, int H, int TX, float sigma_cut, float alpha_min, float det_eps,
+k_project_count(int n, ClipSet cs, int tile_shift, float sigma_cut, float alpha_min,
+                float det_eps,
                 const float* __restrict__ params, float4* __restrict__ rec,
                 int4* __restrict__ rect, int* __restrict__ count, int* __restrict__ tile_cnt,
                 long long* __restrict__ block_sum, WsHeader* __restrict__ hdr, int adam_tick,
@@ -91,9 +100,11 @@ k_project_count(int n, int W, int H, int TX, float sigma_cut, float alpha_min, f
     hdr->bc1 = (float)(1.0 - p1);
     hdr->bc2 = (float)(1.0 - p2);
   }
-  if (i < n) project_one(i, n, W, H, sigma_cut, alpha_min, det_eps, params, rec, rect, count);
+  if (i < n)
+    project_one(i, n, clip_of_gaussian(cs, i), tile_shift, sigma_cut, alpha_min, det_eps, params,
+                rec, rect, count);
   __syncwarp();
-  count_block(n, TX, rect, count, tile_cnt, block_sum);
+  count_block(n, rect, count, tile_cnt, block_sum);
 }
 
 // ---------------------------------------------------------------------------
@@ -131,11 +142,20 @@ __device__ __forceinline__ long long block_scan64(long long v, long long* warp_s
 
 constexpr int kTileItems = 4;  // tiles per thread of a tile-scan CTA
 
+// Render-queue class of a list of length len: 0 (empty), 1 + floor(log2(len))
+// capped at kBuckets - 1.
+__device__ __forceinline__ int length_class(int len) {
+  return len <= 0 ? 0 : min(kBuckets - 1, 32 - __clz(len));
+}
+
 __global__ void __launch_bounds__(kGB)
 k_bin_scan(int n, int nbg, int num_tiles, int64_t max_entries, int* __restrict__ count,
            const long long* __restrict__ block_sum, int* __restrict__ tile_cnt,
-           int* __restrict__ cursor, int2* __restrict__ ranges, WsHeader* __restrict__ hdr) {
+           int* __restrict__ cursor, int2* __restrict__ ranges, int* __restrict__ bucket,
+           uint32_t* __restrict__ rank, WsHeader* __restrict__ hdr) {
   __shared__ long long warp_sum[32];
+  __shared__ int s_hist[kBuckets];
+  __shared__ int s_base[kBuckets];
   const int t = threadIdx.x;
   if ((int)blockIdx.x < nbg) {
     // total and this block's prefix from the block sums
@@ -171,6 +191,8 @@ k_bin_scan(int n, int nbg, int num_tiles, int64_t max_entries, int* __restrict__
   block_scan64(tot, warp_sum, &total);
   block_scan64(pre, warp_sum, &prefix);
   const bool over = total > max_entries;
+  if (t < kBuckets) s_hist[t] = 0;
+  __syncthreads();
   {
     const int base = c0 + t * kTileItems;
     int c[kTileItems];
@@ -182,17 +204,29 @@ k_bin_scan(int n, int nbg, int num_tiles, int64_t max_entries, int* __restrict__
     }
     long long chunk;
     long long run = prefix + block_scan64(v, warp_sum, &chunk);
+    int cls[kTileItems], r[kTileItems];
 #pragma unroll
     for (int k = 0; k < kTileItems; k++) {
       const int i = base + k;
+      cls[k] = length_class(over ? 0 : c[k]);
+      r[k] = 0;
       if (i < num_tiles) {
         const int s = over ? 0 : (int)run;
         // an empty tile's range is (0, 0) wherever it sits in the list
         ranges[i] = (over || c[k] == 0) ? make_int2(0, 0) : make_int2(s, s + c[k]);
         cursor[i] = s;
+        r[k] = atomicAdd(&s_hist[cls[k]], 1);
       }
       run += c[k];
     }
+    __syncthreads();
+    // this block's first rank in each class
+    if (t < kBuckets) s_base[t] = s_hist[t] ? atomicAdd(&bucket[t], s_hist[t]) : 0;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kTileItems; k++)
+      if (base + k < num_tiles)
+        rank[base + k] = ((uint32_t)cls[k] << 28) | (uint32_t)(s_base[cls[k]] + r[k]);
   }
   if (tb == 0 && t == 0) {
     hdr->entries_raw = total;
@@ -209,7 +243,7 @@ k_bin_scan(int n, int nbg, int num_tiles, int64_t max_entries, int* __restrict__
 constexpr int kInFlight = 4;
 
 __global__ void __launch_bounds__(kGB)
-k_bin_scatter(int n, int TX, const int4* __restrict__ rect, const WsHeader* __restrict__ hdr,
+k_bin_scatter(int n, const int4* __restrict__ rect, const WsHeader* __restrict__ hdr,
               int* __restrict__ cursor, uint32_t* __restrict__ list) {
   __shared__ int s_start[kGB / 32][33];
   if (hdr->entries_raw != (int64_t)hdr->n_entries) return;  // over capacity
@@ -217,7 +251,7 @@ k_bin_scatter(int n, int TX, const int4* __restrict__ rect, const WsHeader* __re
   const int g_base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31;
   const int g = g_base + lane;
   const int4 rc = g < n ? rect[g] : make_int4(0, 0, 0, 0);
-  const int cnt = (rc.z - rc.x) * (rc.w - rc.y);
+  const int cnt = rc.z * rc.w;
   int incl = cnt;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -244,10 +278,9 @@ k_bin_scatter(int n, int TX, const int4* __restrict__ rect, const WsHeader* __re
           if (start[lo + step] <= e) lo += step;
         gi[u] = (uint32_t)(g_base + lo);
         const int4 ro = rect[g_base + lo];
-        const int w = ro.z - ro.x;
         const int j = e - start[lo];
-        const int dy = j / w;
-        pos[u] = atomicAdd(&cursor[(ro.y + dy) * TX + ro.x + (j - dy * w)], 1);
+        const int dy = j / ro.z;
+        pos[u] = atomicAdd(&cursor[ro.x + dy * ro.y + (j - dy * ro.z)], 1);
       }
     }
 #pragma unroll
@@ -310,17 +343,35 @@ __device__ __forceinline__ void warp_sort_list(uint32_t* __restrict__ seg, int l
 
 // Segment sort: one warp per tile, bitonic network in registers for lists of
 // up to 512; longer lists are queued for k_sort_long.  Also resets the tile's
-// entry counter for the next binning (its last reader, the scan, is done).
+// entry counter for the next binning (its last reader, the scan, is done) and
+// places the tile in the render queue: after all tiles of longer classes, at
+// the next free position of its class.
 __global__ void __launch_bounds__(256)
 k_sort_short(int num_tiles, const int2* __restrict__ ranges, uint32_t* __restrict__ list,
              int* __restrict__ long_tiles, int* __restrict__ tile_cnt,
-             WsHeader* __restrict__ hdr) {
+             const int* __restrict__ bucket, const uint32_t* __restrict__ rank,
+             int* __restrict__ order, WsHeader* __restrict__ hdr) {
   const int lane = threadIdx.x & 31;
   const int tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (tile >= num_tiles) return;
-  if (lane == 0) tile_cnt[tile] = 0;
   const int2 rg = ranges[tile];
   const int len = rg.y - rg.x;
+  {
+    // queue position: the tiles of all longer classes, then the rank in its own
+    const uint32_t rk = rank[tile];
+    const int cls = (int)(rk >> 28);
+    int x = lane < kBuckets && lane > cls ? bucket[lane] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) {
+      tile_cnt[tile] = 0;
+      const int q = x + (int)(rk & 0x0fffffffu);
+      if (q < num_tiles)
+        order[q] = tile;
+      else
+        set_status(hdr, GS2D_ERR_BOUNDS);  // class sizes out of step with the ranks
+    }
+  }
   uint32_t* seg = list + rg.x;
   if (len <= 1) return;
   if (len <= 32)
@@ -343,9 +394,12 @@ k_sort_short(int num_tiles, const int2* __restrict__ ranges, uint32_t* __restric
 // zeroed so that no gradient is reduced from this binning.
 __global__ void __launch_bounds__(1024)
 k_sort_long(int2* __restrict__ ranges, uint32_t* __restrict__ list,
-            const int* __restrict__ long_tiles, WsHeader* __restrict__ hdr) {
+            const int* __restrict__ long_tiles, int* __restrict__ bucket,
+            WsHeader* __restrict__ hdr) {
   extern __shared__ uint32_t s_keys[];
   const int t = threadIdx.x;
+  // the queue classes were last read by k_sort_short: clear them for the next binning
+  if (blockIdx.x == 0 && t < 2 * kBuckets) bucket[t] = 0;
   const int count = hdr->long_count;
   for (int q = blockIdx.x; q < count; q += gridDim.x) {
     const int tile = long_tiles[q];
@@ -388,12 +442,21 @@ k_sort_long(int2* __restrict__ ranges, uint32_t* __restrict__ list,
 cudaError_t launch_project(const gs2d_plan& p, void* ws, const float* params, cudaStream_t s) {
   if (p.n == 0) return cudaSuccess;
   k_project<<<(p.n + kGB - 1) / kGB, kGB, 0, s>>>(
-      p.n, p.width, p.height, p.cfg.sigma_cut, p.cfg.alpha_min, p.cfg.det_eps, params,
+      p.n, clip_set(p, ws), tile_shift_of(p.tile), p.cfg.sigma_cut, p.cfg.alpha_min,
+      p.cfg.det_eps, params,
       ws_ptr<float4>(ws, p, kOffRec), ws_ptr<int4>(ws, p, kOffRect), ws_ptr<int>(ws, p, kOffCount));
   return cudaGetLastError();
 }
 
 static bool g_long_attr_set = false;
+
+cudaError_t prime_binning() {
+  if (g_long_attr_set) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(k_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kLongMax * (int)sizeof(uint32_t));
+  if (e == cudaSuccess) g_long_attr_set = true;
+  return e;
+}
 
 // Scans, scatter and segment sorts (everything after the counts).
 static cudaError_t launch_bin_rest(const gs2d_plan& p, void* ws, cudaStream_t s) {
@@ -404,31 +467,29 @@ static cudaError_t launch_bin_rest(const gs2d_plan& p, void* ws, cudaStream_t s)
   int* long_tiles = ws_ptr<int>(ws, p, kOffLong);
   uint32_t* list = ws_ptr<uint32_t>(ws, p, kOffList);
   int2* ranges = ws_ptr<int2>(ws, p, kOffRanges);
+  int* bucket = ws_ptr<int>(ws, p, kOffBucket);
+  int* order = ws_ptr<int>(ws, p, kOffOrder);
+  uint32_t* rank = ws_ptr<uint32_t>(ws, p, kOffRank);
   const int nbg = (p.n + kGB - 1) / kGB;
   const int nbt = (p.num_tiles + kGB * kTileItems - 1) / (kGB * kTileItems);
   k_bin_scan<<<nbg + nbt, kGB, 0, s>>>(p.n, nbg, p.num_tiles, p.max_entries, count,
                                      ws_ptr<long long>(ws, p, kOffBlockSum), tile_cnt, cursor,
-                                     ranges, hdr);
+                                     ranges, bucket, rank, hdr);
   if (p.n > 0)
-    k_bin_scatter<<<nbg, kGB, 0, s>>>(p.n, p.tiles_x, ws_ptr<int4>(ws, p, kOffRect), hdr, cursor,
-                                      list);
+    k_bin_scatter<<<nbg, kGB, 0, s>>>(p.n, ws_ptr<int4>(ws, p, kOffRect), hdr, cursor, list);
   k_sort_short<<<(p.num_tiles + 7) / 8, 256, 0, s>>>(p.num_tiles, ranges, list, long_tiles,
-                                                    tile_cnt, hdr);
-  const int smem = kLongMax * (int)sizeof(uint32_t);
-  if (!g_long_attr_set) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(k_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    g_long_attr_set = true;
-  }
-  k_sort_long<<<152, 1024, smem, s>>>(ranges, list, long_tiles, hdr);
+                                                    tile_cnt, bucket, rank, order, hdr);
+  const cudaError_t e = prime_binning();
+  if (e != cudaSuccess) return e;
+  k_sort_long<<<152, 1024, kLongMax * (int)sizeof(uint32_t), s>>>(ranges, list, long_tiles, bucket,
+                                                                  hdr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bin_sort(const gs2d_plan& p, void* ws, cudaStream_t s) {
   if (p.n > 0)
     k_count_tiles<<<(p.n + kGB - 1) / kGB, kGB, 0, s>>>(
-        p.n, p.tiles_x, ws_ptr<int4>(ws, p, kOffRect), ws_ptr<int>(ws, p, kOffCount),
+        p.n, ws_ptr<int4>(ws, p, kOffRect), ws_ptr<int>(ws, p, kOffCount),
         ws_ptr<int>(ws, p, kOffTileCnt), ws_ptr<long long>(ws, p, kOffBlockSum));
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -439,7 +500,8 @@ cudaError_t launch_prepare(const gs2d_plan& p, void* ws, const float* params, bo
                            cudaStream_t s) {
   const int blocks = (p.n + kGB - 1) / kGB;
   k_project_count<<<blocks > 0 ? blocks : 1, kGB, 0, s>>>(
-      p.n, p.width, p.height, p.tiles_x, p.cfg.sigma_cut, p.cfg.alpha_min, p.cfg.det_eps, params,
+      p.n, clip_set(p, ws), tile_shift_of(p.tile), p.cfg.sigma_cut, p.cfg.alpha_min,
+      p.cfg.det_eps, params,
       ws_ptr<float4>(ws, p, kOffRec), ws_ptr<int4>(ws, p, kOffRect), ws_ptr<int>(ws, p, kOffCount),
       ws_ptr<int>(ws, p, kOffTileCnt), ws_ptr<long long>(ws, p, kOffBlockSum),
       ws_ptr<WsHeader>(ws, p, kOffHeader), adam_tick ? 1 : 0, p.cfg.beta1, p.cfg.beta2);

@@ -11,22 +11,19 @@
 namespace gs2d {
 
 constexpr uint64_t kPlanMagic = 0x67733264706c616eull;  // "gs2dplan"
-constexpr int kTile = 16;                               // tile edge (pixels)
-constexpr int kTilePix = kTile * kTile;                 // 256 pixels per tile
-constexpr int kScanThreads = 1024;
-constexpr int kScanItems = 8;  // per thread in the count scans
-constexpr int kPartials = 8;   // backward accumulators per (tile, Gaussian)
+constexpr int kTileDefault = 16;   // tile edge (pixels)
+constexpr int kStageDefault = 64;  // Gaussians per shared-memory batch
+constexpr int kPartials = 8;       // backward accumulators per (tile, Gaussian)
+constexpr int kBuckets = 16;       // list-length classes of the render queue
 
-// log2(e) / 2: scales the Cholesky-form coordinates so that
-// q = u1^2 + u2^2 = sigma * log2(e), and exp(-sigma) = 2^-q.
-constexpr float kSc2 = 0.72134752044448170368f;  // log2(e)/2
 constexpr float kLn2 = 0.69314718055994530942f;
 
 // Workspace sections (byte offsets stored in gs2d_plan::off).
 enum WsSection {
   kOffHeader = 0,   // WsHeader
+  kOffClips,        // gs2d_clip[num_clips] (batch plans)
   kOffRec,          // float4[3][n]  render records (SoA of float4 rows)
-  kOffRect,         // int4[n]       tile rectangle [tx0, ty0, tx1, ty1)
+  kOffRect,         // int4[n]       tile rectangle (first tile, row stride, w, h)
   kOffCount,        // int32[n + 1]  per-Gaussian tile counts, then exclusive offsets
   kOffBlockSum,     // int64[n / 256 + 1]  entry counts per block of 256 Gaussians
   kOffTileCnt,      // int32[num_tiles]  entries per tile (zero between calls)
@@ -34,11 +31,16 @@ enum WsSection {
   kOffLong,         // int32[num_tiles + 1]  tiles whose list needs the CTA sort
   kOffList,         // uint32[max_entries]  Gaussian indices, tile-major
   kOffRanges,       // int2[num_tiles]
+  kOffOrder,        // int32[num_tiles]  render queue: tiles, longest list first
+  kOffRank,         // uint32[num_tiles]  (class << 28 | rank in class) of each tile
+  kOffBucket,       // int32[2][kBuckets]  queue class sizes (zero between calls)
   kOffPartial,      // float[max_entries][kPartials] backward sums per (tile, Gaussian)
-  kOffLossPart,     // float2[num_tiles]  per-tile (sum sq err, sum sq err clamped)
-  kOffGrad,         // float[9 n] gradient scratch of the fit loop
+  kOffLossPart,     // float2[num_tiles]  per-tile (sse, clamped sse) / (3 W H of the clip)
+  kOffClipLoss,     // float2[num_clips]
+  kOffGrad,         // float[9 n] gradient scratch
   kNumSections
 };
+static_assert(kNumSections <= 24, "gs2d_plan::off holds 24 sections");
 
 struct WsHeader {
   int32_t status;       // first device-detected error (gs2d_status), 0 if none
@@ -50,9 +52,42 @@ struct WsHeader {
   float loss[2];        // last reduced {loss, clamped mse}
   unsigned long long pairs, hits;  // gs2d_count_pairs results
   double pw1, pw2;      // beta1^step, beta2^step
-  int32_t pad[46];
+  int32_t queue;        // next render-queue ticket (reset by the last block)
+  int32_t done;         // render blocks that have left the queue
+  int32_t pad[44];
 };
 static_assert(sizeof(WsHeader) == 256, "header is one 256-byte block");
+
+// The clips a kernel sees: a one-clip plan passes its clip by value, a batch
+// the device table (clips ordered by g_off and tile_off).
+struct ClipSet {
+  int count;
+  const gs2d_clip* table;
+  gs2d_clip one;
+};
+
+// Clip owning Gaussian i: the last clip whose g_off <= i (clips without
+// Gaussians share g_off with their successor, which then owns i).
+__device__ __forceinline__ gs2d_clip clip_of_gaussian(const ClipSet& cs, int i) {
+  if (cs.count == 1) return cs.one;
+  int lo = 0, hi = cs.count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (cs.table[mid].g_off <= i) lo = mid; else hi = mid - 1;
+  }
+  return cs.table[lo];
+}
+
+// Clip owning global tile t (every clip has at least one tile).
+__device__ __forceinline__ gs2d_clip clip_of_tile(const ClipSet& cs, int t) {
+  if (cs.count == 1) return cs.one;
+  int lo = 0, hi = cs.count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (cs.table[mid].tile_off <= t) lo = mid; else hi = mid - 1;
+  }
+  return cs.table[lo];
+}
 
 // Per-Gaussian render record, three float4 rows.
 //   r0 = (mu_x, mu_y, a1, a2)      a1 = s/l1, a2 = s/l3, s = sqrt(log2(e)/2)
@@ -85,15 +120,19 @@ __device__ __forceinline__ void set_status(WsHeader* h, int code) {
 }
 
 // Projection of Gaussian i (Sec. 3.1 parameters -> screen-space record, tile
-// rectangle and tile count).  The rectangle uses only single-rounded operations
-// (no FMA contraction) so it is reproducible on the host; the rest of the
-// record is ordinary FP32.  Culled Gaussians (non-finite, det <= det_eps,
-// |w| < alpha_min, off-image) get count 0.
-__device__ __forceinline__ void project_one(int i, int n, int W, int H, float sigma_cut,
-                                            float alpha_min, float det_eps,
+// rectangle and tile count) in the frame of its clip.  The rectangle uses only
+// single-rounded operations (no FMA contraction) so it is reproducible on the
+// host; the rest of the record is ordinary FP32.  Culled Gaussians
+// (non-finite, det <= det_eps, |w| < alpha_min, off-image) get count 0.
+// The rectangle is stored as (first tile, tile-row stride, width, height) in
+// the plan's tile numbering: tile (x0 + dx, y0 + dy) of the clip is
+// first + dy * stride + dx.
+__device__ __forceinline__ void project_one(int i, int n, const gs2d_clip& cl, int tile_shift,
+                                            float sigma_cut, float alpha_min, float det_eps,
                                             const float* __restrict__ params,
                                             float4* __restrict__ rec, int4* __restrict__ rect,
                                             int* __restrict__ count) {
+  const int W = cl.width, H = cl.height;
   const float mx = params[i], my = params[n + i];
   const float l1 = params[2 * n + i], l2 = params[3 * n + i], l3 = params[4 * n + i];
   const float cr = params[5 * n + i], cg = params[6 * n + i], cb = params[7 * n + i];
@@ -119,9 +158,10 @@ __device__ __forceinline__ void project_one(int i, int n, int W, int H, float si
     fx1 = fx1 > (float)(W - 1) ? (float)(W - 1) : fx1;
     fy1 = fy1 > (float)(H - 1) ? (float)(H - 1) : fy1;
     if (fx0 <= fx1 && fy0 <= fy1) {
-      rc = make_int4((int)fx0 / kTile, (int)fy0 / kTile, (int)fx1 / kTile + 1,
-                     (int)fy1 / kTile + 1);
-      cnt = (rc.z - rc.x) * (rc.w - rc.y);
+      const int tx0 = (int)fx0 >> tile_shift, ty0 = (int)fy0 >> tile_shift;
+      const int tx1 = ((int)fx1 >> tile_shift) + 1, ty1 = ((int)fy1 >> tile_shift) + 1;
+      rc = make_int4(cl.tile_off + ty0 * cl.tiles_x + tx0, cl.tiles_x, tx1 - tx0, ty1 - ty0);
+      cnt = rc.z * rc.w;
     }
   }
   rect[i] = rc;
@@ -146,6 +186,59 @@ __device__ __forceinline__ void project_one(int i, int n, int W, int H, float si
   rec[2 * n + i] = r2;
 }
 
+__host__ __device__ inline int tile_shift_of(int tile) {
+  return tile == 8 ? 3 : (tile == 32 ? 5 : 4);
+}
+
+// Clip set of a plan (the table lives in the workspace of a batch plan).
+inline ClipSet clip_set(const gs2d_plan& p, const void* ws) {
+  ClipSet cs;
+  cs.count = p.num_clips;
+  cs.table = ws_ptr<gs2d_clip>(ws, p, kOffClips);
+  cs.one = gs2d_clip{p.width, p.height, p.n, p.tiles_x, p.tiles_y, 0, 0, 0, 0};
+  return cs;
+}
+
+// Arguments of the render kernels (csrc/render_impl.cuh).
+enum RenderMode { kModeFwd = 0, kModeBwd = 1, kModeL2 = 2, kModeCount = 3 };
+
+struct RenderArgs {
+  ClipSet clips;
+  int n, num_tiles;
+  const int2* ranges;
+  const uint32_t* list;
+  const float4* rec;
+  const int4* rect;
+  const int* offs;
+  const int* order;
+  WsHeader* hdr;
+  float* img;            // fwd, l2 (optional)
+  const float* target;   // l2
+  const float* dimg;     // bwd
+  float* partial;        // bwd, l2
+  float2* loss_part;     // l2
+};
+
+// One instantiation set per tile edge (render_t8.cu, render_t16.cu, render_t32.cu).
+cudaError_t launch_render_t8(int stage, int launch, RenderMode mode, const RenderArgs& a,
+                              cudaStream_t s);
+cudaError_t launch_render_t16(int stage, int launch, RenderMode mode, const RenderArgs& a,
+                              cudaStream_t s);
+cudaError_t launch_render_t32(int stage, int launch, RenderMode mode, const RenderArgs& a,
+                              cudaStream_t s);
+
+cudaError_t prime_render_t8(int stage, int launch);
+cudaError_t prime_render_t16(int stage, int launch);
+cudaError_t prime_render_t32(int stage, int launch);
+// One-time per-device setup of the binning launches (shared-memory opt-in).
+cudaError_t prime_binning();
+// prime_binning + the render occupancy query of the plan's fit loop.
+cudaError_t prime_fit_launches(const gs2d_plan& p);
+
+// Thread blocks of a persistent launch: resident blocks per SM x SMs of the
+// current device, at most `work` blocks.
+int persistent_grid(const void* kernel, int threads, int work);
+
 // ---- launchers implemented in the .cu files (return cudaGetLastError) ----
 cudaError_t launch_project(const gs2d_plan& p, void* ws, const float* params, cudaStream_t s);
 cudaError_t launch_bin_sort(const gs2d_plan& p, void* ws, cudaStream_t s);
@@ -162,6 +255,7 @@ cudaError_t launch_adam(float* params, const float* grads, float* m, float* v, i
                         cudaStream_t s);
 cudaError_t launch_loss_reduce(const gs2d_plan& p, void* ws, float* loss, cudaStream_t s);
 cudaError_t launch_count_pairs(const gs2d_plan& p, void* ws, cudaStream_t s);
+cudaError_t launch_clip_losses(const gs2d_plan& p, void* ws, cudaStream_t s);
 // project + bin_sort; with adam_tick the fit loop's Adam step counter and bias
 // corrections advance in the same launch.
 cudaError_t launch_prepare(const gs2d_plan& p, void* ws, const float* params, bool adam_tick,

@@ -91,12 +91,14 @@ extern "C" gs2d_status gs2d_render_fwd_noalloc(const float* params, int32_t n, i
   cudaStream_t s = (cudaStream_t)stream;
   // The array keeps the previous call's contents, laid out for whatever frame
   // that call had.  The header (status word and counters) and the per-tile
-  // entry counters must start at zero; every other section is written before
-  // it is read within one call.
+  // entry counters and the render-queue class counters must start at zero;
+  // every other section is written before it is read within one call.
   if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), s);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(ws_ptr<int>(ws, plan, kOffTileCnt), 0,
                         (size_t)plan.num_tiles * sizeof(int), s);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(ws_ptr<int>(ws, plan, kOffBucket), 0, 2 * kBuckets * sizeof(int), s);
   if (e == cudaSuccess) e = launch_project(plan, ws, params, s);
   if (e == cudaSuccess) e = launch_bin_sort(plan, ws, s);
   if (e == cudaSuccess) e = launch_render_fwd(plan, ws, img, s);

@@ -20,8 +20,10 @@ from . import _native as nat
 @dataclasses.dataclass
 class RasterConfig:
     """Constants of the rasterizer and the optimiser (project readings; the paper
-    fixes none): tile 16, sigma <= 4.5, |alpha| >= 1/255, det Sigma > 1e-8,
-    Adam lr 1e-2, betas (0.9, 0.999), eps 1e-8."""
+    fixes none): tile 16, stage 64, sigma <= 4.5, |alpha| >= 1/255,
+    det Sigma > 1e-8, Adam lr 1e-2, betas (0.9, 0.999), eps 1e-8.  tile (8, 16,
+    32), stage (32, 64, 128 Gaussians per shared-memory batch) and launch
+    (persistent queue or one block per tile) choose the render schedule only."""
 
     tile: int = 16
     sigma_cut: float = 4.5
@@ -31,10 +33,12 @@ class RasterConfig:
     beta1: float = 0.9
     beta2: float = 0.999
     eps: float = 1e-8
+    stage: int = 64
+    launch: int = nat.LAUNCH_GRID
 
     def to_c(self) -> nat.Config:
         return nat.Config(self.tile, self.sigma_cut, self.alpha_min, self.det_eps, self.lr,
-                          self.beta1, self.beta2, self.eps)
+                          self.beta1, self.beta2, self.eps, self.stage, self.launch)
 
 
 def _stream(stream) -> int:
@@ -185,3 +189,98 @@ def adam_step(params: torch.Tensor, grads: torch.Tensor, m: torch.Tensor, v: tor
         mp = _check(mask, "mask", (params.numel() // 9,), dtype=torch.uint8)
     cfg = (config or RasterConfig()).to_c()
     nat.adam_step(*ptrs, params.numel(), step, mp, cfg, _stream(stream))
+
+
+class BatchRasterizer(GaussianRasterizer):
+    """One plan + workspace for a batch of independent clips of different sizes
+    (gs2d_plan_init_batch): ``sizes`` = [(width, height, n), ...].  Parameters
+    are one ``[9, n_total]`` tensor (clip c owns columns ``offsets[c]`` ...);
+    images are one flat float32 tensor of ``pixels * 3`` values, clip c's
+    ``[3, H, W]`` image at ``pix_off[c]`` (see ``clip_view``).  Every step runs
+    once over all clips; each clip keeps its own loss."""
+
+    def __init__(self, sizes, max_entries: int = 0, config: RasterConfig | None = None,
+                 device=None):
+        self.config = config or RasterConfig()
+        self.sizes = [(int(w), int(h), int(n)) for (w, h, n) in sizes]
+        self.plan, self.clips = nat.plan_init_batch(self.sizes, max_entries, self.config.to_c())
+        self.width, self.height, self.n = 0, 0, int(self.plan.n)
+        self.device = torch.device(device) if device is not None else torch.device("cuda")
+        self.ws = torch.zeros(int(self.plan.ws_bytes), dtype=torch.uint8, device=self.device)
+        if self.ws.data_ptr() % 256:
+            raise RuntimeError("workspace allocation is not 256-byte aligned")
+        nat.ws_set_clips(self.plan, self.ws_ptr, self.clips, _stream(None))
+        self.version = 0
+        self.offsets = [int(c.g_off) for c in self.clips]
+        self.pix_off = [int(c.pix_off) for c in self.clips]
+
+    def image_shape(self):
+        return (3 * int(self.plan.pixels),)
+
+    def clip_view(self, flat: torch.Tensor, c: int) -> torch.Tensor:
+        """Clip c's [3, H, W] view of a batch image buffer."""
+        w, h, _ = self.sizes[c]
+        o = self.pix_off[c]
+        return flat[o:o + 3 * w * h].view(3, h, w)
+
+    def pack_images(self, images) -> torch.Tensor:
+        """Concatenates per-clip [3, H, W] tensors into the batch layout."""
+        return torch.cat([im.reshape(-1) for im in images]).contiguous()
+
+    def pack_params(self, params) -> torch.Tensor:
+        """Concatenates per-clip [9, n_c] tensors into one [9, n_total]."""
+        return torch.cat(list(params), dim=1).contiguous()
+
+    def clip_losses(self, stream=None):
+        """[(mse, clamped mse)] per clip of the last render_l2."""
+        return nat.clip_losses(self.plan, self.ws_ptr, _stream(stream))
+
+    def encode_frame(self, *args, **kwargs):
+        raise TypeError("a batch plan is fitted with encode_batch")
+
+    def encode_batch(self, targets: torch.Tensor, params: torch.Tensor, iters: int,
+                     adam_state=None, stream=None):
+        """Fits every clip (params in place) for ``iters`` iterations; returns the
+        per-clip PSNR of the fitted Gaussians (gs2d_encode_batch)."""
+        if adam_state is None:
+            adam_state = (torch.empty_like(params), torch.empty_like(params))
+        m, v = adam_state
+        shape = (9, self.n)
+        return nat.encode_batch(self.plan, self.ws_ptr, _check(targets, "targets",
+                                                                self.image_shape()),
+                                _check(params, "params", shape), _check(m, "adam_m", shape),
+                                _check(v, "adam_v", shape), iters, _stream(stream))
+
+
+_TUNED = {}
+
+
+def autotune(sizes, params: torch.Tensor, targets: torch.Tensor, tiles=(8, 16, 32),
+             stages=(32, 64, 128), launches=(nat.LAUNCH_PERSISTENT, nat.LAUNCH_GRID),
+             reps: int = 5, config: RasterConfig | None = None, max_entries: int = 0,
+             stream=None, cache: bool = True):
+    """Picks the render schedule (tile, stage, launch) for a batch
+    (gs2d_autotune).  ``params``/``targets`` in the batch layout of
+    ``BatchRasterizer(sizes)``.  Returns {"tile", "stage", "launch", "config",
+    "ms": {(tile, stage, launch): ms per fit iteration}}; the result is cached
+    per (sizes, candidates) unless ``cache`` is False."""
+    sizes = [(int(w), int(h), int(n)) for (w, h, n) in sizes]
+    key = (tuple(sizes), tuple(tiles), tuple(stages), tuple(launches), max_entries)
+    if cache and key in _TUNED:
+        return _TUNED[key]
+    base = (config or RasterConfig()).to_c()
+    nbytes = nat.autotune_ws_bytes(sizes, list(tiles), max_entries, base)
+    if nbytes == 0:
+        raise ValueError("invalid batch or candidate tiles")
+    n_total = sum(n for (_, _, n) in sizes)
+    pixels = sum(w * h for (w, h, _) in sizes)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=params.device)
+    table, bt, bs, bl = nat.autotune(sizes, _check(params, "params", (9, n_total)),
+                                     _check(targets, "targets", (3 * pixels,)), ws.data_ptr(),
+                                     nbytes, list(tiles), list(stages), list(launches), reps,
+                                     _stream(stream), max_entries, base)
+    cfg = dataclasses.replace(config or RasterConfig(), tile=bt, stage=bs, launch=bl)
+    res = {"tile": bt, "stage": bs, "launch": bl, "config": cfg, "ms": table}
+    if cache:
+        _TUNED[key] = res
+    return res

@@ -38,20 +38,22 @@ def test_struct_layouts_match(nat):
     lib = nat.load()
     assert lib.gs2d_sizeof_plan() == ctypes.sizeof(nat.Plan)
     assert lib.gs2d_sizeof_config() == ctypes.sizeof(nat.Config)
+    assert ctypes.sizeof(nat.Clip) == 40
 
 
 def test_default_config(nat):
     c = nat.default_config()
-    assert c.tile == 16 and abs(c.sigma_cut - 4.5) < 1e-7
+    assert c.tile == 16 and c.stage == 64 and c.launch == nat.LAUNCH_GRID
+    assert abs(c.sigma_cut - 4.5) < 1e-7
     assert abs(c.alpha_min - 1 / 255) < 1e-9 and abs(c.lr - 1e-2) < 1e-9
 
 
 def test_plan_layout(nat):
     p = nat.plan_init(1920, 1080, 20000)
     assert (p.tiles_x, p.tiles_y, p.num_tiles) == (120, 68, 8160)
-    assert p.tile_bits == 13 and p.sort_passes == 1
-    assert p.max_entries == max(1 << 20, 16 * 20000)
-    offs = list(p.off)[:13]
+    assert p.tile_bits == 13 and p.num_clips == 1 and p.stage == 64
+    assert p.max_entries == max(1 << 20, 16 * 20000) and p.pixels == 1920 * 1080
+    offs = list(p.off)[:18]
     assert all(o % 256 == 0 for o in offs)
     assert offs == sorted(offs) and p.ws_bytes > offs[-1]
     q = nat.plan_init(16, 16, 5)
@@ -66,11 +68,65 @@ def test_plan_rejects_bad_sizes(nat, args):
     assert e.value.status == nat.GS2D_ERR_INVALID_ARG
 
 
-def test_plan_rejects_bad_config(nat):
+@pytest.mark.parametrize("tile,stage,tiles", [(8, 32, (8, 6)), (16, 128, (4, 3)), (32, 0, (2, 2))])
+def test_plan_tile_and_stage(nat, tile, stage, tiles):
     c = nat.default_config()
-    c.tile = 8
+    c.tile, c.stage = tile, stage
+    p = nat.plan_init(64, 48, 10, 0, c)
+    assert (p.tiles_x, p.tiles_y) == tiles and p.tile == tile
+    assert p.stage == (stage or 64)
+    assert p.max_entries == max(1 << 20, (64 if tile == 8 else 16) * 10)
+
+
+def test_batch_plan_offsets(nat):
+    """Clip table: Gaussians side by side, tiles and images one after another."""
+    sizes = [(640, 360, 2000), (17, 9, 0), (1280, 720, 5000), (1, 1, 3)]
+    p, clips = nat.plan_init_batch(sizes)
+    assert p.num_clips == 4 and p.n == 7003 and p.width == 0 and p.height == 0
+    q, qc = nat.plan_init_batch([(100, 70, 5)])  # one clip: a single-frame plan
+    assert (q.width, q.height, q.tiles_x, q.tiles_y) == (100, 70, 7, 5)
+    g, t, px = 0, 0, 0
+    for c, (w, h, n) in zip(clips, sizes):
+        assert (c.width, c.height, c.n) == (w, h, n)
+        assert (c.tiles_x, c.tiles_y) == (-(-w // 16), -(-h // 16))
+        assert (c.g_off, c.tile_off, c.pix_off) == (g, t, 3 * px)
+        g, t, px = g + n, t + c.tiles_x * c.tiles_y, px + w * h
+    assert p.num_tiles == t and p.pixels == px
+    offs = list(p.off)[:18]
+    assert all(o % 256 == 0 for o in offs) and offs == sorted(offs)
+
+
+def test_batch_plan_rejects_bad_clips(nat):
+    for sizes in ([], [(0, 5, 1)], [(5, 5, -1)]):
+        with pytest.raises((nat.Gs2dError, ValueError)):
+            if not sizes:
+                p = nat.Plan()
+                nat.check(nat.load().gs2d_plan_init_batch(ctypes.byref(p), None, 0, 0, None))
+            else:
+                nat.plan_init_batch(sizes)
+    p, clips = nat.plan_init_batch([(32, 32, 4), (16, 16, 2)])
+    clips[1].tile_off += 1                      # not the table the plan was laid out from
     with pytest.raises(nat.Gs2dError):
-        nat.plan_init(64, 64, 10, 0, c)
+        nat.ws_set_clips(p, 0x1000, clips, 0)
+
+
+def test_autotune_ws_bytes_covers_every_candidate(nat):
+    sizes = [(640, 360, 2000), (320, 200, 800)]
+    most = nat.autotune_ws_bytes(sizes, [8, 16, 32])
+    for t in (8, 16, 32):
+        c = nat.default_config()
+        c.tile = t
+        p, _ = nat.plan_init_batch(sizes, 0, c)
+        assert p.ws_bytes <= most
+    assert nat.autotune_ws_bytes(sizes, [12]) == 0
+
+
+def test_plan_rejects_bad_config(nat):
+    for tile, stage, launch in ((12, 64, 0), (16, 48, 0), (64, 64, 0), (16, 64, 2)):
+        c = nat.default_config()
+        c.tile, c.stage, c.launch = tile, stage, launch
+        with pytest.raises(nat.Gs2dError):
+            nat.plan_init(64, 64, 10, 0, c)
     c = nat.default_config()
     c.sigma_cut = -1.0
     with pytest.raises(nat.Gs2dError):

@@ -1,0 +1,275 @@
+"""Render schedules (tile 8/16/32, stage 32/64/128), batches of clips, the
+batched encode and the autotuner, through the C ABI.
+
+The schedule may change nothing but the order of FP32 additions inside a tile,
+so every schedule is held to the same oracle bars as the default one (keys,
+order and ranges bit-exact in the schedule's own tiling).  A batch computes
+each clip exactly as the clip alone would: same tiles, same per-tile order,
+same per-Gaussian reduction order, the clip's own loss -- so batched results
+are compared with single-clip results bit for bit.
+"""
+
+import numpy as np
+import pytest
+
+from gs2d_inputs import random_gaussians, smooth_noise_target
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 1e-5
+GRAD_REL = 1e-3
+
+SCHEDULES = [(8, 32, 0), (8, 128, 1), (16, 32, 1), (16, 128, 0), (32, 32, 0), (32, 64, 1),
+             (32, 128, 0), (16, 64, 1)]
+
+
+@pytest.fixture(scope="module")
+def gs():
+    from paper_2505_09324_gb300 import _native, build
+    build.build()
+    _native.load()
+    import paper_2505_09324_gb300 as pkg
+    return pkg
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def check_image(img_gpu, ref, lo, hi, tol=IMG_TOL):
+    g = img_gpu.detach().cpu().numpy().astype(np.float64)
+    worst = max(((ref + lo - tol) - g).max(initial=0.0), (g - (ref + hi + tol)).max(initial=0.0))
+    assert worst <= 0.0, f"image off by {worst + tol:.3e} beyond the interval"
+
+
+def check_grads(g_gpu, ref, unc, rel=GRAD_REL):
+    g = g_gpu.detach().cpu().numpy().astype(np.float64)
+    rms = np.sqrt(np.mean(ref * ref, axis=1, keepdims=True))
+    bound = rel * np.abs(ref) + rel * rms + unc
+    bad = np.abs(g - ref) > bound
+    assert not bad.any(), f"{bad.sum()} gradient entries off"
+
+
+def loss_bound(ref_img, lo, hi, target, tol=IMG_TOL):
+    e = tol + np.maximum(-lo, hi)
+    d = np.abs(ref_img - np.asarray(target, np.float64))
+    m = ref_img.size
+    return (2 * np.sum(d * e) + np.sum(e * e)) / m + 1e-5 * np.sum(d * d) / m
+
+
+def oracle_bins(oracle, p, W, H, tile):
+    cfg = oracle.Config(tile=tile)
+    keys, ranges = oracle.sorted_keys(p, W, H, cfg)
+    _, count, total = oracle.tile_rects(p, W, H, cfg)
+    return keys, ranges, count, total
+
+
+def dense_case(W, H, n, seed):
+    """Random Gaussians plus a cluster that puts hundreds into a few tiles
+    (lists longer than every stage size)."""
+    p = random_gaussians(n, W, H, seed=seed)
+    g = np.random.Generator(np.random.PCG64(seed + 100))
+    k = n // 2
+    p[0, :k] = g.uniform(W / 2 - 6, W / 2 + 6, k)
+    p[1, :k] = g.uniform(H / 2 - 6, H / 2 + 6, k)
+    p[5:8, :k] *= 0.05
+    return p
+
+
+# ---------------------------------------------------------------------------
+# schedules on one frame
+
+@pytest.mark.parametrize("tile,stage,launch", SCHEDULES)
+def test_schedule_bins_bit_exact(gs, oracle, tile, stage, launch):
+    W, H, n = 100, 70, 400
+    p = dense_case(W, H, n, seed=3)
+    cfg = gs.RasterConfig(tile=tile, stage=stage, launch=launch)
+    r = gs.GaussianRasterizer(W, H, n, config=cfg)
+    r.prepare(to_dev(p))
+    got = r.read_bins()
+    keys, ranges, count, total = oracle_bins(oracle, p, W, H, tile)
+    assert got["n_entries"] == total
+    np.testing.assert_array_equal(got["keys"].astype(np.uint64), keys >> np.uint64(32))
+    np.testing.assert_array_equal(got["values"].astype(np.uint64), keys & np.uint64(0xFFFFFFFF))
+    np.testing.assert_array_equal(got["ranges"], ranges)
+    np.testing.assert_array_equal(got["counts"], count)
+
+
+@pytest.mark.parametrize("tile,stage,launch", SCHEDULES)
+def test_schedule_render_l2_matches_oracle(gs, oracle, tile, stage, launch):
+    W, H, n = 100, 70, 400
+    p = dense_case(W, H, n, seed=5)
+    target = smooth_noise_target(W, H, seed=6)
+    cfg = gs.RasterConfig(tile=tile, stage=stage, launch=launch)
+    r = gs.GaussianRasterizer(W, H, n, config=cfg)
+    r.prepare(to_dev(p))
+    grads, loss, img = r.render_l2(to_dev(p), to_dev(target), want_image=True)
+    res = oracle.loss_and_grad(p, target)
+    check_image(img, res["img"], res["amb_lo"], res["amb_hi"])
+    assert abs(float(loss[0]) - res["loss"]) <= loss_bound(res["img"], res["amb_lo"],
+                                                           res["amb_hi"], target)
+    check_grads(grads, res["grad"], res["grad_unc"])
+    # the separate forward and backward calls agree with the fused one
+    check_image(r.render_fwd(), res["img"], res["amb_lo"], res["amb_hi"])
+    dimg = res["dimg"]
+    gref, unc = oracle.render_grad(p, W, H, dimg, uncertainty=True)
+    check_grads(r.render_bwd(to_dev(p), to_dev(dimg)), gref, unc)
+
+
+def test_persistent_queue_repeats_exactly(gs):
+    """Back-to-back persistent launches reuse the queue counter (reset by the
+    last block of each launch): results repeat bit for bit."""
+    W, H, n = 256, 256, 2000
+    p = to_dev(random_gaussians(n, W, H, seed=0))
+    t = to_dev(smooth_noise_target(W, H, seed=1))
+    for tile, launch in ((8, 0), (16, 0), (32, 0), (16, 1)):
+        r = gs.GaussianRasterizer(W, H, n, config=gs.RasterConfig(tile=tile, launch=launch))
+        r.prepare(p)
+        imgs = [r.render_fwd().clone() for _ in range(3)]
+        g1, _, _ = r.render_l2(p, t)
+        g1 = g1.clone()
+        g2, _, _ = r.render_l2(p, t)
+        for im in imgs[1:]:
+            assert torch.equal(im, imgs[0])
+        assert torch.equal(g1, g2)
+        assert r.status() == 0
+
+
+# ---------------------------------------------------------------------------
+# batches
+
+BATCH = [(100, 70, 300, 11), (33, 17, 40, 5), (64, 64, 250, 7), (1, 1, 1, 2), (48, 40, 0, 3),
+         (130, 45, 500, 9)]
+
+
+def batch_inputs(sizes_seeds):
+    ps = [dense_case(W, H, n, seed) if n >= 100 else random_gaussians(n, W, H, seed=seed)
+          for (W, H, n, seed) in sizes_seeds]
+    ts = [smooth_noise_target(W, H, seed=seed + 50) for (W, H, _, seed) in sizes_seeds]
+    return ps, ts
+
+
+@pytest.mark.parametrize("tile,stage", [(16, 64), (8, 32), (32, 128)])
+def test_batch_bins_bit_exact(gs, oracle, tile, stage):
+    ps, ts = batch_inputs(BATCH)
+    sizes = [(W, H, n) for (W, H, n, _) in BATCH]
+    b = gs.BatchRasterizer(sizes, config=gs.RasterConfig(tile=tile, stage=stage))
+    b.prepare(b.pack_params([to_dev(p) for p in ps]))
+    got = b.read_bins()
+    # expected: the clips' own sorted lists, one after another, in batch numbering
+    keys, vals, ranges, counts = [], [], [], []
+    e0 = 0
+    for c, ((W, H, n, _), p) in enumerate(zip(BATCH, ps)):
+        k, rg, cnt, total = oracle_bins(oracle, p, W, H, tile)
+        clip = b.clips[c]
+        keys.append((k >> np.uint64(32)) + np.uint64(clip.tile_off))
+        vals.append((k & np.uint64(0xFFFFFFFF)) + np.uint64(clip.g_off))
+        rg = rg.astype(np.int64)
+        nz = rg[:, 1] > rg[:, 0]
+        rg[nz] += e0
+        ranges.append(rg)
+        counts.append(cnt)
+        e0 += total
+    assert got["n_entries"] == e0
+    np.testing.assert_array_equal(got["keys"].astype(np.uint64), np.concatenate(keys))
+    np.testing.assert_array_equal(got["values"].astype(np.uint64), np.concatenate(vals))
+    np.testing.assert_array_equal(got["ranges"], np.concatenate(ranges))
+    np.testing.assert_array_equal(got["counts"], np.concatenate(counts))
+
+
+@pytest.mark.parametrize("tile,stage,launch", [(16, 64, 0), (8, 128, 1), (32, 32, 0)])
+def test_batch_render_l2_matches_oracle_and_single_clips(gs, oracle, tile, stage, launch):
+    ps, ts = batch_inputs(BATCH)
+    sizes = [(W, H, n) for (W, H, n, _) in BATCH]
+    cfg = gs.RasterConfig(tile=tile, stage=stage, launch=launch)
+    b = gs.BatchRasterizer(sizes, config=cfg)
+    P = b.pack_params([to_dev(p) for p in ps])
+    T = b.pack_images([to_dev(t) for t in ts])
+    b.prepare(P)
+    grads, loss, img = b.render_l2(P, T, want_image=True)
+    clip_losses = b.clip_losses()
+    total = 0.0
+    for c, ((W, H, n, _), p, t) in enumerate(zip(BATCH, ps, ts)):
+        g0 = b.offsets[c]
+        res = oracle.loss_and_grad(p, t)
+        check_image(b.clip_view(img, c), res["img"], res["amb_lo"], res["amb_hi"])
+        bound = loss_bound(res["img"], res["amb_lo"], res["amb_hi"], t)
+        assert abs(clip_losses[c][0] - res["loss"]) <= bound
+        total += res["loss"]
+        if n:
+            check_grads(grads[:, g0:g0 + n], res["grad"], res["grad_unc"])
+        # the clip alone gives the same bits
+        r = gs.GaussianRasterizer(W, H, n, config=cfg)
+        r.prepare(to_dev(p))
+        g1, l1, im1 = r.render_l2(to_dev(p), to_dev(t), want_image=True)
+        assert torch.equal(im1, b.clip_view(img, c))
+        assert torch.equal(g1, grads[:, g0:g0 + n])
+        assert float(l1[0]) == clip_losses[c][0] and float(l1[1]) == clip_losses[c][1]
+    assert abs(float(loss[0]) - total) <= 1e-5 * total + 1e-7
+
+
+def test_encode_batch_equals_encode_frame_per_clip(gs):
+    ps, ts = batch_inputs(BATCH)
+    sizes = [(W, H, n) for (W, H, n, _) in BATCH]
+    b = gs.BatchRasterizer(sizes)
+    P = b.pack_params([to_dev(p) for p in ps])
+    T = b.pack_images([to_dev(t) for t in ts])
+    iters = 30
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        psnr = b.encode_batch(T, P, iters, stream=stream)
+    stream.synchronize()
+    for c, ((W, H, n, _), p, t) in enumerate(zip(BATCH, ps, ts)):
+        r = gs.GaussianRasterizer(W, H, n)
+        q = to_dev(p)
+        with torch.cuda.stream(stream):
+            out = r.encode_frame(to_dev(t), q, iters, target_psnr=0.0, check_every=iters,
+                                 stream=stream)
+        stream.synchronize()
+        assert out["iters"] == iters
+        g0 = b.offsets[c]
+        assert torch.equal(q, P[:, g0:g0 + n]), f"clip {c} differs from its own encode"
+        # the reported PSNR is that of the fitted Gaussians
+        r.prepare(q)
+        _, l2, _ = r.render_l2(q, to_dev(t))
+        mse = float(l2[1])
+        expect = 10 * np.log10(1 / mse) if mse > 0 else np.inf
+        assert abs(psnr[c] - expect) <= 1e-4 * abs(expect) + 1e-4
+
+
+def test_autotune_picks_a_measured_candidate(gs):
+    sizes = [(320, 180, 1500), (160, 90, 400)]
+    ps = [to_dev(random_gaussians(n, W, H, seed=k)) for k, (W, H, n) in enumerate(sizes)]
+    ts = [to_dev(smooth_noise_target(W, H, seed=k + 5)) for k, (W, H, _) in enumerate(sizes)]
+    P = torch.cat(ps, dim=1).contiguous()
+    T = torch.cat([t.reshape(-1) for t in ts]).contiguous()
+    before = P.clone()
+    res = gs.autotune(sizes, P, T, reps=3, cache=False)
+    assert torch.equal(P, before)  # params untouched
+    ms = res["ms"]
+    assert len(ms) == 18 and all(v > 0 for v in ms.values())
+    assert (res["tile"], res["stage"], res["launch"]) in ms
+    assert ms[(res["tile"], res["stage"], res["launch"])] == min(ms.values())
+    # a batch planned with the chosen schedule renders like the default one
+    b0 = gs.BatchRasterizer(sizes)
+    b1 = gs.BatchRasterizer(sizes, config=res["config"])
+    for b in (b0, b1):
+        b.prepare(P)
+    i0 = b0.render_fwd()
+    i1 = b1.render_fwd()
+    assert float((i0 - i1).abs().max()) <= 1e-5
+
+
+def test_one_clip_batch_is_the_single_frame_plan(gs):
+    W, H, n = 200, 120, 900
+    p = to_dev(dense_case(W, H, n, seed=21))
+    t = to_dev(smooth_noise_target(W, H, seed=22))
+    r = gs.GaussianRasterizer(W, H, n)
+    b = gs.BatchRasterizer([(W, H, n)])
+    r.prepare(p)
+    b.prepare(p)
+    g1, l1, i1 = r.render_l2(p, t, want_image=True)
+    g2, l2, i2 = b.render_l2(p, t.reshape(-1), want_image=True)
+    assert r.read_bins()["n_entries"] == b.read_bins()["n_entries"] > 0
+    assert torch.equal(g1, g2) and torch.equal(l1, l2) and torch.equal(i1.reshape(-1), i2)

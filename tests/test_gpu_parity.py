@@ -221,27 +221,50 @@ def test_render_l2_matches_oracle(gs, oracle, name, W, H, n, seed):
     check_grads(grads, res["grad"], res["grad_unc"])
 
 
-def test_full_size_1080p_sampled(gs, oracle):
-    """Config-2 size (1920x1080, 20k Gaussians) in the launch configuration the
-    benchmark times: sampled pixels of the render and sampled Gaussians of the
-    fused L2 gradient against the oracle."""
+@pytest.fixture(scope="module")
+def full_size_case(oracle):
+    """The benchmark's workload (1920x1080 conferencing frame, 20k Gaussians from
+    the oracle's ROI initialiser, background positions of seed 11) with oracle
+    references at sampled pixels and for sampled Gaussians."""
+    from gs2d_inputs import background_positions
+    from oracle import superpixel
     W, H, n = 1920, 1080, 20000
     frame, mask = conferencing_frame(W, H, seed=1)
-    p = conferencing_gaussians(frame, mask, n, seed=1)
-    r = gs.GaussianRasterizer(W, H, n)
-    r.prepare(to_dev(p))
-    grads, loss, img = r.render_l2(to_dev(p), to_dev(frame), want_image=True)
+    bg = background_positions(mask, n, seed=11)
+    p = superpixel.roi_init(frame, mask, n, 0.7, bg.T.astype(np.float64))[0].astype(np.float32)
     g = np.random.Generator(np.random.PCG64(77))
     xy = np.stack([g.integers(0, W, 3000), g.integers(0, H, 3000)], axis=1)
-    ref, lo, hi = oracle.render_pixels(p, xy, ambiguity=True)
-    gi = img.cpu().numpy()[:, xy[:, 1], xy[:, 0]].astype(np.float64)
-    assert np.all(gi >= ref + lo - IMG_TOL) and np.all(gi <= ref + hi + IMG_TOL)
+    pix = oracle.render_pixels(p, xy, ambiguity=True)
     which = np.sort(g.choice(n, 300, replace=False))
     res = oracle.loss_and_grad(p, frame, fast=True, which=which)
+    return {"W": W, "H": H, "n": n, "frame": frame, "p": p, "xy": xy, "pix": pix,
+            "which": which, "res": res}
+
+
+FULL_SCHEDULES = [(t, s, la) for t in (8, 16, 32) for s in (32, 64, 128) for la in (0, 1)]
+
+
+@pytest.mark.parametrize("tile,stage,launch", FULL_SCHEDULES)
+def test_full_size_1080p_sampled(gs, full_size_case, tile, stage, launch):
+    """Config-2 size (1920x1080, 20k Gaussians) in every launch configuration the
+    benchmark's autotuner may pick: sampled pixels of the render and sampled
+    Gaussians of the fused L2 gradient against the oracle."""
+    c = full_size_case
+    W, H, n, frame, p = c["W"], c["H"], c["n"], c["frame"], c["p"]
+    cfg = gs.RasterConfig(tile=tile, stage=stage, launch=launch)
+    r = gs.GaussianRasterizer(W, H, n, config=cfg)
+    r.prepare(to_dev(p))
+    grads, loss, img = r.render_l2(to_dev(p), to_dev(frame), want_image=True)
+    assert r.status() == 0
+    xy = c["xy"]
+    ref, lo, hi = c["pix"]
+    gi = img.cpu().numpy()[:, xy[:, 1], xy[:, 0]].astype(np.float64)
+    assert np.all(gi >= ref + lo - IMG_TOL) and np.all(gi <= ref + hi + IMG_TOL)
+    res = c["res"]
     assert abs(float(loss[0]) - res["loss"]) <= loss_bound(res["img"], res["amb_lo"],
                                                            res["amb_hi"], frame)
     # RMS floor from all Gaussians' oracle gradient would need them all; use the sample
-    check_grads(grads, res["grad"], res["grad_unc"], which=which)
+    check_grads(grads, res["grad"], res["grad_unc"], which=c["which"])
 
 
 def test_capacity_overflow_is_reported(gs, oracle):
