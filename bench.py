@@ -76,6 +76,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-sequence", action="store_true")
+    ap.add_argument("--seq-frames", type=int, default=60)
+    ap.add_argument("--seq-iters", type=int, default=300)
     ap.add_argument("--batch-clips", type=int, default=32)
     ap.add_argument("--batch-frames", type=int, default=2)
     ap.add_argument("--batch-iters", type=int, default=300)
@@ -295,6 +298,34 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def measure_sequence(args, dev, rast, params0):
+    """Frame sequence of the moving-subject scene at the benchmark size
+    (subject translating 0-4 px and rotating 0-1 degree per frame): frame 0
+    from the ROI initialisation, every later frame warm-started from the
+    previous frame's fit, `seq_iters` iterations per frame."""
+    import torch
+
+    from gs2d_inputs import conferencing_frame, random_motion
+    from paper_2505_09324_gb300 import encode_sequence
+
+    mo = random_motion(SEED + 1)
+    frames = (torch.from_numpy(conferencing_frame(W, H, seed=SEED, t=t, motion=mo)[0]).to(dev)
+              for t in range(args.seq_frames))
+    p = params0.clone()
+    side = torch.cuda.Stream(dev)
+    with torch.cuda.stream(side):
+        recs = encode_sequence(rast, frames, p, args.seq_iters, args.seq_iters, stream=side)
+    side.synchronize()
+    later = recs[1:] or recs
+    return {"frames": len(recs), "iters_per_frame": args.seq_iters,
+            "frame0": recs[0],
+            "warm_s_per_frame_mean": statistics.fmean(r["seconds"] for r in later),
+            "warm_psnr_min": min(r["psnr"] for r in later),
+            "warm_psnr_mean": statistics.fmean(r["psnr"] for r in later),
+            "motion": {"v_px_per_frame": mo.v, "omega_deg_per_frame": mo.omega},
+            "timing": "wall clock per gs2d_encode_frame call (graph replays, one PSNR check)"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -491,6 +522,7 @@ def run_ours(args):
                   "plain_random_init": rnd}
 
     batch = None if args.no_batch else measure_batch(args, dev)
+    seq = None if args.no_sequence else measure_sequence(args, dev, rast, params0)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -526,7 +558,7 @@ def run_ours(args):
                                                       for (a, b, c), v in tuned["ms"].items()}},
                 "pairs": {"listed_first": pairs0, "hits_first": hits0, "listed_last": pairs1,
                           "hits_last": hits1},
-                "encode": encode, "batch": batch}
+                "encode": encode, "batch": batch, "sequence": seq}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

@@ -8,7 +8,7 @@ the C ABI of ``include/gs2d.h``; this package is a thin binding over it.
 """
 
 from .raster import (BatchRasterizer, GaussianRasterizer, RasterConfig, adam_step,  # noqa: F401
-                     autotune, roi_init)
+                     autotune, encode_sequence, roi_init)
 
 __all__ = ["BatchRasterizer", "GaussianRasterizer", "RasterConfig", "adam_step", "autotune",
-           "roi_init"]
+           "encode_sequence", "roi_init"]

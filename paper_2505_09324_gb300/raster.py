@@ -153,6 +153,28 @@ class GaussianRasterizer:
         return {"status": st, "iters": done, "psnr": final, "trace": trace}
 
 
+def encode_sequence(rast: GaussianRasterizer, frames, params: torch.Tensor, iters_first: int,
+                    iters_next: int, stream=None):
+    """Fits a frame sequence with inter-frame reuse (Sec. 3.2: P-frames start
+    from the previous frame's optimised Gaussians): frame 0 for ``iters_first``
+    iterations from ``params`` (an initialiser's output), every later frame
+    for ``iters_next`` iterations from the previous frame's fit; the Adam
+    moments restart per frame.  ``frames`` yields [3, H, W] float32 CUDA
+    tensors.  ``params`` is updated in place (ends as the last frame's fit).
+    Returns one {"iters", "psnr", "seconds"} record per frame (wall clock
+    around each gs2d_encode_frame call, which synchronises the stream)."""
+    import time
+    out = []
+    adam = (torch.empty_like(params), torch.empty_like(params))
+    for k, frame in enumerate(frames):
+        iters = iters_first if k == 0 else iters_next
+        t0 = time.perf_counter()
+        r = rast.encode_frame(frame, params, iters, target_psnr=0.0, check_every=iters,
+                              adam_state=adam, stream=stream)
+        out.append({"iters": r["iters"], "psnr": r["psnr"], "seconds": time.perf_counter() - t0})
+    return out
+
+
 def roi_init(frame: torch.Tensor, mask: torch.Tensor, n: int, roi_frac: float,
              bg_xy: torch.Tensor, stream=None):
     """Region-of-interest superpixel initialiser (gs2d_roi_init).  frame:
