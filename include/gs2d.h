@@ -314,6 +314,27 @@ gs2d_status gs2d_autotune(gs2d_clip* clips, int32_t num_clips, int64_t max_entri
                           int32_t num_launches, int32_t reps, float* ms, int32_t* best_tile,
                           int32_t* best_stage, int32_t* best_launch, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned initialiser (Sec. 3.2 B: a regressor from the frame to the N
+ * Gaussians' parameters, trained with a Chamfer loss on the means).  Its
+ * convolutions run as GEMMs on the BF16 tensor cores.
+ * ------------------------------------------------------------------------- */
+
+/* C[M][N] = A[M][K] . B[N][K]^T (+ bias[N], then max(., 0) if relu) with BF16
+ * A and B (device, row-major, K contiguous, leading dimensions lda, ldb in
+ * elements, multiples of 8; 16-byte aligned), FP32 accumulation, output
+ * either FP32 (out_f32) or BF16 (out_bf16), exactly one non-NULL, leading
+ * dimension ldc.  splits > 1 splits K over thread blocks; partial (device,
+ * gs2d_gemm_partial_bytes bytes) then holds FP32 partial sums that a second
+ * kernel adds in split order (deterministic).  status: device int32 or NULL;
+ * a block whose pipeline stalls for more than a second sets it to
+ * GS2D_ERR_TIMEOUT and leaves its output tile unwritten. */
+gs2d_status gs2d_gemm_bf16(const void* A, int32_t lda, const void* B, int32_t ldb, int32_t M,
+                           int32_t N, int32_t K, const float* bias, int32_t relu, float* out_f32,
+                           void* out_bf16, int32_t ldc, int32_t splits, float* partial,
+                           int32_t* status, void* stream);
+uint64_t gs2d_gemm_partial_bytes(int32_t M, int32_t N, int32_t ldc, int32_t K, int32_t splits);
+
 /* Copies the sorted list state to host memory for inspection (tests and
  * tools): n_entries (host, int64), keys (host, may be NULL: tile ids of the
  * sorted list, max_keys entries at most), values (host, may be NULL: Gaussian

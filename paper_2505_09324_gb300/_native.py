@@ -28,6 +28,7 @@ EXPORTS = (
     "gs2d_render_bwd", "gs2d_render_l2",
     "gs2d_adam_step", "gs2d_encode_frame", "gs2d_clip_losses", "gs2d_encode_batch",
     "gs2d_autotune_ws_bytes", "gs2d_autotune",
+    "gs2d_gemm_bf16", "gs2d_gemm_partial_bytes",
     "gs2d_read_bins", "gs2d_count_pairs", "gs2d_ws_status",
     "gs2d_roi_init_scratch_bytes", "gs2d_roi_init",
     "gs2d_last_error",
@@ -125,6 +126,9 @@ def load(build_if_missing: bool = False):
             "gs2d_roi_init": (i32, [P, P, i32, i32, i32, f32, P, P, ctypes.POINTER(i32), P,
                                     ctypes.c_uint64, P]),
             "gs2d_last_error": (i32, [ctypes.c_char_p, ctypes.c_size_t]),
+            "gs2d_gemm_bf16": (i32, [P, i32, P, i32, i32, i32, i32, P, i32, P, P, i32, i32, P, P,
+                                     P]),
+            "gs2d_gemm_partial_bytes": (ctypes.c_uint64, [i32, i32, i32, i32, i32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -322,3 +326,11 @@ def count_pairs(plan: Plan, ws: int, stream: int):
 
 def ws_status(plan: Plan, ws: int, reset: bool, stream: int) -> int:
     return int(load().gs2d_ws_status(ctypes.byref(plan), _p(ws), int(reset), _p(stream)))
+
+
+def gemm_bf16(A: int, lda: int, B: int, ldb: int, M: int, N: int, K: int, bias: int, relu: bool,
+              out_f32: int, out_bf16: int, ldc: int, splits: int, partial: int, status: int,
+              stream: int):
+    check(load().gs2d_gemm_bf16(_p(A), lda, _p(B), ldb, M, N, K, _p(bias), int(relu), _p(out_f32),
+                                _p(out_bf16), ldc, splits, _p(partial), _p(status), _p(stream)),
+          "gs2d_gemm_bf16")

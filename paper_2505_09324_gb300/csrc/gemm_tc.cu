@@ -1,0 +1,412 @@
+// BF16 tensor-core GEMM on the 5th-generation tensor cores (tcgen05), the dense
+// contraction of the learned initialiser's convolutions (forward, weight
+// gradient and input gradient are each one GEMM over an im2col operand):
+//
+//   C[M][N] = A[M][K] . B[N][K]^T      A, B bf16, both K-contiguous (K-major);
+//                                       FP32 accumulation in tensor memory.
+//
+// One CTA computes a 128 x BN tile (BN = 32 ... 256) over a range of K:
+//   warp 0, one lane   TMA producer: 128 x 64 A and BN x 64 B boxes per stage
+//                      into 128-byte-swizzled shared memory, STAGES deep;
+//   warp 1, one lane   MMA issuer: four 128 x BN x 16 tcgen05.mma per stage,
+//                      a tcgen05.commit per stage frees the stage, one more
+//                      signals the finished accumulator;
+//   warps 0-3          epilogue: tcgen05.ld of the warp's 32 accumulator rows
+//                      (TMEM lanes), bias, ReLU, store as FP32 or BF16.
+// Long K is split over gridDim.z (split-K): each split writes an FP32 partial
+// tile and k_splitk_reduce sums the splits in a fixed order (deterministic).
+//
+// Every wait on an mbarrier is bounded in time (%globaltimer, 1 s): on a
+// timeout the kernel records GS2D_ERR_TIMEOUT in the caller's status word,
+// skips the rest of its work, still frees its tensor memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <stdio.h>
+
+#include <mutex>
+
+#include "gs2d_internal.cuh"
+#include "tc_gemm.cuh"
+
+namespace gs2d {
+namespace {
+
+constexpr int kBM = 128;    // accumulator rows (TMEM lanes)
+constexpr int kBK = 64;     // K per stage: one 128-byte swizzle row of bf16
+constexpr int kStages = 4;
+constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Waits for the phase of the given parity to complete; false after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_test(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    for (int i = 0; i < 64; i++)
+      if (mbar_test(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand in the 128-byte swizzle
+// layout (8-row atoms of 1024 bytes; stride between atoms 1024 bytes; the
+// leading-dimension offset is unused for this layout), descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
+         ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+template <int BN>
+struct GemmShape {
+  static constexpr int kTmemCols = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
+  static constexpr int kABytes = kBM * kBK * 2;  // 16 KB
+  static constexpr int kBBytes = BN * kBK * 2;
+  static constexpr int kStageBytes = kABytes + kBBytes;
+  static constexpr int kSmem = kStages * kStageBytes + 1024;  // + alignment slack
+};
+
+template <int BN>
+__global__ void __launch_bounds__(128, 1)
+k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+            TcGemmArgs g) {
+  using Sh = GemmShape<BN>;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], accum;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+  const int kt0 = blockIdx.z * g.kt_per_split;
+  const int nk = min(g.num_kt, kt0 + g.kt_per_split) - kt0;  // >= 1 (host)
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; s++) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&accum, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s_tmem)),
+                 "r"(Sh::kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+
+  if (warp == 0 && lane == 0) {
+    // producer
+    for (int i = 0; i < nk; i++) {
+      const int s = i % kStages;
+      const uint32_t ph = (uint32_t)(i / kStages) & 1u;
+      if (!mbar_wait(&empty[s], ph ^ 1u)) {  // the preceding phase: free at first
+        s_fail = 1;
+        break;
+      }
+      uint8_t* a_s = smem + s * Sh::kStageBytes;
+      uint8_t* b_s = a_s + Sh::kABytes;
+      mbar_expect_tx(&full[s], (uint32_t)Sh::kStageBytes);
+      tma_load_2d(a_s, &ta, &full[s], (kt0 + i) * kBK, m0);
+      tma_load_2d(b_s, &tb, &full[s], (kt0 + i) * kBK, n0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    constexpr uint32_t idesc = idesc_bf16(kBM, BN);
+    for (int i = 0; i < nk; i++) {
+      const int s = i % kStages;
+      const uint32_t ph = (uint32_t)(i / kStages) & 1u;
+      if (!mbar_wait(&full[s], ph)) {
+        s_fail = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a_s = smem_u32(smem + s * Sh::kStageBytes);
+      const uint32_t b_s = a_s + Sh::kABytes;
+      const uint64_t ad = sw128_desc(a_s), bd = sw128_desc(b_s);
+#pragma unroll
+      for (int kk = 0; kk < kBK / 16; kk++)  // 16 bf16 = 32 bytes = 2 descriptor units
+        mma_bf16(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+      mma_commit(&empty[s]);
+    }
+    mma_commit(&accum);
+  }
+  __syncwarp();
+
+  // epilogue: warp w holds accumulator rows 32 w ... 32 w + 31
+  const bool ready = mbar_wait(&accum, 0);
+  tc_fence_after();
+  if (!ready) s_fail = 1;
+  __syncthreads();
+  if (!s_fail) {
+    const int row = m0 + warp * 32 + lane;
+    const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+    float* out32 = g.out_f32 ? g.out_f32 + (size_t)blockIdx.z * g.split_stride : nullptr;
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 16) {
+      float v[16];
+      tmem_ld16(tbase + (uint32_t)c, v);
+      if (row < g.M) {
+        const int n = n0 + c;
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+          if (n + j < g.N) {
+            float x = v[j];
+            if (g.bias) x += g.bias[n + j];
+            if (g.relu) x = fmaxf(x, 0.0f);
+            if (g.out_bf16)
+              g.out_bf16[(size_t)row * g.ldc + n + j] = __float2bfloat16_rn(x);
+            else
+              out32[(size_t)row * g.ldc + n + j] = x;
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(Sh::kTmemCols));
+  if (threadIdx.x == 0 && s_fail && g.status) atomicCAS(g.status, 0, (int)GS2D_ERR_TIMEOUT);
+}
+
+// Sum of the split-K partials in split order, then bias, ReLU and the store.
+__global__ void __launch_bounds__(256)
+k_splitk_reduce(TcGemmArgs g, int splits, const float* __restrict__ partial) {
+  const size_t total = (size_t)g.M * g.N;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int m = (int)(i / g.N), n = (int)(i % g.N);
+    const size_t o = (size_t)m * g.ldc + n;
+    float x = 0.0f;
+    for (int z = 0; z < splits; z++) x += partial[(size_t)z * g.split_stride + o];
+    if (g.bias) x += g.bias[n];
+    if (g.relu) x = fmaxf(x, 0.0f);
+    if (g.out_bf16)
+      g.out_bf16[o] = __float2bfloat16_rn(x);
+    else
+      g.out_f32[o] = x;
+  }
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                 const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                 const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn() {
+  static std::once_flag once;
+  static EncodeTiled fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+  });
+  return fn;
+}
+
+// 2D bf16 tensor map of a rows x cols (K-contiguous) matrix with leading
+// dimension ld (elements), box 64 (K) x box_rows, 128-byte swizzle,
+// out-of-range elements read as zero.
+bool make_map(CUtensorMap* map, const void* base, int rows, int cols, int ld, int box_rows) {
+  EncodeTiled fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+template <int BN>
+cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const TcGemmArgs& g,
+                      dim3 grid, cudaStream_t s) {
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(k_gemm_bf16<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                GemmShape<BN>::kSmem);
+  });
+  if (attr != cudaSuccess) return attr;
+  k_gemm_bf16<BN><<<grid, 128, GemmShape<BN>::kSmem, s>>>(ta, tb, g);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Tile width for N columns: one tile up to 256, else the fewest tiles of a
+// multiple of 16 columns.
+int tc_gemm_bn(int n) {
+  if (n <= 32) return 32;
+  if (n <= 64) return 64;
+  if (n <= 96) return 96;
+  if (n <= 128) return 128;
+  if (n <= 192) return 192;
+  if (n <= 256) return 256;
+  const int tiles = (n + 255) / 256;
+  const int per = (n + tiles - 1) / tiles;
+  return per <= 192 ? 192 : 256;
+}
+
+cudaError_t tc_gemm(const TcGemmProblem& pr, cudaStream_t s) {
+  if (pr.M <= 0 || pr.N <= 0 || pr.K <= 0) return cudaSuccess;
+  if (pr.lda % 8 || pr.ldb % 8 || (reinterpret_cast<uintptr_t>(pr.A) & 15) ||
+      (reinterpret_cast<uintptr_t>(pr.B) & 15))
+    return cudaErrorInvalidValue;  // TMA: 16-byte aligned rows
+  const int bn = tc_gemm_bn(pr.N);
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, pr.A, pr.M, pr.K, pr.lda, kBM) ||
+      !make_map(&tb, pr.B, pr.N, pr.K, pr.ldb, bn))
+    return cudaErrorInvalidValue;
+  const int num_kt = (pr.K + kBK - 1) / kBK;
+  int splits = pr.splits < 1 ? 1 : pr.splits;
+  if (splits > num_kt) splits = num_kt;
+  const int per = (num_kt + splits - 1) / splits;
+  splits = (num_kt + per - 1) / per;  // every split gets at least one k-tile
+  TcGemmArgs g;
+  g.M = pr.M;
+  g.N = pr.N;
+  g.num_kt = num_kt;
+  g.kt_per_split = per;
+  g.ldc = pr.ldc;
+  g.bias = pr.bias;
+  g.relu = pr.relu;
+  g.status = pr.status;
+  g.split_stride = (size_t)pr.M * pr.ldc;
+  if (splits == 1) {
+    g.out_f32 = pr.out_f32;
+    g.out_bf16 = pr.out_bf16;
+  } else {
+    if (!pr.partial) return cudaErrorInvalidValue;
+    g.out_f32 = pr.partial;  // FP32 partials, epilogue in the reduction
+    g.out_bf16 = nullptr;
+    g.bias = nullptr;
+    g.relu = 0;
+  }
+  const dim3 grid((pr.M + kBM - 1) / kBM, (pr.N + bn - 1) / bn, splits);
+  cudaError_t e;
+  switch (bn) {
+    case 32: e = launch_bn<32>(ta, tb, g, grid, s); break;
+    case 64: e = launch_bn<64>(ta, tb, g, grid, s); break;
+    case 96: e = launch_bn<96>(ta, tb, g, grid, s); break;
+    case 128: e = launch_bn<128>(ta, tb, g, grid, s); break;
+    case 192: e = launch_bn<192>(ta, tb, g, grid, s); break;
+    default: e = launch_bn<256>(ta, tb, g, grid, s); break;
+  }
+  if (e != cudaSuccess || splits == 1) return e;
+  TcGemmArgs r = g;
+  r.out_f32 = pr.out_f32;
+  r.out_bf16 = pr.out_bf16;
+  r.bias = pr.bias;
+  r.relu = pr.relu;
+  const size_t total = (size_t)pr.M * pr.N;
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
+  k_splitk_reduce<<<blocks, 256, 0, s>>>(r, splits, pr.partial);
+  return cudaGetLastError();
+}
+
+size_t tc_gemm_partial_floats(int M, int N, int ldc, int K, int splits) {
+  const int num_kt = (K + kBK - 1) / kBK;
+  if (splits > num_kt) splits = num_kt;
+  if (splits <= 1) return 0;
+  (void)N;
+  return (size_t)splits * M * ldc;
+}
+
+}  // namespace gs2d

@@ -1,0 +1,41 @@
+// BF16 tcgen05 GEMM (csrc/gemm_tc.cu): C[M][N] = A[M][K] . B[N][K]^T with
+// optional split-K, bias and ReLU; FP32 or BF16 output.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace gs2d {
+
+struct TcGemmArgs {
+  int M, N, num_kt, kt_per_split, ldc;
+  size_t split_stride;     // floats between split partials
+  float* out_f32;          // FP32 output (or the split partials)
+  __nv_bfloat16* out_bf16; // BF16 output (one split only)
+  const float* bias;       // [N] or NULL
+  int relu;
+  int* status;             // device status word (GS2D_ERR_TIMEOUT) or NULL
+};
+
+struct TcGemmProblem {
+  const __nv_bfloat16* A;  // [M][lda], K-contiguous, 16-byte aligned rows
+  int lda;
+  const __nv_bfloat16* B;  // [N][ldb], K-contiguous
+  int ldb;
+  int M, N, K;
+  float* out_f32;          // [M][ldc] or NULL
+  __nv_bfloat16* out_bf16; // [M][ldc] or NULL (exactly one output)
+  int ldc;
+  const float* bias;
+  int relu;
+  int splits;              // split-K factor (1: none)
+  float* partial;          // splits x M x ldc floats when splits > 1
+  int* status;
+};
+
+cudaError_t tc_gemm(const TcGemmProblem& pr, cudaStream_t s);
+int tc_gemm_bn(int n);
+size_t tc_gemm_partial_floats(int M, int N, int ldc, int K, int splits);
+
+}  // namespace gs2d
