@@ -335,6 +335,81 @@ gs2d_status gs2d_gemm_bf16(const void* A, int32_t lda, const void* B, int32_t ld
                            int32_t* status, void* stream);
 uint64_t gs2d_gemm_partial_bytes(int32_t M, int32_t N, int32_t ldc, int32_t K, int32_t splits);
 
+/* Network input: frames (device, B x [3][H][W] float32) and masks (device,
+ * B x [H][W] uint8, or NULL = all zero) -> x (device, [B][H][W][8] BF16 NHWC:
+ * r, g, b, mask, 0, 0, 0, 0; 16-byte aligned). */
+gs2d_status gs2d_cnn_input(const float* frames, const uint8_t* masks, int32_t B, int32_t H,
+                           int32_t W, void* x, void* stream);
+
+/* im2col of x (device, [B][Hi][Wi][C] BF16, C a multiple of 8) for a ks x ks
+ * convolution with stride and zero padding pad: col (device, BF16
+ * [B Ho Wo][ldk], Ho = (Hi + 2 pad - ks) / stride + 1, likewise Wo) with
+ * col[p][(ky ks + kx) C + ci] = x at (oy stride + ky - pad, ox stride + kx -
+ * pad), zero outside the image, 1 at column ks^2 C (the bias column of the
+ * weights) and 0 up to ldk (a multiple of 8, > ks^2 C).  A convolution is then
+ * gs2d_gemm_bf16(col, W) with W [Co][ldk]. */
+gs2d_status gs2d_im2col(const void* x, int32_t B, int32_t Hi, int32_t Wi, int32_t C, int32_t ks,
+                        int32_t stride, int32_t pad, void* col, int32_t ldk, void* stream);
+
+/* Gradient of gs2d_im2col: dx[b][iy][ix][ci] = sum over the taps that read
+ * (iy, ix) of dcol (device, float32 [B Ho Wo][ldk]), multiplied by (act > 0)
+ * when act (device, [B][Hi][Wi][C] BF16, the ReLU output fed to the im2col) is
+ * not NULL (the ReLU backward); dx: device BF16, same shape as act.
+ * Deterministic (a gather, no atomics). */
+gs2d_status gs2d_col2im(const float* dcol, int32_t ldk, int32_t B, int32_t Hi, int32_t Wi,
+                        int32_t C, int32_t ks, int32_t stride, int32_t pad, const void* act,
+                        void* dx, void* stream);
+
+/* out[c][r] = in[r][c] for a BF16 R x C matrix (device; leading dimensions
+ * ld_in >= C, ld_out >= R). */
+gs2d_status gs2d_transpose_bf16(const void* in, int32_t R, int32_t C, int32_t ld_in, void* out,
+                                int32_t ld_out, void* stream);
+
+/* dz = dx * (act > 0) over rows x cols: dx float32, act and dz BF16 (device,
+ * leading dimensions ldx, lda, ldz). */
+gs2d_status gs2d_relu_bwd(const float* dx, int32_t rows, int32_t cols, int32_t ldx,
+                          const void* act, int32_t lda, void* dz, int32_t ldz, void* stream);
+
+/* FP32 master weights w (device [co][ldk]) -> BF16 copy wb ([co][ldk]) and
+ * BF16 transpose wt ([ldk][co]); either output may be NULL. */
+gs2d_status gs2d_cast_weights(const float* w, int32_t co, int32_t ldk, void* wb, void* wt,
+                              void* stream);
+
+/* Head of the learned initialiser.  out (device float32 [B gh gw][ldo]): per
+ * cell of a gh x gw grid of cell_px-pixel cells, `slots` groups of nine
+ * numbers o0 .. o8 (columns 9 s .. 9 s + 8) decoding to one Gaussian:
+ * mu = cell centre + cell_px/2 tanh(o0, o1), l1 = scale exp(o2), l2 = scale o3,
+ * l3 = scale exp(o4) (exponents clamped to [-4, 3]), colour 0.5 + o5..o7,
+ * w = 0.25 + o8.  Each frame keeps the n slots with the largest |w| (ties:
+ * lower slot index first), in slot order: params (device float32,
+ * B x [9][n]) and sel (device int32 B x n, slot = cell slots + s).  Needs
+ * gh gw slots 4 bytes of shared memory (at most 200 KB). */
+gs2d_status gs2d_head_decode(const float* out, int32_t ldo, int32_t B, int32_t gh, int32_t gw,
+                             int32_t slots, int32_t cell_px, float scale, int32_t n,
+                             float* params, int32_t* sel, void* stream);
+uint64_t gs2d_head_smem_bytes(int32_t gh, int32_t gw, int32_t slots);
+
+/* Backward of gs2d_head_decode: dparams (device float32, B x [9][n]) ->
+ * dout (device BF16 [B gh gw][ldo]; zero for unselected slots and unused
+ * columns). */
+gs2d_status gs2d_head_decode_bwd(const float* out, int32_t ldo, int32_t B, int32_t gh,
+                                 int32_t gw, int32_t slots, int32_t cell_px, float scale,
+                                 int32_t n, const int32_t* sel, const float* dparams, void* dout,
+                                 void* stream);
+
+/* Chamfer distance (Sec. 3.2 B) between the predicted means (rows 0, 1 of
+ * params, device float32 B x [9][n]) and target means (rows 0, 1 of
+ * targets, B x [9][m]), per frame: mean over predictions of the squared
+ * distance to the nearest target plus mean over targets of the squared
+ * distance to the nearest prediction (brute force).  loss: device float32[B]
+ * or NULL.  dparams: device B x [9][n] or NULL; rows 0, 1 get
+ * += lambda d(Chamfer)/d(mu) (float atomics: the order of additions varies
+ * between runs).  scratch: device, gs2d_chamfer_scratch_bytes(n, m, B). */
+gs2d_status gs2d_chamfer(const float* params, int32_t n, const float* targets, int32_t m,
+                         int32_t B, float lambda, float* dparams, float* loss, void* scratch,
+                         void* stream);
+uint64_t gs2d_chamfer_scratch_bytes(int32_t n, int32_t m, int32_t B);
+
 /* Copies the sorted list state to host memory for inspection (tests and
  * tools): n_entries (host, int64), keys (host, may be NULL: tile ids of the
  * sorted list, max_keys entries at most), values (host, may be NULL: Gaussian

@@ -28,7 +28,9 @@ EXPORTS = (
     "gs2d_render_bwd", "gs2d_render_l2",
     "gs2d_adam_step", "gs2d_encode_frame", "gs2d_clip_losses", "gs2d_encode_batch",
     "gs2d_autotune_ws_bytes", "gs2d_autotune",
-    "gs2d_gemm_bf16", "gs2d_gemm_partial_bytes",
+    "gs2d_gemm_bf16", "gs2d_gemm_partial_bytes", "gs2d_cnn_input", "gs2d_im2col", "gs2d_col2im",
+    "gs2d_transpose_bf16", "gs2d_relu_bwd", "gs2d_cast_weights", "gs2d_head_decode",
+    "gs2d_head_smem_bytes", "gs2d_head_decode_bwd", "gs2d_chamfer", "gs2d_chamfer_scratch_bytes",
     "gs2d_read_bins", "gs2d_count_pairs", "gs2d_ws_status",
     "gs2d_roi_init_scratch_bytes", "gs2d_roi_init",
     "gs2d_last_error",
@@ -129,6 +131,18 @@ def load(build_if_missing: bool = False):
             "gs2d_gemm_bf16": (i32, [P, i32, P, i32, i32, i32, i32, P, i32, P, P, i32, i32, P, P,
                                      P]),
             "gs2d_gemm_partial_bytes": (ctypes.c_uint64, [i32, i32, i32, i32, i32]),
+            "gs2d_cnn_input": (i32, [P, P, i32, i32, i32, P, P]),
+            "gs2d_im2col": (i32, [P, i32, i32, i32, i32, i32, i32, i32, P, i32, P]),
+            "gs2d_col2im": (i32, [P, i32, i32, i32, i32, i32, i32, i32, i32, P, P, P]),
+            "gs2d_transpose_bf16": (i32, [P, i32, i32, i32, P, i32, P]),
+            "gs2d_relu_bwd": (i32, [P, i32, i32, i32, P, i32, P, i32, P]),
+            "gs2d_cast_weights": (i32, [P, i32, i32, P, P, P]),
+            "gs2d_head_decode": (i32, [P, i32, i32, i32, i32, i32, i32, f32, i32, P, P, P]),
+            "gs2d_head_smem_bytes": (ctypes.c_uint64, [i32, i32, i32]),
+            "gs2d_head_decode_bwd": (i32, [P, i32, i32, i32, i32, i32, i32, f32, i32, P, P, P,
+                                           P]),
+            "gs2d_chamfer": (i32, [P, i32, P, i32, i32, f32, P, P, P, P]),
+            "gs2d_chamfer_scratch_bytes": (ctypes.c_uint64, [i32, i32, i32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -334,3 +348,13 @@ def gemm_bf16(A: int, lda: int, B: int, ldb: int, M: int, N: int, K: int, bias: 
     check(load().gs2d_gemm_bf16(_p(A), lda, _p(B), ldb, M, N, K, _p(bias), int(relu), _p(out_f32),
                                 _p(out_bf16), ldc, splits, _p(partial), _p(status), _p(stream)),
           "gs2d_gemm_bf16")
+
+
+def call(name: str, *args):
+    """Calls a gs2d_* entry point whose arguments are plain ints / floats /
+    device pointers (0 = NULL) and raises on an error status."""
+    fn = getattr(load(), name)
+    conv = []
+    for a, t in zip(args, fn.argtypes):
+        conv.append(_p(a) if t is ctypes.c_void_p else a)
+    check(fn(*conv), name)

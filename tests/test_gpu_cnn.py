@@ -98,3 +98,160 @@ def test_gemm_padded_leading_dimension(nat):
     got = run_gemm(nat, a, b, lda=104, ldc=48)
     ref = cnn.gemm(a, b)
     assert np.all(np.abs(got - ref) <= REL * cnn.gemm_abs(a, b) + 1e-30)
+
+
+# ---------------------------------------------------------------------------
+# convolution helpers and the head
+
+def to_np_bf16(t):
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+def dev_f32(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def bf16_ulp_close(got, ref, ulps=1):
+    """|got - bf16_round(ref)| within `ulps` BF16 units of the value (rounding
+    of an FP32 result that differs from the double-precision one in the last
+    FP32 bits may land on the neighbouring BF16 value)."""
+    r = cnn.bf16_round(ref).astype(np.float64)
+    tol = ulps * np.maximum(np.abs(r), 1e-30) * 2.0 ** -7
+    return np.all(np.abs(got - r) <= tol)
+
+
+def test_cnn_input_layout(nat):
+    from gs2d_inputs import conferencing_frame
+    f, m = conferencing_frame(37, 21, seed=1)
+    x = torch.empty((2, 21, 37, 8), dtype=torch.bfloat16, device="cuda")
+    frames = dev_f32(np.stack([f, f[:, ::-1].copy()]))
+    masks = torch.from_numpy(np.stack([m, ~m]).astype(np.uint8)).cuda()
+    nat.call("gs2d_cnn_input", frames.data_ptr(), masks.data_ptr(), 2, 21, 37, x.data_ptr(), 0)
+    got = to_np_bf16(x)
+    want = np.zeros((2, 21, 37, 8))
+    want[0, ..., :3] = f.transpose(1, 2, 0)
+    want[1, ..., :3] = f[:, ::-1].transpose(1, 2, 0)
+    want[0, ..., 3] = m
+    want[1, ..., 3] = ~m
+    np.testing.assert_array_equal(got, cnn.bf16_round(want).astype(np.float64))
+
+
+@pytest.mark.parametrize("B,H,W,C,ks,st,pad", [(2, 9, 7, 8, 3, 2, 1), (1, 33, 20, 32, 3, 2, 1),
+                                                (3, 5, 6, 16, 1, 1, 0), (1, 8, 8, 8, 3, 1, 1)])
+def test_im2col_and_col2im(nat, B, H, W, C, ks, st, pad):
+    g = np.random.Generator(np.random.PCG64(H * W + C))
+    x = cnn.bf16_round(g.normal(size=(B, H, W, C)))
+    ldk = -(-(ks * ks * C + 1) // 8) * 8
+    Ho, Wo = cnn.out_size(H, ks, st, pad), cnn.out_size(W, ks, st, pad)
+    dx = bf16_dev(x)
+    col = torch.full((B * Ho * Wo, ldk), 7.0, dtype=torch.bfloat16, device="cuda")
+    nat.call("gs2d_im2col", dx.data_ptr(), B, H, W, C, ks, st, pad, col.data_ptr(), ldk, 0)
+    np.testing.assert_array_equal(to_np_bf16(col), cnn.im2col(x, ks, st, pad, ldk))
+    # gradient, with and without the ReLU mask
+    dcol = g.normal(size=(B * Ho * Wo, ldk)).astype(np.float32)
+    act = cnn.bf16_round(g.normal(size=x.shape))
+    ref = cnn.col2im(dcol, x.shape, ks, st, pad)
+    d_dcol, d_act = dev_f32(dcol), bf16_dev(act)  # held: the calls below are asynchronous
+    for use_act in (False, True):
+        out = torch.empty(x.shape, dtype=torch.bfloat16, device="cuda")
+        nat.call("gs2d_col2im", d_dcol.data_ptr(), ldk, B, H, W, C, ks, st, pad,
+                 d_act.data_ptr() if use_act else 0, out.data_ptr(), 0)
+        want = ref * (act > 0) if use_act else ref
+        assert bf16_ulp_close(to_np_bf16(out), want)
+
+
+def test_transpose_relu_bwd_cast(nat):
+    g = np.random.Generator(np.random.PCG64(5))
+    a = cnn.bf16_round(g.normal(size=(70, 45)))
+    out = torch.zeros((45, 72), dtype=torch.bfloat16, device="cuda")
+    d_a = bf16_dev(a)  # device buffers stay referenced until the calls have run
+    nat.call("gs2d_transpose_bf16", d_a.data_ptr(), 70, 45, 45, out.data_ptr(), 72, 0)
+    np.testing.assert_array_equal(to_np_bf16(out)[:, :70], a.T)
+    dx = g.normal(size=(70, 45)).astype(np.float32)
+    dz = torch.zeros((70, 48), dtype=torch.bfloat16, device="cuda")
+    d_dx = dev_f32(dx)
+    nat.call("gs2d_relu_bwd", d_dx.data_ptr(), 70, 45, 45, d_a.data_ptr(), 45, dz.data_ptr(), 48,
+             0)
+    np.testing.assert_array_equal(to_np_bf16(dz)[:, :45], cnn.bf16_round(dx * (a > 0)))
+    w = g.normal(size=(24, 80)).astype(np.float32)
+    wb = torch.empty((24, 80), dtype=torch.bfloat16, device="cuda")
+    wt = torch.empty((80, 24), dtype=torch.bfloat16, device="cuda")
+    d_w = dev_f32(w)
+    nat.call("gs2d_cast_weights", d_w.data_ptr(), 24, 80, wb.data_ptr(), wt.data_ptr(), 0)
+    np.testing.assert_array_equal(to_np_bf16(wb), cnn.bf16_round(w))
+    np.testing.assert_array_equal(to_np_bf16(wt), cnn.bf16_round(w).T)
+
+
+@pytest.mark.parametrize("B,H,W,ci,co", [(2, 40, 33, 8, 32), (1, 24, 30, 32, 64),
+                                         (2, 12, 9, 256, 384)])
+def test_conv_layer_via_im2col_gemm(nat, B, H, W, ci, co):
+    """A stride-2 3 x 3 convolution with bias and ReLU as im2col + tensor-core
+    GEMM (BF16 out) against the direct convolution of the oracle."""
+    g = np.random.Generator(np.random.PCG64(co + H))
+    ks, st, pad = 3, 2, 1
+    ldk = -(-(ks * ks * ci + 1) // 8) * 8
+    x = cnn.bf16_round(g.normal(size=(B, H, W, ci)))
+    w = np.zeros((co, ldk), np.float32)
+    w[:, :ks * ks * ci + 1] = g.normal(size=(co, ks * ks * ci + 1)) / np.sqrt(9 * ci)
+    w = cnn.bf16_round(w)
+    Ho, Wo = cnn.out_size(H, ks, st, pad), cnn.out_size(W, ks, st, pad)
+    P = B * Ho * Wo
+    col = torch.empty((P, ldk), dtype=torch.bfloat16, device="cuda")
+    d_x, d_w = bf16_dev(x), bf16_dev(w)
+    nat.call("gs2d_im2col", d_x.data_ptr(), B, H, W, ci, ks, st, pad, col.data_ptr(), ldk, 0)
+    z = torch.empty((P, co), dtype=torch.bfloat16, device="cuda")
+    st_ = torch.zeros(1, dtype=torch.int32, device="cuda")
+    nat.gemm_bf16(col.data_ptr(), ldk, d_w.data_ptr(), ldk, P, co, ldk, 0, True, 0,
+                  z.data_ptr(), co, 1, 0, st_.data_ptr(), 0)
+    torch.cuda.synchronize()
+    ref = np.maximum(cnn.conv(x, w[:, :ks * ks * ci + 1], ks, st, pad), 0.0).reshape(P, co)
+    scale = cnn.gemm_abs(cnn.im2col(x, ks, st, pad, ldk), w)
+    got = to_np_bf16(z)
+    assert np.all(np.abs(got - ref) <= REL * scale + np.abs(ref) * 2.0 ** -8 + 1e-30)
+
+
+def test_head_decode_select_and_backward(nat):
+    g = np.random.Generator(np.random.PCG64(11))
+    B, gh, gw, slots, ldo, n, cell, scale = 2, 5, 7, 10, 96, 300, 32, 6.0
+    out = (g.normal(size=(B * gh * gw, ldo)) * 0.8).astype(np.float32)
+    out[0, 9 * 3 + 8] = out[0, 9 * 4 + 8]          # a tie in |w|
+    out[5, 2] = 5.0                                 # clamped exponent
+    d_out = dev_f32(out)
+    params = torch.empty((B, 9, n), device="cuda")
+    sel = torch.empty((B, n), dtype=torch.int32, device="cuda")
+    nat.call("gs2d_head_decode", d_out.data_ptr(), ldo, B, gh, gw, slots, cell, scale, n,
+             params.data_ptr(), sel.data_ptr(), 0)
+    ref_p, ref_sel = cnn.head_decode(out, gh, gw, slots, cell, scale, n)
+    np.testing.assert_array_equal(sel.cpu().numpy(), ref_sel)
+    got = params.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(got - ref_p) <= 1e-6 * np.abs(ref_p) + 1e-5)
+    dp = g.normal(size=(B, 9, n)).astype(np.float32)
+    dout = torch.full((B * gh * gw, ldo), 3.0, dtype=torch.bfloat16, device="cuda")
+    d_dp = dev_f32(dp)
+    nat.call("gs2d_head_decode_bwd", d_out.data_ptr(), ldo, B, gh, gw, slots, cell, scale, n,
+             sel.data_ptr(), d_dp.data_ptr(), dout.data_ptr(), 0)
+    ref_d = cnn.head_decode_bwd(out, ref_sel, dp, gh, gw, slots, cell, scale)
+    assert bf16_ulp_close(to_np_bf16(dout), ref_d, ulps=2)
+
+
+def test_chamfer_loss_and_gradient(nat):
+    g = np.random.Generator(np.random.PCG64(12))
+    B, n, m = 2, 700, 500
+    P = np.zeros((B, 9, n), np.float32)
+    Q = np.zeros((B, 9, m), np.float32)
+    P[:, :2] = g.uniform(0, 300, (B, 2, n))
+    Q[:, :2] = g.uniform(0, 300, (B, 2, m))
+    scratch = torch.empty(nat.load().gs2d_chamfer_scratch_bytes(n, m, B), dtype=torch.uint8,
+                          device="cuda")
+    loss = torch.empty(B, device="cuda")
+    dP = torch.zeros((B, 9, n), device="cuda")
+    lam = 0.5
+    d_P, d_Q = dev_f32(P), dev_f32(Q)
+    nat.call("gs2d_chamfer", d_P.data_ptr(), n, d_Q.data_ptr(), m, B, lam, dP.data_ptr(),
+             loss.data_ptr(), scratch.data_ptr(), 0)
+    for b in range(B):
+        ref_l, ref_g = cnn.chamfer(P[b, :2].T, Q[b, :2].T)
+        assert abs(float(loss[b]) - ref_l) <= 1e-5 * ref_l
+        got = dP[b, :2].cpu().numpy().T.astype(np.float64)
+        assert np.all(np.abs(got - lam * ref_g) <= 1e-4 * np.abs(lam * ref_g).max())
+        assert float(dP[b, 2:].abs().max()) == 0.0
