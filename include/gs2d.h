@@ -378,36 +378,41 @@ gs2d_status gs2d_cast_weights(const float* w, int32_t co, int32_t ldk, void* wb,
 /* Head of the learned initialiser.  out (device float32 [B gh gw][ldo]): per
  * cell of a gh x gw grid of cell_px-pixel cells, `slots` groups of nine
  * numbers o0 .. o8 (columns 9 s .. 9 s + 8) decoding to one Gaussian:
- * mu = cell centre + cell_px/2 tanh(o0, o1), l1 = scale exp(o2), l2 = scale o3,
- * l3 = scale exp(o4) (exponents clamped to [-4, 3]), colour 0.5 + o5..o7,
- * w = 0.25 + o8.  Each frame keeps the n slots with the largest |w| (ties:
- * lower slot index first), in slot order: params (device float32,
- * B x [9][n]) and sel (device int32 B x n, slot = cell slots + s).  Needs
- * gh gw slots 4 bytes of shared memory (at most 200 KB). */
+ * mu = cell origin + anchor(s) + cell_px/2 tanh(o0, o1) with slot anchors on a
+ * q x r grid inside the cell (q = ceil(sqrt(slots)), r = ceil(slots / q),
+ * anchor(s) = cell_px ((s mod q + 1/2) / q, (s div q + 1/2) / r)),
+ * l1 = scale exp(o2), l2 = scale o3, l3 = scale exp(o4) (exponents clamped to
+ * [-4, 3]), colour 0.5 + o5..o7, w = 0.25 + o8.  Each frame keeps the n slots
+ * with the largest |w| (ties: lower slot index first), in slot order: params
+ * (device float32 [9][ldp], frame b in columns b n ... b n + n - 1; ldp >= B n:
+ * the batch layout of gs2d_plan_init_batch for equal clips) and sel (device
+ * int32 B x n, slot = cell slots + s).  Needs gh gw slots 4 bytes of shared
+ * memory (at most 200 KB). */
 gs2d_status gs2d_head_decode(const float* out, int32_t ldo, int32_t B, int32_t gh, int32_t gw,
                              int32_t slots, int32_t cell_px, float scale, int32_t n,
-                             float* params, int32_t* sel, void* stream);
+                             float* params, int32_t ldp, int32_t* sel, void* stream);
 uint64_t gs2d_head_smem_bytes(int32_t gh, int32_t gw, int32_t slots);
 
-/* Backward of gs2d_head_decode: dparams (device float32, B x [9][n]) ->
- * dout (device BF16 [B gh gw][ldo]; zero for unselected slots and unused
- * columns). */
+/* Backward of gs2d_head_decode: dparams (device float32 [9][ldp], layout of
+ * params) -> dout (device BF16 [B gh gw][ldo]; zero for unselected slots and
+ * unused columns). */
 gs2d_status gs2d_head_decode_bwd(const float* out, int32_t ldo, int32_t B, int32_t gh,
                                  int32_t gw, int32_t slots, int32_t cell_px, float scale,
-                                 int32_t n, const int32_t* sel, const float* dparams, void* dout,
-                                 void* stream);
+                                 int32_t n, const int32_t* sel, const float* dparams,
+                                 int32_t ldp, void* dout, void* stream);
 
 /* Chamfer distance (Sec. 3.2 B) between the predicted means (rows 0, 1 of
- * params, device float32 B x [9][n]) and target means (rows 0, 1 of
- * targets, B x [9][m]), per frame: mean over predictions of the squared
- * distance to the nearest target plus mean over targets of the squared
- * distance to the nearest prediction (brute force).  loss: device float32[B]
- * or NULL.  dparams: device B x [9][n] or NULL; rows 0, 1 get
- * += lambda d(Chamfer)/d(mu) (float atomics: the order of additions varies
- * between runs).  scratch: device, gs2d_chamfer_scratch_bytes(n, m, B). */
-gs2d_status gs2d_chamfer(const float* params, int32_t n, const float* targets, int32_t m,
-                         int32_t B, float lambda, float* dparams, float* loss, void* scratch,
-                         void* stream);
+ * params, device float32 [9][ldp], frame b in columns b n ...) and target
+ * means (rows 0, 1 of targets, [9][ldq], frame b in columns b m ...), per
+ * frame: mean over predictions of the squared distance to the nearest target
+ * plus mean over targets of the squared distance to the nearest prediction
+ * (brute force).  loss: device float32[B] or NULL.  dparams: device, layout
+ * of params, or NULL; rows 0, 1 get += lambda d(Chamfer)/d(mu) (float
+ * atomics: the order of additions varies between runs).  scratch: device,
+ * gs2d_chamfer_scratch_bytes(n, m, B). */
+gs2d_status gs2d_chamfer(const float* params, int32_t n, int32_t ldp, const float* targets,
+                         int32_t m, int32_t ldq, int32_t B, float lambda, float* dparams,
+                         float* loss, void* scratch, void* stream);
 uint64_t gs2d_chamfer_scratch_bytes(int32_t n, int32_t m, int32_t B);
 
 /* Copies the sorted list state to host memory for inspection (tests and

@@ -147,6 +147,16 @@ def head_select(out, gh: int, gw: int, slots: int, n: int) -> np.ndarray:
     return np.array(sel, dtype=np.int64)
 
 
+def slot_anchor(s: int, slots: int):
+    """Offset of slot s inside its cell, as a fraction of the cell: slots on a
+    q x r grid, q = ceil(sqrt(slots)), r = ceil(slots / q)."""
+    q = 1
+    while q * q < slots:
+        q += 1
+    r = -(-slots // q)
+    return ((s % q) + 0.5) / q, ((s // q) + 0.5) / r
+
+
 def head_decode(out, gh: int, gw: int, slots: int, cell_px: int, scale: float, n: int):
     """Decoded Gaussians of the selected slots, double precision: params
     [B, 9, n] and sel [B, n]."""
@@ -159,10 +169,11 @@ def head_decode(out, gh: int, gw: int, slots: int, cell_px: int, scale: float, n
         for j, slot in enumerate(sel[b]):
             cell, s = divmod(int(slot), slots)
             cy, cx = divmod(cell, gw)
+            ax, ay = slot_anchor(s, slots)
             v = o[b, cell, 9 * s:9 * s + 9]
             params[b, :, j] = [
-                (cx + 0.5) * cell_px + half * np.tanh(v[0]),
-                (cy + 0.5) * cell_px + half * np.tanh(v[1]),
+                (cx + ax) * cell_px + half * np.tanh(v[0]),
+                (cy + ay) * cell_px + half * np.tanh(v[1]),
                 scale * np.exp(np.clip(v[2], EXP_LO, EXP_HI)),
                 scale * v[3],
                 scale * np.exp(np.clip(v[4], EXP_LO, EXP_HI)),

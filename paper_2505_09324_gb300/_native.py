@@ -137,11 +137,11 @@ def load(build_if_missing: bool = False):
             "gs2d_transpose_bf16": (i32, [P, i32, i32, i32, P, i32, P]),
             "gs2d_relu_bwd": (i32, [P, i32, i32, i32, P, i32, P, i32, P]),
             "gs2d_cast_weights": (i32, [P, i32, i32, P, P, P]),
-            "gs2d_head_decode": (i32, [P, i32, i32, i32, i32, i32, i32, f32, i32, P, P, P]),
+            "gs2d_head_decode": (i32, [P, i32, i32, i32, i32, i32, i32, f32, i32, P, i32, P, P]),
             "gs2d_head_smem_bytes": (ctypes.c_uint64, [i32, i32, i32]),
-            "gs2d_head_decode_bwd": (i32, [P, i32, i32, i32, i32, i32, i32, f32, i32, P, P, P,
-                                           P]),
-            "gs2d_chamfer": (i32, [P, i32, P, i32, i32, f32, P, P, P, P]),
+            "gs2d_head_decode_bwd": (i32, [P, i32, i32, i32, i32, i32, i32, f32, i32, P, P, i32,
+                                           P, P]),
+            "gs2d_chamfer": (i32, [P, i32, i32, P, i32, i32, i32, f32, P, P, P, P]),
             "gs2d_chamfer_scratch_bytes": (ctypes.c_uint64, [i32, i32, i32]),
         }
         for name, (res, args) in sig.items():

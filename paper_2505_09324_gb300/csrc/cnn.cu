@@ -278,7 +278,9 @@ extern "C" gs2d_status gs2d_cast_weights(const float* w, int32_t co, int32_t ldk
 // Head: the network's last layer gives, per cell of a gh x gw grid of cell_px
 // pixel cells and per slot s of `slots`, nine numbers o0 .. o8 (columns
 // 9 s ... 9 s + 8 of the cell's row) that decode into one Gaussian:
-//   mu    = cell centre + (cell_px / 2) tanh(o0, o1)
+//   mu    = cell origin + anchor(s) + (cell_px / 2) tanh(o0, o1)
+//           anchor(s) = cell_px ((s mod q + 1/2) / q, (s div q + 1/2) / r),
+//           q = ceil(sqrt(slots)) columns, r = ceil(slots / q) rows
 //   l1    = scale exp(clamp(o2, -4, 3)),  l2 = scale o3,  l3 = scale exp(clamp(o4, -4, 3))
 //   c     = 0.5 + (o5, o6, o7),           w  = 0.25 + o8
 // Each frame keeps the n slots with the largest |w| (ties: lower slot index),
@@ -288,12 +290,20 @@ namespace {
 
 constexpr float kExpLo = -4.0f, kExpHi = 3.0f;
 
-__device__ __forceinline__ void decode_slot(const float* __restrict__ o, int cell, int gw,
-                                            int cell_px, float scale, float g[9]) {
+__host__ __device__ inline int anchor_cols(int slots) {
+  int q = 1;
+  while (q * q < slots) q++;
+  return q;
+}
+
+__device__ __forceinline__ void decode_slot(const float* __restrict__ o, int cell, int gw, int s,
+                                            int slots, int cell_px, float scale, float g[9]) {
   const float half = 0.5f * (float)cell_px;
   const int cy = cell / gw, cx = cell % gw;
-  g[0] = ((float)cx + 0.5f) * (float)cell_px + half * tanhf(o[0]);
-  g[1] = ((float)cy + 0.5f) * (float)cell_px + half * tanhf(o[1]);
+  const int q = anchor_cols(slots), r = (slots + q - 1) / q;
+  const float ax = ((float)(s % q) + 0.5f) / (float)q, ay = ((float)(s / q) + 0.5f) / (float)r;
+  g[0] = ((float)cx + ax) * (float)cell_px + half * tanhf(o[0]);
+  g[1] = ((float)cy + ay) * (float)cell_px + half * tanhf(o[1]);
   g[2] = scale * expf(fminf(fmaxf(o[2], kExpLo), kExpHi));
   g[3] = scale * o[3];
   g[4] = scale * expf(fminf(fmaxf(o[4], kExpLo), kExpHi));
@@ -307,7 +317,8 @@ __device__ __forceinline__ void decode_slot(const float* __restrict__ o, int cel
 // index-order compaction.
 __global__ void __launch_bounds__(1024)
 k_head_decode(const float* __restrict__ out, int ldo, int gh, int gw, int slots, int cell_px,
-              float scale, int n, float* __restrict__ params, int* __restrict__ sel) {
+              float scale, int n, float* __restrict__ params, int ldp,
+              int* __restrict__ sel) {
   extern __shared__ uint32_t s_key[];
   __shared__ int s_hist[256];
   __shared__ int s_scan[1024];
@@ -382,10 +393,10 @@ k_head_decode(const float* __restrict__ out, int ldo, int gh, int gw, int slots,
     if (take && j < n) {
       const int cell = i / slots, s = i % slots;
       float g[9];
-      decode_slot(ob + (size_t)cell * ldo + 9 * s, cell, gw, cell_px, scale, g);
-      float* pb = params + (size_t)b * 9 * n;
+      decode_slot(ob + (size_t)cell * ldo + 9 * s, cell, gw, s, slots, cell_px, scale, g);
+      float* pb = params + (size_t)b * n;
 #pragma unroll
-      for (int r = 0; r < 9; r++) pb[(size_t)r * n + j] = g[r];
+      for (int r = 0; r < 9; r++) pb[(size_t)r * ldp + j] = g[r];
       sel[(size_t)b * n + j] = i;
     }
     taken_before += take_total;
@@ -399,7 +410,7 @@ k_head_decode(const float* __restrict__ out, int ldo, int gh, int gw, int slots,
 __global__ void k_head_decode_bwd(const float* __restrict__ out, int ldo, int B, int gh, int gw,
                                   int slots, int cell_px, float scale, int n,
                                   const int* __restrict__ sel, const float* __restrict__ dparams,
-                                  bf16* __restrict__ dout) {
+                                  int ldp, bf16* __restrict__ dout) {
   const int cells = gh * gw;
   const size_t total = (size_t)B * n;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
@@ -409,10 +420,10 @@ __global__ void k_head_decode_bwd(const float* __restrict__ out, int ldo, int B,
     const int cell = slot / slots, s = slot % slots;
     const size_t row = (size_t)b * cells + cell;
     const float* o = out + row * ldo + 9 * s;
-    const float* dp = dparams + (size_t)b * 9 * n;
+    const float* dp = dparams + (size_t)b * n;
     float d[9];
 #pragma unroll
-    for (int r = 0; r < 9; r++) d[r] = dp[(size_t)r * n + j];
+    for (int r = 0; r < 9; r++) d[r] = dp[(size_t)r * ldp + j];
     const float half = 0.5f * (float)cell_px;
     float g[9];
     const float t0 = tanhf(o[0]), t1 = tanhf(o[1]);
@@ -434,21 +445,21 @@ __global__ void k_head_decode_bwd(const float* __restrict__ out, int ldo, int B,
 // Nearest neighbour of every point of P among Q (per frame): points are rows
 // 0, 1 of [9][count] parameter blocks.
 __global__ void __launch_bounds__(256)
-k_nearest(const float* __restrict__ P, int np, const float* __restrict__ Q, int nq,
-          int* __restrict__ nn, float* __restrict__ dist) {
+k_nearest(const float* __restrict__ P, int np, int ldp, const float* __restrict__ Q, int nq,
+          int ldq, int* __restrict__ nn, float* __restrict__ dist) {
   __shared__ float2 s_q[1024];
   const int b = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const float* pb = P + (size_t)b * 9 * np;
-  const float* qb = Q + (size_t)b * 9 * nq;
-  const float px = i < np ? pb[i] : 0.0f, py = i < np ? pb[np + i] : 0.0f;
+  const float* pb = P + (size_t)b * np;
+  const float* qb = Q + (size_t)b * nq;
+  const float px = i < np ? pb[i] : 0.0f, py = i < np ? pb[ldp + i] : 0.0f;
   float best = INFINITY;
   int arg = 0;
   for (int j0 = 0; j0 < nq; j0 += 1024) {
     const int cnt = min(1024, nq - j0);
     __syncthreads();
     for (int k = threadIdx.x; k < cnt; k += blockDim.x)
-      s_q[k] = make_float2(qb[j0 + k], qb[nq + j0 + k]);
+      s_q[k] = make_float2(qb[j0 + k], qb[(size_t)ldq + j0 + k]);
     __syncthreads();
     for (int k = 0; k < cnt; k++) {
       const float dx = px - s_q[k].x, dy = py - s_q[k].y;
@@ -470,23 +481,23 @@ k_nearest(const float* __restrict__ P, int np, const float* __restrict__ Q, int 
 // nearest predicted point (accumulated with atomics).  Also the per-frame
 // loss (a fixed-order sum).
 __global__ void __launch_bounds__(256)
-k_chamfer_grad(const float* __restrict__ P, int np, const float* __restrict__ Q, int nq,
-               const int* __restrict__ nn1, const int* __restrict__ nn2, float lambda,
+k_chamfer_grad(const float* __restrict__ P, int np, int ldp, const float* __restrict__ Q, int nq,
+               int ldq, const int* __restrict__ nn1, const int* __restrict__ nn2, float lambda,
                float* __restrict__ dP) {
   const int b = blockIdx.y;
-  const float* pb = P + (size_t)b * 9 * np;
-  const float* qb = Q + (size_t)b * 9 * nq;
-  float* db = dP + (size_t)b * 9 * np;
+  const float* pb = P + (size_t)b * np;
+  const float* qb = Q + (size_t)b * nq;
+  float* db = dP + (size_t)b * np;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < np) {
     const int j = nn1[(size_t)b * np + i];
     atomicAdd(&db[i], lambda * 2.0f * (pb[i] - qb[j]) / (float)np);
-    atomicAdd(&db[np + i], lambda * 2.0f * (pb[np + i] - qb[nq + j]) / (float)np);
+    atomicAdd(&db[ldp + i], lambda * 2.0f * (pb[ldp + i] - qb[ldq + j]) / (float)np);
   }
   if (i < nq) {
     const int k = nn2[(size_t)b * nq + i];
     atomicAdd(&db[k], lambda * 2.0f * (pb[k] - qb[i]) / (float)nq);
-    atomicAdd(&db[np + k], lambda * 2.0f * (pb[np + k] - qb[nq + i]) / (float)nq);
+    atomicAdd(&db[ldp + k], lambda * 2.0f * (pb[ldp + k] - qb[ldq + i]) / (float)nq);
   }
 }
 
@@ -517,9 +528,11 @@ extern "C" uint64_t gs2d_head_smem_bytes(int32_t gh, int32_t gw, int32_t slots) 
 
 extern "C" gs2d_status gs2d_head_decode(const float* out, int32_t ldo, int32_t B, int32_t gh,
                                         int32_t gw, int32_t slots, int32_t cell_px, float scale,
-                                        int32_t n, float* params, int32_t* sel, void* stream) {
+                                        int32_t n, float* params, int32_t ldp, int32_t* sel,
+                                        void* stream) {
   const uint64_t smem = gs2d_head_smem_bytes(gh, gw, slots);
   if (B < 0 || gh < 1 || gw < 1 || slots < 1 || ldo < 9 * slots || cell_px < 1 || n < 0 ||
+      (int64_t)ldp < (int64_t)B * n ||
       (int64_t)n > (int64_t)gh * gw * slots || smem > 200 * 1024 ||
       (B > 0 && (!out || !params || !sel)))
     return set_error(GS2D_ERR_INVALID_ARG, "gs2d_head_decode: arguments");
@@ -532,15 +545,17 @@ extern "C" gs2d_status gs2d_head_decode(const float* out, int32_t ldo, int32_t B
     attr = true;
   }
   k_head_decode<<<B, 1024, (size_t)smem, (cudaStream_t)stream>>>(out, ldo, gh, gw, slots, cell_px,
-                                                                  scale, n, params, sel);
+                                                                  scale, n, params, ldp, sel);
   return launched("gs2d_head_decode");
 }
 
 extern "C" gs2d_status gs2d_head_decode_bwd(const float* out, int32_t ldo, int32_t B, int32_t gh,
                                             int32_t gw, int32_t slots, int32_t cell_px,
                                             float scale, int32_t n, const int32_t* sel,
-                                            const float* dparams, void* dout, void* stream) {
+                                            const float* dparams, int32_t ldp, void* dout,
+                                            void* stream) {
   if (B < 0 || gh < 1 || gw < 1 || slots < 1 || ldo < 9 * slots || n < 0 ||
+      (int64_t)ldp < (int64_t)B * n ||
       (B > 0 && (!out || !sel || !dparams || !dout)))
     return set_error(GS2D_ERR_INVALID_ARG, "gs2d_head_decode_bwd: arguments");
   cudaStream_t s = (cudaStream_t)stream;
@@ -550,7 +565,7 @@ extern "C" gs2d_status gs2d_head_decode_bwd(const float* out, int32_t ldo, int32
   const size_t total = (size_t)B * n;
   if (total == 0) return set_error(GS2D_OK, "");
   k_head_decode_bwd<<<grid_for(total, 256), 256, 0, s>>>(out, ldo, B, gh, gw, slots, cell_px,
-                                                         scale, n, sel, dparams,
+                                                         scale, n, sel, dparams, ldp,
                                                          static_cast<bf16*>(dout));
   return launched("gs2d_head_decode_bwd");
 }
@@ -559,22 +574,23 @@ extern "C" uint64_t gs2d_chamfer_scratch_bytes(int32_t n, int32_t m, int32_t B) 
   return (uint64_t)B * ((uint64_t)n + m) * (sizeof(int) + sizeof(float)) + 64;
 }
 
-extern "C" gs2d_status gs2d_chamfer(const float* params, int32_t n, const float* targets,
-                                    int32_t m, int32_t B, float lambda, float* dparams,
-                                    float* loss, void* scratch, void* stream) {
-  if (n < 1 || m < 1 || B < 1 || !params || !targets || !scratch)
+extern "C" gs2d_status gs2d_chamfer(const float* params, int32_t n, int32_t ldp,
+                                    const float* targets, int32_t m, int32_t ldq, int32_t B,
+                                    float lambda, float* dparams, float* loss, void* scratch,
+                                    void* stream) {
+  if (n < 1 || m < 1 || B < 1 || !params || !targets || !scratch ||
+      (int64_t)ldp < (int64_t)B * n || (int64_t)ldq < (int64_t)B * m)
     return set_error(GS2D_ERR_INVALID_ARG, "gs2d_chamfer: arguments");
   cudaStream_t s = (cudaStream_t)stream;
   int* nn1 = static_cast<int*>(scratch);
   int* nn2 = nn1 + (size_t)B * n;
   float* d1 = reinterpret_cast<float*>(nn2 + (size_t)B * m);
   float* d2 = d1 + (size_t)B * n;
-  k_nearest<<<dim3((n + 255) / 256, B), 256, 0, s>>>(params, n, targets, m, nn1, d1);
-  k_nearest<<<dim3((m + 255) / 256, B), 256, 0, s>>>(targets, m, params, n, nn2, d2);
+  k_nearest<<<dim3((n + 255) / 256, B), 256, 0, s>>>(params, n, ldp, targets, m, ldq, nn1, d1);
+  k_nearest<<<dim3((m + 255) / 256, B), 256, 0, s>>>(targets, m, ldq, params, n, ldp, nn2, d2);
   if (dparams)
-    k_chamfer_grad<<<dim3((std::max(n, m) + 255) / 256, B), 256, 0, s>>>(params, n, targets, m,
-                                                                         nn1, nn2, lambda,
-                                                                         dparams);
+    k_chamfer_grad<<<dim3((std::max(n, m) + 255) / 256, B), 256, 0, s>>>(
+        params, n, ldp, targets, m, ldq, nn1, nn2, lambda, dparams);
   if (loss) k_chamfer_loss<<<B, 1024, 0, s>>>(d1, n, d2, m, loss);
   return launched("gs2d_chamfer");
 }

@@ -217,19 +217,22 @@ def test_head_decode_select_and_backward(nat):
     out[0, 9 * 3 + 8] = out[0, 9 * 4 + 8]          # a tie in |w|
     out[5, 2] = 5.0                                 # clamped exponent
     d_out = dev_f32(out)
-    params = torch.empty((B, 9, n), device="cuda")
+    ldp = B * n + 8
+    params = torch.empty((9, ldp), device="cuda")
     sel = torch.empty((B, n), dtype=torch.int32, device="cuda")
     nat.call("gs2d_head_decode", d_out.data_ptr(), ldo, B, gh, gw, slots, cell, scale, n,
-             params.data_ptr(), sel.data_ptr(), 0)
+             params.data_ptr(), ldp, sel.data_ptr(), 0)
     ref_p, ref_sel = cnn.head_decode(out, gh, gw, slots, cell, scale, n)
     np.testing.assert_array_equal(sel.cpu().numpy(), ref_sel)
-    got = params.cpu().numpy().astype(np.float64)
+    got = params.cpu().numpy()[:, :B * n].reshape(9, B, n).transpose(1, 0, 2).astype(np.float64)
     assert np.all(np.abs(got - ref_p) <= 1e-6 * np.abs(ref_p) + 1e-5)
     dp = g.normal(size=(B, 9, n)).astype(np.float32)
     dout = torch.full((B * gh * gw, ldo), 3.0, dtype=torch.bfloat16, device="cuda")
-    d_dp = dev_f32(dp)
+    flat = np.zeros((9, ldp), np.float32)
+    flat[:, :B * n] = dp.transpose(1, 0, 2).reshape(9, B * n)
+    d_dp = dev_f32(flat)
     nat.call("gs2d_head_decode_bwd", d_out.data_ptr(), ldo, B, gh, gw, slots, cell, scale, n,
-             sel.data_ptr(), d_dp.data_ptr(), dout.data_ptr(), 0)
+             sel.data_ptr(), d_dp.data_ptr(), ldp, dout.data_ptr(), 0)
     ref_d = cnn.head_decode_bwd(out, ref_sel, dp, gh, gw, slots, cell, scale)
     assert bf16_ulp_close(to_np_bf16(dout), ref_d, ulps=2)
 
@@ -237,21 +240,21 @@ def test_head_decode_select_and_backward(nat):
 def test_chamfer_loss_and_gradient(nat):
     g = np.random.Generator(np.random.PCG64(12))
     B, n, m = 2, 700, 500
-    P = np.zeros((B, 9, n), np.float32)
-    Q = np.zeros((B, 9, m), np.float32)
-    P[:, :2] = g.uniform(0, 300, (B, 2, n))
-    Q[:, :2] = g.uniform(0, 300, (B, 2, m))
+    P = np.zeros((9, B * n), np.float32)
+    Q = np.zeros((9, B * m), np.float32)
+    P[:2] = g.uniform(0, 300, (2, B * n))
+    Q[:2] = g.uniform(0, 300, (2, B * m))
     scratch = torch.empty(nat.load().gs2d_chamfer_scratch_bytes(n, m, B), dtype=torch.uint8,
                           device="cuda")
     loss = torch.empty(B, device="cuda")
-    dP = torch.zeros((B, 9, n), device="cuda")
+    dP = torch.zeros((9, B * n), device="cuda")
     lam = 0.5
     d_P, d_Q = dev_f32(P), dev_f32(Q)
-    nat.call("gs2d_chamfer", d_P.data_ptr(), n, d_Q.data_ptr(), m, B, lam, dP.data_ptr(),
-             loss.data_ptr(), scratch.data_ptr(), 0)
+    nat.call("gs2d_chamfer", d_P.data_ptr(), n, B * n, d_Q.data_ptr(), m, B * m, B, lam,
+             dP.data_ptr(), loss.data_ptr(), scratch.data_ptr(), 0)
     for b in range(B):
-        ref_l, ref_g = cnn.chamfer(P[b, :2].T, Q[b, :2].T)
+        ref_l, ref_g = cnn.chamfer(P[:2, b * n:(b + 1) * n].T, Q[:2, b * m:(b + 1) * m].T)
         assert abs(float(loss[b]) - ref_l) <= 1e-5 * ref_l
-        got = dP[b, :2].cpu().numpy().T.astype(np.float64)
+        got = dP[:2, b * n:(b + 1) * n].cpu().numpy().T.astype(np.float64)
         assert np.all(np.abs(got - lam * ref_g) <= 1e-4 * np.abs(lam * ref_g).max())
-        assert float(dP[b, 2:].abs().max()) == 0.0
+    assert float(dP[2:].abs().max()) == 0.0

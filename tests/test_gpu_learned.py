@@ -1,0 +1,105 @@
+"""The learned initialiser's network on the tensor cores, layer by layer
+against the oracle (each layer fed the GPU's own input to it, so that BF16
+roundings upstream do not mask a wiring error), and a short training run."""
+
+import numpy as np
+import pytest
+
+from oracle import cnn
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL = 2e-5
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    from paper_2505_09324_gb300 import _native, build
+    build.build()
+    _native.load()
+    from paper_2505_09324_gb300.learned import LearnedInitializer, NetConfig
+    from gs2d_inputs import conferencing_frame
+    W, H, n, B = 96, 64, 20, 2
+    net = LearnedInitializer(W, H, n, B, NetConfig(channels=(8, 16, 16, 24, 16, 32), slots=4),
+                             seed=3)
+    fr = [conferencing_frame(W, H, seed=s) for s in (5, 6)]
+    frames = torch.from_numpy(np.stack([f for f, _ in fr])).cuda()
+    masks = torch.from_numpy(np.stack([m for _, m in fr]).astype(np.uint8)).cuda()
+    return net, frames, masks
+
+
+def f64(t):
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+def test_forward_layers_match_oracle(tiny):
+    net, frames, masks = tiny
+    params = net.forward(frames, masks)
+    torch.cuda.synchronize()
+    net.check_status()
+    B = net.B
+    for li in range(net.L):
+        ci, co, ks, ldk = net.layers[li]
+        hi, wi = net.sizes[li]
+        a = f64(net.x[li]).reshape(B, hi, wi, ci)
+        w = f64(net.wb[li])
+        ref = np.maximum(cnn.conv(a, w[:, :9 * ci + 1], 3, 2, 1), 0.0)
+        got = f64(net.x[li + 1]).reshape(ref.shape)
+        scale = cnn.gemm_abs(cnn.im2col(a, 3, 2, 1, ldk), w).reshape(ref.shape)
+        assert np.all(np.abs(got - ref) <= REL * scale + np.abs(ref) * 2.0 ** -8 + 1e-30), li
+    ci, co, ks, ldk = net.layers[-1]
+    a = f64(net.x[net.L]).reshape(B, net.gh, net.gw, ci)
+    w = f64(net.wb[-1])
+    ref = cnn.conv(a, w[:, :ci + 1], 1, 1, 0).reshape(-1, co)
+    scale = cnn.gemm_abs(cnn.im2col(a, 1, 1, 0, ldk), w)
+    assert np.all(np.abs(f64(net.out) - ref) <= REL * scale + 1e-30)
+    # the decoded Gaussians are those of the head output
+    out = net.out.cpu().numpy()
+    ref_p, ref_sel = cnn.head_decode(out, net.gh, net.gw, net.cfg.slots, net.cell,
+                                     net.cfg.scale, net.n)
+    np.testing.assert_array_equal(net.sel.cpu().numpy(), ref_sel)
+    got_p = params.cpu().numpy().reshape(9, B, net.n).transpose(1, 0, 2)
+    assert np.all(np.abs(got_p - ref_p) <= 1e-6 * np.abs(ref_p) + 1e-5)
+
+
+def test_backward_layers_match_oracle(tiny):
+    net, frames, masks = tiny
+    net.forward(frames, masks)
+    g = np.random.Generator(np.random.PCG64(2))
+    dparams = torch.from_numpy(g.normal(size=(9, net.B * net.n)).astype(np.float32)).cuda()
+    net.backward(dparams)
+    torch.cuda.synchronize()
+    net.check_status()
+    B = net.B
+    for li in range(net.L, -1, -1):
+        ci, co, ks, ldk = net.layers[li]
+        col = f64(net.col[li])
+        dz = f64(net.dz[li])
+        ref = dz.T @ col
+        bound = REL * (np.abs(dz).T @ np.abs(col)) + 1e-30
+        assert np.all(np.abs(f64(net.dw[li]) - ref) <= bound), li
+        if li == 0:
+            break
+        hi, wi = net.sizes[li] if li < net.L else net.sizes[-1]
+        stride, pad = (2, 1) if ks == 3 else (1, 0)
+        w = f64(net.wb[li])
+        a = f64(net.x[li]).reshape(B, hi, wi, ci)
+        want = cnn.col2im(dz @ w, a.shape, ks, stride, pad) * (a > 0)
+        got = f64(net.dz[li - 1]).reshape(a.shape)
+        scale = cnn.col2im(np.abs(dz) @ np.abs(w), a.shape, ks, stride, pad) * (a > 0)
+        # FP32 GEMM + FP32 tap sums, then one BF16 rounding
+        assert np.all(np.abs(got - want) <= 1e-4 * scale + np.abs(want) * 2.0 ** -7 + 1e-30), li
+
+
+def test_training_lowers_the_render_loss():
+    from paper_2505_09324_gb300.learned import (LearnedInitializer, NetConfig, make_dataset,
+                                                train)
+    W, H, n, B = 128, 96, 120, 4
+    data = make_dataset(W, H, n, list(range(300, 316)), cap=300)
+    net = LearnedInitializer(W, H, n, B, NetConfig(channels=(8, 16, 32, 32, 32, 64), slots=10,
+                                                   lr=3e-3), seed=1)
+    hist = train(net, data, epochs=12, seed=0)
+    net.check_status()
+    first, last = hist[0]["render_mse_per_frame"], hist[-1]["render_mse_per_frame"]
+    assert np.isfinite(last) and last < 0.5 * first, (first, last)

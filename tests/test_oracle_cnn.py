@@ -130,7 +130,10 @@ def test_head_select_ties_and_order():
     assert sel.tolist() == [[0, 2, 4]]
     p, s2 = cnn.head_decode(out, gh, gw, slots, 32, 6.0, 3)
     assert s2.tolist() == sel.tolist()
-    np.testing.assert_allclose(p[0, 0], [16.0, 16.0, 48.0])     # tanh(0) = 0: cell centres
+    # tanh(0) = 0: the slot anchors; 3 slots on a 2 x 2 grid of quarter cells
+    np.testing.assert_allclose(p[0, 0], [8.0, 8.0, 32 + 24.0])
+    np.testing.assert_allclose(p[0, 1], [8.0, 24.0, 8.0])
+    assert cnn.slot_anchor(9, 10) == (1.5 / 4, 2.5 / 3)
     np.testing.assert_allclose(p[0, 8], [0.75, -0.75, 1.25])
     np.testing.assert_allclose(p[0, 2], [6.0, 6.0, 6.0])        # exp(0) * scale
 
