@@ -47,7 +47,8 @@ WORKLOAD = ("1920x1080 RGB FP32 synthetic conferencing frame (seed 1), 20000 Gau
 # FP32-pipe operations and MUFU ex2 per contributing (pixel, Gaussian) pair of the
 # fused fit kernel: forward 8 (sigma + predicate) + 3 (accumulate); backward 8
 # (recompute) + 3 (colour sums) + 4 (dL/dsigma) + 7 (quadratic-form moments).
-OPS_PER_HIT = 33
+OPS_FWD, OPS_BWD = 11, 22
+OPS_PER_HIT = OPS_FWD + OPS_BWD
 MUFU_PER_HIT = 2
 SMS, FP32_LANES, MUFU_LANES, SM_MAX_MHZ = 152, 128, 32, 2070.0
 # DRAM bytes (read + write) of one k_render_l2 launch from an ncu capture of
@@ -58,7 +59,7 @@ NCU_TRAFFIC = {"bytes": 27485696,
 
 def render_traffic():
     import hashlib
-    path = os.path.join(ROOT, "paper_2505_09324_gb300", "csrc", "render.cu")
+    path = os.path.join(ROOT, "paper_2505_09324_gb300", "csrc", "render_impl.cuh")
     with open(path, "rb") as f:
         sha = hashlib.sha256(f.read()).hexdigest()
     return NCU_TRAFFIC["bytes"] if sha == NCU_TRAFFIC["render_sha256"] else None
@@ -77,6 +78,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-sequence", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--schedule", default="",
+                    help="tile/stage/launch (e.g. 32/128/grid) instead of the autotuner's pick")
     ap.add_argument("--seq-frames", type=int, default=60)
     ap.add_argument("--seq-iters", type=int, default=300)
     ap.add_argument("--batch-clips", type=int, default=32)
@@ -326,6 +330,49 @@ def measure_sequence(args, dev, rast, params0):
             "timing": "wall clock per gs2d_encode_frame call (graph replays, one PSNR check)"}
 
 
+def measure_learned(dev, frame, mask, peaks):
+    """Inference of the learned initialiser (Sec. 3.2 B regressor) for a batch
+    of 8 frames of the benchmark size: frame + mask -> 20k Gaussians per frame.
+    The time does not depend on the weights (a seeded random network); the
+    dense contractions run on the BF16 tensor cores.  Roofline: algorithmic
+    FLOPs of the convolutions (2 x output pixels x channels out x taps x
+    channels in, bias included) over the whole forward time, against the
+    measured BF16 peak."""
+    import torch
+
+    from paper_2505_09324_gb300.learned import LearnedInitializer
+
+    B = 8
+    net = LearnedInitializer(W, H, N_GAUSS, B, seed=0, device=dev)
+    frames = frame.unsqueeze(0).expand(B, -1, -1, -1).contiguous()
+    masks = mask.unsqueeze(0).expand(B, -1, -1).contiguous()
+    for _ in range(3):
+        net.forward(frames, masks)
+    torch.cuda.synchronize(dev)
+    reps = 20
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        net.forward(frames, masks)
+    b.record()
+    torch.cuda.synchronize(dev)
+    net.check_status()
+    ms = a.elapsed_time(b) / reps
+    flops = 0
+    for li, (ci, co, ks, ldk) in enumerate(net.layers):
+        h, w = net.sizes[li + 1] if li < net.L else net.sizes[-1]
+        cout = 9 * net.cfg.slots if li == net.L else co
+        flops += 2 * B * h * w * cout * (ks * ks * ci + 1)
+    tflops = flops / ms / 1e9
+    peak = peaks.get("bf16_tflops")
+    return {"batch": B, "ms_per_batch": ms, "ms_per_frame": ms / B, "params": net.num_params(),
+            "gflop_per_frame": flops / B / 1e9,
+            "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak,
+                         "unit": "TFLOP/s (BF16)", "frac": tflops / peak if peak else None,
+                         "peak_source": peaks.get("source"),
+                         "note": "whole forward (im2col, GEMMs, head) timed; GEMM FLOPs only"}}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -362,7 +409,14 @@ def run_ours(args):
 
     # render schedule (tile, stage, launch form) picked by the autotuner on this
     # workload, before the timed region
-    tuned = autotune([(W, H, N_GAUSS)], params0, frame.reshape(-1), reps=10, cache=False)
+    if args.schedule:
+        from paper_2505_09324_gb300 import RasterConfig
+        t_, s_, l_ = args.schedule.split("/")
+        la = {"persistent": 0, "grid": 1}[l_]
+        tuned = {"tile": int(t_), "stage": int(s_), "launch": la, "ms": {},
+                 "config": RasterConfig(tile=int(t_), stage=int(s_), launch=la)}
+    else:
+        tuned = autotune([(W, H, N_GAUSS)], params0, frame.reshape(-1), reps=10, cache=False)
     rast = GaussianRasterizer(W, H, N_GAUSS, device=dev, config=tuned["config"])
     plan, ws = rast.plan, rast.ws_ptr
     params = params0.clone()
@@ -427,6 +481,29 @@ def run_ours(args):
     rast.prepare(params)
     pairs1, hits1 = rast.count_pairs()
 
+    # the forward and the backward pass alone, at this state (L2 flushed each time)
+    img = torch.empty_like(frame)
+    dimg = torch.empty_like(frame)
+    sep = {"fwd": [], "bwd": []}
+    for r in range(25):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        nat.render_fwd(plan, ws, img.data_ptr(), sp)
+        b.record(stream)
+        if r == 0:
+            torch.sub(img, frame, out=dimg)
+            dimg.mul_(2.0 / img.numel())
+        flush.zero_()
+        c, d = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c.record(stream)
+        nat.render_bwd(plan, ws, params.data_ptr(), dimg.data_ptr(), grads.data_ptr(), sp)
+        d.record(stream)
+        torch.cuda.synchronize(dev)
+        if r >= 5:
+            sep["fwd"].append(a.elapsed_time(b))
+            sep["bwd"].append(c.elapsed_time(d))
+
     per = {"prepare": [], "render_l2": [], "adam": [], "step": []}
     for e in ev:
         per["prepare"].append(e[0].elapsed_time(e[1]))
@@ -450,11 +527,22 @@ def run_ours(args):
     peak_fp32 = SMS * FP32_LANES * f_hz / 1e12
     peak_mufu = SMS * MUFU_LANES * f_hz / 1e12
     achieved = OPS_PER_HIT * hits / t_render / 1e12
+    passes = {}
+    for name, ops in (("fwd", OPS_FWD), ("bwd", OPS_BWD)):
+        t_s = statistics.fmean(sep[name]) * 1e-3
+        ach = ops * hits1 / t_s / 1e12
+        passes[name] = {"ms": t_s * 1e3, "ops_per_hit": ops, "achieved": ach,
+                        "frac": ach / peak_fp32,
+                        "call": "gs2d_render_fwd" if name == "fwd" else
+                                "gs2d_render_bwd (k_render backward + per-Gaussian reduction)"}
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_fp32,
-                "unit": "Top/s (FP32 pipe)", "frac": achieved / peak_fp32, "traffic": render_traffic(),
-                "kernel": "render_l2 (k_render_l2 + k_reduce_chain)",
+                "unit": "Top/s (FP32 pipe)", "frac": achieved / peak_fp32,
+                "traffic": render_traffic(),
+                "kernel": "gs2d_render_l2: k_render (fused forward + L2 + backward) + "
+                          "k_reduce_chain",
                 "mufu_frac": MUFU_PER_HIT * hits / t_render / 1e12 / peak_mufu,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz; MUFU 32/SM/clk"}
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz; MUFU 32/SM/clk",
+                "passes": passes}
 
     # end to end through the public API with host buffers
     h_frame = torch.from_numpy(frame_np).pin_memory()
@@ -523,6 +611,13 @@ def run_ours(args):
 
     batch = None if args.no_batch else measure_batch(args, dev)
     seq = None if args.no_sequence else measure_sequence(args, dev, rast, params0)
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+        peaks["source"] = "of measured (MEASURED_PEAKS.json bf16_tflops, burst)"
+    except OSError:
+        peaks = {"bf16_tflops": 1900.0, "source": "of fallback (1.9 PFLOP/s bf16 burst)"}
+    learned = None if args.no_learned else measure_learned(dev, frame, mask, peaks)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -558,7 +653,7 @@ def run_ours(args):
                                                       for (a, b, c), v in tuned["ms"].items()}},
                 "pairs": {"listed_first": pairs0, "hits_first": hits0, "listed_last": pairs1,
                           "hits_last": hits1},
-                "encode": encode, "batch": batch, "sequence": seq}
+                "encode": encode, "batch": batch, "sequence": seq, "learned_init": learned}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

@@ -209,7 +209,8 @@ gs2d_status gs2d_render_bwd(const gs2d_plan* plan, void* ws, const float* params
                             const float* dimg, float* grads, void* stream);
 
 /* Fused forward + L2 loss + backward for fitting: L = mean over 3HW of
- * (C - target)^2 (a batch plan: the sum of that over the clips).  target: device [3][H][W].  grads: device 9n floats
+ * (C - target)^2 (a batch plan: the sum of that over the clips).
+ * target: device [3][H][W].  grads: device 9n floats
  * (dL/dparams).  img: device [3][H][W] or NULL (the rendered image is then not
  * stored).  loss: device, 2 floats or NULL: {L, mean squared error of C
  * clamped to [0, 1]} (the latter gives PSNR = -10 log10).  Needs

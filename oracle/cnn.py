@@ -55,7 +55,8 @@ def out_size(n: int, ks: int, stride: int, pad: int) -> int:
 
 def conv(x, w, ks: int, stride: int, pad: int) -> np.ndarray:
     """Direct convolution by explicit sums over the ks x ks taps:
-    out[b, oy, ox, co] = w[co, ks^2 C] + sum_{ky, kx, ci} x[b, iy, ix, ci] w[co, (ky ks + kx) C + ci]
+    out[b, oy, ox, co] = w[co, ks^2 C]
+                         + sum_{ky, kx, ci} x[b, iy, ix, ci] w[co, (ky ks + kx) C + ci]
     with iy = oy stride + ky - pad (zero outside the image)."""
     x = np.asarray(x, np.float64)
     w = np.asarray(w, np.float64)

@@ -46,7 +46,8 @@ gs2d_status check_plan(const gs2d_plan* p, const void* ws) {
 bool cfg_valid(const gs2d_config& c) {
   return (c.tile == 8 || c.tile == 16 || c.tile == 32) &&
          (c.stage == 0 || c.stage == 32 || c.stage == 64 || c.stage == 128) &&
-         (c.launch == GS2D_LAUNCH_PERSISTENT || c.launch == GS2D_LAUNCH_GRID) && c.sigma_cut > 0.0f && isfinite(c.sigma_cut) && c.alpha_min > 0.0f &&
+         (c.launch == GS2D_LAUNCH_PERSISTENT || c.launch == GS2D_LAUNCH_GRID) &&
+         c.sigma_cut > 0.0f && isfinite(c.sigma_cut) && c.alpha_min > 0.0f &&
          isfinite(c.alpha_min) && c.det_eps >= 0.0f && isfinite(c.det_eps) && c.lr > 0.0f &&
          isfinite(c.lr) && c.beta1 >= 0.0f && c.beta1 < 1.0f && c.beta2 >= 0.0f &&
          c.beta2 < 1.0f && c.eps > 0.0f && isfinite(c.eps);
@@ -305,7 +306,8 @@ static cudaError_t reset_fit(const gs2d_plan& p, void* ws, float* m, float* v, c
   cudaError_t e = cudaSuccess;
   if (pbytes) e = cudaMemsetAsync(m, 0, pbytes, s);
   if (e == cudaSuccess && pbytes) e = cudaMemsetAsync(v, 0, pbytes, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ws_ptr<WsHeader>(ws, p, kOffHeader), 0, sizeof(WsHeader), s);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(ws_ptr<WsHeader>(ws, p, kOffHeader), 0, sizeof(WsHeader), s);
   return e;
 }
 
@@ -342,7 +344,8 @@ gs2d_status gs2d_encode_frame(const gs2d_plan* plan, void* ws, const float* targ
     return fail(GS2D_ERR_INVALID_ARG, "params or Adam state is NULL");
   if (iters < 0 || check_every < 1) return fail(GS2D_ERR_INVALID_ARG, "iters / check_every");
   if (plan->num_clips != 1)
-    return fail(GS2D_ERR_INVALID_ARG, "gs2d_encode_frame takes a one-clip plan (gs2d_encode_batch)");
+    return fail(GS2D_ERR_INVALID_ARG,
+                "gs2d_encode_frame takes a one-clip plan (gs2d_encode_batch)");
   const gs2d_plan& p = *plan;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = reset_fit(p, ws, adam_m, adam_v, s);

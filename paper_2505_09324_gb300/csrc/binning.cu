@@ -452,8 +452,8 @@ static bool g_long_attr_set = false;
 
 cudaError_t prime_binning() {
   if (g_long_attr_set) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(k_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kLongMax * (int)sizeof(uint32_t));
+  const cudaError_t e = cudaFuncSetAttribute(
+      k_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize, kLongMax * (int)sizeof(uint32_t));
   if (e == cudaSuccess) g_long_attr_set = true;
   return e;
 }

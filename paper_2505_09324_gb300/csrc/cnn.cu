@@ -138,11 +138,12 @@ __global__ void k_col2im(const float* __restrict__ dcol, int ldk, int B, int Hi,
   }
 }
 
-// out[c][r] = in[r][c], 32 x 32 tiles through shared memory.
+// out[c][r] = in[r][c], 32 x 32 tiles through shared memory (row tiles on
+// the grid's x dimension, which allows 2^31 - 1 of them).
 __global__ void k_transpose(const bf16* __restrict__ in, int R, int C, int ld_in,
                             bf16* __restrict__ out, int ld_out) {
   __shared__ bf16 tile[32][33];
-  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const int r = r0 + i, c = c0 + threadIdx.x;
     if (r < R && c < C) tile[i][threadIdx.x] = in[(size_t)r * ld_in + c];
@@ -244,7 +245,8 @@ extern "C" gs2d_status gs2d_transpose_bf16(const void* in, int32_t R, int32_t C,
   if (R < 0 || C < 0 || ld_in < C || ld_out < R || (R * C > 0 && (!in || !out)))
     return set_error(GS2D_ERR_INVALID_ARG, "gs2d_transpose_bf16: arguments");
   if (R == 0 || C == 0) return set_error(GS2D_OK, "");
-  const dim3 grid((C + 31) / 32, (R + 31) / 32), block(32, 8);
+  if ((C + 31) / 32 > 65535) return set_error(GS2D_ERR_INVALID_ARG, "gs2d_transpose_bf16: C");
+  const dim3 grid((R + 31) / 32, (C + 31) / 32), block(32, 8);
   k_transpose<<<grid, block, 0, (cudaStream_t)stream>>>(static_cast<const bf16*>(in), R, C, ld_in,
                                                         static_cast<bf16*>(out), ld_out);
   return launched("gs2d_transpose_bf16");

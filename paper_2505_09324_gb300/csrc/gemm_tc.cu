@@ -7,7 +7,8 @@
 //
 // One CTA computes a 128 x BN tile (BN = 32 ... 256) over a range of K:
 //   warp 0, one lane   TMA producer: 128 x 64 A and BN x 64 B boxes per stage
-//                      into 128-byte-swizzled shared memory, STAGES deep;
+//                      into 128-byte-swizzled shared memory, ST deep (2 for
+//                      short K, so that more blocks share an SM; else 4);
 //   warp 1, one lane   MMA issuer: four 128 x BN x 16 tcgen05.mma per stage,
 //                      a tcgen05.commit per stage frees the stage, one more
 //                      signals the finished accumulator;
@@ -33,7 +34,6 @@ namespace {
 
 constexpr int kBM = 128;    // accumulator rows (TMEM lanes)
 constexpr int kBK = 64;     // K per stage: one 128-byte swizzle row of bf16
-constexpr int kStages = 4;
 constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -138,20 +138,21 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-template <int BN>
+template <int BN, int ST>
 struct GemmShape {
   static constexpr int kTmemCols = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
   static constexpr int kABytes = kBM * kBK * 2;  // 16 KB
   static constexpr int kBBytes = BN * kBK * 2;
   static constexpr int kStageBytes = kABytes + kBBytes;
-  static constexpr int kSmem = kStages * kStageBytes + 1024;  // + alignment slack
+  static constexpr int kSmem = ST * kStageBytes + 1024;  // + alignment slack
 };
 
-template <int BN>
+template <int BN, int ST>
 __global__ void __launch_bounds__(128, 1)
 k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
             TcGemmArgs g) {
-  using Sh = GemmShape<BN>;
+  constexpr int kStages = ST;
+  using Sh = GemmShape<BN, ST>;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages], accum;
   __shared__ uint32_t s_tmem;
@@ -314,18 +315,27 @@ bool make_map(CUtensorMap* map, const void* base, int rows, int cols, int ld, in
          CUDA_SUCCESS;
 }
 
-template <int BN>
-cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const TcGemmArgs& g,
-                      dim3 grid, cudaStream_t s) {
+template <int BN, int ST>
+cudaError_t launch_bn_st(const CUtensorMap& ta, const CUtensorMap& tb, const TcGemmArgs& g,
+                         dim3 grid, cudaStream_t s) {
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(k_gemm_bf16<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                GemmShape<BN>::kSmem);
+    attr = cudaFuncSetAttribute(k_gemm_bf16<BN, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                GemmShape<BN, ST>::kSmem);
   });
   if (attr != cudaSuccess) return attr;
-  k_gemm_bf16<BN><<<grid, 128, GemmShape<BN>::kSmem, s>>>(ta, tb, g);
+  k_gemm_bf16<BN, ST><<<grid, 128, GemmShape<BN, ST>::kSmem, s>>>(ta, tb, g);
   return cudaGetLastError();
+}
+
+// Two stages when every block runs few k-tiles (more blocks per SM hide the
+// per-block latency), four otherwise.
+template <int BN>
+cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const TcGemmArgs& g,
+                      dim3 grid, cudaStream_t s) {
+  return g.kt_per_split <= 8 ? launch_bn_st<BN, 2>(ta, tb, g, grid, s)
+                             : launch_bn_st<BN, 4>(ta, tb, g, grid, s);
 }
 
 }  // namespace

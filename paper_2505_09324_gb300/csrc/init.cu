@@ -263,7 +263,8 @@ gs2d_status roi_init(const float* frame, const uint8_t* mask, int W, int H, int 
   int* label = reinterpret_cast<int*>(base);
   double* cen = reinterpret_cast<double*>(base + a256(hw * 4));
   double* seed_xy = reinterpret_cast<double*>(base + a256(hw * 4) + a256(5ull * n * 8));
-  int* cell_of = reinterpret_cast<int*>(base + a256(hw * 4) + a256(5ull * n * 8) + a256(2ull * n * 8));
+  int* cell_of =
+      reinterpret_cast<int*>(base + a256(hw * 4) + a256(5ull * n * 8) + a256(2ull * n * 8));
   // seeds on the host (the mask comes back once)
   std::vector<uint8_t> hmask(hw);
   cudaError_t e = cudaMemcpyAsync(hmask.data(), mask, hw, cudaMemcpyDeviceToHost, s);
@@ -313,7 +314,8 @@ gs2d_status roi_init(const float* frame, const uint8_t* mask, int W, int H, int 
   a.cen = cen;
   a.label = label;
   if (M > 0) {
-    e = cudaMemcpyAsync(seed_xy, sxy.data(), sxy.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(seed_xy, sxy.data(), sxy.size() * sizeof(double),
+                        cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(cell_of, cells.data(), cells.size() * sizeof(int),
                           cudaMemcpyHostToDevice, s);

@@ -52,7 +52,8 @@ cudaError_t launch_adam(float* params, const float* grads, float* m, float* v, i
   if (count <= 0) return cudaSuccess;
   const float ibc1 = (float)(1.0 / (1.0 - pow((double)cfg.beta1, (double)step)));
   const float ibc2 = (float)(1.0 / (1.0 - pow((double)cfg.beta2, (double)step)));
-  const bool aligned = ((uintptr_t)params | (uintptr_t)grads | (uintptr_t)m | (uintptr_t)v) % 16 == 0;
+  const bool aligned =
+      ((uintptr_t)params | (uintptr_t)grads | (uintptr_t)m | (uintptr_t)v) % 16 == 0;
   if (!mask && aligned && count % 4 == 0) {
     const int64_t c4 = count / 4;
     int64_t blocks = (c4 + 255) / 256;

@@ -33,8 +33,10 @@
 // order).
 //
 // Backward: the blend is recomputed from the saved lists (no per-pixel state
-// is stored by the forward pass).  A group of T lanes takes one Gaussian;
-// lane = column of its box, looping over the box rows.  Per lane it keeps
+// is stored by the forward pass).  A group of T lanes takes one Gaussian and
+// lays itself over the Gaussian's box inside the tile: box columns rounded up
+// to a power of two c, T / c rows per step, each lane one column and every
+// (T / c)-th row of the box.  Per lane it keeps
 // sum g e (3), sum S, sum S u2, sum S u2^2 with S = (g . c') e; the moments
 // in u1 follow by multiplying with the lane's constant u1.  The group reduces
 // the eight sums with a transposing shuffle tree and writes one 32-byte
@@ -192,7 +194,6 @@ __device__ __forceinline__ void bwd_batch(const TileSmem<S>& sm, const float4* _
   using G = TileGeom<T>;
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int h = lane / T, j = lane % T;
-  const float px = ox + (float)j + 0.5f;
   for (int base = wid * G::GPW; base < cnt; base += G::NW * G::GPW) {  // warp-uniform
     const int gi = base + h;
     float v[8];
@@ -200,20 +201,29 @@ __device__ __forceinline__ void bwd_batch(const TileSmem<S>& sm, const float4* _
     for (int k = 0; k < 8; k++) v[k] = 0.0f;
     if (gi < cnt) {
       const int4 bb = sm.bb[gi];
-      if (j >= bb.x && j <= bb.y) {
+      // c = box width rounded up to a power of two; lane j: column j % c,
+      // rows bb.z + j / c, + T / c, ...
+      const int bw = bb.y - bb.x + 1;
+      const int lc = bw <= 1 ? 0 : 32 - __clz(bw - 1);  // log2 c
+      const int col = bb.x + (j & ((1 << lc) - 1));
+      const int rstep = T >> lc;
+      const int y0 = bb.z + (j >> lc);
+      if (bw > 0 && col <= bb.y && y0 <= bb.w) {
+        const float px = ox + (float)col + 0.5f;
         const float4 r0 = sm.r0[gi], r1 = sm.r1[gi];
         const float cr = r1.z, cg = r1.w, cb = sm.cb[gi];
         const float u1 = r0.z * (px - r0.x);
         const float c0 = r1.x * u1;
         const float u1sq = u1 * u1;
-        float dy = (oy + (float)bb.z + 0.5f) - r0.y;
+        const float fstep = (float)rstep;
+        float dy = (oy + (float)y0 + 0.5f) - r0.y;
         float ge0 = 0.f, ge1 = 0.f, ge2 = 0.f, ss = 0.f, s2 = 0.f, s22 = 0.f;
-        for (int y = bb.z; y <= bb.w; y++, dy += 1.0f) {
+        for (int y = y0; y <= bb.w; y += rstep, dy += fstep) {
           const float u2 = fmaf(r0.w, dy, c0);
           const float q = fmaf(u2, u2, u1sq);
           if (q <= r1.y) {
             const float e = ex2_approx(-q);
-            const float4 g = s_g[y * T + j];
+            const float4 g = s_g[y * T + col];
             ge0 = fmaf(g.x, e, ge0);
             ge1 = fmaf(g.y, e, ge1);
             ge2 = fmaf(g.z, e, ge2);
@@ -394,8 +404,14 @@ __device__ __forceinline__ void process_tile(const RenderArgs& a, const TileFram
   }
 }
 
+// Blocks per SM the register budget must allow (about 50 registers per
+// thread of the 64 K per SM; 32 blocks at most): 32, 20, 5 for T = 8, 16, 32.
+template <int T>
+constexpr int kMinBlocks = 65536 / (TileGeom<T>::NT * 50) < 32 ? 65536 / (TileGeom<T>::NT * 50)
+                                                                 : 32;
+
 template <int T, int S, int MODE, int LAUNCH>
-__global__ void __launch_bounds__(TileGeom<T>::NT) k_render(RenderArgs a) {
+__global__ void __launch_bounds__(TileGeom<T>::NT, kMinBlocks<T>) k_render(RenderArgs a) {
   __shared__ TileSmem<S> sm;
   __shared__ ModeSmem<T, MODE> ms;
   if constexpr (LAUNCH == GS2D_LAUNCH_GRID) {
