@@ -231,6 +231,9 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUte
     const int row = m0 + warp * 32 + lane;
     const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
     float* out32 = g.out_f32 ? g.out_f32 + (size_t)blockIdx.z * g.split_stride : nullptr;
+    // rows of 16-byte aligned, full 16-column chunks take vector stores
+    const void* obase = g.out_bf16 ? (const void*)g.out_bf16 : (const void*)out32;
+    const bool vec_ok = (g.ldc % 8) == 0 && (reinterpret_cast<uintptr_t>(obase) & 15) == 0;
 #pragma unroll 1
     for (int c = 0; c < BN; c += 16) {
       float v[16];
@@ -239,14 +242,35 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUte
         const int n = n0 + c;
 #pragma unroll
         for (int j = 0; j < 16; j++) {
-          if (n + j < g.N) {
-            float x = v[j];
-            if (g.bias) x += g.bias[n + j];
-            if (g.relu) x = fmaxf(x, 0.0f);
-            if (g.out_bf16)
-              g.out_bf16[(size_t)row * g.ldc + n + j] = __float2bfloat16_rn(x);
-            else
-              out32[(size_t)row * g.ldc + n + j] = x;
+          float x = v[j];
+          if (g.bias && n + j < g.N) x += g.bias[n + j];
+          if (g.relu) x = fmaxf(x, 0.0f);
+          v[j] = x;
+        }
+        const size_t o = (size_t)row * g.ldc + n;
+        if (vec_ok && n + 16 <= g.N) {
+          if (g.out_bf16) {
+            __align__(16) __nv_bfloat162 h[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+            uint4* dst = reinterpret_cast<uint4*>(g.out_bf16 + o);
+            dst[0] = reinterpret_cast<const uint4*>(h)[0];
+            dst[1] = reinterpret_cast<const uint4*>(h)[1];
+          } else {
+            float4* dst = reinterpret_cast<float4*>(out32 + o);
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+              dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; j++) {
+            if (n + j < g.N) {
+              if (g.out_bf16)
+                g.out_bf16[o + j] = __float2bfloat16_rn(v[j]);
+              else
+                out32[o + j] = v[j];
+            }
           }
         }
       }
