@@ -599,6 +599,27 @@ def run_ours(args):
                     "status": out["status"]}
 
         roi = encode_from(params0)
+        # from the learned initialiser shipped with the package (trained on
+        # synthetic frames of other seeds), when it matches the frame size
+        from paper_2505_09324_gb300.learned import packaged
+        net = packaged(W, H, N_GAUSS, batch=1, device=dev)
+        learned_enc = None
+        if net is not None:
+            net.forward(frame.unsqueeze(0), mask.unsqueeze(0))  # warm-up
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            p_learn = net.forward(frame.unsqueeze(0), mask.unsqueeze(0)).clone()
+            torch.cuda.synchronize(dev)
+            init_l = time.perf_counter() - t0
+            rast.prepare(p_learn)
+            _, l0, _ = rast.render_l2(p_learn, frame)
+            psnr0 = float(10 * np.log10(1.0 / max(float(l0[1]), 1e-30)))
+            if psnr0 >= args.target_psnr:
+                learned_enc = {"seconds": 0.0, "iters": 0, "psnr": psnr0, "reached": True}
+            else:
+                learned_enc = encode_from(p_learn)
+            learned_enc.update(init_s=init_l, psnr_at_init=psnr0,
+                               s_per_frame=init_l + learned_enc["seconds"])
         # plain: means uniform over the frame, Cholesky diagonal log-uniform in
         # [1, 8] px, off-diagonal N(0, 1) px, random colours, weights in [0.2, 1]
         from gs2d_inputs import random_gaussians
@@ -607,7 +628,7 @@ def run_ours(args):
         encode = {"target_psnr": args.target_psnr, "cap_iters": args.encode_iters,
                   "roi_init": {**roi, "init_s": init_s, "n_roi": n_roi,
                                "s_per_frame": init_s + roi["seconds"]},
-                  "plain_random_init": rnd}
+                  "plain_random_init": rnd, "learned_init": learned_enc}
 
     batch = None if args.no_batch else measure_batch(args, dev)
     seq = None if args.no_sequence else measure_sequence(args, dev, rast, params0)

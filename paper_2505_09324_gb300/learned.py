@@ -220,9 +220,37 @@ class LearnedInitializer:
         return {f"w{i}": w.cpu().numpy() for i, w in enumerate(self.w32)}
 
     def load_state(self, st: dict):
+        """Weights from state(), or BF16 bit patterns (uint16) of them."""
         for i, w in enumerate(self.w32):
-            w.copy_(torch.from_numpy(st[f"w{i}"]))
+            a = np.asarray(st[f"w{i}"])
+            if a.dtype == np.uint16:
+                a = (a.astype(np.uint32) << 16).view(np.float32)
+            w.copy_(torch.from_numpy(np.ascontiguousarray(a, np.float32)))
         self._cast()
+
+
+PACKAGED = "data/learned_init_1920x1080_20k.npz"
+
+
+def packaged(width: int, height: int, n: int, batch: int = 1, device=None):
+    """The initialiser trained by `python -m paper_2505_09324_gb300.learned`
+    on 5000 synthetic 1920 x 1080 conferencing frames (seeds 10000 ... 14999,
+    Gaussians fitted to 35 dB by the ROI-initialised encoder), shipped with the
+    package as BF16 weights; None for other sizes."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), PACKAGED)
+    if not os.path.exists(path):
+        return None
+    st = dict(np.load(path))
+    meta = json.loads(bytes(st.pop("meta")).decode())
+    if (meta["width"], meta["height"], meta["n"]) != (width, height, n):
+        return None
+    net = LearnedInitializer(width, height, n, batch,
+                             NetConfig(channels=tuple(meta["channels"]), slots=meta["slots"],
+                                       scale=meta["scale"]), device=device)
+    net.load_state(st)
+    return net
 
 
 class Trainer:
