@@ -51,10 +51,11 @@ OPS_FWD, OPS_BWD = 11, 22
 OPS_PER_HIT = OPS_FWD + OPS_BWD
 MUFU_PER_HIT = 2
 SMS, FP32_LANES, MUFU_LANES, SM_MAX_MHZ = 152, 128, 32, 2070.0
-# DRAM bytes (read + write) of one k_render_l2 launch from an ncu capture of
-# this workload, valid for the render source with this sha256 (else null)
-NCU_TRAFFIC = {"bytes": 27485696,
-               "render_sha256": "b62803e7ad2a07d91951dbfcd0d3c61a828db2a0ca610a35fb3da29706d950b7"}
+# DRAM bytes (read + write) of one fused render launch (k_render, tile 32,
+# stage 128, grid) from an ncu capture of this workload, valid for the render
+# source with this sha256 (else null)
+NCU_TRAFFIC = {"bytes": 26738176,
+               "render_sha256": "63b396422cc05d9a16ec30f15493b55b5907c008498be1def5a680184f0a10da"}
 
 
 def render_traffic():
