@@ -39,7 +39,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 W, H, N_GAUSS, SEED, ROI_FRAC = 1920, 1080, 20000, 1, 0.7
-BANDS = 8  # oracle samples: one horizontal band of H / BANDS rows per step
+BANDS = 16  # oracle samples: one horizontal band of H / BANDS rows per step
 METRIC = "fwd+bwd ms/iter @1080p,20k Gaussians; encode s/frame to 35 dB PSNR vs plain"
 UNIT = "ms/iter"
 WORKLOAD = ("1920x1080 RGB FP32 synthetic conferencing frame (seed 1), 20000 Gaussians from "
@@ -93,6 +93,19 @@ def parse():
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
             int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def whole_job(total_ms: float, steps: int, world: int, device=None):
+    """Max over ranks of the timed region (ms) and the whole-job value, ms per
+    frame-iteration: every rank fits its own frame for `steps` iterations, so
+    the job processed steps x world of them in the slowest rank's time."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, total_ms / (steps * world)
 
 
 def workload(seed):
@@ -511,13 +524,8 @@ def run_ours(args):
         per["render_l2"].append(e[1].elapsed_time(e[2]))
         per["adam"].append(e[2].elapsed_time(e[3]))
         per["step"].append(e[0].elapsed_time(e[3]))
-    total_ms = sum(per["step"])
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms, value = whole_job(sum(per["step"]), K, world, dev)
     ms_per_step = total_ms / K
-    value = total_ms / (K * world)
 
     # roofline of the dominant call (fused forward + loss + backward + reduction);
     # the work per step changes along the fit: use the mean of the contributing
