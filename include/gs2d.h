@@ -229,6 +229,22 @@ gs2d_status gs2d_render_l2(const gs2d_plan* plan, void* ws, const float* params,
 gs2d_status gs2d_adam_step(float* params, const float* grads, float* m, float* v, int64_t count,
                            int32_t step, const uint8_t* mask, const gs2d_config* cfg, void* stream);
 
+/* One iteration of the fitting loop of gs2d_encode_frame / gs2d_encode_batch
+ * (Sec. 3.2 A), as those loops run it: projection and binning of params, the
+ * fused forward + L2 loss + backward render, and the per-Gaussian reduction
+ * fused with the Adam update of params, adam_m, adam_v (device, 9n floats
+ * each).  The Adam step counter lives in the workspace header: it starts at
+ * zero in a zero-filled workspace and advances by one per call;
+ * gs2d_fit_reset restarts the optimiser.  target: device, the plan's image
+ * layout. */
+gs2d_status gs2d_fit_step(const gs2d_plan* plan, void* ws, const float* target, float* params,
+                          float* adam_m, float* adam_v, void* stream);
+
+/* Restarts the optimiser of gs2d_fit_step: zeroes adam_m and adam_v (device,
+ * 9n floats each) and the workspace header (step counter, status word). */
+gs2d_status gs2d_fit_reset(const gs2d_plan* plan, void* ws, float* adam_m, float* adam_v,
+                           void* stream);
+
 /* Device scratch (bytes, 256-byte aligned start) that gs2d_roi_init needs for
  * a W x H frame and n Gaussians. */
 uint64_t gs2d_roi_init_scratch_bytes(int32_t width, int32_t height, int32_t n);

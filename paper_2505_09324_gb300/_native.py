@@ -26,7 +26,8 @@ EXPORTS = (
     "gs2d_plan_init_batch", "gs2d_ws_set_clips",
     "gs2d_project", "gs2d_bin_sort", "gs2d_prepare", "gs2d_render_fwd", "gs2d_render_fwd_noalloc",
     "gs2d_render_bwd", "gs2d_render_l2",
-    "gs2d_adam_step", "gs2d_encode_frame", "gs2d_clip_losses", "gs2d_encode_batch",
+    "gs2d_adam_step", "gs2d_fit_step", "gs2d_fit_reset", "gs2d_encode_frame", "gs2d_clip_losses",
+    "gs2d_encode_batch",
     "gs2d_autotune_ws_bytes", "gs2d_autotune",
     "gs2d_gemm_bf16", "gs2d_gemm_partial_bytes", "gs2d_cnn_input", "gs2d_im2col", "gs2d_col2im",
     "gs2d_transpose_bf16", "gs2d_relu_bwd", "gs2d_cast_weights", "gs2d_head_decode",
@@ -121,6 +122,8 @@ def load(build_if_missing: bool = False):
             "gs2d_render_l2": (i32, [pp, P, P, P, P, P, P, P]),
             "gs2d_adam_step": (i32, [P, P, P, P, i64, i32, P, ctypes.POINTER(Config), P]),
             "gs2d_encode_frame": (i32, [pp, P, P, P, P, P, i32, f32, i32, P, P, P, P]),
+            "gs2d_fit_step": (i32, [pp, P, P, P, P, P, P]),
+            "gs2d_fit_reset": (i32, [pp, P, P, P, P]),
             "gs2d_read_bins": (i32, [pp, P, P, P, P, i64, P, P, P]),
             "gs2d_count_pairs": (i32, [pp, P, ctypes.POINTER(i64), ctypes.POINTER(i64), P]),
             "gs2d_ws_status": (i32, [pp, P, i32, P]),
@@ -288,6 +291,16 @@ def adam_step(params: int, grads: int, m: int, v: int, count: int, step: int, ma
     cfg = ctypes.byref(config) if config is not None else None
     check(load().gs2d_adam_step(_p(params), _p(grads), _p(m), _p(v), count, step, _p(mask), cfg,
                                 _p(stream)), "gs2d_adam_step")
+
+
+def fit_step(plan: Plan, ws: int, target: int, params: int, m: int, v: int, stream: int):
+    check(load().gs2d_fit_step(ctypes.byref(plan), _p(ws), _p(target), _p(params), _p(m), _p(v),
+                               _p(stream)), "gs2d_fit_step")
+
+
+def fit_reset(plan: Plan, ws: int, m: int, v: int, stream: int):
+    check(load().gs2d_fit_reset(ctypes.byref(plan), _p(ws), _p(m), _p(v), _p(stream)),
+          "gs2d_fit_reset")
 
 
 def encode_frame(plan: Plan, ws: int, target: int, params: int, m: int, v: int, iters: int,

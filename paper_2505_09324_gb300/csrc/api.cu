@@ -152,7 +152,7 @@ gs2d_status gs2d_plan_init_batch(gs2d_plan* plan, gs2d_clip* clips, int32_t num_
   sz[kOffRec] = 3 * nn * sizeof(float4);
   sz[kOffRect] = nn * sizeof(int4);
   sz[kOffCount] = (nn + 1) * sizeof(int);
-  sz[kOffBlockSum] = (nn / 256 + 1) * sizeof(long long);
+  sz[kOffBlockSum] = (nn / 32 + 1) * sizeof(long long);  // blocks of >= 32 Gaussians
   sz[kOffTileCnt] = nt * sizeof(int);
   sz[kOffCursor] = nt * sizeof(int);
   sz[kOffLong] = (nt + 1) * sizeof(int);
@@ -331,6 +331,25 @@ static cudaGraphExec_t capture_fit(const gs2d_plan& p, void* ws, const float* ta
   }
   cudaGetLastError();  // a failed capture falls back to plain launches
   return exec;
+}
+
+gs2d_status gs2d_fit_step(const gs2d_plan* plan, void* ws, const float* target, float* params,
+                          float* adam_m, float* adam_v, void* stream) {
+  gs2d_status st = check_plan(plan, ws);
+  if (st) return st;
+  if (!target) return fail(GS2D_ERR_INVALID_ARG, "target is NULL");
+  if (plan->n > 0 && (!params || !adam_m || !adam_v))
+    return fail(GS2D_ERR_INVALID_ARG, "params or Adam state is NULL");
+  return cuda_check(fit_iteration(*plan, ws, target, params, adam_m, adam_v, (cudaStream_t)stream),
+                    "gs2d_fit_step");
+}
+
+gs2d_status gs2d_fit_reset(const gs2d_plan* plan, void* ws, float* adam_m, float* adam_v,
+                           void* stream) {
+  gs2d_status st = check_plan(plan, ws);
+  if (st) return st;
+  if (plan->n > 0 && (!adam_m || !adam_v)) return fail(GS2D_ERR_INVALID_ARG, "Adam state is NULL");
+  return cuda_check(reset_fit(*plan, ws, adam_m, adam_v, (cudaStream_t)stream), "gs2d_fit_reset");
 }
 
 gs2d_status gs2d_encode_frame(const gs2d_plan* plan, void* ws, const float* target, float* params,

@@ -25,7 +25,7 @@ enum WsSection {
   kOffRec,          // float4[3][n]  render records (SoA of float4 rows)
   kOffRect,         // int4[n]       tile rectangle (first tile, row stride, w, h)
   kOffCount,        // int32[n + 1]  per-Gaussian tile counts, then exclusive offsets
-  kOffBlockSum,     // int64[n / 256 + 1]  entry counts per block of 256 Gaussians
+  kOffBlockSum,     // int64[n / 32 + 1]  entry counts per block of Gaussians
   kOffTileCnt,      // int32[num_tiles]  entries per tile (zero between calls)
   kOffCursor,       // int32[num_tiles]  next free slot of each tile's list
   kOffLong,         // int32[num_tiles + 1]  tiles whose list needs the CTA sort

@@ -78,3 +78,26 @@ def test_autograd_fit_loop_tracks_fused_fit_loop(gs):
     d = (q.detach() - fused).abs()
     scale = p0.abs().amax(dim=1, keepdim=True).clamp_min(1e-3)
     assert float((d / scale).max()) < 1e-3
+
+
+def test_fit_step_equals_the_encoder_loop(gs):
+    """gs2d_fit_step, called k times after gs2d_fit_reset, is the encoder's
+    iteration: the same Gaussians bit for bit as gs2d_encode_frame(k)."""
+    from paper_2505_09324_gb300 import _native as nat
+    W, H, n, k = 160, 96, 400, 12
+    frames, masks = sequence(W, H, 1, 7)
+    bg = torch.from_numpy(background_positions(masks[0], n, seed=8)).cuda()
+    p0, _ = gs.roi_init(frames[0], torch.from_numpy(masks[0].astype(np.uint8)).cuda(), n, 0.7, bg)
+    r = gs.GaussianRasterizer(W, H, n)
+    a = p0.clone()
+    r.encode_frame(frames[0], a, k, target_psnr=0.0, check_every=k)
+    b = p0.clone()
+    m, v = torch.empty_like(b), torch.empty_like(b)
+    s = int(torch.cuda.current_stream().cuda_stream)
+    nat.fit_reset(r.plan, r.ws_ptr, m.data_ptr(), v.data_ptr(), s)
+    for _ in range(k):
+        nat.fit_step(r.plan, r.ws_ptr, frames[0].data_ptr(), b.data_ptr(), m.data_ptr(),
+                     v.data_ptr(), s)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    assert not torch.equal(a, p0)
