@@ -245,6 +245,38 @@ gs2d_status gs2d_fit_step(const gs2d_plan* plan, void* ws, const float* target, 
 gs2d_status gs2d_fit_reset(const gs2d_plan* plan, void* ws, float* adam_m, float* adam_v,
                            void* stream);
 
+/* P-frames (Sec. 3.2 C, selective Gaussian optimisation): the residual
+ * between the current frame and the reference marks the changed pixels
+ * (max over channels of |reference - frame| > threshold; reading: the
+ * reference is the render of the reference Gaussians, what a decoder holds);
+ * the per-tile lists of the current binning (the paper's pixel-to-Gaussian
+ * metadata) give the Gaussians that contribute to a changed pixel (the
+ * renderer's cut-off predicate).  reference, frame: device, the plan's image
+ * layout.  selected: device uint8[n] out (1 = selected).  n_selected: host
+ * int32 out or NULL (synchronises the stream when given).  Needs
+ * gs2d_prepare of the reference Gaussians on ws. */
+gs2d_status gs2d_select_changed(const gs2d_plan* plan, void* ws, const float* reference,
+                                const float* frame, float threshold, uint8_t* selected,
+                                int32_t* n_selected, void* stream);
+
+/* One P-frame fit iteration: projection and binning of all Gaussians, the
+ * fused render + L2 + backward over only the tiles that the selected
+ * Gaussians' rectangles cover (every pixel a selected Gaussian reaches, so
+ * their gradients are those of the full-frame loss), and the reduction + Adam
+ * of only the selected Gaussians (the others keep params, adam_m, adam_v).
+ * Adam step counter as for gs2d_fit_step. */
+gs2d_status gs2d_pframe_step(const gs2d_plan* plan, void* ws, const float* target, float* params,
+                             float* adam_m, float* adam_v, const uint8_t* selected,
+                             void* stream);
+
+/* Fits a P-frame: `iters` gs2d_pframe_step iterations replayed as a captured
+ * CUDA graph (moments zeroed first), then final_psnr (host, may be NULL) = the
+ * full-frame PSNR of the result.  Synchronises the stream. */
+gs2d_status gs2d_encode_pframe(const gs2d_plan* plan, void* ws, const float* target,
+                               float* params, float* adam_m, float* adam_v,
+                               const uint8_t* selected, int32_t iters, float* final_psnr,
+                               void* stream);
+
 /* Device scratch (bytes, 256-byte aligned start) that gs2d_roi_init needs for
  * a W x H frame and n Gaussians. */
 uint64_t gs2d_roi_init_scratch_bytes(int32_t width, int32_t height, int32_t n);

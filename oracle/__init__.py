@@ -264,3 +264,30 @@ def adam_step(p, g, m, v, step: int, lr: float = 1e-2, beta1: float = 0.9,
     mhat = m / (1.0 - beta1 ** step)
     vhat = v / (1.0 - beta2 ** step)
     return p - lr * mhat / (np.sqrt(vhat) + eps), m, v
+
+
+def contributes(params, xy, cfg: Config = Config()):
+    """Which Gaussians contribute to Eq. 2 at the integer pixels ``xy[k] = (x, y)``
+    (the cut-off predicate of the notation above, double precision, pixel
+    centres at +0.5): ``(definite [k, n], ambiguous [k, n])`` boolean arrays,
+    ambiguous where sigma lies within amb_tol max(1, tau) of tau (a single
+    precision evaluation may decide those either way)."""
+    p = _params64(params)
+    mx, my, l1, l2, l3 = p[0], p[1], p[2], p[3], p[4]
+    w = p[8]
+    sxx, sxy, syy = l1 * l1, l1 * l2, l2 * l2 + l3 * l3
+    det = sxx * syy - sxy * sxy
+    finite = np.all(np.isfinite(p), axis=0)
+    ok = finite & (det > cfg.det_eps) & (np.abs(w) >= cfg.alpha_min)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        tau = np.minimum(cfg.sigma_cut, np.log(np.abs(w) / cfg.alpha_min))
+        a, b, c = syy / det, -sxy / det, sxx / det
+    xy = np.asarray(xy, np.float64).reshape(-1, 2)
+    dx = (xy[:, 0:1] + 0.5) - mx[None, :]
+    dy = (xy[:, 1:2] + 0.5) - my[None, :]
+    with np.errstate(invalid="ignore"):
+        sig = 0.5 * (a * dx * dx + c * dy * dy) + b * dx * dy
+    band = cfg.amb_tol * np.maximum(1.0, tau)
+    definite = ok[None, :] & (sig <= tau - band)
+    ambiguous = ok[None, :] & (np.abs(sig - tau) < band)
+    return definite, ambiguous

@@ -27,6 +27,7 @@ EXPORTS = (
     "gs2d_project", "gs2d_bin_sort", "gs2d_prepare", "gs2d_render_fwd", "gs2d_render_fwd_noalloc",
     "gs2d_render_bwd", "gs2d_render_l2",
     "gs2d_adam_step", "gs2d_fit_step", "gs2d_fit_reset", "gs2d_encode_frame", "gs2d_clip_losses",
+    "gs2d_select_changed", "gs2d_pframe_step", "gs2d_encode_pframe",
     "gs2d_encode_batch",
     "gs2d_autotune_ws_bytes", "gs2d_autotune",
     "gs2d_gemm_bf16", "gs2d_gemm_partial_bytes", "gs2d_cnn_input", "gs2d_im2col", "gs2d_col2im",
@@ -124,6 +125,9 @@ def load(build_if_missing: bool = False):
             "gs2d_encode_frame": (i32, [pp, P, P, P, P, P, i32, f32, i32, P, P, P, P]),
             "gs2d_fit_step": (i32, [pp, P, P, P, P, P, P]),
             "gs2d_fit_reset": (i32, [pp, P, P, P, P]),
+            "gs2d_select_changed": (i32, [pp, P, P, P, f32, P, ctypes.POINTER(i32), P]),
+            "gs2d_pframe_step": (i32, [pp, P, P, P, P, P, P, P]),
+            "gs2d_encode_pframe": (i32, [pp, P, P, P, P, P, P, i32, ctypes.POINTER(f32), P]),
             "gs2d_read_bins": (i32, [pp, P, P, P, P, i64, P, P, P]),
             "gs2d_count_pairs": (i32, [pp, P, ctypes.POINTER(i64), ctypes.POINTER(i64), P]),
             "gs2d_ws_status": (i32, [pp, P, i32, P]),
@@ -301,6 +305,30 @@ def fit_step(plan: Plan, ws: int, target: int, params: int, m: int, v: int, stre
 def fit_reset(plan: Plan, ws: int, m: int, v: int, stream: int):
     check(load().gs2d_fit_reset(ctypes.byref(plan), _p(ws), _p(m), _p(v), _p(stream)),
           "gs2d_fit_reset")
+
+
+def select_changed(plan: Plan, ws: int, reference: int, frame: int, threshold: float,
+                   selected: int, stream: int) -> int:
+    cnt = ctypes.c_int32(0)
+    check(load().gs2d_select_changed(ctypes.byref(plan), _p(ws), _p(reference), _p(frame),
+                                     threshold, _p(selected), ctypes.byref(cnt), _p(stream)),
+          "gs2d_select_changed")
+    return cnt.value
+
+
+def pframe_step(plan: Plan, ws: int, target: int, params: int, m: int, v: int, selected: int,
+                stream: int):
+    check(load().gs2d_pframe_step(ctypes.byref(plan), _p(ws), _p(target), _p(params), _p(m),
+                                  _p(v), _p(selected), _p(stream)), "gs2d_pframe_step")
+
+
+def encode_pframe(plan: Plan, ws: int, target: int, params: int, m: int, v: int, selected: int,
+                  iters: int, stream: int) -> float:
+    psnr = ctypes.c_float(0.0)
+    check(load().gs2d_encode_pframe(ctypes.byref(plan), _p(ws), _p(target), _p(params), _p(m),
+                                    _p(v), _p(selected), iters, ctypes.byref(psnr), _p(stream)),
+          "gs2d_encode_pframe")
+    return psnr.value
 
 
 def encode_frame(plan: Plan, ws: int, target: int, params: int, m: int, v: int, iters: int,

@@ -164,6 +164,8 @@ gs2d_status gs2d_plan_init_batch(gs2d_plan* plan, gs2d_clip* clips, int32_t num_
   sz[kOffPartial] = me * kPartials * sizeof(float);
   sz[kOffLossPart] = nt * sizeof(float2);
   sz[kOffClipLoss] = (uint64_t)num_clips * sizeof(float2);
+  sz[kOffActive] = nt;
+  sz[kOffActOrder] = (nt + 1) * sizeof(int);
   sz[kOffGrad] = 9 * nn * sizeof(float);
   uint64_t off = 0;
   for (int sec = 0; sec < kNumSections; sec++) {
@@ -402,6 +404,97 @@ gs2d_status gs2d_encode_frame(const gs2d_plan* plan, void* ws, const float* targ
   if (final_psnr) *final_psnr = psnr;
   if (e != cudaSuccess) return cuda_check(e, "gs2d_encode_frame");
   if (result != GS2D_OK) return result;
+  return ok();
+}
+
+gs2d_status gs2d_select_changed(const gs2d_plan* plan, void* ws, const float* reference,
+                                const float* frame, float threshold, uint8_t* selected,
+                                int32_t* n_selected, void* stream) {
+  gs2d_status st = check_plan(plan, ws);
+  if (st) return st;
+  if (!reference || !frame || (plan->n > 0 && !selected))
+    return fail(GS2D_ERR_INVALID_ARG, "gs2d_select_changed: NULL pointer");
+  if (!(threshold >= 0.0f)) return fail(GS2D_ERR_INVALID_ARG, "threshold must be >= 0");
+  const gs2d_plan& p = *plan;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = p.n > 0 ? cudaMemsetAsync(selected, 0, (size_t)p.n, s) : cudaSuccess;
+  if (e == cudaSuccess) e = launch_select_changed(p, ws, reference, frame, threshold, selected, s);
+  if (e == cudaSuccess && n_selected) {
+    int* cnt = ws_ptr<int>(ws, p, kOffActOrder) + p.num_tiles;  // free outside P-frame steps
+    e = launch_count_flags(p.n, selected, cnt, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(n_selected, cnt, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  return cuda_check(e, "gs2d_select_changed");
+}
+
+static cudaError_t pframe_iteration(const gs2d_plan& p, void* ws, const float* target,
+                                    float* params, float* m, float* v, const uint8_t* select,
+                                    cudaStream_t s) {
+  cudaError_t e = launch_prepare(p, ws, params, true, s);
+  if (e == cudaSuccess) e = launch_pframe_step(p, ws, target, params, m, v, select, s);
+  return e;
+}
+
+gs2d_status gs2d_pframe_step(const gs2d_plan* plan, void* ws, const float* target, float* params,
+                             float* adam_m, float* adam_v, const uint8_t* selected,
+                             void* stream) {
+  gs2d_status st = check_plan(plan, ws);
+  if (st) return st;
+  if (!target || (plan->n > 0 && (!params || !adam_m || !adam_v || !selected)))
+    return fail(GS2D_ERR_INVALID_ARG, "gs2d_pframe_step: NULL pointer");
+  return cuda_check(pframe_iteration(*plan, ws, target, params, adam_m, adam_v, selected,
+                                     (cudaStream_t)stream),
+                    "gs2d_pframe_step");
+}
+
+gs2d_status gs2d_encode_pframe(const gs2d_plan* plan, void* ws, const float* target,
+                               float* params, float* adam_m, float* adam_v,
+                               const uint8_t* selected, int32_t iters, float* final_psnr,
+                               void* stream) {
+  gs2d_status st = check_plan(plan, ws);
+  if (st) return st;
+  if (!target || (plan->n > 0 && (!params || !adam_m || !adam_v || !selected)))
+    return fail(GS2D_ERR_INVALID_ARG, "gs2d_encode_pframe: NULL pointer");
+  if (iters < 0) return fail(GS2D_ERR_INVALID_ARG, "iters < 0");
+  const gs2d_plan& p = *plan;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = reset_fit(p, ws, adam_m, adam_v, s);
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess && s != nullptr && iters > 0 && prime_fit_launches(p) == cudaSuccess) {
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      cudaError_t ce = pframe_iteration(p, ws, target, params, adam_m, adam_v, selected, s);
+      cudaError_t ee = cudaStreamEndCapture(s, &graph);
+      if (ce == cudaSuccess && ee == cudaSuccess && graph &&
+          cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+        exec = nullptr;
+      if (graph) cudaGraphDestroy(graph);
+    }
+  }
+  cudaGetLastError();  // a failed capture falls back to plain launches
+  for (int it = 0; it < iters && e == cudaSuccess; it++)
+    e = exec ? cudaGraphLaunch(exec, s)
+             : pframe_iteration(p, ws, target, params, adam_m, adam_v, selected, s);
+  if (exec) cudaGraphExecDestroy(exec);
+  // full-frame PSNR of the result
+  if (e == cudaSuccess) e = launch_prepare(p, ws, params, false, s);
+  if (e == cudaSuccess)
+    e = launch_render_l2(p, ws, params, target, ws_ptr<float>(ws, p, kOffGrad), nullptr,
+                         nullptr, s);
+  if (e == cudaSuccess) e = launch_loss_reduce(p, ws, nullptr, s);
+  WsHeader h;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&h, ws_ptr<WsHeader>(ws, p, kOffHeader), sizeof(h),
+                        cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_check(e, "gs2d_encode_pframe");
+  if (final_psnr) {
+    const double mse = h.loss[1];
+    *final_psnr = mse > 0.0 ? (float)(10.0 * log10(1.0 / mse)) : INFINITY;
+  }
+  if (h.status != 0) return fail((gs2d_status)h.status, "device status %d", h.status);
   return ok();
 }
 

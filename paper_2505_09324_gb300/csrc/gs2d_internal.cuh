@@ -37,6 +37,8 @@ enum WsSection {
   kOffPartial,      // float[max_entries][kPartials] backward sums per (tile, Gaussian)
   kOffLossPart,     // float2[num_tiles]  per-tile (sse, clamped sse) / (3 W H of the clip)
   kOffClipLoss,     // float2[num_clips]
+  kOffActive,       // uint8[num_tiles] P-frame: tile touched by a selected Gaussian
+  kOffActOrder,     // int32[num_tiles + 1] P-frame: active tiles (count last)
   kOffGrad,         // float[9 n] gradient scratch
   kNumSections
 };
@@ -200,7 +202,7 @@ inline ClipSet clip_set(const gs2d_plan& p, const void* ws) {
 }
 
 // Arguments of the render kernels (csrc/render_impl.cuh).
-enum RenderMode { kModeFwd = 0, kModeBwd = 1, kModeL2 = 2, kModeCount = 3 };
+enum RenderMode { kModeFwd = 0, kModeBwd = 1, kModeL2 = 2, kModeCount = 3, kModeSelect = 4 };
 
 struct RenderArgs {
   ClipSet clips;
@@ -217,6 +219,11 @@ struct RenderArgs {
   const float* dimg;     // bwd
   float* partial;        // bwd, l2
   float2* loss_part;     // l2
+  const int* active;     // device count of tiles in `order` to render, or NULL (all)
+  const float* ref;      // select: reference render
+  const float* frame;    // select: current frame
+  float threshold;       // select: change threshold on max_c |ref - frame|
+  uint8_t* selected;     // select: per-Gaussian flag out
 };
 
 // One instantiation set per tile edge (render_t8.cu, render_t16.cu, render_t32.cu).
@@ -256,6 +263,13 @@ cudaError_t launch_adam(float* params, const float* grads, float* m, float* v, i
 cudaError_t launch_loss_reduce(const gs2d_plan& p, void* ws, float* loss, cudaStream_t s);
 cudaError_t launch_count_pairs(const gs2d_plan& p, void* ws, cudaStream_t s);
 cudaError_t launch_clip_losses(const gs2d_plan& p, void* ws, cudaStream_t s);
+cudaError_t launch_select_changed(const gs2d_plan& p, void* ws, const float* ref,
+                                  const float* frame, float threshold, uint8_t* selected,
+                                  cudaStream_t s);
+cudaError_t launch_count_flags(int n, const uint8_t* flags, int* out, cudaStream_t s);
+cudaError_t launch_pframe_step(const gs2d_plan& p, void* ws, const float* target,
+                               float* params, float* m, float* v, const uint8_t* select,
+                               cudaStream_t s);
 // project + bin_sort; with adam_tick the fit loop's Adam step counter and bias
 // corrections advance in the same launch.
 cudaError_t launch_prepare(const gs2d_plan& p, void* ws, const float* params, bool adam_tick,

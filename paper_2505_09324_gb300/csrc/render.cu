@@ -88,14 +88,16 @@ __global__ void __launch_bounds__(256)
 k_reduce_chain_adam(int n, float* __restrict__ params, const int* __restrict__ offs,
                     const float4* __restrict__ partial, const WsHeader* __restrict__ hdr,
                     float* __restrict__ m, float* __restrict__ v, float lr, float b1, float b2,
-                    float eps) {
+                    float eps, const uint8_t* __restrict__ select) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = gt / kRL, sub = gt % kRL;
   const bool ok = hdr->entries_raw == (int64_t)hdr->n_entries;  // else over capacity
+  // a P-frame updates only the selected Gaussians (the others keep params, m, v)
+  const bool on = i < n && (!select || select[i]);
   float a[kPartials], gr[9];
-  const bool any = gather_partials(partial, offs, i, i < n && ok, sub, a);
+  const bool any = gather_partials(partial, offs, i, on && ok, sub, a);
   if (!ok) return;  // the same for every thread of the grid
-  const bool act = i < n;
+  const bool act = on;
   if (act && any)
     chain_grads(params, n, i, a, gr);
   else
@@ -227,6 +229,11 @@ static RenderArgs render_args(const gs2d_plan& p, void* ws) {
   a.dimg = nullptr;
   a.partial = ws_ptr<float>(ws, p, kOffPartial);
   a.loss_part = ws_ptr<float2>(ws, p, kOffLossPart);
+  a.active = nullptr;
+  a.ref = nullptr;
+  a.frame = nullptr;
+  a.threshold = 0.0f;
+  a.selected = nullptr;
   return a;
 }
 
@@ -307,7 +314,96 @@ cudaError_t launch_fit_step(const gs2d_plan& p, void* ws, const float* target, f
   k_reduce_chain_adam<<<(p.n * kRL + 255) / 256, 256, 0, s>>>(
       p.n, params, ws_ptr<int>(ws, p, kOffCount),
       reinterpret_cast<const float4*>(ws_ptr<float>(ws, p, kOffPartial)),
-      ws_ptr<WsHeader>(ws, p, kOffHeader), m, v, p.cfg.lr, p.cfg.beta1, p.cfg.beta2, p.cfg.eps);
+      ws_ptr<WsHeader>(ws, p, kOffHeader), m, v, p.cfg.lr, p.cfg.beta1, p.cfg.beta2, p.cfg.eps,
+      nullptr);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// P-frames (Sec. 3.2 C, selective Gaussian optimisation): the Gaussians that
+// contribute to pixels changed since the reference are selected; each fit
+// iteration renders only the tiles those Gaussians' rectangles cover (which
+// hold every pixel a selected Gaussian reaches, so their gradients are the
+// full-frame ones) and updates only them.
+
+// Tiles of every selected Gaussian's rectangle; block 0 also zeroes the count
+// of the active-tile list (its last reader, the previous render, is done).
+__global__ void __launch_bounds__(256)
+k_active_mark(int n, const uint8_t* __restrict__ select, const int4* __restrict__ rect,
+              uint8_t* __restrict__ active, int* __restrict__ act_count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *act_count = 0;
+  if (i >= n || !select[i]) return;
+  const int4 rc = rect[i];  // (first tile, row stride, width, height)
+  for (int dy = 0; dy < rc.w; dy++)
+    for (int dx = 0; dx < rc.z; dx++) active[rc.x + dy * rc.y + dx] = 1;
+}
+
+// Active tiles into a list (any order: tiles are independent); clears the marks.
+__global__ void __launch_bounds__(256)
+k_active_compact(int num_tiles, uint8_t* __restrict__ active, int* __restrict__ act_order,
+                 int* __restrict__ act_count) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= num_tiles || !active[t]) return;
+  active[t] = 0;
+  act_order[atomicAdd(act_count, 1)] = t;
+}
+
+__global__ void __launch_bounds__(256)
+k_count_flags(int n, const uint8_t* __restrict__ flags, int* __restrict__ out) {
+  __shared__ int s_c;
+  if (threadIdx.x == 0) s_c = 0;
+  __syncthreads();
+  int c = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    c += flags[i] != 0;
+  atomicAdd(&s_c, c);
+  __syncthreads();
+  if (threadIdx.x == 0) atomicAdd(out, s_c);
+}
+
+cudaError_t launch_count_flags(int n, const uint8_t* flags, int* out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int), s);
+  if (e != cudaSuccess || n == 0) return e;
+  k_count_flags<<<std::min(152 * 4, (n + 255) / 256), 256, 0, s>>>(n, flags, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_select_changed(const gs2d_plan& p, void* ws, const float* ref,
+                                  const float* frame, float threshold, uint8_t* selected,
+                                  cudaStream_t s) {
+  RenderArgs a = render_args(p, ws);
+  a.ref = ref;
+  a.frame = frame;
+  a.threshold = threshold;
+  a.selected = selected;
+  return launch_render(p, kModeSelect, a, s);
+}
+
+// One P-frame iteration after projection and binning: active tiles, the fused
+// render over them, reduction + Adam of the selected Gaussians.
+cudaError_t launch_pframe_step(const gs2d_plan& p, void* ws, const float* target,
+                               float* params, float* m, float* v, const uint8_t* select,
+                               cudaStream_t s) {
+  if (p.n == 0) return cudaSuccess;
+  uint8_t* active = ws_ptr<uint8_t>(ws, p, kOffActive);
+  int* act_order = ws_ptr<int>(ws, p, kOffActOrder);
+  int* act_count = act_order + p.num_tiles;
+  k_active_mark<<<(p.n + 255) / 256, 256, 0, s>>>(p.n, select, ws_ptr<int4>(ws, p, kOffRect),
+                                                  active, act_count);
+  k_active_compact<<<(p.num_tiles + 255) / 256, 256, 0, s>>>(p.num_tiles, active, act_order,
+                                                             act_count);
+  RenderArgs a = render_args(p, ws);
+  a.target = target;
+  a.order = act_order;
+  a.active = act_count;
+  cudaError_t e = launch_render(p, kModeL2, a, s);
+  if (e != cudaSuccess) return e;
+  k_reduce_chain_adam<<<(p.n * kRL + 255) / 256, 256, 0, s>>>(
+      p.n, params, ws_ptr<int>(ws, p, kOffCount),
+      reinterpret_cast<const float4*>(ws_ptr<float>(ws, p, kOffPartial)),
+      ws_ptr<WsHeader>(ws, p, kOffHeader), m, v, p.cfg.lr, p.cfg.beta1, p.cfg.beta2, p.cfg.eps,
+      select);
   return cudaGetLastError();
 }
 

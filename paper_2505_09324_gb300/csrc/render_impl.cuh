@@ -294,6 +294,46 @@ __device__ __forceinline__ void process_tile(const RenderArgs& a, const TileFram
     return;
   }
 
+  if constexpr (MODE == kModeSelect) {
+    // Gaussians that contribute to a changed pixel of this tile (the
+    // renderer's predicate); a pixel changed if max_c |ref - frame| > threshold
+    bool changed[R];
+    bool any = false;
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      changed[r] = false;
+      if (x < f.W && y0 + r < f.H) {
+        const size_t o = f.pix + (size_t)(y0 + r) * f.W + x;
+        float d = fabsf(a.ref[o] - a.frame[o]);
+        d = fmaxf(d, fabsf(a.ref[HW + o] - a.frame[HW + o]));
+        d = fmaxf(d, fabsf(a.ref[2 * HW + o] - a.frame[2 * HW + o]));
+        changed[r] = d > a.threshold;
+        any |= changed[r];
+      }
+    }
+    if (!__syncthreads_or(any)) return;  // the whole tile unchanged
+    for (int b = rg.x; b < rg.y; b += S) {
+      const int cnt = min(S, rg.y - b);
+      __syncthreads();
+      stage_batch<T, S>(sm, a, f, b, cnt);
+      __syncthreads();
+      if (!any) continue;
+      for (int j = 0; j < cnt; j++) {
+        const float4 r0 = sm.r0[j], r1 = sm.r1[j];
+        const float u1 = r0.z * (px - r0.x);
+        const float c0 = r1.x * u1;
+        bool hit = false;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+          const float u2 = fmaf(r0.w, py[r] - r0.y, c0);
+          hit |= changed[r] && fmaf(u2, u2, u1 * u1) <= r1.y;
+        }
+        if (hit) a.selected[a.list[b + j]] = 1;  // every writer stores 1
+      }
+    }
+    return;
+  }
+
   if constexpr (MODE == kModeCount) {
     if (t == 0) ms.hits = 0;
     unsigned hits = 0;
@@ -415,6 +455,7 @@ __global__ void __launch_bounds__(TileGeom<T>::NT, kMinBlocks<T>) k_render(Rende
   __shared__ TileSmem<S> sm;
   __shared__ ModeSmem<T, MODE> ms;
   if constexpr (LAUNCH == GS2D_LAUNCH_GRID) {
+    if (a.active && (int)blockIdx.x >= *a.active) return;  // a P-frame's subset
     const int tile = a.order[blockIdx.x];
     if ((unsigned)tile >= (unsigned)a.num_tiles) {  // a stale queue: report, skip
       if (threadIdx.x == 0) set_status(a.hdr, GS2D_ERR_BOUNDS);
@@ -425,9 +466,10 @@ __global__ void __launch_bounds__(TileGeom<T>::NT, kMinBlocks<T>) k_render(Rende
     __shared__ int s_next[2];
     if (threadIdx.x == 0) s_next[0] = atomicAdd(&a.hdr->queue, 1);
     __syncthreads();
+    const int limit = a.active ? min(*a.active, a.num_tiles) : a.num_tiles;
     for (int k = 0;; k ^= 1) {
       const int q = s_next[k];
-      if (q >= a.num_tiles) break;
+      if (q >= limit) break;
       // next ticket now, stored after the tile: its latency overlaps the work
       int next = 0;
       if (threadIdx.x == 0) next = atomicAdd(&a.hdr->queue, 1);
@@ -466,6 +508,7 @@ cudaError_t launch_form(RenderMode mode, const RenderArgs& a, cudaStream_t s) {
     case kModeBwd: return launch_mode<T, S, kModeBwd, LAUNCH>(a, s);
     case kModeL2: return launch_mode<T, S, kModeL2, LAUNCH>(a, s);
     case kModeCount: return launch_mode<T, S, kModeCount, LAUNCH>(a, s);
+    case kModeSelect: return launch_mode<T, S, kModeSelect, LAUNCH>(a, s);
   }
   return cudaErrorInvalidValue;
 }

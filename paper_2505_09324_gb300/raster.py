@@ -136,6 +136,32 @@ class GaussianRasterizer:
     def status(self, reset: bool = False, stream=None) -> int:
         return nat.ws_status(self.plan, self.ws_ptr, reset, _stream(stream))
 
+    def select_changed(self, reference: torch.Tensor, frame: torch.Tensor, threshold: float,
+                       stream=None):
+        """P-frame selection (gs2d_select_changed) on the current binning (of
+        the reference Gaussians): (uint8 [n] flags, count)."""
+        sel = torch.empty(self.n, dtype=torch.uint8, device=self.device)
+        cnt = nat.select_changed(self.plan, self.ws_ptr,
+                                 _check(reference, "reference", self.image_shape()),
+                                 _check(frame, "frame", self.image_shape()), float(threshold),
+                                 sel.data_ptr(), _stream(stream))
+        return sel, cnt
+
+    def encode_pframe(self, target: torch.Tensor, params: torch.Tensor,
+                      selected: torch.Tensor, iters: int, adam_state=None, stream=None) -> float:
+        """Fits only the selected Gaussians (params in place) for `iters`
+        iterations over the tiles they cover; returns the full-frame PSNR."""
+        if adam_state is None:
+            adam_state = (torch.empty_like(params), torch.empty_like(params))
+        m, v = adam_state
+        shape = (9, self.n)
+        return nat.encode_pframe(self.plan, self.ws_ptr,
+                                 _check(target, "target", self.image_shape()),
+                                 _check(params, "params", shape), _check(m, "adam_m", shape),
+                                 _check(v, "adam_v", shape),
+                                 _check(selected, "selected", (self.n,), dtype=torch.uint8),
+                                 iters, _stream(stream))
+
     def encode_frame(self, target: torch.Tensor, params: torch.Tensor, iters: int,
                      target_psnr: float = 0.0, check_every: int = 50, adam_state=None,
                      stream=None):
@@ -154,24 +180,38 @@ class GaussianRasterizer:
 
 
 def encode_sequence(rast: GaussianRasterizer, frames, params: torch.Tensor, iters_first: int,
-                    iters_next: int, stream=None):
+                    iters_next: int, stream=None, selective_threshold: float | None = None):
     """Fits a frame sequence with inter-frame reuse (Sec. 3.2: P-frames start
     from the previous frame's optimised Gaussians): frame 0 for ``iters_first``
     iterations from ``params`` (an initialiser's output), every later frame
     for ``iters_next`` iterations from the previous frame's fit; the Adam
-    moments restart per frame.  ``frames`` yields [3, H, W] float32 CUDA
-    tensors.  ``params`` is updated in place (ends as the last frame's fit).
-    Returns one {"iters", "psnr", "seconds"} record per frame (wall clock
-    around each gs2d_encode_frame call, which synchronises the stream)."""
+    moments restart per frame.  With ``selective_threshold`` the later frames
+    are P-frames (Sec. 3.2 C): only the Gaussians contributing to pixels whose
+    residual against the previous fit's render exceeds the threshold are
+    fitted (gs2d_select_changed, gs2d_encode_pframe).  ``frames`` yields
+    [3, H, W] float32 CUDA tensors.  ``params`` is updated in place (ends as
+    the last frame's fit).  Returns one {"iters", "psnr", "seconds"[,
+    "selected"]} record per frame (wall clock around the frame's calls, which
+    synchronise the stream)."""
     import time
     out = []
     adam = (torch.empty_like(params), torch.empty_like(params))
+    ref = None
     for k, frame in enumerate(frames):
         iters = iters_first if k == 0 else iters_next
         t0 = time.perf_counter()
-        r = rast.encode_frame(frame, params, iters, target_psnr=0.0, check_every=iters,
-                              adam_state=adam, stream=stream)
-        out.append({"iters": r["iters"], "psnr": r["psnr"], "seconds": time.perf_counter() - t0})
+        if k == 0 or selective_threshold is None:
+            r = rast.encode_frame(frame, params, iters, target_psnr=0.0, check_every=iters,
+                                  adam_state=adam, stream=stream)
+            out.append({"iters": r["iters"], "psnr": r["psnr"],
+                        "seconds": time.perf_counter() - t0})
+            continue
+        rast.prepare(params, stream=stream)
+        ref = rast.render_fwd(out=ref, stream=stream)
+        sel, cnt = rast.select_changed(ref, frame, selective_threshold, stream=stream)
+        psnr = rast.encode_pframe(frame, params, sel, iters, adam_state=adam, stream=stream)
+        out.append({"iters": iters, "psnr": psnr, "seconds": time.perf_counter() - t0,
+                    "selected": cnt})
     return out
 
 

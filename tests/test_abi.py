@@ -53,7 +53,7 @@ def test_plan_layout(nat):
     assert (p.tiles_x, p.tiles_y, p.num_tiles) == (120, 68, 8160)
     assert p.tile_bits == 13 and p.num_clips == 1 and p.stage == 64
     assert p.max_entries == max(1 << 20, 16 * 20000) and p.pixels == 1920 * 1080
-    offs = list(p.off)[:18]
+    offs = list(p.off)[:20]
     assert all(o % 256 == 0 for o in offs)
     assert offs == sorted(offs) and p.ws_bytes > offs[-1]
     q = nat.plan_init(16, 16, 5)
@@ -92,7 +92,7 @@ def test_batch_plan_offsets(nat):
         assert (c.g_off, c.tile_off, c.pix_off) == (g, t, 3 * px)
         g, t, px = g + n, t + c.tiles_x * c.tiles_y, px + w * h
     assert p.num_tiles == t and p.pixels == px
-    offs = list(p.off)[:18]
+    offs = list(p.off)[:20]
     assert all(o % 256 == 0 for o in offs) and offs == sorted(offs)
 
 

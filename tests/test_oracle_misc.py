@@ -49,3 +49,25 @@ def test_generators_are_seeded_and_shaped():
     f, m = conferencing_frame(320, 180, seed=1)
     assert f.shape == (3, 180, 320) and m.shape == (180, 320)
     assert abs(m.mean() - 0.3) < 0.01
+
+
+def test_contributes_matches_single_gaussian_renders(oracle):
+    """The per-pair predicate against the oracle's renderer: a Gaussian
+    contributes at a pixel exactly when its render alone is non-zero there."""
+    import numpy as np
+    from gs2d_inputs import random_gaussians
+    W, H = 40, 30
+    p = random_gaussians(12, W, H, seed=4).astype(np.float64)
+    p[8, 3] = 0.001          # invisible (|w| < 1/255)
+    p[2, 5] = 1e-5           # degenerate
+    g = np.random.Generator(np.random.PCG64(5))
+    xy = np.stack([g.integers(0, W, 300), g.integers(0, H, 300)], axis=1)
+    definite, ambiguous = oracle.contributes(p, xy)
+    for i in range(p.shape[1]):
+        single = p[:, i:i + 1].copy()
+        single[5:8] = 1.0        # a non-zero colour shows every contribution
+        vals = oracle.render_pixels(single, xy)[0]
+        nz = vals != 0.0
+        sure = ~ambiguous[:, i]
+        assert np.array_equal(nz[sure], definite[sure, i]), i
+    assert not definite[:, 3].any() and not definite[:, 5].any()
