@@ -599,15 +599,20 @@ def run_ours(args):
     encode = None
     if not args.no_encode:
         side = torch.cuda.Stream(dev)
+        # fits from an initialiser use the fast learning-rate schedule
+        import dataclasses
+        from paper_2505_09324_gb300.raster import FAST_FIT
+        fast = GaussianRasterizer(W, H, N_GAUSS, device=dev,
+                                  config=dataclasses.replace(tuned["config"], **FAST_FIT))
 
-        def encode_from(p_start):
+        def encode_from(p_start, r_enc=fast, every=5):
             p_enc = p_start.clone()
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             with torch.cuda.stream(side):
-                out = rast.encode_frame(frame, p_enc, args.encode_iters,
-                                        target_psnr=args.target_psnr, check_every=25,
-                                        stream=side)
+                out = r_enc.encode_frame(frame, p_enc, args.encode_iters,
+                                         target_psnr=args.target_psnr, check_every=every,
+                                         stream=side)
             side.synchronize()
             secs = time.perf_counter() - t0
             return {"seconds": secs, "iters": out["iters"], "psnr": out["psnr"],
@@ -616,6 +621,7 @@ def run_ours(args):
                     "status": out["status"]}
 
         roi = encode_from(params0)
+        roi_plain_schedule = encode_from(params0, rast, 25)
         # from the learned initialiser shipped with the package (trained on
         # synthetic frames of other seeds), when it matches the frame size
         from paper_2505_09324_gb300.learned import packaged
@@ -628,8 +634,8 @@ def run_ours(args):
             p_learn = net.forward(frame.unsqueeze(0), mask.unsqueeze(0)).clone()
             torch.cuda.synchronize(dev)
             init_l = time.perf_counter() - t0
-            rast.prepare(p_learn)
-            _, l0, _ = rast.render_l2(p_learn, frame)
+            fast.prepare(p_learn)
+            _, l0, _ = fast.render_l2(p_learn, frame)
             psnr0 = float(10 * np.log10(1.0 / max(float(l0[1]), 1e-30)))
             if psnr0 >= args.target_psnr:
                 learned_enc = {"seconds": 0.0, "iters": 0, "psnr": psnr0, "reached": True}
@@ -642,10 +648,20 @@ def run_ours(args):
         from gs2d_inputs import random_gaussians
         p_rand = torch.from_numpy(random_gaussians(N_GAUSS, W, H, seed=SEED + 20)).to(dev)
         rnd = encode_from(p_rand)
+        rnd_plain_schedule = encode_from(p_rand, rast, 25)
         encode = {"target_psnr": args.target_psnr, "cap_iters": args.encode_iters,
+                  "schedule": {"lr": tuned["config"].lr, **FAST_FIT,
+                               "psnr_checks_every": 5},
+                  "roi_init_plain_adam": {**roi_plain_schedule,
+                                          "note": "constant lr 1e-2 for every parameter, "
+                                                  "PSNR checked every 25 iterations"},
                   "roi_init": {**roi, "init_s": init_s, "n_roi": n_roi,
                                "s_per_frame": init_s + roi["seconds"]},
-                  "plain_random_init": rnd, "learned_init": learned_enc}
+                  "plain_random_init": rnd,
+                  "plain_random_init_plain_adam": {**rnd_plain_schedule,
+                                                   "note": "constant lr 1e-2, PSNR checked "
+                                                           "every 25 iterations"},
+                  "learned_init": learned_enc}
 
     batch = None if args.no_batch else measure_batch(args, dev)
     seq = None if args.no_sequence else measure_sequence(args, dev, rast, params0)

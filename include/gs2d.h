@@ -55,7 +55,7 @@ typedef enum {
 
 /* Rasterizer and optimiser constants.  The paper fixes none of them; these
  * are the project's readings (gs2d_config_default): tile 16, stage 64,
- * launch GS2D_LAUNCH_GRID,
+ * launch GS2D_LAUNCH_GRID, learning-rate scales and decay 1,
  * sigma_cut 4.5 (the 3-sigma ellipse), alpha_min 1/255, det_eps 1e-8, Adam
  * lr 1e-2, betas (0.9, 0.999), eps 1e-8.  Tile, stage and launch change only the
  * schedule (which pixels and Gaussians a thread block handles together), never
@@ -73,6 +73,12 @@ typedef struct {
   int32_t launch;    /* render launch form: GS2D_LAUNCH_PERSISTENT (one wave of
                         blocks taking tiles from a queue) or GS2D_LAUNCH_GRID
                         (one block per tile, in queue order) */
+  /* Learning-rate schedule of the fit loop (gs2d_fit_step, gs2d_encode_*):
+   * parameter row r of step t moves with lr * scale(r) * lr_decay^(t-1),
+   * scale = lr_mu (rows mu_x, mu_y), lr_shape (l1, l2, l3), lr_color
+   * (c_r, c_g, c_b), lr_weight (w); all 1 by default (plain Adam).
+   * gs2d_adam_step ignores them. */
+  float lr_mu, lr_shape, lr_color, lr_weight, lr_decay;
 } gs2d_config;
 
 enum { GS2D_LAUNCH_PERSISTENT = 0, GS2D_LAUNCH_GRID = 1 };

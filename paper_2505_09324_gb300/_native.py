@@ -49,7 +49,10 @@ class Config(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("sigma_cut", ctypes.c_float),
                 ("alpha_min", ctypes.c_float), ("det_eps", ctypes.c_float),
                 ("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
-                ("eps", ctypes.c_float), ("stage", ctypes.c_int32), ("launch", ctypes.c_int32)]
+                ("eps", ctypes.c_float), ("stage", ctypes.c_int32), ("launch", ctypes.c_int32),
+                ("lr_mu", ctypes.c_float), ("lr_shape", ctypes.c_float),
+                ("lr_color", ctypes.c_float), ("lr_weight", ctypes.c_float),
+                ("lr_decay", ctypes.c_float)]
 
 
 LAUNCH_PERSISTENT = 0

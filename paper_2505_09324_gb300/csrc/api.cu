@@ -50,7 +50,10 @@ bool cfg_valid(const gs2d_config& c) {
          c.sigma_cut > 0.0f && isfinite(c.sigma_cut) && c.alpha_min > 0.0f &&
          isfinite(c.alpha_min) && c.det_eps >= 0.0f && isfinite(c.det_eps) && c.lr > 0.0f &&
          isfinite(c.lr) && c.beta1 >= 0.0f && c.beta1 < 1.0f && c.beta2 >= 0.0f &&
-         c.beta2 < 1.0f && c.eps > 0.0f && isfinite(c.eps);
+         c.beta2 < 1.0f && c.eps > 0.0f && isfinite(c.eps) && c.lr_mu >= 0.0f &&
+         isfinite(c.lr_mu) && c.lr_shape >= 0.0f && isfinite(c.lr_shape) && c.lr_color >= 0.0f &&
+         isfinite(c.lr_color) && c.lr_weight >= 0.0f && isfinite(c.lr_weight) &&
+         c.lr_decay > 0.0f && c.lr_decay <= 1.0f;
 }
 
 }  // namespace
@@ -76,6 +79,8 @@ void gs2d_config_default(gs2d_config* cfg) {
   cfg->eps = 1e-8f;
   cfg->stage = kStageDefault;
   cfg->launch = GS2D_LAUNCH_GRID;
+  cfg->lr_mu = cfg->lr_shape = cfg->lr_color = cfg->lr_weight = 1.0f;
+  cfg->lr_decay = 1.0f;
 }
 
 size_t gs2d_sizeof_plan(void) { return sizeof(gs2d_plan); }

@@ -89,7 +89,7 @@ k_project_count(int n, ClipSet cs, int tile_shift, float sigma_cut, float alpha_
                 const float* __restrict__ params, float4* __restrict__ rec,
                 int4* __restrict__ rect, int* __restrict__ count, int* __restrict__ tile_cnt,
                 long long* __restrict__ block_sum, WsHeader* __restrict__ hdr, int adam_tick,
-                float b1, float b2) {
+                float b1, float b2, float lr, float lr_decay) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0 && adam_tick) {
     const int t = ++hdr->step;
@@ -99,6 +99,9 @@ k_project_count(int n, ClipSet cs, int tile_shift, float sigma_cut, float alpha_
     hdr->pw2 = p2;
     hdr->bc1 = (float)(1.0 - p1);
     hdr->bc2 = (float)(1.0 - p2);
+    const double pd = t == 1 ? 1.0 : hdr->pwd * lr_decay;
+    hdr->pwd = pd;
+    hdr->lr_now = (float)(lr * pd);
   }
   if (i < n)
     project_one(i, n, clip_of_gaussian(cs, i), tile_shift, sigma_cut, alpha_min, det_eps, params,
@@ -504,7 +507,8 @@ cudaError_t launch_prepare(const gs2d_plan& p, void* ws, const float* params, bo
       p.cfg.det_eps, params,
       ws_ptr<float4>(ws, p, kOffRec), ws_ptr<int4>(ws, p, kOffRect), ws_ptr<int>(ws, p, kOffCount),
       ws_ptr<int>(ws, p, kOffTileCnt), ws_ptr<long long>(ws, p, kOffBlockSum),
-      ws_ptr<WsHeader>(ws, p, kOffHeader), adam_tick ? 1 : 0, p.cfg.beta1, p.cfg.beta2);
+      ws_ptr<WsHeader>(ws, p, kOffHeader), adam_tick ? 1 : 0, p.cfg.beta1, p.cfg.beta2,
+      p.cfg.lr, p.cfg.lr_decay);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_bin_rest(p, ws, s);

@@ -56,7 +56,9 @@ struct WsHeader {
   double pw1, pw2;      // beta1^step, beta2^step
   int32_t queue;        // next render-queue ticket (reset by the last block)
   int32_t done;         // render blocks that have left the queue
-  int32_t pad[44];
+  double pwd;           // lr_decay^(step - 1)
+  float lr_now;         // lr * lr_decay^(step - 1)
+  int32_t pad[41];
 };
 static_assert(sizeof(WsHeader) == 256, "header is one 256-byte block");
 

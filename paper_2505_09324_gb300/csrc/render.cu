@@ -87,8 +87,8 @@ k_reduce_chain(int n, const float* __restrict__ params, const int* __restrict__ 
 __global__ void __launch_bounds__(256)
 k_reduce_chain_adam(int n, float* __restrict__ params, const int* __restrict__ offs,
                     const float4* __restrict__ partial, const WsHeader* __restrict__ hdr,
-                    float* __restrict__ m, float* __restrict__ v, float lr, float b1, float b2,
-                    float eps, const uint8_t* __restrict__ select) {
+                    float* __restrict__ m, float* __restrict__ v, float4 lr_rows, float b1,
+                    float b2, float eps, const uint8_t* __restrict__ select) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = gt / kRL, sub = gt % kRL;
   const bool ok = hdr->entries_raw == (int64_t)hdr->n_entries;  // else over capacity
@@ -105,9 +105,12 @@ k_reduce_chain_adam(int n, float* __restrict__ params, const int* __restrict__ o
   __syncwarp();  // every lane of the group has read the parameters
   if (!act) return;
   const float ibc1 = 1.0f / hdr->bc1, ibc2 = 1.0f / hdr->bc2;
+  const float lr_now = hdr->lr_now;  // lr * lr_decay^(step - 1)
 #pragma unroll
   for (int r = sub; r < 9; r += kRL) {
     const size_t k = (size_t)r * n + i;
+    const float lr = lr_now * (r < 2 ? lr_rows.x : (r < 5 ? lr_rows.y : (r < 8 ? lr_rows.z
+                                                                            : lr_rows.w)));
     const float g = gr[r];
     const float mm = fmaf(b1, m[k], (1.0f - b1) * g);
     const float vv = fmaf(b2, v[k], (1.0f - b2) * g * g);
@@ -212,6 +215,10 @@ int persistent_grid(const void* kernel, int threads, int work) {
   return std::max(1, std::min(work, blocks));
 }
 
+static float4 lr_rows(const gs2d_config& c) {
+  return make_float4(c.lr_mu, c.lr_shape, c.lr_color, c.lr_weight);
+}
+
 static RenderArgs render_args(const gs2d_plan& p, void* ws) {
   RenderArgs a;
   a.clips = clip_set(p, ws);
@@ -314,7 +321,8 @@ cudaError_t launch_fit_step(const gs2d_plan& p, void* ws, const float* target, f
   k_reduce_chain_adam<<<(p.n * kRL + 255) / 256, 256, 0, s>>>(
       p.n, params, ws_ptr<int>(ws, p, kOffCount),
       reinterpret_cast<const float4*>(ws_ptr<float>(ws, p, kOffPartial)),
-      ws_ptr<WsHeader>(ws, p, kOffHeader), m, v, p.cfg.lr, p.cfg.beta1, p.cfg.beta2, p.cfg.eps,
+      ws_ptr<WsHeader>(ws, p, kOffHeader), m, v, lr_rows(p.cfg), p.cfg.beta1, p.cfg.beta2,
+      p.cfg.eps,
       nullptr);
   return cudaGetLastError();
 }
@@ -402,7 +410,8 @@ cudaError_t launch_pframe_step(const gs2d_plan& p, void* ws, const float* target
   k_reduce_chain_adam<<<(p.n * kRL + 255) / 256, 256, 0, s>>>(
       p.n, params, ws_ptr<int>(ws, p, kOffCount),
       reinterpret_cast<const float4*>(ws_ptr<float>(ws, p, kOffPartial)),
-      ws_ptr<WsHeader>(ws, p, kOffHeader), m, v, p.cfg.lr, p.cfg.beta1, p.cfg.beta2, p.cfg.eps,
+      ws_ptr<WsHeader>(ws, p, kOffHeader), m, v, lr_rows(p.cfg), p.cfg.beta1, p.cfg.beta2,
+      p.cfg.eps,
       select);
   return cudaGetLastError();
 }

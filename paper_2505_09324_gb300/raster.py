@@ -35,10 +35,32 @@ class RasterConfig:
     eps: float = 1e-8
     stage: int = 64
     launch: int = nat.LAUNCH_GRID
+    # fit-loop learning-rate scales per parameter group and decay per step
+    lr_mu: float = 1.0
+    lr_shape: float = 1.0
+    lr_color: float = 1.0
+    lr_weight: float = 1.0
+    lr_decay: float = 1.0
+
+    @classmethod
+    def fast_fit(cls, **overrides):
+        """The FAST_FIT schedule (plus any other field overrides)."""
+        return cls(**{**FAST_FIT, **overrides})
 
     def to_c(self) -> nat.Config:
         return nat.Config(self.tile, self.sigma_cut, self.alpha_min, self.det_eps, self.lr,
-                          self.beta1, self.beta2, self.eps, self.stage, self.launch)
+                          self.beta1, self.beta2, self.eps, self.stage, self.launch, self.lr_mu,
+                          self.lr_shape, self.lr_color, self.lr_weight, self.lr_decay)
+
+
+# Learning-rate schedule for fitting a frame from an initialiser (the
+# "dynamic learning rate scheduler" the paper credits without specifying it;
+# tuned on the 1080p conferencing workload: 35 dB in about 35 iterations from
+# the ROI initialisation instead of about 230, monotone PSNR over long fits).
+# Warm starts (P-frames) keep the plain rate: with fresh Adam moments every
+# parameter's first step is a full learning rate.
+FAST_FIT = {"lr_mu": 50.0, "lr_shape": 30.0, "lr_color": 10.0, "lr_weight": 3.0,
+            "lr_decay": 0.995}
 
 
 def _stream(stream) -> int:

@@ -339,3 +339,35 @@ def test_encode_loop_tracks_oracle_trajectory(gs, oracle):
     assert abs(l_gpu - l_ref) <= 1e-3 * l_ref
     # the fit reduced the loss
     assert l_ref < 0.5 * oracle.l2_loss(oracle.render(p0, W, H), target)[0]
+
+
+def test_fast_schedule_tracks_oracle_trajectory(gs, oracle):
+    """The fit loop with the per-group learning rates and decay of the fast
+    schedule against an oracle-driven loop applying Adam row group by row
+    group with lr * scale * decay^(t-1)."""
+    from paper_2505_09324_gb300.raster import FAST_FIT
+    W, H, n, iters = 64, 64, 50, 20
+    p0 = random_gaussians(n, W, H, seed=25, l_range=(2.0, 6.0))
+    target = smooth_noise_target(W, H, seed=26)
+    cfg = gs.RasterConfig.fast_fit()
+    r = gs.GaussianRasterizer(W, H, n, config=cfg)
+    tp = to_dev(p0)
+    r.encode_frame(to_dev(target), tp, iters, check_every=iters)
+    rows = {"lr_mu": slice(0, 2), "lr_shape": slice(2, 5), "lr_color": slice(5, 8),
+            "lr_weight": slice(8, 9)}
+    p = p0.astype(np.float64)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    for it in range(1, iters + 1):
+        g = oracle.loss_and_grad(p.astype(np.float32), target)["grad"]
+        for key, sl in rows.items():
+            lr = cfg.lr * FAST_FIT[key] * FAST_FIT["lr_decay"] ** (it - 1)
+            p[sl], m[sl], v[sl] = oracle.adam_step(p[sl], g[sl], m[sl], v[sl], it, lr=lr)
+    got = tp.cpu().numpy().astype(np.float64)
+    l_gpu = oracle.l2_loss(oracle.render(got, W, H), target)[0]
+    l_ref = oracle.l2_loss(oracle.render(p, W, H), target)[0]
+    l_0 = oracle.l2_loss(oracle.render(p0, W, H), target)[0]
+    assert abs(l_gpu - l_ref) <= 2e-2 * l_ref, (l_gpu, l_ref)
+    assert l_ref < 0.2 * l_0
+    scale = np.abs(p).max(axis=1, keepdims=True) + 1e-3
+    assert np.median(np.abs(got - p) / scale) < 1e-3
