@@ -83,6 +83,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-sequence", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-quant", action="store_true")
+    ap.add_argument("--quant-iters", type=int, default=100)
     ap.add_argument("--schedule", default="",
                     help="tile/stage/launch (e.g. 32/128/grid) instead of the autotuner's pick")
     ap.add_argument("--seq-frames", type=int, default=60)
@@ -355,6 +357,97 @@ def measure_sequence(args, dev, rast, params0):
     return {"frames": len(frames), "iters_per_frame": args.seq_iters, **res,
             "motion": {"v_px_per_frame": mo.v, "omega_deg_per_frame": mo.omega},
             "timing": "wall clock per frame (graph replays, selection, one PSNR check)"}
+
+
+def measure_quant(args, dev, config, frame, mask, bg_xy):
+    """Quantisation of the fitted Gaussians (Sec. 3.3 A; Table 3 compares the
+    latency PTQ and QAT add to 1000 fitting iterations).  PTQ ranges are
+    calibrated on fits of four other synthetic conferencing frames (the
+    training stage); the benchmark frame is fitted from the ROI
+    initialisation with the fast schedule for `quant_iters` iterations and
+    then quantised in one call.  QAT fits the same frame for the same number
+    of iterations with the quantiser inside the loop (ranges refined every
+    step).  Latencies are CUDA-event device times on the launching stream."""
+    import dataclasses
+
+    import torch
+
+    from paper_2505_09324_gb300 import GaussianRasterizer, Quantizer, roi_init
+    from paper_2505_09324_gb300 import _native as nat
+    from paper_2505_09324_gb300.raster import FAST_FIT
+
+    fast = GaussianRasterizer(W, H, N_GAUSS, device=dev,
+                              config=dataclasses.replace(config, **FAST_FIT))
+    iters = args.quant_iters
+
+    def fit(fr, mk, bg):
+        p, _ = roi_init(fr, mk, N_GAUSS, ROI_FRAC, bg)
+        fast.encode_frame(fr, p, iters, check_every=iters)
+        return p
+
+    calib = []
+    for k in range(4):
+        f2, m2, b2 = workload(SEED + 100 + k)
+        calib.append(fit(torch.from_numpy(f2).to(dev),
+                         torch.from_numpy(m2.astype("uint8")).to(dev),
+                         torch.from_numpy(b2).to(dev)))
+    q = Quantizer.calibrate(calib)
+    q_refine = Quantizer(q.bits, refine=True)
+    p0, _ = roi_init(frame, mask, N_GAUSS, ROI_FRAC, bg_xy)
+    p_fit = p0.clone()
+    fast.encode_frame(frame, p_fit, iters, check_every=iters)
+    psnr_float = fast.psnr(frame, p_fit)
+
+    def event_ms(fn, reps):
+        fn()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    ptq = {}
+    s = int(torch.cuda.current_stream(dev).cuda_stream)
+    codes = torch.empty((9, N_GAUSS), dtype=torch.int16, device=dev)
+    vals = torch.empty_like(p_fit)
+    rng = torch.empty((2, 9), device=dev)
+    for name, qq in (("calibrated", q), ("per_frame_ranges", q_refine)):
+        def call(qq=qq):
+            nat.quantize(p_fit.data_ptr(), N_GAUSS, qq.c, codes.data_ptr(), vals.data_ptr(),
+                         rng.data_ptr(), s)
+        walls = []
+        for _ in range(30):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            call()
+            torch.cuda.synchronize(dev)
+            walls.append(time.perf_counter() - t0)
+        ptq[name] = {"psnr": fast.psnr(frame, vals),
+                     "latency_ms": 1e3 * statistics.median(walls),
+                     "device_ms": event_ms(call, 1)}
+    p_qat = p0.clone()
+    qat = fast.encode_frame_qat(frame, p_qat, iters, q_refine)
+    # per-iteration device time, fit step with and without the quantiser
+    pp, m, v = p_fit.clone(), torch.zeros_like(p_fit), torch.zeros_like(p_fit)
+    tgt = frame.data_ptr()
+    plain_ms = event_ms(lambda: nat.fit_step(fast.plan, fast.ws_ptr, tgt, pp.data_ptr(),
+                                             m.data_ptr(), v.data_ptr(), s), 200)
+    qat_ms = event_ms(lambda: nat.fit_step_qat(fast.plan, fast.ws_ptr, tgt, pp.data_ptr(),
+                                               m.data_ptr(), v.data_ptr(), q_refine.c, s), 200)
+    return {"fit_iters": iters, "bits": list(q.bits), "bits_per_gaussian": q.bits_per_gaussian,
+            "frame_bytes": q.frame_bytes(N_GAUSS),
+            "bpp": 8 * q.frame_bytes(N_GAUSS) / (W * H),
+            "psnr_float": psnr_float, "ptq": ptq,
+            "qat": {"psnr_float": qat["psnr"], "psnr_quantised": qat["psnr_q"],
+                    "ms_per_iter": qat_ms, "ms_per_iter_without": plain_ms,
+                    "overhead_ms_per_1000_iters": 1000 * (qat_ms - plain_ms)},
+            "calibration": "row spans over 4 fitted frames of other seeds",
+            "timing": "PTQ latency: wall clock of one synchronised call (median of 30); "
+                      "device: CUDA events around one call; QAT: CUDA events over 200 fit "
+                      "steps launched one by one (no graph)"}
 
 
 def measure_learned(dev, frame, mask, peaks):
@@ -672,6 +765,8 @@ def run_ours(args):
     except OSError:
         peaks = {"bf16_tflops": 1900.0, "source": "of fallback (1.9 PFLOP/s bf16 burst)"}
     learned = None if args.no_learned else measure_learned(dev, frame, mask, peaks)
+    quant = None if args.no_quant else measure_quant(args, dev, tuned["config"], frame, mask,
+                                                     bg_xy)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -707,7 +802,8 @@ def run_ours(args):
                                                       for (a, b, c), v in tuned["ms"].items()}},
                 "pairs": {"listed_first": pairs0, "hits_first": hits0, "listed_last": pairs1,
                           "hits_last": hits1},
-                "encode": encode, "batch": batch, "sequence": seq, "learned_init": learned}
+                "encode": encode, "batch": batch, "sequence": seq, "learned_init": learned,
+                "quantisation": quant}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

@@ -283,6 +283,43 @@ gs2d_status gs2d_encode_pframe(const gs2d_plan* plan, void* ws, const float* tar
                                const uint8_t* selected, int32_t iters, float* final_psnr,
                                void* stream);
 
+/* Quantisation of Gaussians (Sec. 3.3 A: distinct quantisers for the mean,
+ * the Cholesky factor and the colour; the paper adopts GaussianImage's, which
+ * it does not specify).  Per parameter row r (mu_x, mu_y, l1, l2, l3, c_r,
+ * c_g, c_b, w): bits[r] = -16 stores the row as IEEE half (round to nearest
+ * even, NaN coded 0x7E00); bits[r] in 1 ... 16 is a uniform scalar quantiser
+ * over [lo[r], hi[r]]:
+ * code = clamp(rint((x - lo) * scale), 0, 2^b - 1), value = lo + code * step,
+ * in single-rounded float operations, with scale = (2^b - 1) / (hi - lo) and
+ * step = (hi - lo) / (2^b - 1) evaluated in double and rounded to float;
+ * bits[r] = 0 keeps float32.  Non-finite inputs are coded 0.
+ * refine = 0: lo, scale and step are the caller's (hi documents the range).
+ * refine != 0: each uniform row's range is [min, max] of the row's finite
+ * values, derived on the device for every call (QAT's quantisation
+ * parameters follow the Gaussians); a row with no spread gets scale = step = 0
+ * (every code 0, value lo). */
+typedef struct {
+  int32_t bits[9];
+  int32_t refine;
+  float lo[9], hi[9];
+  float scale[9], step[9];
+} gs2d_quant;
+
+/* Post-training quantisation: codes (device uint16 [9][n], or NULL; halves as
+ * their bit patterns, unquantised rows as 0), dequantised parameters (device
+ * float [9][n], or NULL) and the ranges used (device float [2][9]: lo row, hi
+ * row; 0 for rows that are not uniform; or NULL) of params (device float
+ * [9][n]).  For n > 0 at least one of codes and dequant must be given. */
+gs2d_status gs2d_quantize(const float* params, int32_t n, const gs2d_quant* q, uint16_t* codes,
+                          float* dequant, float* ranges, void* stream);
+
+/* Quantisation-aware fit iteration (Sec. 3.3 A, QAT): params are
+ * fake-quantised with q, the frame is rendered from the quantised values and
+ * the gradient taken there, and Adam updates the float params (the
+ * straight-through estimator).  Otherwise as gs2d_fit_step. */
+gs2d_status gs2d_fit_step_qat(const gs2d_plan* plan, void* ws, const float* target, float* params,
+                              float* adam_m, float* adam_v, const gs2d_quant* q, void* stream);
+
 /* Device scratch (bytes, 256-byte aligned start) that gs2d_roi_init needs for
  * a W x H frame and n Gaussians. */
 uint64_t gs2d_roi_init_scratch_bytes(int32_t width, int32_t height, int32_t n);

@@ -7,8 +7,9 @@ the frame-fitting loop are hand-written CUDA kernels in ``libgs2d.so`` behind
 the C ABI of ``include/gs2d.h``; this package is a thin binding over it.
 """
 
+from .quant import Quantizer  # noqa: F401
 from .raster import (BatchRasterizer, GaussianRasterizer, RasterConfig, adam_step,  # noqa: F401
                      autotune, encode_sequence, roi_init)
 
-__all__ = ["BatchRasterizer", "GaussianRasterizer", "RasterConfig", "adam_step", "autotune",
-           "encode_sequence", "roi_init"]
+__all__ = ["BatchRasterizer", "GaussianRasterizer", "Quantizer", "RasterConfig", "adam_step",
+           "autotune", "encode_sequence", "roi_init"]

@@ -27,7 +27,8 @@ EXPORTS = (
     "gs2d_project", "gs2d_bin_sort", "gs2d_prepare", "gs2d_render_fwd", "gs2d_render_fwd_noalloc",
     "gs2d_render_bwd", "gs2d_render_l2",
     "gs2d_adam_step", "gs2d_fit_step", "gs2d_fit_reset", "gs2d_encode_frame", "gs2d_clip_losses",
-    "gs2d_select_changed", "gs2d_pframe_step", "gs2d_encode_pframe",
+    "gs2d_select_changed", "gs2d_pframe_step", "gs2d_encode_pframe", "gs2d_quantize",
+    "gs2d_fit_step_qat",
     "gs2d_encode_batch",
     "gs2d_autotune_ws_bytes", "gs2d_autotune",
     "gs2d_gemm_bf16", "gs2d_gemm_partial_bytes", "gs2d_cnn_input", "gs2d_im2col", "gs2d_col2im",
@@ -64,6 +65,13 @@ class Clip(ctypes.Structure):
                 ("tiles_x", ctypes.c_int32), ("tiles_y", ctypes.c_int32),
                 ("g_off", ctypes.c_int32), ("tile_off", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("pix_off", ctypes.c_int64)]
+
+
+class Quant(ctypes.Structure):
+    _fields_ = [("bits", ctypes.c_int32 * 9), ("refine", ctypes.c_int32),
+                ("lo", ctypes.c_float * 9),
+                ("hi", ctypes.c_float * 9), ("scale", ctypes.c_float * 9),
+                ("step", ctypes.c_float * 9)]
 
 
 class Plan(ctypes.Structure):
@@ -131,6 +139,8 @@ def load(build_if_missing: bool = False):
             "gs2d_select_changed": (i32, [pp, P, P, P, f32, P, ctypes.POINTER(i32), P]),
             "gs2d_pframe_step": (i32, [pp, P, P, P, P, P, P, P]),
             "gs2d_encode_pframe": (i32, [pp, P, P, P, P, P, P, i32, ctypes.POINTER(f32), P]),
+            "gs2d_quantize": (i32, [P, i32, ctypes.POINTER(Quant), P, P, P, P]),
+            "gs2d_fit_step_qat": (i32, [pp, P, P, P, P, P, ctypes.POINTER(Quant), P]),
             "gs2d_read_bins": (i32, [pp, P, P, P, P, i64, P, P, P]),
             "gs2d_count_pairs": (i32, [pp, P, ctypes.POINTER(i64), ctypes.POINTER(i64), P]),
             "gs2d_ws_status": (i32, [pp, P, i32, P]),
@@ -402,3 +412,32 @@ def call(name: str, *args):
     for a, t in zip(args, fn.argtypes):
         conv.append(_p(a) if t is ctypes.c_void_p else a)
     check(fn(*conv), name)
+
+
+def make_quant(bits, lo=None, hi=None, refine: bool = False) -> Quant:
+    """Quantiser spec: bits per row (-16 half, 0 none, 1..16 uniform over
+    [lo, hi]); scale and step computed in double, rounded to float.  With
+    refine the library derives each uniform row's range on the device."""
+    q = Quant()
+    q.refine = int(bool(refine))
+    for r in range(9):
+        b = int(bits[r])
+        q.bits[r] = b
+        if b > 0 and not refine:
+            lo_r, hi_r = float(lo[r]), float(hi[r])
+            q.lo[r], q.hi[r] = lo_r, hi_r
+            levels = (1 << b) - 1
+            q.scale[r] = levels / (hi_r - lo_r)
+            q.step[r] = (hi_r - lo_r) / levels
+    return q
+
+
+def quantize(params: int, n: int, q: Quant, codes: int, dequant: int, ranges: int, stream: int):
+    check(load().gs2d_quantize(_p(params), n, ctypes.byref(q), _p(codes), _p(dequant),
+                               _p(ranges), _p(stream)), "gs2d_quantize")
+
+
+def fit_step_qat(plan: Plan, ws: int, target: int, params: int, m: int, v: int, q: Quant,
+                 stream: int):
+    check(load().gs2d_fit_step_qat(ctypes.byref(plan), _p(ws), _p(target), _p(params), _p(m),
+                                   _p(v), ctypes.byref(q), _p(stream)), "gs2d_fit_step_qat")

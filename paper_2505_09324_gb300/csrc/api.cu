@@ -171,6 +171,7 @@ gs2d_status gs2d_plan_init_batch(gs2d_plan* plan, gs2d_clip* clips, int32_t num_
   sz[kOffClipLoss] = (uint64_t)num_clips * sizeof(float2);
   sz[kOffActive] = nt;
   sz[kOffActOrder] = (nt + 1) * sizeof(int);
+  sz[kOffQuant] = 9 * nn * sizeof(float);
   sz[kOffGrad] = 9 * nn * sizeof(float);
   uint64_t off = 0;
   for (int sec = 0; sec < kNumSections; sec++) {

@@ -39,6 +39,7 @@ enum WsSection {
   kOffClipLoss,     // float2[num_clips]
   kOffActive,       // uint8[num_tiles] P-frame: tile touched by a selected Gaussian
   kOffActOrder,     // int32[num_tiles + 1] P-frame: active tiles (count last)
+  kOffQuant,        // float[9 n] quantisation-aware fitting: the fake-quantised parameters
   kOffGrad,         // float[9 n] gradient scratch
   kNumSections
 };
@@ -257,8 +258,11 @@ cudaError_t launch_render_bwd(const gs2d_plan& p, void* ws, const float* params,
 cudaError_t launch_render_l2(const gs2d_plan& p, void* ws, const float* params,
                              const float* target, float* grads, float* img, float* loss,
                              cudaStream_t s);
+// params_eval: the values the render used, when they differ from params (the
+// chain rule is taken there; Adam updates params)
 cudaError_t launch_fit_step(const gs2d_plan& p, void* ws, const float* target, float* params,
-                            float* m, float* v, cudaStream_t s);
+                            float* m, float* v, cudaStream_t s,
+                            const float* params_eval = nullptr);
 cudaError_t launch_adam(float* params, const float* grads, float* m, float* v, int64_t count,
                         int32_t step, const uint8_t* mask, const gs2d_config& cfg,
                         cudaStream_t s);
@@ -269,6 +273,9 @@ cudaError_t launch_select_changed(const gs2d_plan& p, void* ws, const float* ref
                                   const float* frame, float threshold, uint8_t* selected,
                                   cudaStream_t s);
 cudaError_t launch_count_flags(int n, const uint8_t* flags, int* out, cudaStream_t s);
+// Quantisation (quant.cu): codes, dequantised values and ranges of params.
+cudaError_t launch_quantize(const float* params, int n, const gs2d_quant& q, uint16_t* codes,
+                            float* dequant, float* ranges, cudaStream_t s);
 cudaError_t launch_pframe_step(const gs2d_plan& p, void* ws, const float* target,
                                float* params, float* m, float* v, const uint8_t* select,
                                cudaStream_t s);

@@ -1,0 +1,206 @@
+// Quantisation of Gaussian parameters (Sec. 3.3 A): IEEE half or uniform
+// scalar quantisers per parameter row; post-training quantisation and the
+// fake quantisation of quantisation-aware fitting (QAT).
+#include <cooperative_groups.h>
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include "gs2d_internal.cuh"
+
+namespace gs2d {
+namespace {
+
+struct QuantArgs {
+  int bits[9];
+  float lo[9], hi[9], scale[9], step[9];
+};
+
+// One parameter: code and dequantised value.
+__device__ __forceinline__ void quant_one(float x, int b, float lo, float scale, float step,
+                                          uint16_t& c, float& y) {
+  c = 0;
+  y = x;
+  if (b < 0) {  // IEEE half, round to nearest even; NaN as 0x7E00
+    const __half h = __float2half_rn(x);
+    c = isnan(x) ? (uint16_t)0x7E00 : __half_as_ushort(h);
+    y = __half2float(h);
+  } else if (b > 0) {
+    const float top = (float)((1 << b) - 1);
+    float k = isfinite(x) ? rintf(__fmul_rn(__fsub_rn(x, lo), scale)) : 0.0f;
+    k = fminf(fmaxf(k, 0.0f), top);
+    c = (uint16_t)k;
+    y = __fadd_rn(lo, __fmul_rn(k, step));
+  }
+}
+
+// Caller-given ranges: grid-stride over all 9 n parameters.
+__global__ void __launch_bounds__(256)
+k_quantize(const float* __restrict__ params, int n, QuantArgs q, uint16_t* __restrict__ codes,
+           float* __restrict__ dequant, float* __restrict__ ranges) {
+  if (ranges && blockIdx.x == 0 && threadIdx.x < 9) {
+    const int r = threadIdx.x;
+    ranges[r] = q.bits[r] > 0 ? q.lo[r] : 0.0f;
+    ranges[9 + r] = q.bits[r] > 0 ? q.hi[r] : 0.0f;
+  }
+  const size_t total = (size_t)9 * n;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / n);
+    uint16_t c;
+    float y;
+    quant_one(params[t], q.bits[r], q.lo[r], q.scale[r], q.step[r], c, y);
+    if (codes) codes[t] = c;
+    if (dequant) dequant[t] = y;
+  }
+}
+
+// Refined ranges: a cluster of kRefineCluster blocks takes one row (blockIdx.y);
+// each block reduces [min, max] of the finite values of its chunk, the
+// cluster combines the partial ranges through distributed shared memory
+// (min and max are order-independent, so every block derives the same range),
+// then each block quantises its chunk.
+constexpr int kRefineCluster = 8;
+constexpr int kRefineThreads = 256;
+
+__global__ void __cluster_dims__(kRefineCluster, 1, 1) __launch_bounds__(kRefineThreads)
+k_quantize_refine(const float* __restrict__ params, int n, QuantArgs q,
+                  uint16_t* __restrict__ codes, float* __restrict__ dequant,
+                  float* __restrict__ ranges) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  __shared__ float s_lo[kRefineThreads / 32], s_hi[kRefineThreads / 32];
+  __shared__ float s_part[2];
+  __shared__ float s_q[3];
+  const int r = blockIdx.y;
+  const int b = q.bits[r];
+  const int chunk = (n + kRefineCluster - 1) / kRefineCluster;
+  const int i0 = min(n, (int)blockIdx.x * chunk), i1 = min(n, i0 + chunk);
+  const float* row = params + (size_t)r * n;
+  float lo = INFINITY, hi = -INFINITY;
+  if (b > 0)
+    for (int i = i0 + threadIdx.x; i < i1; i += kRefineThreads) {
+      const float x = row[i];
+      if (isfinite(x)) {
+        lo = fminf(lo, x);
+        hi = fmaxf(hi, x);
+      }
+    }
+  for (int o = 16; o; o >>= 1) {
+    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s_lo[threadIdx.x >> 5] = lo;
+    s_hi[threadIdx.x >> 5] = hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kRefineThreads / 32; w++) {
+      lo = fminf(lo, s_lo[w]);
+      hi = fmaxf(hi, s_hi[w]);
+    }
+    s_part[0] = lo;
+    s_part[1] = hi;
+  }
+  cluster.sync();  // every block's partial range is visible cluster-wide
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < kRefineCluster; k++) {
+      const float* part = cluster.map_shared_rank(s_part, k);
+      lo = fminf(lo, part[0]);
+      hi = fmaxf(hi, part[1]);
+    }
+    if (!(lo <= hi)) lo = hi = 0.0f;  // no finite value (or not a uniform row)
+    float scale = 0.0f, step = 0.0f;
+    if (b > 0 && hi > lo) {
+      const double levels = (double)((1 << b) - 1);
+      const double d = (double)hi - (double)lo;
+      scale = __double2float_rn(levels / d);
+      step = __double2float_rn(d / levels);
+    }
+    s_q[0] = b > 0 ? lo : 0.0f;
+    s_q[1] = scale;
+    s_q[2] = step;
+    if (ranges && blockIdx.x == 0) {
+      ranges[r] = b > 0 ? lo : 0.0f;
+      ranges[9 + r] = b > 0 ? hi : 0.0f;
+    }
+  }
+  __syncthreads();
+  const float qlo = s_q[0], scale = s_q[1], step = s_q[2];
+  for (int i = i0 + threadIdx.x; i < i1; i += kRefineThreads) {
+    uint16_t c;
+    float y;
+    quant_one(row[i], b, qlo, scale, step, c, y);
+    if (codes) codes[(size_t)r * n + i] = c;
+    if (dequant) dequant[(size_t)r * n + i] = y;
+  }
+  cluster.sync();  // no block leaves while a peer may still read its s_part
+}
+
+}  // namespace
+
+cudaError_t launch_quantize(const float* params, int n, const gs2d_quant& q, uint16_t* codes,
+                            float* dequant, float* ranges, cudaStream_t s) {
+  QuantArgs a;
+  for (int r = 0; r < 9; r++) {
+    a.bits[r] = q.bits[r];
+    // refined ranges of an empty set are [0, 0]
+    a.lo[r] = q.refine ? 0.0f : q.lo[r];
+    a.hi[r] = q.refine ? 0.0f : q.hi[r];
+    a.scale[r] = q.scale[r];
+    a.step[r] = q.step[r];
+  }
+  if (n > 0 && q.refine) {
+    k_quantize_refine<<<dim3(kRefineCluster, 9), kRefineThreads, 0, s>>>(params, n, a, codes,
+                                                                         dequant, ranges);
+    return cudaGetLastError();
+  }
+  const size_t want = ((size_t)9 * (n > 0 ? n : 0) + 255) / 256;
+  const int blocks = (int)(want < 1 ? 1 : (want < 152 * 8 ? want : 152 * 8));
+  k_quantize<<<blocks, 256, 0, s>>>(params, n > 0 ? n : 0, a, codes, dequant, ranges);
+  return cudaGetLastError();
+}
+
+}  // namespace gs2d
+
+using namespace gs2d;
+
+static bool quant_valid(const gs2d_quant* q) {
+  if (!q) return false;
+  for (int r = 0; r < 9; r++) {
+    const int b = q->bits[r];
+    if (!(b == -16 || (b >= 0 && b <= 16))) return false;
+    if (b > 0 && !q->refine &&
+        !(isfinite(q->lo[r]) && isfinite(q->scale[r]) && isfinite(q->step[r]) &&
+          q->scale[r] > 0.0f && q->step[r] > 0.0f))
+      return false;
+  }
+  return true;
+}
+
+extern "C" gs2d_status gs2d_quantize(const float* params, int32_t n, const gs2d_quant* q,
+                                     uint16_t* codes, float* dequant, float* ranges,
+                                     void* stream) {
+  if (n < 0 || !quant_valid(q) || (n > 0 && (!params || (!codes && !dequant))))
+    return set_error(GS2D_ERR_INVALID_ARG, "gs2d_quantize: arguments");
+  const cudaError_t e =
+      launch_quantize(params, n, *q, codes, dequant, ranges, (cudaStream_t)stream);
+  if (e != cudaSuccess) return set_error(GS2D_ERR_CUDA, cudaGetErrorString(e));
+  return set_error(GS2D_OK, "");
+}
+
+extern "C" gs2d_status gs2d_fit_step_qat(const gs2d_plan* plan, void* ws, const float* target,
+                                         float* params, float* adam_m, float* adam_v,
+                                         const gs2d_quant* q, void* stream) {
+  if (!plan || plan->magic != kPlanMagic || !ws || ((uintptr_t)ws % 256) || !target ||
+      !quant_valid(q) || (plan->n > 0 && (!params || !adam_m || !adam_v)))
+    return set_error(GS2D_ERR_INVALID_ARG, "gs2d_fit_step_qat: arguments");
+  const gs2d_plan& p = *plan;
+  cudaStream_t s = (cudaStream_t)stream;
+  float* pq = ws_ptr<float>(ws, p, kOffQuant);
+  cudaError_t e = launch_quantize(params, p.n, *q, nullptr, pq, nullptr, s);
+  if (e == cudaSuccess) e = launch_prepare(p, ws, pq, true, s);
+  if (e == cudaSuccess) e = launch_fit_step(p, ws, target, params, adam_m, adam_v, s, pq);
+  if (e != cudaSuccess) return set_error(GS2D_ERR_CUDA, cudaGetErrorString(e));
+  return set_error(GS2D_OK, "");
+}

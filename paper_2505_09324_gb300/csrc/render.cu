@@ -88,7 +88,8 @@ __global__ void __launch_bounds__(256)
 k_reduce_chain_adam(int n, float* __restrict__ params, const int* __restrict__ offs,
                     const float4* __restrict__ partial, const WsHeader* __restrict__ hdr,
                     float* __restrict__ m, float* __restrict__ v, float4 lr_rows, float b1,
-                    float b2, float eps, const uint8_t* __restrict__ select) {
+                    float b2, float eps, const uint8_t* __restrict__ select,
+                    const float* __restrict__ params_eval) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = gt / kRL, sub = gt % kRL;
   const bool ok = hdr->entries_raw == (int64_t)hdr->n_entries;  // else over capacity
@@ -98,8 +99,10 @@ k_reduce_chain_adam(int n, float* __restrict__ params, const int* __restrict__ o
   const bool any = gather_partials(partial, offs, i, on && ok, sub, a);
   if (!ok) return;  // the same for every thread of the grid
   const bool act = on;
+  // the chain rule at the parameters that were rendered (the fake-quantised
+  // ones of quantisation-aware fitting; the same array otherwise)
   if (act && any)
-    chain_grads(params, n, i, a, gr);
+    chain_grads(params_eval ? params_eval : params, n, i, a, gr);
   else
     for (int r = 0; r < 9; r++) gr[r] = 0.0f;
   __syncwarp();  // every lane of the group has read the parameters
@@ -313,7 +316,7 @@ cudaError_t launch_count_pairs(const gs2d_plan& p, void* ws, cudaStream_t s) {
 // One fit iteration after projection and binning (which advanced the Adam
 // step counter): fused render + loss + backward, then reduction + chain + Adam.
 cudaError_t launch_fit_step(const gs2d_plan& p, void* ws, const float* target, float* params,
-                            float* m, float* v, cudaStream_t s) {
+                            float* m, float* v, cudaStream_t s, const float* params_eval) {
   RenderArgs a = render_args(p, ws);
   a.target = target;
   cudaError_t e = launch_render(p, kModeL2, a, s);
@@ -322,8 +325,7 @@ cudaError_t launch_fit_step(const gs2d_plan& p, void* ws, const float* target, f
       p.n, params, ws_ptr<int>(ws, p, kOffCount),
       reinterpret_cast<const float4*>(ws_ptr<float>(ws, p, kOffPartial)),
       ws_ptr<WsHeader>(ws, p, kOffHeader), m, v, lr_rows(p.cfg), p.cfg.beta1, p.cfg.beta2,
-      p.cfg.eps,
-      nullptr);
+      p.cfg.eps, nullptr, params_eval);
   return cudaGetLastError();
 }
 
@@ -411,8 +413,7 @@ cudaError_t launch_pframe_step(const gs2d_plan& p, void* ws, const float* target
       p.n, params, ws_ptr<int>(ws, p, kOffCount),
       reinterpret_cast<const float4*>(ws_ptr<float>(ws, p, kOffPartial)),
       ws_ptr<WsHeader>(ws, p, kOffHeader), m, v, lr_rows(p.cfg), p.cfg.beta1, p.cfg.beta2,
-      p.cfg.eps,
-      select);
+      p.cfg.eps, select, nullptr);
   return cudaGetLastError();
 }
 

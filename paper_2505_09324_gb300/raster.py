@@ -11,6 +11,7 @@ Eq. 1, colour; w weights the colour, c' = w c in Eq. 2).  Images are float32
 from __future__ import annotations
 
 import dataclasses
+import math
 
 import torch
 
@@ -199,6 +200,38 @@ class GaussianRasterizer:
         if st not in (nat.GS2D_OK, nat.GS2D_ERR_CAPACITY):
             nat.check(st, "gs2d_encode_frame")
         return {"status": st, "iters": done, "psnr": final, "trace": trace}
+
+    def encode_frame_qat(self, target: torch.Tensor, params: torch.Tensor, iters: int,
+                         quantizer, adam_state=None, stream=None):
+        """Quantisation-aware fit (Sec. 3.3 A, QAT): ``iters`` iterations of
+        gs2d_fit_step_qat from fresh Adam moments, each rendering the Gaussians
+        as ``quantizer`` codes them (straight-through gradient to the float
+        ``params``, updated in place).  Returns the PSNR of the float and of
+        the quantised fit, and the quantiser's output for the final params."""
+        if adam_state is None:
+            adam_state = (torch.empty_like(params), torch.empty_like(params))
+        m, v = adam_state
+        shape = (9, self.n)
+        t = _check(target, "target", self.image_shape())
+        p = _check(params, "params", shape)
+        mp, vp = _check(m, "adam_m", shape), _check(v, "adam_v", shape)
+        s = _stream(stream)
+        nat.fit_reset(self.plan, self.ws_ptr, mp, vp, s)
+        for _ in range(iters):
+            nat.fit_step_qat(self.plan, self.ws_ptr, t, p, mp, vp, quantizer.c, s)
+        self.version += 1
+        codes, values, ranges = quantizer.quantize(params, stream=stream)
+        return {"psnr": self.psnr(target, params, stream), "psnr_q": self.psnr(target, values,
+                                                                               stream),
+                "codes": codes, "values": values, "ranges": ranges}
+
+    def psnr(self, target: torch.Tensor, params: torch.Tensor, stream=None) -> float:
+        """PSNR of the clamped render of ``params`` against ``target``
+        (re-bins the workspace)."""
+        self.prepare(params, stream=stream)
+        _, loss, _ = self.render_l2(params, target, stream=stream)
+        mse = float(loss[1].item())
+        return 10.0 * math.log10(1.0 / max(mse, 1e-30))
 
 
 def encode_sequence(rast: GaussianRasterizer, frames, params: torch.Tensor, iters_first: int,

@@ -53,7 +53,7 @@ def test_plan_layout(nat):
     assert (p.tiles_x, p.tiles_y, p.num_tiles) == (120, 68, 8160)
     assert p.tile_bits == 13 and p.num_clips == 1 and p.stage == 64
     assert p.max_entries == max(1 << 20, 16 * 20000) and p.pixels == 1920 * 1080
-    offs = list(p.off)[:20]
+    offs = list(p.off)[:21]
     assert all(o % 256 == 0 for o in offs)
     assert offs == sorted(offs) and p.ws_bytes > offs[-1]
     q = nat.plan_init(16, 16, 5)
@@ -92,7 +92,7 @@ def test_batch_plan_offsets(nat):
         assert (c.g_off, c.tile_off, c.pix_off) == (g, t, 3 * px)
         g, t, px = g + n, t + c.tiles_x * c.tiles_y, px + w * h
     assert p.num_tiles == t and p.pixels == px
-    offs = list(p.off)[:20]
+    offs = list(p.off)[:21]
     assert all(o % 256 == 0 for o in offs) and offs == sorted(offs)
 
 
@@ -147,3 +147,39 @@ def test_calls_reject_bad_arguments_without_touching_the_gpu(nat):
     with pytest.raises(nat.Gs2dError):
         nat.adam_step(0x1000, 0x1000, 0x1000, 0x1000, 9, 0, 0, None, 0)  # step 0
     assert "step" in nat.last_error()
+
+
+def test_quantizer_arguments_checked_before_any_launch(nat):
+    ok = nat.make_quant([-16] * 9)
+    bad_bits = nat.Quant()
+    bad_bits.bits[0] = 17
+    assert nat.load().gs2d_quantize(None, 0, ctypes.byref(bad_bits), None, None, None,
+                                    None) == nat.GS2D_ERR_INVALID_ARG
+    # neither codes nor values asked for
+    assert nat.load().gs2d_quantize(ctypes.c_void_p(256), 4, ctypes.byref(ok), None, None,
+                                    None, None) == nat.GS2D_ERR_INVALID_ARG
+    # a uniform row without a valid range (and no refine)
+    nr = nat.Quant()
+    nr.bits[0], nr.lo[0], nr.hi[0] = 8, 1.0, 1.0        # scale and step 0
+    assert nat.load().gs2d_quantize(None, 0, ctypes.byref(nr), None, None, None,
+                                    None) == nat.GS2D_ERR_INVALID_ARG
+    p = nat.plan_init(64, 64, 10)
+    assert nat.load().gs2d_fit_step_qat(ctypes.byref(p), None, None, None, None, None,
+                                        ctypes.byref(ok), None) == nat.GS2D_ERR_INVALID_ARG
+
+
+def test_quantizer_spec_host_side():
+    import numpy as np
+    from paper_2505_09324_gb300.quant import HALF, Quantizer
+    bits = (HALF, HALF, 8, 8, 8, 8, 8, 8, 8)
+    q = Quantizer.calibrate([np.tile(np.linspace(-1, 1, 1001, dtype=np.float32), (9, 1))],
+                            bits, coverage=1.0)
+    assert q.bits_per_gaussian == 32 + 7 * 8
+    assert q.lo[2] == -1.0 and q.hi[2] == 1.0
+    assert q.c.scale[2] == np.float32(255 / 2) and q.c.step[2] == np.float32(2 / 255)
+    assert q.frame_bytes(20000) == 20000 * 88 // 8 + 7 * 8
+    assert Quantizer(refine=True).bits_per_gaussian == 2 * 16 + 3 * 10 + 4 * 8
+    with pytest.raises(ValueError):
+        Quantizer([HALF] * 8)
+    with pytest.raises(ValueError):
+        Quantizer([8] * 9)               # uniform rows need ranges or refine
