@@ -37,12 +37,15 @@ def bitsback_saving(m: int) -> float:
     return log2_factorial(m) - math.log2(m)
 
 
-def code_entropy_bits(codes, bits) -> np.ndarray:
-    """Ideal order-0 code length, per parameter row, of [9, n] codes: the
-    sum over the row's distinct symbols s of -c_s log2(c_s / n).  Rows kept
-    as float32 (bits 0) count 32 bits per value; IEEE-half rows are coded
-    like the others (16-bit symbols)."""
+def code_entropy_bits(codes, bits, select=None) -> np.ndarray:
+    """Ideal order-0 code length, per parameter row, of [9, n] codes (only the
+    columns with select[i] != 0 when select is given): the sum over the
+    row's distinct symbols s of -c_s log2(c_s / n).  Rows kept as float32
+    (bits 0) count 32 bits per value; IEEE-half rows are coded like the
+    others (16-bit symbols)."""
     c = np.asarray(codes, np.uint16).reshape(9, -1)
+    if select is not None:
+        c = c[:, np.asarray(select).astype(bool)]
     n = c.shape[1]
     out = np.zeros(9)
     for r in range(9):
@@ -56,19 +59,20 @@ def code_entropy_bits(codes, bits) -> np.ndarray:
     return out
 
 
-def sequence_bits(counts, K: int, n: int, bits_i_frame, bits_per_coded: float):
-    """Eq. 3-4 over a sequence.  counts[k] = Gaussians coded in frame k (n on
-    an I-frame); bits_i_frame[k] = vanilla-coded size of frame k when it is
-    an I-frame; bits_per_coded = code bits of one P-frame Gaussian (its codes
-    plus its index).  Returns a dict with the I-frame bits, the P-frame bits
-    before bits-back, the total bits-back saving and the total."""
+def sequence_bits(counts, payload_bits, K: int):
+    """Eq. 3-4 over a sequence of F frames.  counts[k] = Gaussians coded in
+    frame k; payload_bits[k] = its coded size before bits-back (an I-frame:
+    the vanilla entropy-coded Gaussians; a P-frame: its coded Gaussians with
+    their indices).  Frame k is an I-frame when k mod K = 0; every P-frame
+    saves bitsback_saving(counts[k]).  Returns the I-frame bits, the P-frame
+    bits before bits-back, the total saving and the total."""
     F = len(counts)
     i_bits = p_bits = saving = 0.0
     for k in range(F):
         if k % K == 0:
-            i_bits += float(bits_i_frame[k])
+            i_bits += float(payload_bits[k])
         else:
-            p_bits += counts[k] * bits_per_coded
+            p_bits += float(payload_bits[k])
             saving += bitsback_saving(counts[k])
     return {"i_bits": i_bits, "p_bits": p_bits, "savings": saving,
             "total_bits": i_bits + p_bits - saving,

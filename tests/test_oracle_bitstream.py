@@ -38,7 +38,8 @@ def test_sequence_with_constant_p_counts_is_eq4():
     F, K, N = 60, 4, 20000
     m = N // 20
     counts = [N if k % K == 0 else m for k in range(F)]
-    res = B.sequence_bits(counts, K, N, [1e6] * F, 100.0)
+    payload = [1e6 if k % K == 0 else m * 100.0 for k in range(F)]
+    res = B.sequence_bits(counts, payload, K)
     assert res["i_frames"] == F // K and res["p_frames"] == F - F // K
     # Eq. 4: S_total = (F - F/K) S_P
     assert res["savings"] == pytest.approx((F - F / K) * B.bitsback_saving(m), rel=1e-12)
@@ -68,3 +69,8 @@ def test_code_entropy_closed_forms():
     rng = np.random.default_rng(0)
     r = rng.integers(0, 1 << 10, (9, 3000)).astype(np.uint16)
     assert np.all(B.code_entropy_bits(r, [10] * 9) <= 10 * 3000 + 1e-6)
+    # a selection codes only its columns
+    sel = np.zeros(n, np.uint8)
+    sel[::2] = 1
+    es = B.code_entropy_bits(c, bits, sel)
+    assert es[0] == pytest.approx((n // 2) * 11.0) and es[2] == 0.0
