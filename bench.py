@@ -28,6 +28,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -90,6 +91,7 @@ def parse():
     ap.add_argument("--seq-frames", type=int, default=60)
     ap.add_argument("--seq-iters", type=int, default=300)
     ap.add_argument("--seq-threshold", type=float, default=0.02)
+    ap.add_argument("--seq-gop", type=int, default=4)
     ap.add_argument("--batch-clips", type=int, default=32)
     ap.add_argument("--batch-frames", type=int, default=2)
     ap.add_argument("--batch-iters", type=int, default=300)
@@ -322,7 +324,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def measure_sequence(args, dev, rast, params0):
+def measure_sequence(args, dev, rast, params0, quantizer):
     """Frame sequence of the moving-subject scene at the benchmark size
     (subject translating 0-4 px and rotating 0-1 degree per frame): frame 0
     from the ROI initialisation, every later frame warm-started from the
@@ -335,31 +337,81 @@ def measure_sequence(args, dev, rast, params0):
     from gs2d_inputs import conferencing_frame, random_motion
     from paper_2505_09324_gb300 import encode_sequence
 
+    from paper_2505_09324_gb300.quant import frame_bits, sequence_bits
+
     mo = random_motion(SEED + 1)
     frames = [torch.from_numpy(conferencing_frame(W, H, seed=SEED, t=t, motion=mo)[0]).to(dev)
               for t in range(args.seq_frames)]
+    F = len(frames)
     side = torch.cuda.Stream(dev)
     res = {}
-    for name, thr in (("warm_start", None), ("selective", args.seq_threshold)):
+    runs = (("warm_start", None, 1), ("selective", args.seq_threshold, F),
+            ("selective_gop", args.seq_threshold, args.seq_gop))
+    for name, thr, gop in runs:
         p = params0.clone()
+        sizes = []
+
+        def on_frame(k, params, sel):
+            # coded size with the calibrated quantiser (outside the frame's timing)
+            with torch.cuda.stream(side):
+                sizes.append(frame_bits(quantizer, params, sel, stream=side))
+
         with torch.cuda.stream(side):
             recs = encode_sequence(rast, frames, p, args.seq_iters, args.seq_iters, stream=side,
-                                   selective_threshold=thr)
+                                   selective_threshold=thr, gop=None if gop == F else gop,
+                                   on_frame=on_frame)
         side.synchronize()
         later = recs[1:] or recs
-        res[name] = {"frame0": recs[0],
+        counts = [r["coded"] for r in recs]
+        acc = sequence_bits(counts, sizes, gop)
+        m = N_GAUSS // 20
+        res[name] = {"frame0": recs[0], "gop": gop,
                      "s_per_frame_mean": statistics.fmean(r["seconds"] for r in later),
                      "psnr_min": min(r["psnr"] for r in later),
-                     "psnr_mean": statistics.fmean(r["psnr"] for r in later)}
+                     "psnr_mean": statistics.fmean(r["psnr"] for r in later),
+                     "bits": {**acc, "bpp": acc["total_bits"] / (F * W * H),
+                              "bpp_without_bitsback": (acc["i_bits"] + acc["p_bits"])
+                              / (F * W * H),
+                              "coded_mean": statistics.fmean(counts),
+                              "eq4_savings_at_n_over_20": acc["p_frames"]
+                              * (math.lgamma(m + 1) - math.log(m)) / math.log(2)}}
         if thr is not None:
             res[name]["threshold"] = thr
-            res[name]["selected_frac_mean"] = statistics.fmean(r["selected"] for r in later) / N_GAUSS
-    return {"frames": len(frames), "iters_per_frame": args.seq_iters, **res,
+            res[name]["selected_frac_mean"] = statistics.fmean(
+                r["selected"] for r in later if "selected" in r) / N_GAUSS
+    return {"frames": F, "iters_per_frame": args.seq_iters, **res,
+            "bits_note": "ideal order-0 entropy of the calibrated quantiser's codes per row "
+                         "(I-frames: all Gaussians; P-frames: the selected ones plus a "
+                         "ceil(log2 N)-bit index each), bits-back per Eq. 3-4",
             "motion": {"v_px_per_frame": mo.v, "omega_deg_per_frame": mo.omega},
             "timing": "wall clock per frame (graph replays, selection, one PSNR check)"}
 
 
-def measure_quant(args, dev, config, frame, mask, bg_xy):
+def calibrated_quantizer(dev, config, iters=100):
+    """PTQ calibration on the training side: the default quantiser's ranges
+    from fits (ROI initialisation, fast schedule, `iters` iterations) of four
+    conferencing frames of other seeds."""
+    import dataclasses
+
+    import torch
+
+    from paper_2505_09324_gb300 import GaussianRasterizer, Quantizer, roi_init
+    from paper_2505_09324_gb300.raster import FAST_FIT
+
+    fast = GaussianRasterizer(W, H, N_GAUSS, device=dev,
+                              config=dataclasses.replace(config, **FAST_FIT))
+    calib = []
+    for k in range(4):
+        f2, m2, b2 = workload(SEED + 100 + k)
+        f2 = torch.from_numpy(f2).to(dev)
+        p, _ = roi_init(f2, torch.from_numpy(m2.astype("uint8")).to(dev), N_GAUSS, ROI_FRAC,
+                        torch.from_numpy(b2).to(dev))
+        fast.encode_frame(f2, p, iters, check_every=iters)
+        calib.append(p)
+    return Quantizer.calibrate(calib)
+
+
+def measure_quant(args, dev, config, frame, mask, bg_xy, q):
     """Quantisation of the fitted Gaussians (Sec. 3.3 A; Table 3 compares the
     latency PTQ and QAT add to 1000 fitting iterations).  PTQ ranges are
     calibrated on fits of four other synthetic conferencing frames (the
@@ -380,18 +432,6 @@ def measure_quant(args, dev, config, frame, mask, bg_xy):
                               config=dataclasses.replace(config, **FAST_FIT))
     iters = args.quant_iters
 
-    def fit(fr, mk, bg):
-        p, _ = roi_init(fr, mk, N_GAUSS, ROI_FRAC, bg)
-        fast.encode_frame(fr, p, iters, check_every=iters)
-        return p
-
-    calib = []
-    for k in range(4):
-        f2, m2, b2 = workload(SEED + 100 + k)
-        calib.append(fit(torch.from_numpy(f2).to(dev),
-                         torch.from_numpy(m2.astype("uint8")).to(dev),
-                         torch.from_numpy(b2).to(dev)))
-    q = Quantizer.calibrate(calib)
     q_refine = Quantizer(q.bits, refine=True)
     p0, _ = roi_init(frame, mask, N_GAUSS, ROI_FRAC, bg_xy)
     p_fit = p0.clone()
@@ -757,7 +797,10 @@ def run_ours(args):
                   "learned_init": learned_enc}
 
     batch = None if args.no_batch else measure_batch(args, dev)
-    seq = None if args.no_sequence else measure_sequence(args, dev, rast, params0)
+    quantizer = None
+    if not (args.no_sequence and args.no_quant):
+        quantizer = calibrated_quantizer(dev, tuned["config"])
+    seq = None if args.no_sequence else measure_sequence(args, dev, rast, params0, quantizer)
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             peaks = json.load(f)
@@ -766,7 +809,7 @@ def run_ours(args):
         peaks = {"bf16_tflops": 1900.0, "source": "of fallback (1.9 PFLOP/s bf16 burst)"}
     learned = None if args.no_learned else measure_learned(dev, frame, mask, peaks)
     quant = None if args.no_quant else measure_quant(args, dev, tuned["config"], frame, mask,
-                                                     bg_xy)
+                                                     bg_xy, quantizer)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

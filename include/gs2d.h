@@ -320,6 +320,36 @@ gs2d_status gs2d_quantize(const float* params, int32_t n, const gs2d_quant* q, u
 gs2d_status gs2d_fit_step_qat(const gs2d_plan* plan, void* ws, const float* target, float* params,
                               float* adam_m, float* adam_v, const gs2d_quant* q, void* stream);
 
+/* Bitstream accounting (Sec. 3.3 B, Eq. 3-4).
+ *
+ * gs2d_code_entropy: ideal order-0 code length, per parameter row, of the
+ * [9][n] codes of gs2d_quantize (device uint16), counting only the columns
+ * with select[i] != 0 when select (device uint8 [n]) is given: for each row,
+ * T log2 T - sum over symbols of c log2 c, with T the counted columns and c
+ * each symbol's count (a vanilla entropy coder with one static model per row
+ * approaches it; the model is not counted).  bits (host int32 [9]) are the
+ * quantiser's widths: 16-bit symbols for half rows, 2^b for uniform rows
+ * (codes masked to that width), 32 bits per value for rows with bits 0.
+ * out_bits: device double [9].  scratch: device memory of at least
+ * gs2d_code_entropy_scratch_bytes(), cleared by the call.  Deterministic. */
+size_t gs2d_code_entropy_scratch_bytes(void);
+gs2d_status gs2d_code_entropy(const uint16_t* codes, int32_t n, const int32_t* bits,
+                              const uint8_t* select, void* scratch, size_t scratch_bytes,
+                              double* out_bits, void* stream);
+
+/* Totals of a coded sequence (host arithmetic, Eq. 3-4).  counts[k] (host
+ * int32 [frames]): Gaussians coded in frame k; payload_bits[k] (host double
+ * [frames]): its size before bits-back coding.  Frame k is an I-frame when
+ * k % gop == 0 (vanilla coding of all Gaussians); every other frame is a
+ * P-frame whose bits-back coding saves log2(m!) - log2(m) bits for m =
+ * counts[k] (Eq. 3; 0 for m <= 1), summed over the P-frames (Eq. 4). */
+typedef struct {
+  double i_bits, p_bits, savings, total_bits;
+  int32_t i_frames, p_frames;
+} gs2d_seq_bits;
+gs2d_status gs2d_sequence_bits(const int32_t* counts, const double* payload_bits, int32_t frames,
+                               int32_t gop, gs2d_seq_bits* out);
+
 /* Device scratch (bytes, 256-byte aligned start) that gs2d_roi_init needs for
  * a W x H frame and n Gaussians. */
 uint64_t gs2d_roi_init_scratch_bytes(int32_t width, int32_t height, int32_t n);

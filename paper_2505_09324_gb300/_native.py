@@ -28,7 +28,8 @@ EXPORTS = (
     "gs2d_render_bwd", "gs2d_render_l2",
     "gs2d_adam_step", "gs2d_fit_step", "gs2d_fit_reset", "gs2d_encode_frame", "gs2d_clip_losses",
     "gs2d_select_changed", "gs2d_pframe_step", "gs2d_encode_pframe", "gs2d_quantize",
-    "gs2d_fit_step_qat",
+    "gs2d_fit_step_qat", "gs2d_code_entropy_scratch_bytes", "gs2d_code_entropy",
+    "gs2d_sequence_bits",
     "gs2d_encode_batch",
     "gs2d_autotune_ws_bytes", "gs2d_autotune",
     "gs2d_gemm_bf16", "gs2d_gemm_partial_bytes", "gs2d_cnn_input", "gs2d_im2col", "gs2d_col2im",
@@ -72,6 +73,12 @@ class Quant(ctypes.Structure):
                 ("lo", ctypes.c_float * 9),
                 ("hi", ctypes.c_float * 9), ("scale", ctypes.c_float * 9),
                 ("step", ctypes.c_float * 9)]
+
+
+class SeqBits(ctypes.Structure):
+    _fields_ = [("i_bits", ctypes.c_double), ("p_bits", ctypes.c_double),
+                ("savings", ctypes.c_double), ("total_bits", ctypes.c_double),
+                ("i_frames", ctypes.c_int32), ("p_frames", ctypes.c_int32)]
 
 
 class Plan(ctypes.Structure):
@@ -141,6 +148,11 @@ def load(build_if_missing: bool = False):
             "gs2d_encode_pframe": (i32, [pp, P, P, P, P, P, P, i32, ctypes.POINTER(f32), P]),
             "gs2d_quantize": (i32, [P, i32, ctypes.POINTER(Quant), P, P, P, P]),
             "gs2d_fit_step_qat": (i32, [pp, P, P, P, P, P, ctypes.POINTER(Quant), P]),
+            "gs2d_code_entropy_scratch_bytes": (ctypes.c_size_t, []),
+            "gs2d_code_entropy": (i32, [P, i32, ctypes.POINTER(i32), P, P, ctypes.c_size_t, P,
+                                        P]),
+            "gs2d_sequence_bits": (i32, [ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double),
+                                         i32, i32, ctypes.POINTER(SeqBits)]),
             "gs2d_read_bins": (i32, [pp, P, P, P, P, i64, P, P, P]),
             "gs2d_count_pairs": (i32, [pp, P, ctypes.POINTER(i64), ctypes.POINTER(i64), P]),
             "gs2d_ws_status": (i32, [pp, P, i32, P]),
@@ -441,3 +453,19 @@ def fit_step_qat(plan: Plan, ws: int, target: int, params: int, m: int, v: int, 
                  stream: int):
     check(load().gs2d_fit_step_qat(ctypes.byref(plan), _p(ws), _p(target), _p(params), _p(m),
                                    _p(v), ctypes.byref(q), _p(stream)), "gs2d_fit_step_qat")
+
+
+def code_entropy(codes: int, n: int, bits, select: int, scratch: int, scratch_bytes: int,
+                 out: int, stream: int):
+    b = (ctypes.c_int32 * 9)(*[int(x) for x in bits])
+    check(load().gs2d_code_entropy(_p(codes), n, b, _p(select), _p(scratch), scratch_bytes,
+                                   _p(out), _p(stream)), "gs2d_code_entropy")
+
+
+def sequence_bits(counts, payload_bits, gop: int) -> dict:
+    F = len(counts)
+    c = (ctypes.c_int32 * max(F, 1))(*[int(x) for x in counts])
+    pb = (ctypes.c_double * max(F, 1))(*[float(x) for x in payload_bits])
+    out = SeqBits()
+    check(load().gs2d_sequence_bits(c, pb, F, gop, ctypes.byref(out)), "gs2d_sequence_bits")
+    return {k: getattr(out, k) for k, _ in SeqBits._fields_}

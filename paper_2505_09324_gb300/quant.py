@@ -17,9 +17,14 @@ Cholesky factor, 8-bit colour and weight: 94 bits per Gaussian, within
   renders the quantised Gaussians inside every fit iteration
   (gs2d_fit_step_qat, straight-through gradient) with ranges re-derived from
   the current Gaussians at each step (``refine``).
+* Bitstream accounting (Sec. 3.3 B, Eq. 3-4): ``code_bits`` (ideal order-0
+  code length of the codes, per row, on the device), ``frame_bits`` (an I-
+  or P-frame's coded size) and ``sequence_bits`` (bits-back totals).
 """
 
 from __future__ import annotations
+
+import math
 
 import numpy as np
 import torch
@@ -101,3 +106,46 @@ class Quantizer:
         nat.quantize(params.data_ptr(), n, self.c, 0 if c is None else c.data_ptr(),
                      0 if v is None else v.data_ptr(), ranges.data_ptr(), int(s.cuda_stream))
         return c, v, ranges
+
+
+_scratch = {}
+
+
+def code_bits(codes: torch.Tensor, bits, select: torch.Tensor | None = None,
+              stream=None) -> torch.Tensor:
+    """gs2d_code_entropy: ideal order-0 code length (bits, float64 [9] on the
+    device) of each row of the [9, n] codes, over the selected columns."""
+    n = codes.shape[1]
+    dev = codes.device
+    nbytes = int(nat.load().gs2d_code_entropy_scratch_bytes())
+    buf = _scratch.get(dev)
+    if buf is None or buf.numel() < nbytes:
+        buf = _scratch[dev] = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    out = torch.empty(9, dtype=torch.float64, device=dev)
+    s = torch.cuda.current_stream(dev) if stream is None else stream
+    nat.code_entropy(codes.data_ptr(), n, bits, 0 if select is None else select.data_ptr(),
+                     buf.data_ptr(), nbytes, out.data_ptr(), int(s.cuda_stream))
+    return out
+
+
+def frame_bits(quantizer: Quantizer, params: torch.Tensor, select: torch.Tensor | None = None,
+               stream=None) -> float:
+    """Coded size of a frame (host float; synchronises): the entropy-coded
+    codes of all Gaussians (an I-frame) or of the selected ones, each with
+    its index of ceil(log2 n) bits (a P-frame), plus the frame's ranges
+    (two float32 per uniform row) when the quantiser refines them per frame."""
+    codes, _, _ = quantizer.quantize(params, values=False, stream=stream)
+    bits = float(code_bits(codes, quantizer.bits, select, stream).sum().item())
+    n = params.shape[1]
+    if select is not None:
+        m = int(select.sum().item())
+        bits += m * math.ceil(math.log2(max(n, 2)))
+    if quantizer.refine:
+        bits += 64 * sum(b > 0 for b in quantizer.bits)
+    return bits
+
+
+def sequence_bits(counts, payload_bits, gop: int) -> dict:
+    """gs2d_sequence_bits: I-frame bits, P-frame bits, bits-back savings
+    (Eq. 3 per P-frame, Eq. 4 summed) and the total of a coded sequence."""
+    return nat.sequence_bits(counts, payload_bits, gop)

@@ -235,7 +235,8 @@ class GaussianRasterizer:
 
 
 def encode_sequence(rast: GaussianRasterizer, frames, params: torch.Tensor, iters_first: int,
-                    iters_next: int, stream=None, selective_threshold: float | None = None):
+                    iters_next: int, stream=None, selective_threshold: float | None = None,
+                    gop: int | None = None, on_frame=None):
     """Fits a frame sequence with inter-frame reuse (Sec. 3.2: P-frames start
     from the previous frame's optimised Gaussians): frame 0 for ``iters_first``
     iterations from ``params`` (an initialiser's output), every later frame
@@ -245,9 +246,13 @@ def encode_sequence(rast: GaussianRasterizer, frames, params: torch.Tensor, iter
     residual against the previous fit's render exceeds the threshold are
     fitted (gs2d_select_changed, gs2d_encode_pframe).  ``frames`` yields
     [3, H, W] float32 CUDA tensors.  ``params`` is updated in place (ends as
-    the last frame's fit).  Returns one {"iters", "psnr", "seconds"[,
-    "selected"]} record per frame (wall clock around the frame's calls, which
-    synchronise the stream)."""
+    the last frame's fit).  With ``gop`` every frame k with k % gop == 0 is an
+    I-frame (all Gaussians fitted and coded); otherwise only frame 0 is.
+    ``on_frame(k, params, selected)`` runs after each frame, outside its
+    timing (selected: the P-frame's uint8 mask, None on an I-frame).
+    Returns one {"iters", "psnr", "seconds", "coded"[, "selected"]} record
+    per frame (wall clock around the frame's calls, which synchronise the
+    stream; coded = Gaussians the frame transmits)."""
     import time
     out = []
     adam = (torch.empty_like(params), torch.empty_like(params))
@@ -255,18 +260,22 @@ def encode_sequence(rast: GaussianRasterizer, frames, params: torch.Tensor, iter
     for k, frame in enumerate(frames):
         iters = iters_first if k == 0 else iters_next
         t0 = time.perf_counter()
-        if k == 0 or selective_threshold is None:
+        if k == 0 or selective_threshold is None or (gop and k % gop == 0):
             r = rast.encode_frame(frame, params, iters, target_psnr=0.0, check_every=iters,
                                   adam_state=adam, stream=stream)
             out.append({"iters": r["iters"], "psnr": r["psnr"],
-                        "seconds": time.perf_counter() - t0})
+                        "seconds": time.perf_counter() - t0, "coded": rast.n})
+            if on_frame is not None:
+                on_frame(k, params, None)
             continue
         rast.prepare(params, stream=stream)
         ref = rast.render_fwd(out=ref, stream=stream)
         sel, cnt = rast.select_changed(ref, frame, selective_threshold, stream=stream)
         psnr = rast.encode_pframe(frame, params, sel, iters, adam_state=adam, stream=stream)
         out.append({"iters": iters, "psnr": psnr, "seconds": time.perf_counter() - t0,
-                    "selected": cnt})
+                    "selected": cnt, "coded": cnt})
+        if on_frame is not None:
+            on_frame(k, params, sel)
     return out
 
 

@@ -183,3 +183,23 @@ def test_quantizer_spec_host_side():
         Quantizer([HALF] * 8)
     with pytest.raises(ValueError):
         Quantizer([8] * 9)               # uniform rows need ranges or refine
+
+
+def test_sequence_bits_host_arithmetic_matches_oracle(nat):
+    """gs2d_sequence_bits is host arithmetic (no device work): Eq. 3-4 totals
+    against the oracle's plain sums (lgamma vs a sum of logarithms)."""
+    import numpy as np
+    from oracle import bitstream as B
+    rng = np.random.default_rng(3)
+    for F, K in ((1, 1), (7, 3), (60, 4), (61, 8), (10, 100)):
+        counts = [int(x) for x in rng.integers(0, 20000, F)]
+        payload = [float(x) for x in rng.uniform(0, 2e6, F)]
+        got = nat.sequence_bits(counts, payload, K)
+        ref = B.sequence_bits(counts, payload, K)
+        for k in ("i_bits", "p_bits", "savings", "total_bits"):
+            assert got[k] == pytest.approx(ref[k], rel=1e-12, abs=1e-9), (F, K, k)
+        assert (got["i_frames"], got["p_frames"]) == (ref["i_frames"], ref["p_frames"])
+    assert nat.sequence_bits([], [], 4)["total_bits"] == 0.0
+    for bad in (([1], [1.0], 0), ([-1, 2], [1.0, 1.0], 2), ([1, 2], [1.0, float("nan")], 2)):
+        with pytest.raises(nat.Gs2dError):
+            nat.sequence_bits(*bad)
