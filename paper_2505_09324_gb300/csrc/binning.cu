@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(kGB)
 k_project(int n, ClipSet cs, int tile_shift, float sigma_cut, float alpha_min, float det_eps,
           const float* __restrict__ params, float4* __restrict__ rec, int4* __restrict__ rect,
           int* __restrict__ count) {
+  pdl_begin();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   project_one(i, n, clip_of_gaussian(cs, i), tile_shift, sigma_cut, alpha_min, det_eps, params,
@@ -77,6 +78,7 @@ __device__ __forceinline__ void count_block(int n, const int4* __restrict__ rect
 __global__ void __launch_bounds__(kGB)
 k_count_tiles(int n, const int4* __restrict__ rect, const int* __restrict__ count,
               int* __restrict__ tile_cnt, long long* __restrict__ block_sum) {
+  pdl_begin();
   count_block(n, rect, count, tile_cnt, block_sum);
 }
 
@@ -90,6 +92,7 @@ k_project_count(int n, ClipSet cs, int tile_shift, float sigma_cut, float alpha_
                 int4* __restrict__ rect, int* __restrict__ count, int* __restrict__ tile_cnt,
                 long long* __restrict__ block_sum, WsHeader* __restrict__ hdr, int adam_tick,
                 float b1, float b2, float lr, float lr_decay) {
+  pdl_begin();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0 && adam_tick) {
     const int t = ++hdr->step;
@@ -156,6 +159,7 @@ k_bin_scan(int n, int nbg, int num_tiles, int64_t max_entries, int* __restrict__
            const long long* __restrict__ block_sum, int* __restrict__ tile_cnt,
            int* __restrict__ cursor, int2* __restrict__ ranges, int* __restrict__ bucket,
            uint32_t* __restrict__ rank, WsHeader* __restrict__ hdr) {
+  pdl_begin();
   __shared__ long long warp_sum[32];
   __shared__ int s_hist[kBuckets];
   __shared__ int s_base[kBuckets];
@@ -248,6 +252,7 @@ constexpr int kInFlight = 4;
 __global__ void __launch_bounds__(kGB)
 k_bin_scatter(int n, const int4* __restrict__ rect, const WsHeader* __restrict__ hdr,
               int* __restrict__ cursor, uint32_t* __restrict__ list) {
+  pdl_begin();
   __shared__ int s_start[kGB / 32][33];
   if (hdr->entries_raw != (int64_t)hdr->n_entries) return;  // over capacity
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -354,6 +359,7 @@ k_sort_short(int num_tiles, const int2* __restrict__ ranges, uint32_t* __restric
              int* __restrict__ long_tiles, int* __restrict__ tile_cnt,
              const int* __restrict__ bucket, const uint32_t* __restrict__ rank,
              int* __restrict__ order, WsHeader* __restrict__ hdr) {
+  pdl_begin();
   const int lane = threadIdx.x & 31;
   const int tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (tile >= num_tiles) return;
@@ -399,6 +405,7 @@ __global__ void __launch_bounds__(1024)
 k_sort_long(int2* __restrict__ ranges, uint32_t* __restrict__ list,
             const int* __restrict__ long_tiles, int* __restrict__ bucket,
             WsHeader* __restrict__ hdr) {
+  pdl_begin();
   extern __shared__ uint32_t s_keys[];
   const int t = threadIdx.x;
   // the queue classes were last read by k_sort_short: clear them for the next binning
@@ -442,13 +449,14 @@ k_sort_long(int2* __restrict__ ranges, uint32_t* __restrict__ list,
 }
 
 // ---------------------------------------------------------------------------
+// Every kernel of the chain starts with pdl_begin() and is launched with
+// launch_pdl: each one's blocks become resident while its predecessor drains.
 cudaError_t launch_project(const gs2d_plan& p, void* ws, const float* params, cudaStream_t s) {
   if (p.n == 0) return cudaSuccess;
-  k_project<<<(p.n + kGB - 1) / kGB, kGB, 0, s>>>(
-      p.n, clip_set(p, ws), tile_shift_of(p.tile), p.cfg.sigma_cut, p.cfg.alpha_min,
-      p.cfg.det_eps, params,
-      ws_ptr<float4>(ws, p, kOffRec), ws_ptr<int4>(ws, p, kOffRect), ws_ptr<int>(ws, p, kOffCount));
-  return cudaGetLastError();
+  return launch_pdl(k_project, (p.n + kGB - 1) / kGB, kGB, 0, s, p.n, clip_set(p, ws),
+                    tile_shift_of(p.tile), p.cfg.sigma_cut, p.cfg.alpha_min, p.cfg.det_eps,
+                    params, ws_ptr<float4>(ws, p, kOffRec), ws_ptr<int4>(ws, p, kOffRect),
+                    ws_ptr<int>(ws, p, kOffCount));
 }
 
 static bool g_long_attr_set = false;
@@ -475,26 +483,29 @@ static cudaError_t launch_bin_rest(const gs2d_plan& p, void* ws, cudaStream_t s)
   uint32_t* rank = ws_ptr<uint32_t>(ws, p, kOffRank);
   const int nbg = (p.n + kGB - 1) / kGB;
   const int nbt = (p.num_tiles + kGB * kTileItems - 1) / (kGB * kTileItems);
-  k_bin_scan<<<nbg + nbt, kGB, 0, s>>>(p.n, nbg, p.num_tiles, p.max_entries, count,
-                                     ws_ptr<long long>(ws, p, kOffBlockSum), tile_cnt, cursor,
-                                     ranges, bucket, rank, hdr);
-  if (p.n > 0)
-    k_bin_scatter<<<nbg, kGB, 0, s>>>(p.n, ws_ptr<int4>(ws, p, kOffRect), hdr, cursor, list);
-  k_sort_short<<<(p.num_tiles + 7) / 8, 256, 0, s>>>(p.num_tiles, ranges, list, long_tiles,
-                                                    tile_cnt, bucket, rank, order, hdr);
-  const cudaError_t e = prime_binning();
-  if (e != cudaSuccess) return e;
-  k_sort_long<<<152, 1024, kLongMax * (int)sizeof(uint32_t), s>>>(ranges, list, long_tiles, bucket,
-                                                                  hdr);
-  return cudaGetLastError();
+  cudaError_t e = prime_binning();
+  if (e == cudaSuccess)
+    e = launch_pdl(k_bin_scan, nbg + nbt, kGB, 0, s, p.n, nbg, p.num_tiles, p.max_entries, count,
+                   ws_ptr<long long>(ws, p, kOffBlockSum), tile_cnt, cursor, ranges, bucket,
+                   rank, hdr);
+  if (e == cudaSuccess && p.n > 0)
+    e = launch_pdl(k_bin_scatter, nbg, kGB, 0, s, p.n, ws_ptr<int4>(ws, p, kOffRect), hdr,
+                   cursor, list);
+  if (e == cudaSuccess)
+    e = launch_pdl(k_sort_short, (p.num_tiles + 7) / 8, 256, 0, s, p.num_tiles, ranges, list,
+                   long_tiles, tile_cnt, bucket, rank, order, hdr);
+  if (e == cudaSuccess)
+    e = launch_pdl(k_sort_long, 152, 1024, kLongMax * sizeof(uint32_t), s, ranges, list,
+                   long_tiles, bucket, hdr);
+  return e;
 }
 
 cudaError_t launch_bin_sort(const gs2d_plan& p, void* ws, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
   if (p.n > 0)
-    k_count_tiles<<<(p.n + kGB - 1) / kGB, kGB, 0, s>>>(
-        p.n, ws_ptr<int4>(ws, p, kOffRect), ws_ptr<int>(ws, p, kOffCount),
-        ws_ptr<int>(ws, p, kOffTileCnt), ws_ptr<long long>(ws, p, kOffBlockSum));
-  const cudaError_t e = cudaGetLastError();
+    e = launch_pdl(k_count_tiles, (p.n + kGB - 1) / kGB, kGB, 0, s, p.n,
+                   ws_ptr<int4>(ws, p, kOffRect), ws_ptr<int>(ws, p, kOffCount),
+                   ws_ptr<int>(ws, p, kOffTileCnt), ws_ptr<long long>(ws, p, kOffBlockSum));
   if (e != cudaSuccess) return e;
   return launch_bin_rest(p, ws, s);
 }
@@ -502,14 +513,13 @@ cudaError_t launch_bin_sort(const gs2d_plan& p, void* ws, cudaStream_t s) {
 cudaError_t launch_prepare(const gs2d_plan& p, void* ws, const float* params, bool adam_tick,
                            cudaStream_t s) {
   const int blocks = (p.n + kGB - 1) / kGB;
-  k_project_count<<<blocks > 0 ? blocks : 1, kGB, 0, s>>>(
-      p.n, clip_set(p, ws), tile_shift_of(p.tile), p.cfg.sigma_cut, p.cfg.alpha_min,
-      p.cfg.det_eps, params,
+  const cudaError_t e = launch_pdl(
+      k_project_count, blocks > 0 ? blocks : 1, kGB, 0, s, p.n, clip_set(p, ws),
+      tile_shift_of(p.tile), p.cfg.sigma_cut, p.cfg.alpha_min, p.cfg.det_eps, params,
       ws_ptr<float4>(ws, p, kOffRec), ws_ptr<int4>(ws, p, kOffRect), ws_ptr<int>(ws, p, kOffCount),
       ws_ptr<int>(ws, p, kOffTileCnt), ws_ptr<long long>(ws, p, kOffBlockSum),
-      ws_ptr<WsHeader>(ws, p, kOffHeader), adam_tick ? 1 : 0, p.cfg.beta1, p.cfg.beta2,
-      p.cfg.lr, p.cfg.lr_decay);
-  const cudaError_t e = cudaGetLastError();
+      ws_ptr<WsHeader>(ws, p, kOffHeader), adam_tick ? 1 : 0, p.cfg.beta1, p.cfg.beta2, p.cfg.lr,
+      p.cfg.lr_decay);
   if (e != cudaSuccess) return e;
   return launch_bin_rest(p, ws, s);
 }

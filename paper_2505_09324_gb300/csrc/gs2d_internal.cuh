@@ -120,6 +120,36 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+// Programmatic dependent launch (sm_90 and later).  A kernel started by
+// launch_pdl may become resident while its predecessor on the stream is still
+// running; its first statement must be pdl_begin(), which waits until the
+// predecessor has completed and its writes are visible, then lets the next
+// kernel start launching.  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... P, typename... A>
+inline cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, A... args) {
+  cudaLaunchConfig_t c = {};
+  c.gridDim = grid;
+  c.blockDim = block;
+  c.dynamicSmemBytes = smem;
+  c.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  c.attrs = at;
+#ifdef GS2D_NO_PDL
+  c.numAttrs = 0;
+#else
+  c.numAttrs = 1;
+#endif
+  return cudaLaunchKernelEx(&c, kernel, static_cast<P>(args)...);
+}
+
 __device__ __forceinline__ void set_status(WsHeader* h, int code) {
   atomicCAS(&h->status, 0, code);
 }

@@ -71,6 +71,7 @@ __global__ void __launch_bounds__(256)
 k_reduce_chain(int n, const float* __restrict__ params, const int* __restrict__ offs,
                const float4* __restrict__ partial, const WsHeader* __restrict__ hdr,
                float* __restrict__ grads) {
+  pdl_begin();
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = gt / kRL, sub = gt % kRL;
   const bool valid = i < n && hdr->entries_raw == (int64_t)hdr->n_entries;
@@ -90,6 +91,7 @@ k_reduce_chain_adam(int n, float* __restrict__ params, const int* __restrict__ o
                     float* __restrict__ m, float* __restrict__ v, float4 lr_rows, float b1,
                     float b2, float eps, const uint8_t* __restrict__ select,
                     const float* __restrict__ params_eval) {
+  pdl_begin();
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = gt / kRL, sub = gt % kRL;
   const bool ok = hdr->entries_raw == (int64_t)hdr->n_entries;  // else over capacity
@@ -128,6 +130,7 @@ k_reduce_chain_adam(int n, float* __restrict__ params, const int* __restrict__ o
 __global__ void __launch_bounds__(1024)
 k_loss_reduce(int num_tiles, const float2* __restrict__ loss_part, WsHeader* __restrict__ hdr,
               float* __restrict__ out) {
+  pdl_begin();
   __shared__ double s_a[32], s_b[32];
   double a = 0.0, b = 0.0;
   for (int t = threadIdx.x; t < num_tiles; t += blockDim.x) {
@@ -163,6 +166,7 @@ k_loss_reduce(int num_tiles, const float2* __restrict__ loss_part, WsHeader* __r
 // Per-clip losses: block c sums the tiles of clip c.
 __global__ void __launch_bounds__(1024)
 k_clip_loss(ClipSet cs, const float2* __restrict__ loss_part, float2* __restrict__ clip_loss) {
+  pdl_begin();
   const int c = blockIdx.x;
   const gs2d_clip cl = cs.count == 1 ? cs.one : cs.table[c];
   __shared__ double s_a[32], s_b[32];
@@ -260,11 +264,10 @@ static cudaError_t launch_render(const gs2d_plan& p, RenderMode mode, const Rend
 static cudaError_t launch_reduce(const gs2d_plan& p, void* ws, const float* params, float* grads,
                                  cudaStream_t s) {
   if (p.n == 0) return cudaSuccess;
-  k_reduce_chain<<<(p.n * kRL + 255) / 256, 256, 0, s>>>(
-      p.n, params, ws_ptr<int>(ws, p, kOffCount),
-      reinterpret_cast<const float4*>(ws_ptr<float>(ws, p, kOffPartial)),
-      ws_ptr<WsHeader>(ws, p, kOffHeader), grads);
-  return cudaGetLastError();
+  return launch_pdl(k_reduce_chain, (p.n * kRL + 255) / 256, 256, 0, s, p.n, params,
+                    ws_ptr<int>(ws, p, kOffCount),
+                    reinterpret_cast<const float4*>(ws_ptr<float>(ws, p, kOffPartial)),
+                    ws_ptr<WsHeader>(ws, p, kOffHeader), grads);
 }
 
 cudaError_t launch_render_fwd(const gs2d_plan& p, void* ws, float* img, cudaStream_t s) {
@@ -283,15 +286,13 @@ cudaError_t launch_render_bwd(const gs2d_plan& p, void* ws, const float* params,
 }
 
 cudaError_t launch_loss_reduce(const gs2d_plan& p, void* ws, float* loss, cudaStream_t s) {
-  k_loss_reduce<<<1, 1024, 0, s>>>(p.num_tiles, ws_ptr<float2>(ws, p, kOffLossPart),
-                                   ws_ptr<WsHeader>(ws, p, kOffHeader), loss);
-  return cudaGetLastError();
+  return launch_pdl(k_loss_reduce, 1, 1024, 0, s, p.num_tiles,
+                    ws_ptr<float2>(ws, p, kOffLossPart), ws_ptr<WsHeader>(ws, p, kOffHeader), loss);
 }
 
 cudaError_t launch_clip_losses(const gs2d_plan& p, void* ws, cudaStream_t s) {
-  k_clip_loss<<<p.num_clips, 1024, 0, s>>>(clip_set(p, ws), ws_ptr<float2>(ws, p, kOffLossPart),
-                                           ws_ptr<float2>(ws, p, kOffClipLoss));
-  return cudaGetLastError();
+  return launch_pdl(k_clip_loss, p.num_clips, 1024, 0, s, clip_set(p, ws),
+                    ws_ptr<float2>(ws, p, kOffLossPart), ws_ptr<float2>(ws, p, kOffClipLoss));
 }
 
 cudaError_t launch_render_l2(const gs2d_plan& p, void* ws, const float* params,
@@ -321,12 +322,11 @@ cudaError_t launch_fit_step(const gs2d_plan& p, void* ws, const float* target, f
   a.target = target;
   cudaError_t e = launch_render(p, kModeL2, a, s);
   if (e != cudaSuccess || p.n == 0) return e;
-  k_reduce_chain_adam<<<(p.n * kRL + 255) / 256, 256, 0, s>>>(
-      p.n, params, ws_ptr<int>(ws, p, kOffCount),
-      reinterpret_cast<const float4*>(ws_ptr<float>(ws, p, kOffPartial)),
-      ws_ptr<WsHeader>(ws, p, kOffHeader), m, v, lr_rows(p.cfg), p.cfg.beta1, p.cfg.beta2,
-      p.cfg.eps, nullptr, params_eval);
-  return cudaGetLastError();
+  return launch_pdl(k_reduce_chain_adam, (p.n * kRL + 255) / 256, 256, 0, s, p.n, params,
+                    ws_ptr<int>(ws, p, kOffCount),
+                    reinterpret_cast<const float4*>(ws_ptr<float>(ws, p, kOffPartial)),
+                    ws_ptr<WsHeader>(ws, p, kOffHeader), m, v, lr_rows(p.cfg), p.cfg.beta1,
+                    p.cfg.beta2, p.cfg.eps, (const uint8_t*)nullptr, params_eval);
 }
 
 // ---------------------------------------------------------------------------
@@ -341,6 +341,7 @@ cudaError_t launch_fit_step(const gs2d_plan& p, void* ws, const float* target, f
 __global__ void __launch_bounds__(256)
 k_active_mark(int n, const uint8_t* __restrict__ select, const int4* __restrict__ rect,
               uint8_t* __restrict__ active, int* __restrict__ act_count) {
+  pdl_begin();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) *act_count = 0;
   if (i >= n || !select[i]) return;
@@ -353,6 +354,7 @@ k_active_mark(int n, const uint8_t* __restrict__ select, const int4* __restrict_
 __global__ void __launch_bounds__(256)
 k_active_compact(int num_tiles, uint8_t* __restrict__ active, int* __restrict__ act_order,
                  int* __restrict__ act_count) {
+  pdl_begin();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= num_tiles || !active[t]) return;
   active[t] = 0;
@@ -399,22 +401,23 @@ cudaError_t launch_pframe_step(const gs2d_plan& p, void* ws, const float* target
   uint8_t* active = ws_ptr<uint8_t>(ws, p, kOffActive);
   int* act_order = ws_ptr<int>(ws, p, kOffActOrder);
   int* act_count = act_order + p.num_tiles;
-  k_active_mark<<<(p.n + 255) / 256, 256, 0, s>>>(p.n, select, ws_ptr<int4>(ws, p, kOffRect),
-                                                  active, act_count);
-  k_active_compact<<<(p.num_tiles + 255) / 256, 256, 0, s>>>(p.num_tiles, active, act_order,
-                                                             act_count);
+  cudaError_t e = launch_pdl(k_active_mark, (p.n + 255) / 256, 256, 0, s, p.n, select,
+                             ws_ptr<int4>(ws, p, kOffRect), active, act_count);
+  if (e == cudaSuccess)
+    e = launch_pdl(k_active_compact, (p.num_tiles + 255) / 256, 256, 0, s, p.num_tiles, active,
+                   act_order, act_count);
+  if (e != cudaSuccess) return e;
   RenderArgs a = render_args(p, ws);
   a.target = target;
   a.order = act_order;
   a.active = act_count;
-  cudaError_t e = launch_render(p, kModeL2, a, s);
+  e = launch_render(p, kModeL2, a, s);
   if (e != cudaSuccess) return e;
-  k_reduce_chain_adam<<<(p.n * kRL + 255) / 256, 256, 0, s>>>(
-      p.n, params, ws_ptr<int>(ws, p, kOffCount),
-      reinterpret_cast<const float4*>(ws_ptr<float>(ws, p, kOffPartial)),
-      ws_ptr<WsHeader>(ws, p, kOffHeader), m, v, lr_rows(p.cfg), p.cfg.beta1, p.cfg.beta2,
-      p.cfg.eps, select, nullptr);
-  return cudaGetLastError();
+  return launch_pdl(k_reduce_chain_adam, (p.n * kRL + 255) / 256, 256, 0, s, p.n, params,
+                    ws_ptr<int>(ws, p, kOffCount),
+                    reinterpret_cast<const float4*>(ws_ptr<float>(ws, p, kOffPartial)),
+                    ws_ptr<WsHeader>(ws, p, kOffHeader), m, v, lr_rows(p.cfg), p.cfg.beta1,
+                    p.cfg.beta2, p.cfg.eps, select, (const float*)nullptr);
 }
 
 // Runs the one-time per-device queries of the fit loop's launches (occupancy

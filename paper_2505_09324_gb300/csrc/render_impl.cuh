@@ -452,6 +452,7 @@ constexpr int kMinBlocks = 65536 / (TileGeom<T>::NT * 50) < 32 ? 65536 / (TileGe
 
 template <int T, int S, int MODE, int LAUNCH>
 __global__ void __launch_bounds__(TileGeom<T>::NT, kMinBlocks<T>) k_render(RenderArgs a) {
+  pdl_begin();
   __shared__ TileSmem<S> sm;
   __shared__ ModeSmem<T, MODE> ms;
   if constexpr (LAUNCH == GS2D_LAUNCH_GRID) {
@@ -497,8 +498,7 @@ cudaError_t launch_mode(const RenderArgs& a, cudaStream_t s) {
     grid = persistent_grid((const void*)k_render<T, S, MODE, LAUNCH>, TileGeom<T>::NT,
                            a.num_tiles);
   if (grid <= 0) return cudaErrorInvalidConfiguration;
-  k_render<T, S, MODE, LAUNCH><<<grid, TileGeom<T>::NT, 0, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_render<T, S, MODE, LAUNCH>, grid, TileGeom<T>::NT, 0, s, a);
 }
 
 template <int T, int S, int LAUNCH>
