@@ -28,9 +28,11 @@
 // that column costs one FADD (dy), one FFMA (u2) and one FFMA (q).
 //
 // Forward: thread <-> one column x R-row strip (R = 2 for T = 8, else 4);
-// a warp covers a band of rows and skips Gaussians whose box misses it
-// (warp-uniform test).  Accumulation is in ascending Gaussian index (the list
-// order).
+// a warp covers a band of rows.  After each batch is staged every warp
+// compacts (by ballot) the batch's Gaussians whose box meets its band into
+// its own ascending list and walks only that list; within a strip the row
+// offset u2 advances by the constant a2 per row.  Accumulation is in ascending
+// Gaussian index (the list order).
 //
 // Backward: the blend is recomputed from the saved lists (no per-pixel state
 // is stored by the forward pass).  A group of T lanes takes one Gaussian and
@@ -133,20 +135,21 @@ __device__ __forceinline__ void stage_batch(TileSmem<S>& sm, const RenderArgs& a
 // Forward accumulation over staged Gaussians [0, cnt) for this thread's column
 // px and rows py[0 .. R).
 template <int T, int S>
-__device__ __forceinline__ void fwd_batch(const TileSmem<S>& sm, int cnt, float px,
-                                          const float (&py)[TileGeom<T>::R], int wid,
+__device__ __forceinline__ void fwd_batch(const TileSmem<S>& sm, const uint8_t* __restrict__ wl,
+                                          int wn, float px, const float (&py)[TileGeom<T>::R],
                                           float (&acc)[TileGeom<T>::R][3]) {
   constexpr int R = TileGeom<T>::R;
-  for (int j = 0; j < cnt; j++) {
-    if (!((sm.wmask[j] >> wid) & 1u)) continue;  // warp-uniform
+  for (int i = 0; i < wn; i++) {
+    const int j = wl[i];
     const float4 r0 = sm.r0[j], r1 = sm.r1[j];
     const float cb = sm.cb[j];
     const float u1 = r0.z * (px - r0.x);
     const float c0 = r1.x * u1;
     const float u1sq = u1 * u1;
+    float u2 = fmaf(r0.w, py[0] - r0.y, c0);
 #pragma unroll
     for (int r = 0; r < R; r++) {
-      const float u2 = fmaf(r0.w, py[r] - r0.y, c0);
+      if (r) u2 += r0.w;
       const float q = fmaf(u2, u2, u1sq);
       if (q <= r1.y) {
         const float e = ex2_approx(-q);
@@ -215,11 +218,10 @@ __device__ __forceinline__ void bwd_batch(const TileSmem<S>& sm, const float4* _
         const float u1 = r0.z * (px - r0.x);
         const float c0 = r1.x * u1;
         const float u1sq = u1 * u1;
-        const float fstep = (float)rstep;
-        float dy = (oy + (float)y0 + 0.5f) - r0.y;
+        const float ustep = r0.w * (float)rstep;
+        float u2 = fmaf(r0.w, (oy + (float)y0 + 0.5f) - r0.y, c0);
         float ge0 = 0.f, ge1 = 0.f, ge2 = 0.f, ss = 0.f, s2 = 0.f, s22 = 0.f;
-        for (int y = y0; y <= bb.w; y += rstep, dy += fstep) {
-          const float u2 = fmaf(r0.w, dy, c0);
+        for (int y = y0; y <= bb.w; y += rstep, u2 += ustep) {
           const float q = fmaf(u2, u2, u1sq);
           if (q <= r1.y) {
             const float e = ex2_approx(-q);
@@ -255,9 +257,27 @@ template <int T, int MODE>
 struct ModeSmem {
   static constexpr int kGrad = (MODE == kModeBwd || MODE == kModeL2) ? T * T : 1;
   float4 g[kGrad];                 // dL/dC of the tile
+  uint8_t wl[TileGeom<T>::NW][128];  // per-warp lists of the staged batch
   float2 red[TileGeom<T>::NW];     // loss partials per warp
   unsigned hits;                   // kModeCount
 };
+
+// Warp wid's list of the staged Gaussians whose box touches its rows, in
+// ascending order; returns its length.
+template <int T, int S>
+__device__ __forceinline__ int warp_list(const TileSmem<S>& sm, int cnt, int wid, int lane,
+                                         uint8_t* __restrict__ wl) {
+  int m = 0;
+  for (int base = 0; base < cnt; base += 32) {
+    const int k = base + lane;
+    const bool on = k < cnt && ((sm.wmask[k] >> wid) & 1u);
+    const unsigned bal = __ballot_sync(0xffffffffu, on);
+    if (on) wl[m + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)k;
+    m += __popc(bal);
+  }
+  __syncwarp();
+  return m;
+}
 
 template <int T, int S, int MODE>
 __device__ __forceinline__ void process_tile(const RenderArgs& a, const TileFrame& f,
@@ -373,7 +393,8 @@ __device__ __forceinline__ void process_tile(const RenderArgs& a, const TileFram
     __syncthreads();
     stage_batch<T, S>(sm, a, f, b, cnt);
     __syncthreads();
-    fwd_batch<T, S>(sm, cnt, px, py, wid, acc);
+    const int wn = warp_list<T, S>(sm, cnt, wid, lane, ms.wl[wid]);
+    fwd_batch<T, S>(sm, ms.wl[wid], wn, px, py, acc);
     staged = b;
   }
   if constexpr (MODE == kModeFwd) {
