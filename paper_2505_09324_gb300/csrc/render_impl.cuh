@@ -199,6 +199,12 @@ __device__ __forceinline__ void bwd_batch(const TileSmem<S>& sm, const float4* _
   const int h = lane / T, j = lane % T;
   for (int base = wid * G::GPW; base < cnt; base += G::NW * G::GPW) {  // warp-uniform
     const int gi = base + h;
+    // Gaussians whose box misses the tile: a zero record, no reduction
+    const bool empty = gi >= cnt || sm.bb[gi].x > sm.bb[gi].y;
+    if (__all_sync(0xffffffffu, empty)) {
+      if (gi < cnt && j < 8) partial[8 * sm.slot[gi] + j] = 0.0f;
+      continue;
+    }
     float v[8];
 #pragma unroll
     for (int k = 0; k < 8; k++) v[k] = 0.0f;
