@@ -350,6 +350,13 @@ typedef struct {
 gs2d_status gs2d_sequence_bits(const int32_t* counts, const double* payload_bits, int32_t frames,
                                int32_t gop, gs2d_seq_bits* out);
 
+/* Frame input (the video frame a fit targets, Sec. 3.2): 8-bit interleaved
+ * RGB (device, row y at rgb + y * row_bytes, pixel x at 3 * x; row_bytes >=
+ * 3 * width) to the planar float32 frame [3][H][W] (device) with value c /
+ * 255 correctly rounded.  Stream-ordered; nothing is allocated. */
+gs2d_status gs2d_frame_from_rgb8(const uint8_t* rgb, int32_t width, int32_t height,
+                                 int64_t row_bytes, float* frame, void* stream);
+
 /* Device scratch (bytes, 256-byte aligned start) that gs2d_roi_init needs for
  * a W x H frame and n Gaussians. */
 uint64_t gs2d_roi_init_scratch_bytes(int32_t width, int32_t height, int32_t n);

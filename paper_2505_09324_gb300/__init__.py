@@ -9,7 +9,7 @@ the C ABI of ``include/gs2d.h``; this package is a thin binding over it.
 
 from .quant import Quantizer  # noqa: F401
 from .raster import (BatchRasterizer, GaussianRasterizer, RasterConfig, adam_step,  # noqa: F401
-                     autotune, encode_sequence, roi_init)
+                     autotune, encode_sequence, frame_from_rgb8, roi_init)
 
 __all__ = ["BatchRasterizer", "GaussianRasterizer", "Quantizer", "RasterConfig", "adam_step",
-           "autotune", "encode_sequence", "roi_init"]
+           "autotune", "encode_sequence", "frame_from_rgb8", "roi_init"]

@@ -279,6 +279,22 @@ def encode_sequence(rast: GaussianRasterizer, frames, params: torch.Tensor, iter
     return out
 
 
+def frame_from_rgb8(rgb: torch.Tensor, out: torch.Tensor | None = None,
+                    stream=None) -> torch.Tensor:
+    """gs2d_frame_from_rgb8: an 8-bit [H, W, 3] RGB frame on the device to the
+    planar float32 [3, H, W] frame (c / 255) the fit loop targets."""
+    if not (isinstance(rgb, torch.Tensor) and rgb.is_cuda and rgb.dtype == torch.uint8
+            and rgb.dim() == 3 and rgb.shape[2] == 3 and rgb.stride(2) == 1
+            and rgb.stride(1) == 3):
+        raise ValueError("rgb must be a uint8 CUDA tensor [H, W, 3] with packed pixels")
+    h, w = rgb.shape[0], rgb.shape[1]
+    if out is None:
+        out = torch.empty((3, h, w), device=rgb.device)
+    nat.frame_from_rgb8(rgb.data_ptr(), w, h, rgb.stride(0), _check(out, "out", (3, h, w)),
+                        _stream(stream))
+    return out
+
+
 def roi_init(frame: torch.Tensor, mask: torch.Tensor, n: int, roi_frac: float,
              bg_xy: torch.Tensor, stream=None):
     """Region-of-interest superpixel initialiser (gs2d_roi_init).  frame:

@@ -1,0 +1,70 @@
+"""8-bit RGB frame input: the device conversion to the planar float frame is
+c / 255 correctly rounded, bit for bit, for packed and padded rows, odd sizes
+and the empty frame; and a fit on the converted frame equals a fit on the
+same frame converted on the host."""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gs():
+    from paper_2505_09324_gb300 import _native, build
+    build.build()
+    _native.load()
+    import paper_2505_09324_gb300 as pkg
+    return pkg
+
+
+@pytest.mark.parametrize("W,H", [(1, 1), (37, 5), (641, 359), (1920, 1080)])
+def test_rgb8_to_planar_bit_exact(gs, W, H):
+    rng = np.random.default_rng(W * 7 + H)
+    rgb = rng.integers(0, 256, (H, W, 3), dtype=np.uint8)
+    got = gs.frame_from_rgb8(torch.from_numpy(rgb).cuda()).cpu().numpy()
+    want = rgb.transpose(2, 0, 1).astype(np.float32) / np.float32(255.0)
+    np.testing.assert_array_equal(got, want)
+    assert got[0, 0, 0] == np.float32(rgb[0, 0, 0]) / np.float32(255)
+
+
+def test_rgb8_padded_rows(gs):
+    from paper_2505_09324_gb300 import _native as nat
+    W, H, pad = 100, 33, 61
+    rng = np.random.default_rng(3)
+    buf = rng.integers(0, 256, (H, 3 * W + pad), dtype=np.uint8)
+    d = torch.from_numpy(buf).cuda()
+    out = torch.full((3, H, W), -1.0, device="cuda")
+    nat.frame_from_rgb8(d.data_ptr(), W, H, 3 * W + pad, out.data_ptr(),
+                        int(torch.cuda.current_stream().cuda_stream))
+    want = buf[:, :3 * W].reshape(H, W, 3).transpose(2, 0, 1).astype(np.float32) / np.float32(255)
+    np.testing.assert_array_equal(out.cpu().numpy(), want)
+
+
+def test_rgb8_empty_and_bad_arguments(gs):
+    from paper_2505_09324_gb300 import _native as nat
+    s = int(torch.cuda.current_stream().cuda_stream)
+    nat.frame_from_rgb8(0, 0, 0, 0, 0, s)                      # empty frame: no-op
+    with pytest.raises(nat.Gs2dError):
+        nat.frame_from_rgb8(0, 4, 4, 12, 0, s)                 # null buffers
+    d = torch.zeros((4, 4, 3), dtype=torch.uint8, device="cuda")
+    out = torch.empty((3, 4, 4), device="cuda")
+    with pytest.raises(nat.Gs2dError):
+        nat.frame_from_rgb8(d.data_ptr(), 4, 4, 11, out.data_ptr(), s)  # row too short
+
+
+def test_fit_on_converted_frame(gs):
+    from gs2d_inputs import random_gaussians
+    W, H, n = 128, 96, 300
+    rng = np.random.default_rng(5)
+    rgb = rng.integers(0, 256, (H, W, 3), dtype=np.uint8)
+    dev_frame = gs.frame_from_rgb8(torch.from_numpy(rgb).cuda())
+    host_frame = torch.from_numpy(rgb.transpose(2, 0, 1).astype(np.float32)
+                                  / np.float32(255)).contiguous().cuda()
+    p0 = torch.from_numpy(random_gaussians(n, W, H, seed=6)).cuda()
+    a, b = p0.clone(), p0.clone()
+    r = gs.GaussianRasterizer(W, H, n)
+    r.encode_frame(dev_frame, a, 20, check_every=20)
+    r.encode_frame(host_frame, b, 20, check_every=20)
+    assert torch.equal(a, b)
