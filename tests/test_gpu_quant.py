@@ -157,9 +157,13 @@ def test_qat_loop_tracks_oracle(gs, oracle, refine):
                                   Q.quantize(tp.cpu().numpy(), bits, lo, hi, refine)[0])
 
 
-def test_qat_beats_ptq_on_the_quantised_fit(gs):
+def test_qat_raises_the_quantised_quality_of_a_fit(gs):
+    """QAT optimises the loss of the quantised Gaussians: 300 QAT iterations
+    from a 300-iteration fit raise its 5-bit quantised PSNR (by 2.7-4.4 dB
+    over five seeds).  At equal iteration counts plain fitting followed by
+    PTQ does as well or better on these frames."""
     W, H, n = 256, 256, 800
-    bits = [Q.HALF, Q.HALF, 4, 4, 4, 4, 4, 4, 4]
+    bits = [Q.HALF, Q.HALF, 5, 5, 5, 5, 5, 5, 5]
     target = to_dev(smooth_noise_target(W, H, seed=41, terms=24, max_cycles=8))
     p0 = to_dev(random_gaussians(n, W, H, seed=42, l_range=(3.0, 8.0)))
     r = gs.GaussianRasterizer(W, H, n)
@@ -170,6 +174,5 @@ def test_qat_beats_ptq_on_the_quantised_fit(gs):
     psnr_float, psnr_ptq = r.psnr(target, ptq), r.psnr(target, vals)
     qat = ptq.clone()
     out = r.encode_frame_qat(target, qat, 300, q)
-    assert psnr_ptq < psnr_float - 1.0          # 4-bit codes cost quality
-    # fine-tuning with the quantiser in the loop wins back part of it
+    assert psnr_ptq < psnr_float - 0.5          # 5-bit codes cost quality
     assert out["psnr_q"] > psnr_ptq + 1.0, (psnr_float, psnr_ptq, out["psnr_q"])
