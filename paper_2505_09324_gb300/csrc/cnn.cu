@@ -315,18 +315,46 @@ __device__ __forceinline__ void decode_slot(const float* __restrict__ o, int cel
   g[8] = 0.25f + o[8];
 }
 
-// One block per frame: radix select of the n-th largest |w| key, then an
-// index-order compaction.
+// Block-wide exclusive prefix of a 0/1 flag over the block's threads (in
+// thread order) by ballots; returns the prefix and leaves the total in *tot.
+__device__ __forceinline__ int block_flag_prefix(bool f, int* s_w, int* tot) {
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+  const unsigned bal = __ballot_sync(0xffffffffu, f);
+  if (lane == 0) s_w[wid] = __popc(bal);
+  __syncthreads();
+  if (wid == 0) {
+    const int c = lane < nw ? s_w[lane] : 0;
+    int inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane < nw) s_w[lane] = inc - c;
+    if (lane == 31) s_w[32] = inc;
+  }
+  __syncthreads();
+  const int pre = s_w[wid] + __popc(bal & ((1u << lane) - 1u));
+  *tot = s_w[32];
+  __syncthreads();  // s_w is reused by the next call
+  return pre;
+}
+
+constexpr int kSelHists = 16;  // warp pairs sharing one private histogram
+
+// One block per frame: radix select of the n-th largest |w| key (MSB first,
+// a byte per pass, histograms private to warp pairs), then a compaction in
+// slot order: every key above the threshold and the lowest-slot keys equal to
+// it.  Writes the selected slot of every output position to sel.
 __global__ void __launch_bounds__(1024)
-k_head_decode(const float* __restrict__ out, int ldo, int gh, int gw, int slots, int cell_px,
-              float scale, int n, float* __restrict__ params, int ldp,
+k_head_select(const float* __restrict__ out, int ldo, int gh, int gw, int slots, int n,
               int* __restrict__ sel) {
   extern __shared__ uint32_t s_key[];
-  __shared__ int s_hist[256];
-  __shared__ int s_scan[1024];
+  __shared__ int s_hist[kSelHists][256];
+  __shared__ int s_w[33];
   __shared__ uint32_t s_prefix;
   __shared__ int s_need;
-  const int b = blockIdx.x, t = threadIdx.x, nt = blockDim.x;
+  const int b = blockIdx.x, t = threadIdx.x, nt = blockDim.x, lane = t & 31, wid = t >> 5;
   const int cells = gh * gw, S = cells * slots;
   const float* ob = out + (size_t)b * cells * ldo;
   for (int i = t; i < S; i += nt) {
@@ -338,72 +366,95 @@ k_head_decode(const float* __restrict__ out, int ldo, int gh, int gw, int slots,
     s_need = n;
   }
   __syncthreads();
-  // MSB-first radix select: after the byte of `shift`, keys above the prefix
-  // are taken, keys equal to it are still open
+  // after the byte of `shift`, keys above the prefix are taken, keys equal to
+  // it are still open
   for (int shift = 24; shift >= 0; shift -= 8) {
-    for (int i = t; i < 256; i += nt) s_hist[i] = 0;
+    for (int i = t; i < kSelHists * 256; i += nt) (&s_hist[0][0])[i] = 0;
     __syncthreads();
     const uint32_t hi_mask = shift == 24 ? 0u : (0xFFFFFFFFu << (shift + 8));
     const uint32_t prefix = s_prefix;
+    int* h = s_hist[wid % kSelHists];
     for (int i = t; i < S; i += nt) {
       const uint32_t k = s_key[i];
-      if ((k & hi_mask) == (prefix & hi_mask)) atomicAdd(&s_hist[(k >> shift) & 255u], 1);
+      if ((k & hi_mask) == (prefix & hi_mask)) atomicAdd(&h[(k >> shift) & 255u], 1);
     }
     __syncthreads();
-    if (t == 0) {
-      int need = s_need, bin = 255;
-      for (; bin > 0; bin--) {
-        if (s_hist[bin] >= need) break;
-        need -= s_hist[bin];
+    if (t < 256) {
+      int c = 0;
+#pragma unroll
+      for (int w = 0; w < kSelHists; w++) c += s_hist[w][t];
+      s_hist[0][t] = c;
+    }
+    __syncthreads();
+    // the bin holding the need-th largest key: lane l scans bins 255 - 8 l
+    // downwards; the lane whose range crosses `need` finds it
+    if (wid == 0) {
+      int c[8], sum = 0;
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        c[k] = s_hist[0][255 - (8 * lane + k)];
+        sum += c[k];
       }
-      s_need = need;
-      s_prefix = prefix | ((uint32_t)bin << shift);
+      int inc = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+      }
+      const int need = s_need, exc = inc - sum;
+      if (exc < need && need <= inc) {
+        int acc = exc;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+          if (acc + c[k] >= need) {
+            s_need = need - acc;
+            s_prefix = prefix | ((uint32_t)(255 - (8 * lane + k)) << shift);
+            break;
+          }
+          acc += c[k];
+        }
+      } else if (lane == 31 && need > inc) {  // fewer keys than needed: bin 0
+        s_need = need - (inc - c[7]);
+        s_prefix = prefix;
+      }
     }
     __syncthreads();
   }
   const uint32_t T = s_prefix;
   const int need_eq = s_need;  // keys equal to T to take, lowest slot first
-  // compaction in slot order, 1024 slots per round
   int taken_before = 0, eq_before = 0;
   for (int base = 0; base < S; base += nt) {
     const int i = base + t;
     const uint32_t k = i < S ? s_key[i] : 0u;
-    const int eq = (i < S && k == T) ? 1 : 0;
-    // exclusive scan of eq
-    s_scan[t] = eq;
-    __syncthreads();
-    for (int o = 1; o < nt; o <<= 1) {
-      const int v = t >= o ? s_scan[t - o] : 0;
-      __syncthreads();
-      s_scan[t] += v;
-      __syncthreads();
-    }
-    const int eq_rank = eq_before + s_scan[t] - eq;
-    const int eq_total = s_scan[nt - 1];
-    __syncthreads();
-    const int take = (i < S && (k > T || (eq && eq_rank < need_eq))) ? 1 : 0;
-    s_scan[t] = take;
-    __syncthreads();
-    for (int o = 1; o < nt; o <<= 1) {
-      const int v = t >= o ? s_scan[t - o] : 0;
-      __syncthreads();
-      s_scan[t] += v;
-      __syncthreads();
-    }
-    const int j = taken_before + s_scan[t] - take;
-    const int take_total = s_scan[nt - 1];
-    if (take && j < n) {
-      const int cell = i / slots, s = i % slots;
-      float g[9];
-      decode_slot(ob + (size_t)cell * ldo + 9 * s, cell, gw, s, slots, cell_px, scale, g);
-      float* pb = params + (size_t)b * n;
-#pragma unroll
-      for (int r = 0; r < 9; r++) pb[(size_t)r * ldp + j] = g[r];
-      sel[(size_t)b * n + j] = i;
-    }
+    const bool eq = i < S && k == T;
+    int eq_total, take_total;
+    const int eq_rank = eq_before + block_flag_prefix(eq, s_w, &eq_total);
+    const bool take = i < S && (k > T || (eq && eq_rank < need_eq));
+    const int j = taken_before + block_flag_prefix(take, s_w, &take_total);
+    if (take && j < n) sel[(size_t)b * n + j] = i;
     taken_before += take_total;
     eq_before += eq_total;
-    __syncthreads();
+  }
+}
+
+// Decoding of the selected slots into Gaussians, one thread per output.
+__global__ void __launch_bounds__(256)
+k_head_decode(const float* __restrict__ out, int ldo, int B, int gh, int gw, int slots,
+              int cell_px, float scale, int n, float* __restrict__ params, int ldp,
+              const int* __restrict__ sel) {
+  const int cells = gh * gw;
+  const size_t total = (size_t)B * n;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(t / n), j = (int)(t % n);
+    const int i = sel[t];
+    const int cell = i / slots, s = i % slots;
+    float g[9];
+    decode_slot(out + ((size_t)b * cells + cell) * ldo + 9 * s, cell, gw, s, slots, cell_px,
+                scale, g);
+    float* pb = params + (size_t)b * n;
+#pragma unroll
+    for (int r = 0; r < 9; r++) pb[(size_t)r * ldp + j] = g[r];
   }
 }
 
@@ -541,13 +592,17 @@ extern "C" gs2d_status gs2d_head_decode(const float* out, int32_t ldo, int32_t B
   if (B == 0 || n == 0) return set_error(GS2D_OK, "");
   static bool attr = false;
   if (!attr) {
-    if (cudaFuncSetAttribute(k_head_decode, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_head_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 * 1024) != cudaSuccess)
       return launched("gs2d_head_decode");
     attr = true;
   }
-  k_head_decode<<<B, 1024, (size_t)smem, (cudaStream_t)stream>>>(out, ldo, gh, gw, slots, cell_px,
-                                                                  scale, n, params, ldp, sel);
+  cudaStream_t s = (cudaStream_t)stream;
+  k_head_select<<<B, 1024, (size_t)smem, s>>>(out, ldo, gh, gw, slots, n, sel);
+  const size_t total = (size_t)B * n;
+  const size_t want = (total + 255) / 256;
+  k_head_decode<<<(int)(want < 152 * 8 ? want : 152 * 8), 256, 0, s>>>(
+      out, ldo, B, gh, gw, slots, cell_px, scale, n, params, ldp, sel);
   return launched("gs2d_head_decode");
 }
 

@@ -171,6 +171,29 @@ class LearnedInitializer:
                  self.sel.data_ptr(), s)
         return self.params
 
+    def capture(self, frames: torch.Tensor, masks: torch.Tensor | None = None):
+        """Records forward() on these input tensors as one CUDA graph; replay()
+        then re-runs the whole network (every launch of it) on whatever the
+        same tensors hold, with no per-launch host work."""
+        side = torch.cuda.Stream(self.dev)
+        side.wait_stream(torch.cuda.current_stream(self.dev))
+        with torch.cuda.stream(side):
+            self.forward(frames, masks)  # one-time setup (kernel attributes) outside the graph
+        side.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=side):
+            self.forward(frames, masks)
+        self._graph = graph
+        return graph
+
+    def replay(self) -> torch.Tensor:
+        """Runs the captured forward on the current stream's timeline;
+        returns the Gaussians ([9, B n], the same tensor as forward's)."""
+        if getattr(self, "_graph", None) is None:
+            raise RuntimeError("capture() first")
+        self._graph.replay()
+        return self.params
+
     def backward(self, dparams: torch.Tensor):
         """Weight gradients (into self.dw) for dL/dparams ([9, B n] float32) of
         the last forward."""

@@ -142,3 +142,27 @@ def test_packaged_initialiser_on_a_held_out_frame():
     _, loss, _ = r.render_l2(p, frame)
     psnr = 10 * np.log10(1.0 / float(loss[1]))
     assert psnr > 30.0, psnr
+
+
+def test_captured_forward_replays_bit_for_bit():
+    """The whole network recorded as one CUDA graph: replays on new contents
+    of the captured input tensors equal direct forward calls, bit for bit."""
+    from gs2d_inputs import conferencing_frame
+    from paper_2505_09324_gb300.learned import packaged
+    W, H, n = 1920, 1080, 20000
+    net = packaged(W, H, n)
+    frame = torch.empty((1, 3, H, W), device="cuda")
+    mask = torch.empty((1, H, W), dtype=torch.uint8, device="cuda")
+    f0, m0 = conferencing_frame(W, H, seed=4242)
+    frame.copy_(torch.from_numpy(f0))
+    mask.copy_(torch.from_numpy(m0.astype(np.uint8)))
+    net.capture(frame, mask)
+    for seed in (4243, 4244):
+        f, m = conferencing_frame(W, H, seed=seed)
+        frame.copy_(torch.from_numpy(f))
+        mask.copy_(torch.from_numpy(m.astype(np.uint8)))
+        got = net.replay().clone()
+        want = net.forward(frame, mask).clone()
+        torch.cuda.synchronize()
+        net.check_status()
+        assert torch.equal(got, want)
