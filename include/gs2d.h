@@ -480,6 +480,18 @@ gs2d_status gs2d_cnn_input(const float* frames, const uint8_t* masks, int32_t B,
 gs2d_status gs2d_im2col(const void* x, int32_t B, int32_t Hi, int32_t Wi, int32_t C, int32_t ks,
                         int32_t stride, int32_t pad, void* col, int32_t ldk, void* stream);
 
+/* Implicit-GEMM convolution on the tensor cores: out = gs2d_gemm_bf16 of
+ * gs2d_im2col(x) and W (the same sums in the same order, bit for bit) without
+ * writing the im2col operand: the kernel gathers each 128-row tile of it from
+ * x into shared memory.  x: device NHWC BF16 [B][Hi][Wi][C], C a multiple of
+ * 8; W: device BF16 [N][ldk], ldk a multiple of 8 and >= ks^2 C + 1 (the
+ * bias in column ks^2 C); relu applies max(., 0); exactly one of out_f32 /
+ * out_bf16 ([B Ho Wo][ldc], device) is non-NULL.  status as gs2d_gemm_bf16. */
+gs2d_status gs2d_conv_bf16(const void* x, int32_t B, int32_t Hi, int32_t Wi, int32_t C,
+                           int32_t ks, int32_t stride, int32_t pad, const void* W, int32_t ldk,
+                           int32_t N, int32_t relu, float* out_f32, void* out_bf16, int32_t ldc,
+                           int32_t* status, void* stream);
+
 /* Gradient of gs2d_im2col: dx[b][iy][ix][ci] = sum over the taps that read
  * (iy, ix) of dcol (device, float32 [B Ho Wo][ldk]), multiplied by (act > 0)
  * when act (device, [B][Hi][Wi][C] BF16, the ReLU output fed to the im2col) is

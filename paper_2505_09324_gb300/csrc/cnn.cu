@@ -55,6 +55,46 @@ extern "C" gs2d_status gs2d_gemm_bf16(const void* A, int32_t lda, const void* B,
   return set_error(GS2D_OK, "");
 }
 
+extern "C" gs2d_status gs2d_conv_bf16(const void* x, int32_t B, int32_t Hi, int32_t Wi,
+                                      int32_t C, int32_t ks, int32_t stride, int32_t pad,
+                                      const void* W, int32_t ldk, int32_t N, int32_t relu,
+                                      float* out_f32, void* out_bf16, int32_t ldc,
+                                      int32_t* status, void* stream) {
+  if (B < 0 || Hi < 1 || Wi < 1 || C < 8 || (C % 8) || ks < 1 || stride < 1 || pad < 0 ||
+      N < 0 || ldk % 8 || ldk < ks * ks * C + 1 || ldc < N)
+    return set_error(GS2D_ERR_INVALID_ARG, "gs2d_conv_bf16: sizes");
+  const int Ho = (Hi + 2 * pad - ks) / stride + 1, Wo = (Wi + 2 * pad - ks) / stride + 1;
+  if (Ho < 1 || Wo < 1) return set_error(GS2D_ERR_INVALID_ARG, "gs2d_conv_bf16: empty output");
+  if (B == 0 || N == 0) return set_error(GS2D_OK, "");
+  if (!x || !W || ((out_f32 == nullptr) == (out_bf16 == nullptr)) || ((uintptr_t)x & 15) ||
+      ((uintptr_t)W & 15))
+    return set_error(GS2D_ERR_INVALID_ARG, "gs2d_conv_bf16: operands");
+  TcConvProblem pr;
+  pr.x = static_cast<const __nv_bfloat16*>(x);
+  pr.B = B;
+  pr.Hi = Hi;
+  pr.Wi = Wi;
+  pr.C = C;
+  pr.ks = ks;
+  pr.stride = stride;
+  pr.pad = pad;
+  pr.W = static_cast<const __nv_bfloat16*>(W);
+  pr.ldk = ldk;
+  pr.N = N;
+  pr.relu = relu;
+  pr.out_f32 = out_f32;
+  pr.out_bf16 = static_cast<__nv_bfloat16*>(out_bf16);
+  pr.ldc = ldc;
+  pr.status = status;
+  const cudaError_t e = tc_conv(pr, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    char msg[200];
+    snprintf(msg, sizeof(msg), "gs2d_conv_bf16: %s", cudaGetErrorString(e));
+    return set_error(GS2D_ERR_CUDA, msg);
+  }
+  return set_error(GS2D_OK, "");
+}
+
 // ---------------------------------------------------------------------------
 // Convolution helpers.  Activations are NHWC BF16 ([B][H][W][C], C a multiple
 // of 8); a ks x ks convolution is the GEMM  Z = col(X) . W^T  with

@@ -34,7 +34,23 @@ struct TcGemmProblem {
   int* status;
 };
 
+// Implicit-GEMM convolution: Z[p][n] = sum_k col(X)[p][k] W[n][k] with col the
+// im2col operand of an NHWC BF16 input (k = tap C + ci, a ones column at
+// k = ks^2 C for the bias), never materialised.
+struct TcConvProblem {
+  const __nv_bfloat16* x;  // [B][Hi][Wi][C], C a multiple of 8, 16-byte aligned
+  int B, Hi, Wi, C, ks, stride, pad;
+  const __nv_bfloat16* W;  // [N][ldk], ldk a multiple of 8, >= ks^2 C + 1
+  int ldk, N;
+  int relu;
+  float* out_f32;          // [M][ldc] or NULL (exactly one output)
+  __nv_bfloat16* out_bf16;
+  int ldc;
+  int* status;
+};
+
 cudaError_t tc_gemm(const TcGemmProblem& pr, cudaStream_t s);
+cudaError_t tc_conv(const TcConvProblem& pr, cudaStream_t s);
 int tc_gemm_bn(int n);
 size_t tc_gemm_partial_floats(int M, int N, int ldc, int K, int splits);
 

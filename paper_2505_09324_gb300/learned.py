@@ -138,9 +138,13 @@ class LearnedInitializer:
             9 * self.cfg.slots * (self.layers[-1][0] + 1)
 
     # ------------------------------------------------------------------
-    def forward(self, frames: torch.Tensor, masks: torch.Tensor | None) -> torch.Tensor:
+    def forward(self, frames: torch.Tensor, masks: torch.Tensor | None,
+                keep_col: bool = True) -> torch.Tensor:
         """frames: [B, 3, H, W] float32 CUDA; masks: [B, H, W] uint8 or None.
-        Returns the Gaussians, [9, B n] float32 (frame b in columns b n ...)."""
+        Returns the Gaussians, [9, B n] float32 (frame b in columns b n ...).
+        keep_col=False (inference) runs the convolutions as implicit GEMMs
+        (gs2d_conv_bf16, the same result bit for bit) and keeps no complete
+        set of im2col operands, which backward() needs."""
         B, s = self.B, self._s()
         if tuple(frames.shape) != (B, 3, self.H, self.W) or frames.dtype != torch.float32:
             raise ValueError("frames must be [B, 3, H, W] float32")
@@ -156,6 +160,16 @@ class LearnedInitializer:
             src = self.x[li]
             hi, wi = self.sizes[li] if li < self.L else self.sizes[-1]
             stride, pad = (2, 1) if ks == 3 else (1, 0)
+            # implicit GEMM unless K is very deep (the last 3 x 3 layer: 37
+            # k-tiles over 32 tiles, where the TMA-fed GEMM over an im2col
+            # operand is faster); the results are identical either way
+            if not keep_col and (ldk + 63) // 64 <= 32:
+                last = li == self.L
+                nat.call("gs2d_conv_bf16", src.data_ptr(), B, hi, wi, ci, ks, stride, pad,
+                         self.wb[li].data_ptr(), ldk, co, 0 if last else 1,
+                         self.out.data_ptr() if last else 0,
+                         0 if last else self.x[li + 1].data_ptr(), co, st, s)
+                continue
             nat.call("gs2d_im2col", src.data_ptr(), B, hi, wi, ci, ks, stride, pad,
                      self.col[li].data_ptr(), ldk, s)
             P = self.col[li].shape[0]
@@ -178,11 +192,12 @@ class LearnedInitializer:
         side = torch.cuda.Stream(self.dev)
         side.wait_stream(torch.cuda.current_stream(self.dev))
         with torch.cuda.stream(side):
-            self.forward(frames, masks)  # one-time setup (kernel attributes) outside the graph
+            # one-time setup (kernel attributes) outside the graph
+            self.forward(frames, masks, keep_col=False)
         side.synchronize()
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=side):
-            self.forward(frames, masks)
+            self.forward(frames, masks, keep_col=False)
         self._graph = graph
         return graph
 
@@ -463,7 +478,7 @@ def evaluate(net: LearnedInitializer, seeds, target_psnr: float = 35.0, cap: int
             frames = torch.stack(buf_f)
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
-            P = net.forward(frames, torch.stack(buf_m)).clone()
+            P = net.forward(frames, torch.stack(buf_m), keep_col=False).clone()
             torch.cuda.synchronize(dev)
             per = (time.perf_counter() - t0) / B
             for b in range(B):

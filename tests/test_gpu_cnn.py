@@ -258,3 +258,58 @@ def test_chamfer_loss_and_gradient(nat):
         got = dP[:2, b * n:(b + 1) * n].cpu().numpy().T.astype(np.float64)
         assert np.all(np.abs(got - lam * ref_g) <= 1e-4 * np.abs(lam * ref_g).max())
     assert float(dP[2:].abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("B,H,W,ci,co,ks,st,pad,out", [
+    (2, 40, 33, 8, 32, 3, 2, 1, "bf16"),     # ragged M (2 x 20 x 17 = 680 rows)
+    (1, 24, 30, 32, 64, 3, 2, 1, "bf16"),
+    (2, 12, 9, 256, 384, 3, 2, 1, "bf16"),   # N over two 192-column tiles, 37 k-tiles
+    (3, 7, 11, 384, 90, 1, 1, 0, "f32"),     # the head: 1 x 1, N = 90, FP32 out
+    (1, 135, 240, 64, 128, 3, 2, 1, "bf16")])
+def test_implicit_conv_equals_im2col_gemm(nat, B, H, W, ci, co, ks, st, pad, out):
+    """gs2d_conv_bf16 gathers the im2col tiles itself: its output equals
+    gs2d_im2col + gs2d_gemm_bf16 bit for bit, and the oracle's convolution
+    within the GEMM bar."""
+    g = np.random.Generator(np.random.PCG64(7 * co + H + ks))
+    ldk = -(-(ks * ks * ci + 1) // 8) * 8
+    x = cnn.bf16_round(g.normal(size=(B, H, W, ci)))
+    w = np.zeros((co, ldk), np.float32)
+    w[:, :ks * ks * ci + 1] = g.normal(size=(co, ks * ks * ci + 1)) / np.sqrt(ks * ks * ci)
+    w = cnn.bf16_round(w)
+    Ho, Wo = cnn.out_size(H, ks, st, pad), cnn.out_size(W, ks, st, pad)
+    P = B * Ho * Wo
+    d_x, d_w = bf16_dev(x), bf16_dev(w)
+    relu = out == "bf16"
+    dt = torch.bfloat16 if out == "bf16" else torch.float32
+    col = torch.empty((P, ldk), dtype=torch.bfloat16, device="cuda")
+    z_ref = torch.empty((P, co), dtype=dt, device="cuda")
+    z = torch.full((P, co), 7.0, dtype=dt, device="cuda")
+    st_ = torch.zeros(1, dtype=torch.int32, device="cuda")
+    nat.call("gs2d_im2col", d_x.data_ptr(), B, H, W, ci, ks, st, pad, col.data_ptr(), ldk, 0)
+    f32 = z_ref.data_ptr() if out == "f32" else 0
+    b16 = z_ref.data_ptr() if out == "bf16" else 0
+    nat.gemm_bf16(col.data_ptr(), ldk, d_w.data_ptr(), ldk, P, co, ldk, 0, relu, f32, b16, co, 1,
+                  0, st_.data_ptr(), 0)
+    nat.call("gs2d_conv_bf16", d_x.data_ptr(), B, H, W, ci, ks, st, pad, d_w.data_ptr(), ldk,
+             co, 1 if relu else 0, z.data_ptr() if out == "f32" else 0,
+             z.data_ptr() if out == "bf16" else 0, co, st_.data_ptr(), 0)
+    torch.cuda.synchronize()
+    assert int(st_.item()) == 0
+    assert torch.equal(z, z_ref)
+    ref = cnn.conv(x, w[:, :ks * ks * ci + 1], ks, st, pad).reshape(P, co)
+    if relu:
+        ref = np.maximum(ref, 0.0)
+    scale = cnn.gemm_abs(cnn.im2col(x, ks, st, pad, ldk), w)
+    got = (to_np_bf16(z) if out == "bf16" else z.cpu().numpy()).astype(np.float64)
+    tol = REL * scale + (np.abs(ref) * 2.0 ** -8 if relu else 0.0) + 1e-30
+    assert np.all(np.abs(got - ref) <= tol)
+
+
+def test_implicit_conv_bad_arguments(nat):
+    d = torch.zeros(64, dtype=torch.bfloat16, device="cuda")
+    with pytest.raises(nat.Gs2dError):   # C not a multiple of 8
+        nat.call("gs2d_conv_bf16", d.data_ptr(), 1, 4, 4, 4, 3, 2, 1, d.data_ptr(), 40, 8, 1, 0,
+                 d.data_ptr(), 8, 0, 0)
+    with pytest.raises(nat.Gs2dError):   # no room for the bias column
+        nat.call("gs2d_conv_bf16", d.data_ptr(), 1, 4, 4, 8, 3, 2, 1, d.data_ptr(), 72, 8, 1, 0,
+                 d.data_ptr(), 8, 0, 0)

@@ -166,3 +166,21 @@ def test_captured_forward_replays_bit_for_bit():
         torch.cuda.synchronize()
         net.check_status()
         assert torch.equal(got, want)
+
+
+def test_implicit_forward_equals_im2col_forward():
+    """Inference without im2col operands (every convolution an implicit GEMM)
+    gives the same Gaussians bit for bit, on the shipped 1080p network and on a
+    small random network with a batch of three."""
+    from gs2d_inputs import conferencing_frame
+    from paper_2505_09324_gb300.learned import LearnedInitializer, packaged
+    for net, W, H, B in ((packaged(1920, 1080, 20000), 1920, 1080, 1),
+                         (LearnedInitializer(200, 136, 200, 3, seed=5), 200, 136, 3)):
+        fr = [conferencing_frame(W, H, seed=300 + b) for b in range(B)]
+        frames = torch.from_numpy(np.stack([f for f, _ in fr])).cuda()
+        masks = torch.from_numpy(np.stack([m for _, m in fr]).astype(np.uint8)).cuda()
+        a = net.forward(frames, masks, keep_col=True).clone()
+        b = net.forward(frames, masks, keep_col=False).clone()
+        torch.cuda.synchronize()
+        net.check_status()
+        assert torch.equal(a, b)
