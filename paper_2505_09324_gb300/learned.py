@@ -530,6 +530,9 @@ def main(argv=None):
     ap.add_argument("--weights", default="", help="write the trained weights (.npz)")
     ap.add_argument("--load", default="", help="start from these weights (.npz)")
     ap.add_argument("--eval-only", action="store_true")
+    ap.add_argument("--time-forward", action="store_true",
+                    help="time the shipped network's forward (with and without im2col "
+                         "operands: 3 warm-up + 20 timed calls each) and exit")
     a = ap.parse_args(argv)
 
     def log(msg):
@@ -538,6 +541,28 @@ def main(argv=None):
     from . import build
     build.build()
     nat.load()
+    if a.time_forward:
+        from gs2d_inputs import conferencing_frame
+        net = packaged(a.width, a.height, a.n, a.batch) or \
+            LearnedInitializer(a.width, a.height, a.n, a.batch)
+        fr = [conferencing_frame(a.width, a.height, seed=1 + b) for b in range(a.batch)]
+        frames = torch.from_numpy(np.stack([f for f, _ in fr])).cuda()
+        masks = torch.from_numpy(np.stack([m for _, m in fr]).astype(np.uint8)).cuda()
+        out = {}
+        for keep in (True, False):
+            for _ in range(3):
+                net.forward(frames, masks, keep_col=keep)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(20):
+                net.forward(frames, masks, keep_col=keep)
+            e1.record()
+            torch.cuda.synchronize()
+            out["ms_im2col" if keep else "ms_implicit"] = e0.elapsed_time(e1) / 20
+        net.check_status()
+        print(json.dumps({"batch": a.batch, **out}))
+        return 0
     t0 = time.perf_counter()
     train_seeds = [10000 + i for i in range(a.train_frames)]
     eval_seeds = [20000 + i for i in range(a.eval_frames)]
