@@ -32,7 +32,15 @@ Gaussians outside the region to the reader; the readings implemented here:
   a = (background pixels) / (n - M), weight 1 / kappa (integral a), colour =
   frame at the mean.
 
-All arithmetic is double precision; sums run over pixels in raster order.
+Arithmetic (a reading: the paper fixes no precision).  The assignment's
+distances and comparisons are single precision (numpy float32, each
+operation rounded once; the centres are kept as float32), the precision the
+GPU kernel decides in.  Every sum over a segment is exact: pixel-centre
+coordinates enter as the integers 2 x + 1 - 2 floor(seed) (twice the offset
+from the seed's pixel), colours as rint(c 2^20) (colours clamped to
+[-32, 32]), so counts, first and second moments are integers whose sums do
+not depend on their order; means and covariances follow from them by a fixed
+sequence of double-precision operations, rounded once to float32 at the end.
 """
 
 from __future__ import annotations
@@ -44,6 +52,8 @@ import numpy as np
 COMPACTNESS = 0.2
 ITERATIONS = 10
 KAPPA = 4.0  # covariance scale: keeps the additive blend of a tiling flat
+COLOUR_SCALE = float(1 << 20)
+COLOUR_LIMIT = 32.0
 
 
 def seeds(mask: np.ndarray, k_target: int, max_seeds: int | None = None):
@@ -68,27 +78,34 @@ def seeds(mask: np.ndarray, k_target: int, max_seeds: int | None = None):
 
 
 def assign(frame, mask, centers_col, centers_xy, seed_cells, S, m=COMPACTNESS):
-    """Label map (int64 [H, W], -1 outside the mask) for the given centres."""
+    """Label map (int64 [H, W], -1 outside the mask) for the given float32
+    centres: a mask pixel joins the candidate minimising, in float32,
+    D = ((r - r_c)^2 + (g - g_c)^2) + (b - b_c)^2 + lam ((dx^2 + dy^2)),
+    lam = float32((m / S)^2), among centres with |dx|, |dy| <= float32(S);
+    candidates are visited in ascending index and only a strictly smaller D
+    replaces the best."""
     _, h, w = frame.shape
     label = np.full((h, w), -1, np.int64)
     ys, xs = np.nonzero(mask)          # the mask pixels, raster order
     if len(xs) == 0 or len(centers_xy) == 0:
         return label
-    col = frame[:, ys, xs].astype(np.float64)
-    PX = xs.astype(np.float64) + 0.5
-    PY = ys.astype(np.float64) + 0.5
-    best = np.full(len(xs), np.inf)
+    f32 = np.float32
+    col = frame[:, ys, xs].astype(f32)
+    PX = (xs.astype(np.float64) + 0.5).astype(f32)
+    PY = (ys.astype(np.float64) + 0.5).astype(f32)
+    S32 = f32(S)
+    lam = f32((m / S) * (m / S))
+    ccol = np.asarray(centers_col, f32)
+    cxy = np.asarray(centers_xy, f32)
+    best = np.full(len(xs), np.inf, f32)
     lab = np.full(len(xs), -1, np.int64)
-    # seed index by grid cell
     gx = int(math.ceil(w / S))
     gy = int(math.ceil(h / S))
     cell_of = np.full((gy, gx), -1, np.int64)
     for idx, (i, j) in enumerate(seed_cells):
         cell_of[j, i] = idx
-    pcx = np.floor(PX / S).astype(np.int64)
-    pcy = np.floor(PY / S).astype(np.int64)
-    lam = (m / S) * (m / S)
-    # candidates in ascending centre index: gather the 25 cells, sort by index
+    pcx = np.floor(PX.astype(np.float64) / S).astype(np.int64)
+    pcy = np.floor(PY.astype(np.float64) / S).astype(np.int64)
     cand_lists = []
     for dj in range(-2, 3):
         for di in range(-2, 3):
@@ -105,11 +122,11 @@ def assign(frame, mask, centers_col, centers_xy, seed_cells, S, m=COMPACTNESS):
         if not valid.any():
             break
         ii = np.where(valid, idx, 0)
-        dx = PX - centers_xy[ii, 0]
-        dy = PY - centers_xy[ii, 1]
-        within = valid & (np.abs(dx) <= S) & (np.abs(dy) <= S)
-        dc = ((col[0] - centers_col[ii, 0]) ** 2 + (col[1] - centers_col[ii, 1]) ** 2) \
-            + (col[2] - centers_col[ii, 2]) ** 2
+        dx = PX - cxy[ii, 0]
+        dy = PY - cxy[ii, 1]
+        within = valid & (np.abs(dx) <= S32) & (np.abs(dy) <= S32)
+        dr, dg, db = col[0] - ccol[ii, 0], col[1] - ccol[ii, 1], col[2] - ccol[ii, 2]
+        dc = (dr * dr + dg * dg) + db * db
         d = dc + lam * (dx * dx + dy * dy)
         take = within & (d < best)
         best = np.where(take, d, best)
@@ -118,27 +135,49 @@ def assign(frame, mask, centers_col, centers_xy, seed_cells, S, m=COMPACTNESS):
     return label
 
 
-def update(frame, label, centers_col, centers_xy, seeds_xy, S):
-    """New centres: mean colour and position of each segment (raster-order
-    double sums), clamped to within S of the seed; empty segments stay."""
+def segment_sums(frame, label, seeds_xy):
+    """Exact integer sums per segment: count, sum of u = 2 x + 1 - 2 floor(qx),
+    of v (the same in y), of u^2, u v, v^2 and of rint(c 2^20) per channel
+    (object arrays of Python ints, [k])."""
     _, h, w = frame.shape
-    k = len(centers_xy)
-    lab = label.reshape(-1)
-    sel = lab >= 0
-    px = (np.arange(w, dtype=np.float64) + 0.5)[None, :].repeat(h, 0).reshape(-1)
-    py = (np.arange(h, dtype=np.float64) + 0.5)[:, None].repeat(w, 1).reshape(-1)
-    cnt = np.bincount(lab[sel], minlength=k).astype(np.float64)
-    new_xy = centers_xy.copy()
-    new_col = centers_col.copy()
-    nz = cnt > 0
-    for d, vals in enumerate((px, py)):
-        s = np.bincount(lab[sel], weights=vals[sel], minlength=k)
-        new_xy[nz, d] = s[nz] / cnt[nz]
-    for ch in range(3):
-        v = frame[ch].astype(np.float64).reshape(-1)
-        s = np.bincount(lab[sel], weights=v[sel], minlength=k)
-        new_col[nz, ch] = s[nz] / cnt[nz]
-    new_xy = np.minimum(np.maximum(new_xy, seeds_xy - S), seeds_xy + S)
+    k = len(seeds_xy)
+    sums = {key: [0] * k for key in ("n", "u", "v", "uu", "uv", "vv", "r", "g", "b")}
+    ys, xs = np.nonzero(label >= 0)
+    if len(xs) == 0 or k == 0:
+        return sums
+    lab = label[ys, xs]
+    fx = np.floor(np.asarray(seeds_xy)[:, 0]).astype(np.int64)
+    fy = np.floor(np.asarray(seeds_xy)[:, 1]).astype(np.int64)
+    u = 2 * xs.astype(np.int64) + 1 - 2 * fx[lab]
+    v = 2 * ys.astype(np.int64) + 1 - 2 * fy[lab]
+    q = [np.rint(np.clip(frame[ch, ys, xs].astype(np.float64), -COLOUR_LIMIT, COLOUR_LIMIT)
+                 * COLOUR_SCALE).astype(np.int64) for ch in range(3)]
+    for key, vals in (("n", np.ones_like(u)), ("u", u), ("v", v), ("uu", u * u), ("uv", u * v),
+                      ("vv", v * v), ("r", q[0]), ("g", q[1]), ("b", q[2])):
+        acc = np.zeros(k, np.int64)
+        np.add.at(acc, lab, vals)      # int64: exact, order-free
+        sums[key] = [int(a) for a in acc]
+    return sums
+
+
+def update(frame, label, centers_col, centers_xy, seeds_xy, S):
+    """New float32 centres: the segment's mean position (u / (2 n) + floor(q)
+    in double) clamped to within S of the seed, and mean colour (sum /
+    (n 2^20) in double); empty segments keep their centre."""
+    sm = segment_sums(frame, label, seeds_xy)
+    new_col = np.asarray(centers_col, np.float32).copy()
+    new_xy = np.asarray(centers_xy, np.float32).copy()
+    for c in range(len(seeds_xy)):
+        n = sm["n"][c]
+        if n == 0:
+            continue
+        qx, qy = float(seeds_xy[c][0]), float(seeds_xy[c][1])
+        mx = float(sm["u"][c]) / float(2 * n) + math.floor(qx)
+        my = float(sm["v"][c]) / float(2 * n) + math.floor(qy)
+        new_xy[c, 0] = np.float32(min(max(mx, qx - S), qx + S))
+        new_xy[c, 1] = np.float32(min(max(my, qy - S), qy + S))
+        for ch, key in enumerate(("r", "g", "b")):
+            new_col[c, ch] = np.float32(float(sm[key][c]) / (float(n) * COLOUR_SCALE))
     return new_col, new_xy
 
 
@@ -150,61 +189,54 @@ def segment(frame, mask, k_target, iterations=ITERATIONS, m=COMPACTNESS, max_see
     _, h, w = frame.shape
     xi = np.clip(np.floor(sxy[:, 0]).astype(np.int64), 0, w - 1)
     yi = np.clip(np.floor(sxy[:, 1]).astype(np.int64), 0, h - 1)
-    ccol = frame[:, yi, xi].T.astype(np.float64)
-    cxy = sxy.copy()
+    ccol = frame[:, yi, xi].T.astype(np.float32)
+    cxy = sxy.astype(np.float32)
     label = np.full((h, w), -1, np.int64)
-    for _ in range(iterations):
+    for it in range(iterations):
         label = assign(frame, mask, ccol, cxy, cells, S, m)
-        ccol, cxy = update(frame, label, ccol, cxy, sxy, S)
+        if it + 1 < iterations:
+            ccol, cxy = update(frame, label, ccol, cxy, sxy, S)
     return S, sxy, label, (ccol, cxy)
 
 
 def gaussians_from_segments(frame, label, sxy, S):
-    """[9, M] float64 Gaussians from the final segments (see module doc)."""
+    """[9, M] float64 Gaussians from the final segments (see module doc), from
+    the exact integer sums: mean = u / (2 n) + floor(q); covariance of the
+    pixel centres (uu / n - (u / n)^2) / 4 etc. in double; Sigma = KAPPA
+    (covariance + I/12); L = chol(Sigma); colour = sum / (n 2^20); weight =
+    n / (2 pi l1 l3)."""
     _, h, w = frame.shape
     k = len(sxy)
     out = np.zeros((9, k), np.float64)
-    lab = label.reshape(-1)
-    sel = lab >= 0
-    px = (np.arange(w, dtype=np.float64) + 0.5)[None, :].repeat(h, 0).reshape(-1)
-    py = (np.arange(h, dtype=np.float64) + 0.5)[:, None].repeat(w, 1).reshape(-1)
-    L = lab[sel]
-    cnt = np.bincount(L, minlength=k).astype(np.float64)
-    sx = np.bincount(L, weights=px[sel], minlength=k)
-    sy = np.bincount(L, weights=py[sel], minlength=k)
+    sm = segment_sums(frame, label, sxy)
+    two_pi = 2.0 * math.pi
     for i in range(k):
-        if cnt[i] == 0:
+        n = sm["n"][i]
+        if n == 0:
             xi = min(max(int(math.floor(sxy[i, 0])), 0), w - 1)
             yi = min(max(int(math.floor(sxy[i, 1])), 0), h - 1)
             s = 2.0 * (S / math.sqrt(12.0))
             out[:, i] = [sxy[i, 0], sxy[i, 1], s, 0.0, s, frame[0, yi, xi], frame[1, yi, xi],
                          frame[2, yi, xi], 1.0]
-    nz = np.nonzero(cnt)[0]
-    mx = sx[nz] / cnt[nz]
-    my = sy[nz] / cnt[nz]
-    # centred second moments (two-pass), raster order
-    dxm = px[sel] - (sx / np.maximum(cnt, 1))[L]
-    dym = py[sel] - (sy / np.maximum(cnt, 1))[L]
-    sxx = np.bincount(L, weights=dxm * dxm, minlength=k)
-    sxy_ = np.bincount(L, weights=dxm * dym, minlength=k)
-    syy = np.bincount(L, weights=dym * dym, minlength=k)
-    vxx = sxx[nz] / cnt[nz] + 1.0 / 12.0
-    vxy = sxy_[nz] / cnt[nz]
-    vyy = syy[nz] / cnt[nz] + 1.0 / 12.0
-    l1 = np.sqrt(vxx)
-    l2 = vxy / l1
-    l3 = np.sqrt(vyy - l2 * l2)
-    # Sigma = KAPPA (cov + I/12): the factor sqrt(KAPPA) = 2 is exact
-    l1, l2, l3 = 2.0 * l1, 2.0 * l2, 2.0 * l3
-    out[0, nz] = mx
-    out[1, nz] = my
-    out[2, nz] = l1
-    out[3, nz] = l2
-    out[4, nz] = l3
-    for ch in range(3):
-        v = frame[ch].astype(np.float64).reshape(-1)
-        out[5 + ch, nz] = np.bincount(L, weights=v[sel], minlength=k)[nz] / cnt[nz]
-    out[8, nz] = cnt[nz] / (2.0 * math.pi * l1 * l3)
+            continue
+        fn = float(n)
+        au, av = float(sm["u"][i]) / fn, float(sm["v"][i]) / fn
+        cxx = (float(sm["uu"][i]) / fn - au * au) / 4.0
+        cxy = (float(sm["uv"][i]) / fn - au * av) / 4.0
+        cyy = (float(sm["vv"][i]) / fn - av * av) / 4.0
+        vxx = cxx + 1.0 / 12.0
+        vyy = cyy + 1.0 / 12.0
+        l1 = math.sqrt(vxx)
+        l2 = cxy / l1
+        l3 = math.sqrt(vyy - l2 * l2)
+        # Sigma = KAPPA (cov + I/12): the factor sqrt(KAPPA) = 2 is exact
+        l1, l2, l3 = 2.0 * l1, 2.0 * l2, 2.0 * l3
+        out[0, i] = float(sm["u"][i]) / float(2 * n) + math.floor(sxy[i, 0])
+        out[1, i] = float(sm["v"][i]) / float(2 * n) + math.floor(sxy[i, 1])
+        out[2, i], out[3, i], out[4, i] = l1, l2, l3
+        for ch, key in enumerate(("r", "g", "b")):
+            out[5 + ch, i] = float(sm[key][i]) / (fn * COLOUR_SCALE)
+        out[8, i] = fn / (two_pi * l1 * l3)
     return out
 
 

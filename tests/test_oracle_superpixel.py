@@ -71,3 +71,27 @@ def test_background_gaussians_and_counts():
     a = (~mask).sum() / (n - M)
     np.testing.assert_allclose(bg[2], math.sqrt(4 * a / (2 * math.pi)))
     assert np.all(bg[3] == 0) and np.all(bg[8] == 0.25)
+
+
+def test_segment_sums_are_exact_and_order_free():
+    """The integer segment sums equal the plain sums of the definitions (u =
+    2 x + 1 - 2 floor(q), colours rint(c 2^20)), whatever the pixel order; the
+    quantised mean colour is within 2^-21 of the exact mean."""
+    from oracle import superpixel as sp
+    frame, mask = conferencing_frame(96, 64, seed=8)
+    S, sxy, label, _ = sp.segment(frame, mask, 60)
+    sm = sp.segment_sums(frame, label, sxy)
+    for c in np.unique(label[label >= 0])[:15]:
+        ys, xs = np.nonzero(label == c)
+        fx, fy = math.floor(sxy[c, 0]), math.floor(sxy[c, 1])
+        u = [2 * int(x) + 1 - 2 * fx for x in xs]
+        v = [2 * int(y) + 1 - 2 * fy for y in ys]
+        assert sm["n"][c] == len(xs)
+        assert (sm["u"][c], sm["v"][c]) == (sum(u), sum(v))
+        assert sm["uu"][c] == sum(a * a for a in u) and sm["uv"][c] == sum(
+            a * b for a, b in zip(u, v))
+        for ch, key in enumerate("rgb"):
+            q = [int(np.rint(float(frame[ch, y, x]) * 2.0 ** 20)) for y, x in zip(ys, xs)]
+            assert sm[key][c] == sum(q)
+            exact = float(np.mean(frame[ch, ys, xs].astype(np.float64)))
+            assert abs(sm[key][c] / (len(xs) * 2.0 ** 20) - exact) <= 2.0 ** -21 + 1e-15
