@@ -1,7 +1,7 @@
 """Region-of-interest superpixel initialiser on the GPU (gs2d_roi_init) against
-the oracle.  The clustering runs in double precision with the same operation
-order and raster-order sums on both sides, so the Gaussians agree bit for bit
-(after the final rounding to float32)."""
+the oracle.  Both sides decide the assignment in single precision with the
+same rounded operations and form every segment sum exactly in integers, so
+the Gaussians agree bit for bit (after the final rounding to float32)."""
 
 import numpy as np
 import pytest
@@ -60,3 +60,11 @@ def test_empty_mask_and_all_mask(gs):
         got, ref, n_roi, M = run_both(gs, frame, mask, 50, 0.7, seed=5)
         assert n_roi == M
         np.testing.assert_array_equal(got, ref)
+
+
+def test_large_segments_bit_exact(gs):
+    """Few, large segments (S of about 180 px): the exact sums stay exact."""
+    frame, mask = conferencing_frame(640, 360, seed=6)
+    got, ref, n_roi, M = run_both(gs, frame, mask, 3, 0.7, seed=7)
+    assert n_roi == M
+    np.testing.assert_array_equal(got, ref)
