@@ -7,7 +7,8 @@ centre, Cholesky factor from the segment covariance, colour = mean segment
 colour.  It leaves the clustering details, the covariance scale and the
 Gaussians outside the region to the reader; the readings implemented here:
 
-* seeds on a square grid of step S = sqrt(A_roi / K) (A_roi = mask pixels),
+* seeds on a square grid of step S = max(1, sqrt(A_roi / K)) (A_roi = mask
+  pixels; at most one superpixel per pixel),
   at ((i + 1/2) S, (j + 1/2) S), kept where the seed's pixel is in the mask;
   the number of region Gaussians is the number of seeds M (at most n);
 * I = 10 K-means iterations in (r, g, b, x, y): a mask pixel p (centre at
@@ -63,7 +64,9 @@ def seeds(mask: np.ndarray, k_target: int, max_seeds: int | None = None):
     area = int(mask.sum())
     if area == 0 or k_target <= 0:
         return 1.0, np.zeros((0, 2)), np.zeros((0, 2), np.int64)
-    S = math.sqrt(area / k_target)
+    # a grid finer than the pixels would put several seeds in one pixel: the
+    # step is at least one pixel (at most one superpixel per ROI pixel)
+    S = max(1.0, math.sqrt(area / k_target))
     gx = int(math.ceil(w / S))
     gy = int(math.ceil(h / S))
     pts, cells = [], []

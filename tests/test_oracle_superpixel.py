@@ -95,3 +95,20 @@ def test_segment_sums_are_exact_and_order_free():
             assert sm[key][c] == sum(q)
             exact = float(np.mean(frame[ch, ys, xs].astype(np.float64)))
             assert abs(sm[key][c] / (len(xs) * 2.0 ** 20) - exact) <= 2.0 ** -21 + 1e-15
+
+
+def test_tiny_roi_one_superpixel_per_pixel():
+    """More superpixels asked for than the ROI has pixels: the seed step is one
+    pixel, every ROI pixel is its own segment, centred on the pixel."""
+    from oracle import superpixel as sp
+    frame, _ = conferencing_frame(40, 30, seed=9)
+    mask = np.zeros((30, 40), bool)
+    mask[10:13, 20:24] = True                      # 12 pixels
+    params, info = sp.roi_init(frame, mask, 100, 0.5, np.zeros((100, 2)))
+    assert info["S"] == 1.0 and info["M"] == 12
+    ys, xs = np.nonzero(mask)
+    np.testing.assert_array_equal(params[0, :12], xs + 0.5)
+    np.testing.assert_array_equal(params[1, :12], ys + 0.5)
+    # a single pixel: Sigma = 4 (0 + I/12), L = diag(1/sqrt(3)), w = 1 / (2 pi / 3)
+    np.testing.assert_allclose(params[2, :12], 1 / math.sqrt(3), rtol=1e-15)
+    np.testing.assert_allclose(params[8, :12], 3 / (2 * math.pi), rtol=1e-15)
