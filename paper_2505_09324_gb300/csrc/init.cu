@@ -22,7 +22,6 @@
 #include <math.h>
 #include <stdio.h>
 
-#include <vector>
 
 #include "gs2d_internal.cuh"
 
@@ -36,17 +35,25 @@ constexpr double kColourScale = 1048576.0;  // 2^20
 constexpr double kColourLimit = 32.0;
 constexpr int kSums = 9;  // n, u, v, uu, uv, vv, r, g, b
 
-struct SpArgs {
-  int W, H, M, gx, gy;
-  double S;
+// Seed grid, derived on the device from the mask's area.
+struct SpGeom {
+  int M, gx, gy, ncell;
+  double S, area;
   float S32, lam32;
+};
+
+struct SpArgs {
+  int W, H, n, k_target;
   const float* frame;
   const uint8_t* mask;
-  const int* cell_of;          // [gy][gx] seed index or -1
-  const double* seed_xy;       // [2][M]
-  float* cen;                  // [5][M]: r, g, b, x, y
+  int* cell_of;                // [gy][gx] seed index or -1
+  double* seed_xy;             // [2][n] (the first M used)
+  float* cen;                  // [5][n]: r, g, b, x, y
   int* label;                  // [H][W]
-  unsigned long long* acc;     // [kSums][M] exact segment sums (two's complement)
+  unsigned long long* acc;     // [kSums][n] exact segment sums (two's complement)
+  SpGeom* geo;
+  unsigned long long* area;    // mask pixel count
+  int* blk;                    // per-block seed counts (the grid compaction)
 };
 
 // Assignment + segment sums: each ROI pixel joins the nearest candidate
@@ -54,6 +61,7 @@ struct SpArgs {
 // (one 64-bit atomic per sum and group of lanes with the same centre).
 __global__ void __launch_bounds__(256) k_sp_assign(SpArgs a) {
   pdl_begin();
+  const SpGeom g = *a.geo;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= a.W * a.H) return;
   const int x = idx % a.W, y = idx / a.W;
@@ -64,15 +72,15 @@ __global__ void __launch_bounds__(256) k_sp_assign(SpArgs a) {
   const size_t HW = (size_t)a.W * a.H;
   const float pr = a.frame[idx], pg = a.frame[HW + idx], pb = a.frame[2 * HW + idx];
   const float px = (float)x + 0.5f, py = (float)y + 0.5f;
-  const int pcx = (int)floor((double)px / a.S), pcy = (int)floor((double)py / a.S);
+  const int pcx = (int)floor((double)px / g.S), pcy = (int)floor((double)py / g.S);
   // candidates of the 5 x 5 cells, visited in ascending centre index
   int cand[25];
   int nc = 0;
   for (int dj = -2; dj <= 2; dj++)
     for (int di = -2; di <= 2; di++) {
       const int cx = pcx + di, cy = pcy + dj;
-      if (cx < 0 || cx >= a.gx || cy < 0 || cy >= a.gy) continue;
-      const int c = a.cell_of[cy * a.gx + cx];
+      if (cx < 0 || cx >= g.gx || cy < 0 || cy >= g.gy) continue;
+      const int c = a.cell_of[cy * g.gx + cx];
       if (c < 0) continue;
       int k = nc++;
       while (k > 0 && cand[k - 1] > c) {  // insertion sort (25 at most)
@@ -81,19 +89,19 @@ __global__ void __launch_bounds__(256) k_sp_assign(SpArgs a) {
       }
       cand[k] = c;
     }
-  const int M = a.M;
+  const int M = a.n;  // array stride
   float best = INFINITY;
   int lab = -1;
   for (int k = 0; k < nc; k++) {
     const int c = cand[k];
     const float dx = __fsub_rn(px, a.cen[3 * M + c]);
     const float dy = __fsub_rn(py, a.cen[4 * M + c]);
-    if (!(fabsf(dx) <= a.S32 && fabsf(dy) <= a.S32)) continue;
+    if (!(fabsf(dx) <= g.S32 && fabsf(dy) <= g.S32)) continue;
     const float dr = __fsub_rn(pr, a.cen[c]), dg = __fsub_rn(pg, a.cen[M + c]),
                 db = __fsub_rn(pb, a.cen[2 * M + c]);
     const float dc = __fadd_rn(__fadd_rn(__fmul_rn(dr, dr), __fmul_rn(dg, dg)), __fmul_rn(db, db));
     const float d =
-        __fadd_rn(dc, __fmul_rn(a.lam32, __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy))));
+        __fadd_rn(dc, __fmul_rn(g.lam32, __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy))));
     if (d < best) {
       best = d;
       lab = c;
@@ -105,7 +113,7 @@ __global__ void __launch_bounds__(256) k_sp_assign(SpArgs a) {
   int val[kSums] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   if (lab >= 0) {
     const int u = 2 * x + 1 - 2 * (int)floor(a.seed_xy[lab]);
-    const int v = 2 * y + 1 - 2 * (int)floor(a.seed_xy[M + lab]);
+    const int v = 2 * y + 1 - 2 * (int)floor(a.seed_xy[a.n + lab]);
     val[0] = 1;
     val[1] = u;
     val[2] = v;
@@ -129,7 +137,7 @@ __global__ void __launch_bounds__(256) k_sp_assign(SpArgs a) {
 }
 
 __device__ __forceinline__ long long acc_get(const SpArgs& a, int k, int c) {
-  return (long long)a.acc[(size_t)k * a.M + c];
+  return (long long)a.acc[(size_t)k * a.n + c];
 }
 
 // Update: each centre moves to its segment's mean (clamped to within S of the
@@ -137,15 +145,16 @@ __device__ __forceinline__ long long acc_get(const SpArgs& a, int k, int c) {
 __global__ void __launch_bounds__(128) k_sp_update(SpArgs a) {
   pdl_begin();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= a.M) return;
-  const int M = a.M;
+  const SpGeom g = *a.geo;
+  if (c >= g.M) return;
+  const int M = a.n;  // array stride
   const long long n = acc_get(a, 0, c);
   if (n > 0) {
-    const double qx = a.seed_xy[c], qy = a.seed_xy[M + c];
+    const double qx = a.seed_xy[c], qy = a.seed_xy[a.n + c];
     const double mx = __dadd_rn(__ddiv_rn((double)acc_get(a, 1, c), (double)(2 * n)), floor(qx));
     const double my = __dadd_rn(__ddiv_rn((double)acc_get(a, 2, c), (double)(2 * n)), floor(qy));
-    a.cen[3 * M + c] = (float)fmin(fmax(mx, __dsub_rn(qx, a.S)), __dadd_rn(qx, a.S));
-    a.cen[4 * M + c] = (float)fmin(fmax(my, __dsub_rn(qy, a.S)), __dadd_rn(qy, a.S));
+    a.cen[3 * M + c] = (float)fmin(fmax(mx, __dsub_rn(qx, g.S)), __dadd_rn(qx, g.S));
+    a.cen[4 * M + c] = (float)fmin(fmax(my, __dsub_rn(qy, g.S)), __dadd_rn(qy, g.S));
     const double den = __dmul_rn((double)n, kColourScale);
 #pragma unroll
     for (int ch = 0; ch < 3; ch++)
@@ -158,9 +167,9 @@ __global__ void __launch_bounds__(128) k_sp_update(SpArgs a) {
 __global__ void __launch_bounds__(128) k_sp_init_centres(SpArgs a) {
   pdl_begin();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= a.M) return;
-  const int M = a.M;
-  const double sx = a.seed_xy[c], sy = a.seed_xy[M + c];
+  if (c >= a.geo->M) return;
+  const int M = a.n;  // array stride
+  const double sx = a.seed_xy[c], sy = a.seed_xy[a.n + c];
   const int xi = min(max((int)floor(sx), 0), a.W - 1), yi = min(max((int)floor(sy), 0), a.H - 1);
   const size_t HW = (size_t)a.W * a.H, idx = (size_t)yi * a.W + xi;
   a.cen[c] = a.frame[idx];
@@ -177,16 +186,17 @@ __global__ void __launch_bounds__(128) k_sp_gaussians(SpArgs a, int n_total,
                                                       float* __restrict__ params) {
   pdl_begin();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= a.M) return;
+  const SpGeom g = *a.geo;
+  if (c >= g.M) return;
   const size_t HW = (size_t)a.W * a.H;
   const long long cnt = acc_get(a, 0, c);
-  const double qx = a.seed_xy[c], qy = a.seed_xy[a.M + c];
+  const double qx = a.seed_xy[c], qy = a.seed_xy[a.n + c];
   const int n = n_total;
   float out[9];
   if (cnt == 0) {
     const int xi = min(max((int)floor(qx), 0), a.W - 1), yi = min(max((int)floor(qy), 0), a.H - 1);
     const size_t idx = (size_t)yi * a.W + xi;
-    const double s = __dmul_rn(2.0, __ddiv_rn(a.S, sqrt(12.0)));
+    const double s = __dmul_rn(2.0, __ddiv_rn(g.S, sqrt(12.0)));
     out[0] = (float)qx;
     out[1] = (float)qy;
     out[2] = (float)s;
@@ -226,25 +236,153 @@ __global__ void __launch_bounds__(128) k_sp_gaussians(SpArgs a, int n_total,
   for (int r = 0; r < 9; r++) params[(size_t)r * n + c] = out[r];
 }
 
+// Mask area (pixel count).
+__global__ void __launch_bounds__(256) k_sp_area(SpArgs a) {
+  pdl_begin();
+  const size_t hw = (size_t)a.W * a.H;
+  unsigned c = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < hw;
+       i += (size_t)gridDim.x * blockDim.x)
+    c += a.mask[i] != 0;
+  for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(a.area, (unsigned long long)c);
+}
+
+// The seed grid from the area: step S = max(1, sqrt(A / K)), cells of the
+// gx x gy grid in raster order; a cell holds a seed when its centre's pixel is
+// in the mask.  Every thread derives the same geometry.
+__device__ __forceinline__ SpGeom seed_geometry(const SpArgs& a) {
+  SpGeom g;
+  g.area = (double)*a.area;
+  g.M = 0;
+  g.S = 1.0;
+  g.gx = 1;
+  g.gy = 1;
+  if (g.area > 0.0 && a.k_target > 0) {
+    g.S = fmax(1.0, __dsqrt_rn(__ddiv_rn(g.area, (double)a.k_target)));
+    g.gx = (int)ceil(__ddiv_rn((double)a.W, g.S));
+    g.gy = (int)ceil(__ddiv_rn((double)a.H, g.S));
+  }
+  g.ncell = g.gx * g.gy;
+  g.S32 = (float)g.S;
+  const double q = __ddiv_rn(kCompactness, g.S);
+  g.lam32 = (float)__dmul_rn(q, q);
+  return g;
+}
+
+__device__ __forceinline__ bool seed_cell(const SpArgs& a, const SpGeom& g, int cell, double* x,
+                                          double* y) {
+  if (g.area <= 0.0 || a.k_target <= 0 || cell >= g.ncell) return false;
+  const int j = cell / g.gx, i = cell - j * g.gx;
+  *x = __dmul_rn((double)i + 0.5, g.S);
+  *y = __dmul_rn((double)j + 0.5, g.S);
+  const int xi = (int)floor(*x), yi = (int)floor(*y);
+  return xi < a.W && yi < a.H && a.mask[(size_t)yi * a.W + xi];
+}
+
+constexpr int kSeedBlocks = 152 * 4;
+
+// Cells [b C, (b + 1) C) of block b, C = ceil(cells / blocks): the seed count.
+__global__ void __launch_bounds__(256) k_sp_seed_count(SpArgs a) {
+  pdl_begin();
+  const SpGeom g = seed_geometry(a);
+  const int chunk = (g.ncell + gridDim.x - 1) / gridDim.x;
+  const int c0 = blockIdx.x * chunk, c1 = min(g.ncell, c0 + chunk);
+  int cnt = 0;
+  for (int cell = c0 + threadIdx.x; cell < c1; cell += blockDim.x) {
+    double x, y;
+    cnt += seed_cell(a, g, cell, &x, &y);
+  }
+  for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  __shared__ int s_w[8];
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s_w[w];
+    a.blk[blockIdx.x] = t;
+  }
+}
+
+// Seeds numbered in raster order of the grid (at most n): each block adds the
+// counts of the blocks before it, then numbers its cells by ballots.
+__global__ void __launch_bounds__(256) k_sp_seed_write(SpArgs a) {
+  pdl_begin();
+  const SpGeom g = seed_geometry(a);
+  __shared__ int s_base, s_w[9];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    int b = 0, tot = 0;
+    for (int k = 0; k < (int)gridDim.x; k++) {
+      if (k < (int)blockIdx.x) b += a.blk[k];
+      tot += a.blk[k];
+    }
+    s_base = b;
+    if (blockIdx.x == 0) {
+      SpGeom out = g;
+      out.M = min(tot, a.n);
+      *a.geo = out;
+    }
+  }
+  __syncthreads();
+  const int chunk = (g.ncell + gridDim.x - 1) / gridDim.x;
+  const int c0 = blockIdx.x * chunk, c1 = min(g.ncell, c0 + chunk);
+  int run = s_base;
+  for (int base = c0; base < c1; base += blockDim.x) {
+    const int cell = base + threadIdx.x;
+    double x = 0.0, y = 0.0;
+    const bool f = cell < c1 && seed_cell(a, g, cell, &x, &y);
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) s_w[wid] = __popc(bal);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int t = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+        const int c = s_w[w];
+        s_w[w] = t;
+        t += c;
+      }
+      s_w[8] = t;
+    }
+    __syncthreads();
+    const int idx = run + s_w[wid] + __popc(bal & ((1u << lane) - 1u));
+    if (cell < c1) {
+      const bool take = f && idx < a.n;
+      a.cell_of[cell] = take ? idx : -1;
+      if (take) {
+        a.seed_xy[idx] = x;
+        a.seed_xy[a.n + idx] = y;
+      }
+    }
+    run += s_w[8];
+    __syncthreads();
+  }
+}
+
 // Isotropic background Gaussians at bg_xy[0 .. nbg).
-__global__ void __launch_bounds__(256) k_sp_background(int W, int H, int M, int nbg, int n,
-                                                       double s, const float* __restrict__ frame,
-                                                       const float* __restrict__ bg_xy,
+__global__ void __launch_bounds__(256) k_sp_background(SpArgs a, const float* __restrict__ bg_xy,
                                                        float* __restrict__ params) {
+  pdl_begin();
+  const SpGeom g = *a.geo;
+  const int M = g.M, n = a.n, nbg = n - M;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nbg) return;
+  const double hw = (double)a.W * (double)a.H;
+  const double abg = __ddiv_rn(__dsub_rn(hw, g.area), (double)nbg);
+  const double s = __dsqrt_rn(__ddiv_rn(__dmul_rn(kKappa, abg > 1.0 ? abg : 1.0),
+                                        __dmul_rn(2.0, 3.141592653589793)));
   const double x = bg_xy[k], y = bg_xy[n + k];
-  const int xi = min(max((int)floor(x), 0), W - 1), yi = min(max((int)floor(y), 0), H - 1);
-  const size_t HW = (size_t)W * H, idx = (size_t)yi * W + xi;
+  const int xi = min(max((int)floor(x), 0), a.W - 1), yi = min(max((int)floor(y), 0), a.H - 1);
+  const size_t HW = (size_t)a.W * a.H, idx = (size_t)yi * a.W + xi;
   const int c = M + k;
   params[c] = (float)x;
   params[n + c] = (float)y;
   params[2 * n + c] = (float)s;
   params[3 * n + c] = 0.0f;
   params[4 * n + c] = (float)s;
-  params[5 * n + c] = frame[idx];
-  params[6 * n + c] = frame[HW + idx];
-  params[7 * n + c] = frame[2 * HW + idx];
+  params[5 * n + c] = a.frame[idx];
+  params[6 * n + c] = a.frame[HW + idx];
+  params[7 * n + c] = a.frame[2 * HW + idx];
   params[8 * n + c] = (float)(1.0 / kKappa);
 }
 
@@ -253,12 +391,14 @@ uint64_t a256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
 }  // namespace
 
 // Scratch layout for a W x H frame with n Gaussians: labels int[H W], centres
-// float[5][n], seeds double[2][n], cell map int[(W+1) (H+1)] (the grid has at
-// most one cell per pixel), segment sums int64[9][n].
+// float[5][n], seeds double[2][n], cell map int[(W+1) (H+1)] (the grid step
+// is at least one pixel), segment sums int64[9][n], the area, the geometry and
+// the per-block seed counts.
 uint64_t roi_init_scratch_bytes(int W, int H, int n) {
   const uint64_t hw = (uint64_t)W * H;
   return a256(hw * 4) + a256(5ull * n * 4) + a256(2ull * n * 8) +
-         a256((uint64_t)(W + 1) * (H + 1) * 4) + a256((uint64_t)kSums * n * 8) + 256;
+         a256((uint64_t)(W + 1) * (H + 1) * 4) + a256((uint64_t)kSums * n * 8) + a256(8) +
+         a256(sizeof(SpGeom)) + a256(kSeedBlocks * 4) + 256;
 }
 
 gs2d_status roi_init(const float* frame, const uint8_t* mask, int W, int H, int n, float roi_frac,
@@ -269,96 +409,52 @@ gs2d_status roi_init(const float* frame, const uint8_t* mask, int W, int H, int 
     return GS2D_ERR_INVALID_ARG;
   }
   const uint64_t hw = (uint64_t)W * H;
-  char* base = static_cast<char*>(scratch);
-  int* label = reinterpret_cast<int*>(base);
-  float* cen = reinterpret_cast<float*>(base + a256(hw * 4));
-  double* seed_xy = reinterpret_cast<double*>(base + a256(hw * 4) + a256(5ull * n * 4));
-  int* cell_of =
-      reinterpret_cast<int*>(base + a256(hw * 4) + a256(5ull * n * 4) + a256(2ull * n * 8));
-  unsigned long long* acc = reinterpret_cast<unsigned long long*>(
-      base + a256(hw * 4) + a256(5ull * n * 4) + a256(2ull * n * 8) +
-      a256((uint64_t)(W + 1) * (H + 1) * 4));
-  // seeds on the host (the mask comes back once)
-  std::vector<uint8_t> hmask(hw);
-  cudaError_t e = cudaMemcpyAsync(hmask.data(), mask, hw, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) {
-    snprintf(err, err_len, "gs2d_roi_init: %s", cudaGetErrorString(e));
-    return GS2D_ERR_CUDA;
-  }
-  uint64_t area = 0;
-  for (uint64_t i = 0; i < hw; i++) area += hmask[i] != 0;
-  const int k_target = (int)llround((double)roi_frac * n);
-  int M = 0, gx = 1, gy = 1;
-  double S = 1.0;
-  std::vector<double> sx, sy;
-  std::vector<int> cells;
-  if (area > 0 && k_target > 0) {
-    S = sqrt((double)area / (double)k_target);
-    gx = (int)ceil((double)W / S);
-    gy = (int)ceil((double)H / S);
-    cells.assign((size_t)gx * gy, -1);
-    for (int j = 0; j < gy; j++)
-      for (int i = 0; i < gx; i++) {
-        const double x = (i + 0.5) * S, y = (j + 0.5) * S;
-        const int xi = (int)floor(x), yi = (int)floor(y);
-        if (xi < W && yi < H && hmask[(size_t)yi * W + xi] && M < n) {
-          cells[(size_t)j * gx + i] = M++;
-          sx.push_back(x);
-          sy.push_back(y);
-        }
-      }
-  }
-  if (n_roi) *n_roi = M;
-  std::vector<double> sxy(sx);
-  sxy.insert(sxy.end(), sy.begin(), sy.end());
+  char* p = static_cast<char*>(scratch);
+  auto take = [&p](uint64_t bytes) {
+    char* q = p;
+    p += a256(bytes);
+    return q;
+  };
   SpArgs a;
   a.W = W;
   a.H = H;
-  a.M = M;
-  a.gx = gx;
-  a.gy = gy;
-  a.S = S;
-  a.S32 = (float)S;
-  a.lam32 = (float)((kCompactness / S) * (kCompactness / S));
+  a.n = n;
+  a.k_target = (int)llround((double)roi_frac * n);
   a.frame = frame;
   a.mask = mask;
-  a.cell_of = cell_of;
-  a.seed_xy = seed_xy;
-  a.cen = cen;
-  a.label = label;
-  a.acc = acc;
-  if (M > 0) {
-    e = cudaMemcpyAsync(seed_xy, sxy.data(), sxy.size() * sizeof(double),
-                        cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(cell_of, cells.data(), cells.size() * sizeof(int),
-                          cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) {
-      const int pb = (int)((hw + 255) / 256), cb = (M + 127) / 128;
-      e = launch_pdl(k_sp_init_centres, cb, 128, 0, s, a);
-      // the last assignment's sums make the Gaussians
-      for (int it = 0; it < kIterations && e == cudaSuccess; it++) {
-        e = launch_pdl(k_sp_assign, pb, 256, 0, s, a);
-        if (e == cudaSuccess && it + 1 < kIterations)
-          e = launch_pdl(k_sp_update, cb, 128, 0, s, a);
-      }
-      if (e == cudaSuccess) e = launch_pdl(k_sp_gaussians, cb, 128, 0, s, a, n, params);
+  a.label = reinterpret_cast<int*>(take(hw * 4));
+  a.cen = reinterpret_cast<float*>(take(5ull * n * 4));
+  a.seed_xy = reinterpret_cast<double*>(take(2ull * n * 8));
+  a.cell_of = reinterpret_cast<int*>(take((uint64_t)(W + 1) * (H + 1) * 4));
+  a.acc = reinterpret_cast<unsigned long long*>(take((uint64_t)kSums * n * 8));
+  a.area = reinterpret_cast<unsigned long long*>(take(8));
+  a.geo = reinterpret_cast<SpGeom*>(take(sizeof(SpGeom)));
+  a.blk = reinterpret_cast<int*>(take(kSeedBlocks * 4));
+  // everything on the device; the region count comes back at the end
+  const int pb = (int)((hw + 255) / 256), cb = (n + 127) / 128;
+  cudaError_t e = cudaMemsetAsync(a.area, 0, 8, s);
+  if (e == cudaSuccess) e = launch_pdl(k_sp_area, 152 * 8, 256, 0, s, a);
+  if (e == cudaSuccess) e = launch_pdl(k_sp_seed_count, kSeedBlocks, 256, 0, s, a);
+  if (e == cudaSuccess) e = launch_pdl(k_sp_seed_write, kSeedBlocks, 256, 0, s, a);
+  if (e == cudaSuccess && n > 0) {
+    e = launch_pdl(k_sp_init_centres, cb, 128, 0, s, a);
+    // the last assignment's sums make the Gaussians
+    for (int it = 0; it < kIterations && e == cudaSuccess; it++) {
+      e = launch_pdl(k_sp_assign, pb, 256, 0, s, a);
+      if (e == cudaSuccess && it + 1 < kIterations) e = launch_pdl(k_sp_update, cb, 128, 0, s, a);
     }
+    if (e == cudaSuccess) e = launch_pdl(k_sp_gaussians, cb, 128, 0, s, a, n, params);
+    if (e == cudaSuccess)
+      e = launch_pdl(k_sp_background, (n + 255) / 256, 256, 0, s, a, bg_xy, params);
   }
-  const int nbg = n - M;
-  if (e == cudaSuccess && nbg > 0) {
-    const double abg = (double)(hw - area) / (double)nbg;
-    const double sd = sqrt(kKappa * (abg > 1.0 ? abg : 1.0) / (2.0 * 3.141592653589793));
-    k_sp_background<<<(nbg + 255) / 256, 256, 0, s>>>(W, H, M, nbg, n, sd, frame, bg_xy, params);
-    e = cudaGetLastError();
-  }
-  // the host vectors above are read by the copies: wait for them
+  SpGeom g;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&g, a.geo, sizeof(g), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     snprintf(err, err_len, "gs2d_roi_init: %s", cudaGetErrorString(e));
     return GS2D_ERR_CUDA;
   }
+  if (n_roi) *n_roi = g.M;
   return GS2D_OK;
 }
 

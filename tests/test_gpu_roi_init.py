@@ -68,3 +68,13 @@ def test_large_segments_bit_exact(gs):
     got, ref, n_roi, M = run_both(gs, frame, mask, 3, 0.7, seed=7)
     assert n_roi == M
     np.testing.assert_array_equal(got, ref)
+
+
+def test_tiny_roi_bit_exact(gs):
+    """More region Gaussians wanted than the mask has pixels: one per pixel."""
+    frame, _ = conferencing_frame(40, 30, seed=9)
+    mask = np.zeros((30, 40), bool)
+    mask[10:13, 20:24] = True
+    got, ref, n_roi, M = run_both(gs, frame, mask, 100, 0.5, seed=3)
+    assert n_roi == M == 12
+    np.testing.assert_array_equal(got, ref)
