@@ -365,20 +365,22 @@ uint64_t gs2d_roi_init_scratch_bytes(int32_t width, int32_t height, int32_t n);
  * into superpixels by K-means; each segment's centre, covariance and mean
  * colour give one Gaussian's mean, Cholesky factor and colour).  Readings:
  * about roi_frac * n segments from seeds on a square grid of step
- * S = sqrt(A / (roi_frac n)) over the mask (A = mask pixels), 10 K-means
+ * S = max(1, sqrt(A / (roi_frac n))) over the mask (A = mask pixels), 10 K-means
  * iterations in (r, g, b, x, y) with distance
  * |dcol|^2 + (0.2 / S)^2 |dxy|^2 among centres within S of the pixel (centres
  * held within S of their seeds), Sigma = 4 (pixel covariance + I/12) (the
  * factor 4 keeps the additive blend of the segments flat), weight =
- * area / (2 pi sqrt(det Sigma)).  The other n - n_roi Gaussians are isotropic
+ * area / (2 pi sqrt(det Sigma)); distances decided in FP32, segment sums
+ * exact in integers (colours quantised to 2^-20, clamped to [-32, 32]), so
+ * the result is reproducible bit for bit.  The other n - n_roi Gaussians are isotropic
  * (variance = 4 x background area per Gaussian / (2 pi), weight 1/4, colour
  * of the frame) at bg_xy (random positions are inputs).
  * frame: device [3][H][W] float32.  mask: device [H][W] uint8 (non-zero = in
  * the region).  bg_xy: device [2][n] float32 (row x, row y); the first
  * n - n_roi columns are used.  params: device, 9n floats out (region
  * Gaussians first, in seed raster order).  n_roi: host int32 out, may be NULL.
- * scratch: device, gs2d_roi_init_scratch_bytes bytes.  Synchronises the
- * stream (seed placement reads the mask on the host). */
+ * scratch: device, gs2d_roi_init_scratch_bytes bytes.  All work runs on the
+ * device; the call synchronises the stream once at the end to return n_roi. */
 gs2d_status gs2d_roi_init(const float* frame, const uint8_t* mask, int32_t width, int32_t height,
                           int32_t n, float roi_frac, const float* bg_xy, float* params,
                           int32_t* n_roi, void* scratch, uint64_t scratch_bytes, void* stream);
