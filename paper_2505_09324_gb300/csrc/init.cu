@@ -73,38 +73,33 @@ __global__ void __launch_bounds__(256) k_sp_assign(SpArgs a) {
   const float pr = a.frame[idx], pg = a.frame[HW + idx], pb = a.frame[2 * HW + idx];
   const float px = (float)x + 0.5f, py = (float)y + 0.5f;
   const int pcx = (int)floor((double)px / g.S), pcy = (int)floor((double)py / g.S);
-  // candidates of the 5 x 5 cells, visited in ascending centre index
-  int cand[25];
-  int nc = 0;
-  for (int dj = -2; dj <= 2; dj++)
-    for (int di = -2; di <= 2; di++) {
-      const int cx = pcx + di, cy = pcy + dj;
-      if (cx < 0 || cx >= g.gx || cy < 0 || cy >= g.gy) continue;
-      const int c = a.cell_of[cy * g.gx + cx];
-      if (c < 0) continue;
-      int k = nc++;
-      while (k > 0 && cand[k - 1] > c) {  // insertion sort (25 at most)
-        cand[k] = cand[k - 1];
-        k--;
-      }
-      cand[k] = c;
-    }
+  // candidates: the seeds of the 5 x 5 cells around the pixel's, visited in
+  // raster order of the cells, which is ascending seed index (seeds are
+  // numbered in raster order of the grid)
   const int M = a.n;  // array stride
   float best = INFINITY;
   int lab = -1;
-  for (int k = 0; k < nc; k++) {
-    const int c = cand[k];
-    const float dx = __fsub_rn(px, a.cen[3 * M + c]);
-    const float dy = __fsub_rn(py, a.cen[4 * M + c]);
-    if (!(fabsf(dx) <= g.S32 && fabsf(dy) <= g.S32)) continue;
-    const float dr = __fsub_rn(pr, a.cen[c]), dg = __fsub_rn(pg, a.cen[M + c]),
-                db = __fsub_rn(pb, a.cen[2 * M + c]);
-    const float dc = __fadd_rn(__fadd_rn(__fmul_rn(dr, dr), __fmul_rn(dg, dg)), __fmul_rn(db, db));
-    const float d =
-        __fadd_rn(dc, __fmul_rn(g.lam32, __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy))));
-    if (d < best) {
-      best = d;
-      lab = c;
+  for (int dj = -2; dj <= 2; dj++) {
+    const int cy = pcy + dj;
+    if (cy < 0 || cy >= g.gy) continue;
+    for (int di = -2; di <= 2; di++) {
+      const int cx = pcx + di;
+      if (cx < 0 || cx >= g.gx) continue;
+      const int c = a.cell_of[cy * g.gx + cx];
+      if (c < 0) continue;
+      const float dx = __fsub_rn(px, a.cen[3 * M + c]);
+      const float dy = __fsub_rn(py, a.cen[4 * M + c]);
+      if (!(fabsf(dx) <= g.S32 && fabsf(dy) <= g.S32)) continue;
+      const float dr = __fsub_rn(pr, a.cen[c]), dg = __fsub_rn(pg, a.cen[M + c]),
+                  db = __fsub_rn(pb, a.cen[2 * M + c]);
+      const float dc =
+          __fadd_rn(__fadd_rn(__fmul_rn(dr, dr), __fmul_rn(dg, dg)), __fmul_rn(db, db));
+      const float d =
+          __fadd_rn(dc, __fmul_rn(g.lam32, __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy))));
+      if (d < best) {
+        best = d;
+        lab = c;
+      }
     }
   }
   a.label[idx] = lab;
