@@ -357,6 +357,22 @@ gs2d_status gs2d_sequence_bits(const int32_t* counts, const double* payload_bits
 gs2d_status gs2d_frame_from_rgb8(const uint8_t* rgb, int32_t width, int32_t height,
                                  int64_t row_bytes, float* frame, void* stream);
 
+/* One fit iteration end to end, as an encoder on the host drives it: the
+ * 8-bit RGB frame (pinned host, H x W x 3, packed rows) is copied to rgb_dev
+ * (device, 3 W H bytes) and converted into frame_dev (device [3][H][W]
+ * float32, gs2d_frame_from_rgb8); params_host (pinned host, 9n floats, or
+ * NULL to keep the device params) is copied to params; then gs2d_fit_step;
+ * then params is copied to params_out_host (pinned host, or NULL).  The
+ * frame's upload and conversion run on an auxiliary stream of the calling
+ * thread (created once per device) and overlap the projection and binning;
+ * the render waits for them, and they wait for the work queued on `stream`
+ * before the call, so the call is ordered on `stream` like the others.
+ * One-clip plans only. */
+gs2d_status gs2d_fit_step_rgb8(const gs2d_plan* plan, void* ws, const uint8_t* rgb_host,
+                               uint8_t* rgb_dev, float* frame_dev, const float* params_host,
+                               float* params, float* adam_m, float* adam_v, float* params_out_host,
+                               void* stream);
+
 /* Device scratch (bytes, 256-byte aligned start) that gs2d_roi_init needs for
  * a W x H frame and n Gaussians. */
 uint64_t gs2d_roi_init_scratch_bytes(int32_t width, int32_t height, int32_t n);

@@ -29,7 +29,7 @@ EXPORTS = (
     "gs2d_adam_step", "gs2d_fit_step", "gs2d_fit_reset", "gs2d_encode_frame", "gs2d_clip_losses",
     "gs2d_select_changed", "gs2d_pframe_step", "gs2d_encode_pframe", "gs2d_quantize",
     "gs2d_fit_step_qat", "gs2d_code_entropy_scratch_bytes", "gs2d_code_entropy",
-    "gs2d_sequence_bits", "gs2d_frame_from_rgb8", "gs2d_conv_bf16",
+    "gs2d_sequence_bits", "gs2d_frame_from_rgb8", "gs2d_conv_bf16", "gs2d_fit_step_rgb8",
     "gs2d_encode_batch",
     "gs2d_autotune_ws_bytes", "gs2d_autotune",
     "gs2d_gemm_bf16", "gs2d_gemm_partial_bytes", "gs2d_cnn_input", "gs2d_im2col", "gs2d_col2im",
@@ -150,6 +150,7 @@ def load(build_if_missing: bool = False):
             "gs2d_fit_step_qat": (i32, [pp, P, P, P, P, P, ctypes.POINTER(Quant), P]),
             "gs2d_code_entropy_scratch_bytes": (ctypes.c_size_t, []),
             "gs2d_frame_from_rgb8": (i32, [P, i32, i32, i64, P, P]),
+            "gs2d_fit_step_rgb8": (i32, [pp, P, P, P, P, P, P, P, P, P, P]),
             "gs2d_conv_bf16": (i32, [P, i32, i32, i32, i32, i32, i32, i32, P, i32, i32, i32, P,
                                      P, i32, P, P]),
             "gs2d_code_entropy": (i32, [P, i32, ctypes.POINTER(i32), P, P, ctypes.c_size_t, P,
@@ -477,3 +478,11 @@ def sequence_bits(counts, payload_bits, gop: int) -> dict:
 def frame_from_rgb8(rgb: int, width: int, height: int, row_bytes: int, frame: int, stream: int):
     check(load().gs2d_frame_from_rgb8(_p(rgb), width, height, row_bytes, _p(frame), _p(stream)),
           "gs2d_frame_from_rgb8")
+
+
+def fit_step_rgb8(plan: Plan, ws: int, rgb_host: int, rgb_dev: int, frame_dev: int,
+                  params_host: int, params: int, m: int, v: int, params_out_host: int,
+                  stream: int):
+    check(load().gs2d_fit_step_rgb8(ctypes.byref(plan), _p(ws), _p(rgb_host), _p(rgb_dev),
+                                    _p(frame_dev), _p(params_host), _p(params), _p(m), _p(v),
+                                    _p(params_out_host), _p(stream)), "gs2d_fit_step_rgb8")

@@ -352,6 +352,72 @@ gs2d_status gs2d_fit_step(const gs2d_plan* plan, void* ws, const float* target, 
                     "gs2d_fit_step");
 }
 
+
+// An auxiliary stream per host thread and device for the frame's upload, so
+// that it overlaps the projection and binning (which need only the params).
+struct AuxStream {
+  int device = -1;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t start = nullptr, frame = nullptr;
+};
+
+static cudaError_t aux_stream(AuxStream** out) {
+  static thread_local AuxStream aux;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (aux.device != dev) {
+    if (aux.stream) {  // another device: start over (the old handles belong to it)
+      aux.stream = nullptr;
+      aux.start = aux.frame = nullptr;
+    }
+    e = cudaStreamCreateWithFlags(&aux.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&aux.start, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&aux.frame, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    aux.device = dev;
+  }
+  *out = &aux;
+  return cudaSuccess;
+}
+
+gs2d_status gs2d_fit_step_rgb8(const gs2d_plan* plan, void* ws, const uint8_t* rgb_host,
+                               uint8_t* rgb_dev, float* frame_dev, const float* params_host,
+                               float* params, float* adam_m, float* adam_v, float* params_out_host,
+                               void* stream) {
+  gs2d_status st = check_plan(plan, ws);
+  if (st) return st;
+  const gs2d_plan& p = *plan;
+  if (p.num_clips != 1) return fail(GS2D_ERR_INVALID_ARG, "gs2d_fit_step_rgb8: one-clip plans only");
+  if (!rgb_host || !rgb_dev || !frame_dev || (p.n > 0 && (!params || !adam_m || !adam_v)))
+    return fail(GS2D_ERR_INVALID_ARG, "gs2d_fit_step_rgb8: NULL pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t rgb_bytes = (size_t)3 * p.width * p.height;
+  const size_t pbytes = (size_t)9 * p.n * sizeof(float);
+  AuxStream* aux = nullptr;
+  cudaError_t e = aux_stream(&aux);
+  // the frame on the auxiliary stream, after everything queued on s so far
+  // (the previous iteration's render reads frame_dev)
+  if (e == cudaSuccess) e = cudaEventRecord(aux->start, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(aux->stream, aux->start, 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(rgb_dev, rgb_host, rgb_bytes, cudaMemcpyHostToDevice, aux->stream);
+  if (e != cudaSuccess) return cuda_check(e, "gs2d_fit_step_rgb8");
+  st = gs2d_frame_from_rgb8(rgb_dev, p.width, p.height, (int64_t)3 * p.width, frame_dev,
+                            aux->stream);
+  if (st) return st;
+  e = cudaEventRecord(aux->frame, aux->stream);
+  // the params, projection and binning on s meanwhile
+  if (e == cudaSuccess && params_host && pbytes)
+    e = cudaMemcpyAsync(params, params_host, pbytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = launch_prepare(p, ws, params, true, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, aux->frame, 0);
+  if (e == cudaSuccess) e = launch_fit_step(p, ws, frame_dev, params, adam_m, adam_v, s);
+  if (e == cudaSuccess && params_out_host && pbytes)
+    e = cudaMemcpyAsync(params_out_host, params, pbytes, cudaMemcpyDeviceToHost, s);
+  return cuda_check(e, "gs2d_fit_step_rgb8");
+}
+
 gs2d_status gs2d_fit_reset(const gs2d_plan* plan, void* ws, float* adam_m, float* adam_v,
                            void* stream) {
   gs2d_status st = check_plan(plan, ws);

@@ -68,3 +68,38 @@ def test_fit_on_converted_frame(gs):
     r.encode_frame(dev_frame, a, 20, check_every=20)
     r.encode_frame(host_frame, b, 20, check_every=20)
     assert torch.equal(a, b)
+
+
+def test_fit_step_rgb8_is_upload_convert_fit_download(gs):
+    """The one-call end-to-end iteration from host buffers equals its parts."""
+    from gs2d_inputs import random_gaussians
+    from paper_2505_09324_gb300 import _native as nat
+    W, H, n = 160, 96, 400
+    rng = np.random.default_rng(8)
+    rgb = torch.from_numpy(rng.integers(0, 256, (H, W, 3), dtype=np.uint8)).pin_memory()
+    p0 = torch.from_numpy(random_gaussians(n, W, H, seed=9)).pin_memory()
+    out = torch.empty_like(p0).pin_memory()
+    r = gs.GaussianRasterizer(W, H, n)
+    s = int(torch.cuda.current_stream().cuda_stream)
+    d_rgb = torch.empty((H, W, 3), dtype=torch.uint8, device="cuda")
+    d_frame = torch.empty((3, H, W), device="cuda")
+    d_p = torch.empty((9, n), device="cuda")
+    m, v = torch.empty_like(d_p), torch.empty_like(d_p)
+    nat.fit_reset(r.plan, r.ws_ptr, m.data_ptr(), v.data_ptr(), s)
+    for _ in range(2):
+        nat.fit_step_rgb8(r.plan, r.ws_ptr, rgb.data_ptr(), d_rgb.data_ptr(), d_frame.data_ptr(),
+                          p0.data_ptr(), d_p.data_ptr(), m.data_ptr(), v.data_ptr(),
+                          out.data_ptr(), s)
+    torch.cuda.synchronize()
+    # the same by parts
+    frame = gs.frame_from_rgb8(rgb.cuda())
+    q = p0.cuda()
+    m2, v2 = torch.empty_like(q), torch.empty_like(q)
+    nat.fit_reset(r.plan, r.ws_ptr, m2.data_ptr(), v2.data_ptr(), s)
+    for _ in range(2):
+        q.copy_(p0)
+        nat.fit_step(r.plan, r.ws_ptr, frame.data_ptr(), q.data_ptr(), m2.data_ptr(),
+                     v2.data_ptr(), s)
+    torch.cuda.synchronize()
+    assert torch.equal(out, q.cpu()) and torch.equal(d_p, q)
+    assert torch.equal(d_frame, frame)
