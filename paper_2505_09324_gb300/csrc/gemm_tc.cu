@@ -532,11 +532,13 @@ cudaError_t launch_conv_st(const CUtensorMap& tb, const ConvGeom& cg, const TcGe
   return cudaGetLastError();
 }
 
+// Two stages up to 16 k-tiles, three beyond: shared memory for more CTAs per
+// SM hides more latency than a deeper pipeline per CTA.
 template <int BN>
 cudaError_t launch_conv(const CUtensorMap& tb, const ConvGeom& cg, const TcGemmArgs& g,
                         dim3 grid, cudaStream_t s) {
-  return g.num_kt <= 8 ? launch_conv_st<BN, 2>(tb, cg, g, grid, s)
-                       : launch_conv_st<BN, 4>(tb, cg, g, grid, s);
+  return g.num_kt <= 16 ? launch_conv_st<BN, 2>(tb, cg, g, grid, s)
+                        : launch_conv_st<BN, 3>(tb, cg, g, grid, s);
 }
 
 // Two stages when every block runs few k-tiles (more blocks per SM hide the
