@@ -68,6 +68,7 @@ struct TileSmem {
   int4 bb[S];        // local box (x0, x1, y0, y1); x0 > x1 when empty
   int slot[S];       // partial slot of the pair
   uint32_t wmask[S]; // bit w: box touches the rows of warp w
+  int next;          // the backward's next Gaussian (warps take them in turn)
 };
 
 // The tile a block works on, in its clip's frame.
@@ -100,6 +101,7 @@ template <int T, int S>
 __device__ __forceinline__ void stage_batch(TileSmem<S>& sm, const RenderArgs& a,
                                             const TileFrame& f, int b, int cnt) {
   using G = TileGeom<T>;
+  if (threadIdx.x == 0) sm.next = 0;
   for (int k = threadIdx.x; k < cnt; k += G::NT) {
     const int g = (int)a.list[b + k];
     const float4 r0 = a.rec[g], r1 = a.rec[a.n + g], r2 = a.rec[2 * a.n + g];
@@ -191,13 +193,17 @@ __device__ __forceinline__ float group_transpose_sum(const float (&v)[8], int j)
 
 // Backward over staged Gaussians [0, cnt); g (dL/dC) of the tile in s_g.
 template <int T, int S>
-__device__ __forceinline__ void bwd_batch(const TileSmem<S>& sm, const float4* __restrict__ s_g,
+__device__ __forceinline__ void bwd_batch(TileSmem<S>& sm, const float4* __restrict__ s_g,
                                           int cnt, float ox, float oy,
                                           float* __restrict__ partial) {
   using G = TileGeom<T>;
-  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int lane = threadIdx.x & 31;
   const int h = lane / T, j = lane % T;
-  for (int base = wid * G::GPW; base < cnt; base += G::NW * G::GPW) {  // warp-uniform
+  for (;;) {  // warps take the next GPW Gaussians as they finish (balance)
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&sm.next, G::GPW);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= cnt) break;
     const int gi = base + h;
     // Gaussians whose box misses the tile: a zero record, no reduction
     const bool empty = gi >= cnt || sm.bb[gi].x > sm.bb[gi].y;
