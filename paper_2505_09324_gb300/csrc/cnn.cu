@@ -1,5 +1,6 @@
 // C ABI of the learned initialiser's building blocks (include/gs2d.h): the
 // BF16 tensor-core GEMM and the convolution helpers around it.
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <stdio.h>
 
@@ -380,59 +381,65 @@ __device__ __forceinline__ int block_flag_prefix(bool f, int* s_w, int* tot) {
   return pre;
 }
 
-constexpr int kSelHists = 16;  // warp pairs sharing one private histogram
+// Selection of the n largest |w| keys of a frame (ties: lowest slot first),
+// in slot order, by a cluster of kSelCluster CTAs per frame: CTA k holds
+// slots [k C, (k + 1) C); an MSB-first radix select, a byte per pass, sums
+// the CTAs' histograms through distributed shared memory (every CTA reads all
+// of them and takes the same decision); the compaction offsets each CTA by
+// the counts of the CTAs before it.  Writes the selected slot of every output
+// position to sel.
+constexpr int kSelCluster = 8;
 
-// One block per frame: radix select of the n-th largest |w| key (MSB first,
-// a byte per pass, histograms private to warp pairs), then a compaction in
-// slot order: every key above the threshold and the lowest-slot keys equal to
-// it.  Writes the selected slot of every output position to sel.
-__global__ void __launch_bounds__(1024)
-k_head_select(const float* __restrict__ out, int ldo, int gh, int gw, int slots, int n,
-              int* __restrict__ sel) {
+__global__ void __cluster_dims__(kSelCluster, 1, 1) __launch_bounds__(512)
+k_head_select_cluster(const float* __restrict__ out, int ldo, int gh, int gw, int slots, int n,
+                      int* __restrict__ sel) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ uint32_t s_key[];
-  __shared__ int s_hist[kSelHists][256];
+  __shared__ int s_hist[2][256];   // this CTA's histogram, double-buffered over passes
+  __shared__ int s_tot[256];       // the cluster's
   __shared__ int s_w[33];
+  __shared__ int s_cnt[2];         // this CTA's keys above T, equal to T
   __shared__ uint32_t s_prefix;
   __shared__ int s_need;
-  const int b = blockIdx.x, t = threadIdx.x, nt = blockDim.x, lane = t & 31, wid = t >> 5;
+  const int b = blockIdx.x / kSelCluster, rank = (int)cluster.block_rank();
+  const int t = threadIdx.x, nt = blockDim.x;
   const int cells = gh * gw, S = cells * slots;
+  const int C = (S + kSelCluster - 1) / kSelCluster;
+  const int i0 = min(S, rank * C), i1 = min(S, i0 + C), len = i1 - i0;
   const float* ob = out + (size_t)b * cells * ldo;
-  for (int i = t; i < S; i += nt) {
-    const int cell = i / slots, s = i % slots;
-    s_key[i] = __float_as_uint(fabsf(0.25f + ob[(size_t)cell * ldo + 9 * s + 8]));
+  for (int i = t; i < len; i += nt) {
+    const int g = i0 + i, cell = g / slots, sl = g % slots;
+    s_key[i] = __float_as_uint(fabsf(0.25f + ob[(size_t)cell * ldo + 9 * sl + 8]));
   }
   if (t == 0) {
     s_prefix = 0;
     s_need = n;
   }
   __syncthreads();
-  // after the byte of `shift`, keys above the prefix are taken, keys equal to
-  // it are still open
-  for (int shift = 24; shift >= 0; shift -= 8) {
-    for (int i = t; i < kSelHists * 256; i += nt) (&s_hist[0][0])[i] = 0;
+  int buf = 0;
+  for (int shift = 24; shift >= 0; shift -= 8, buf ^= 1) {
+    for (int i = t; i < 256; i += nt) s_hist[buf][i] = 0;
     __syncthreads();
     const uint32_t hi_mask = shift == 24 ? 0u : (0xFFFFFFFFu << (shift + 8));
     const uint32_t prefix = s_prefix;
-    int* h = s_hist[wid % kSelHists];
-    for (int i = t; i < S; i += nt) {
+    for (int i = t; i < len; i += nt) {
       const uint32_t k = s_key[i];
-      if ((k & hi_mask) == (prefix & hi_mask)) atomicAdd(&h[(k >> shift) & 255u], 1);
+      if ((k & hi_mask) == (prefix & hi_mask)) atomicAdd(&s_hist[buf][(k >> shift) & 255u], 1);
     }
-    __syncthreads();
-    if (t < 256) {
+    cluster.sync();  // every CTA's histogram of this pass is complete
+    for (int i = t; i < 256; i += nt) {
       int c = 0;
-#pragma unroll
-      for (int w = 0; w < kSelHists; w++) c += s_hist[w][t];
-      s_hist[0][t] = c;
+      for (int r = 0; r < kSelCluster; r++) c += cluster.map_shared_rank(&s_hist[buf][0], r)[i];
+      s_tot[i] = c;
     }
     __syncthreads();
-    // the bin holding the need-th largest key: lane l scans bins 255 - 8 l
-    // downwards; the lane whose range crosses `need` finds it
-    if (wid == 0) {
+    if (t < 32) {
+      const int lane = t;
       int c[8], sum = 0;
 #pragma unroll
       for (int k = 0; k < 8; k++) {
-        c[k] = s_hist[0][255 - (8 * lane + k)];
+        c[k] = s_tot[255 - (8 * lane + k)];
         sum += c[k];
       }
       int inc = sum;
@@ -453,25 +460,55 @@ k_head_select(const float* __restrict__ out, int ldo, int gh, int gw, int slots,
           }
           acc += c[k];
         }
-      } else if (lane == 31 && need > inc) {  // fewer keys than needed: bin 0
+      } else if (lane == 31 && need > inc) {
         s_need = need - (inc - c[7]);
         s_prefix = prefix;
       }
     }
     __syncthreads();
+    // the other buffer is zeroed next pass; no CTA rereads it before then
   }
   const uint32_t T = s_prefix;
-  const int need_eq = s_need;  // keys equal to T to take, lowest slot first
-  int taken_before = 0, eq_before = 0;
-  for (int base = 0; base < S; base += nt) {
+  const int need_eq = s_need;
+  // this CTA's counts above and at T, then the offsets from the CTAs before it
+  if (t == 0) s_cnt[0] = s_cnt[1] = 0;
+  __syncthreads();
+  int above = 0, at = 0;
+  for (int i = t; i < len; i += nt) {
+    above += s_key[i] > T;
+    at += s_key[i] == T;
+  }
+  for (int o = 16; o; o >>= 1) {
+    above += __shfl_xor_sync(0xffffffffu, above, o);
+    at += __shfl_xor_sync(0xffffffffu, at, o);
+  }
+  if ((t & 31) == 0) {
+    atomicAdd(&s_cnt[0], above);
+    atomicAdd(&s_cnt[1], at);
+  }
+  cluster.sync();
+  int eq_before = 0, taken_before = 0;
+  {
+    // keys of lower CTAs taken: all above T, and the first need_eq equal ones
+    int eq_lower = 0, above_lower = 0;
+    for (int r = 0; r < rank; r++) {
+      const int* cr = cluster.map_shared_rank(&s_cnt[0], r);
+      above_lower += cr[0];
+      eq_lower += cr[1];
+    }
+    eq_before = eq_lower;
+    taken_before = above_lower + min(eq_lower, need_eq);
+  }
+  cluster.sync();  // no CTA leaves while a peer may still read its counts
+  for (int base = 0; base < len; base += nt) {
     const int i = base + t;
-    const uint32_t k = i < S ? s_key[i] : 0u;
-    const bool eq = i < S && k == T;
+    const uint32_t k = i < len ? s_key[i] : 0u;
+    const bool eq = i < len && k == T;
     int eq_total, take_total;
     const int eq_rank = eq_before + block_flag_prefix(eq, s_w, &eq_total);
-    const bool take = i < S && (k > T || (eq && eq_rank < need_eq));
+    const bool take = i < len && (k > T || (eq && eq_rank < need_eq));
     const int j = taken_before + block_flag_prefix(take, s_w, &take_total);
-    if (take && j < n) sel[(size_t)b * n + j] = i;
+    if (take && j < n) sel[(size_t)b * n + j] = i0 + i;
     taken_before += take_total;
     eq_before += eq_total;
   }
@@ -630,15 +667,10 @@ extern "C" gs2d_status gs2d_head_decode(const float* out, int32_t ldo, int32_t B
       (B > 0 && (!out || !params || !sel)))
     return set_error(GS2D_ERR_INVALID_ARG, "gs2d_head_decode: arguments");
   if (B == 0 || n == 0) return set_error(GS2D_OK, "");
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k_head_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024) != cudaSuccess)
-      return launched("gs2d_head_decode");
-    attr = true;
-  }
   cudaStream_t s = (cudaStream_t)stream;
-  k_head_select<<<B, 1024, (size_t)smem, s>>>(out, ldo, gh, gw, slots, n, sel);
+  k_head_select_cluster<<<B * kSelCluster, 512,
+                          (size_t)((gh * gw * slots + kSelCluster - 1) / kSelCluster) * 4, s>>>(
+      out, ldo, gh, gw, slots, n, sel);
   const size_t total = (size_t)B * n;
   const size_t want = (total + 255) / 256;
   k_head_decode<<<(int)(want < 152 * 8 ? want : 152 * 8), 256, 0, s>>>(
