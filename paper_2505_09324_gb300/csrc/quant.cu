@@ -37,6 +37,7 @@ __device__ __forceinline__ void quant_one(float x, int b, float lo, float scale,
 __global__ void __launch_bounds__(256)
 k_quantize(const float* __restrict__ params, int n, QuantArgs q, uint16_t* __restrict__ codes,
            float* __restrict__ dequant, float* __restrict__ ranges) {
+  pdl_begin();
   if (ranges && blockIdx.x == 0 && threadIdx.x < 9) {
     const int r = threadIdx.x;
     ranges[r] = q.bits[r] > 0 ? q.lo[r] : 0.0f;
@@ -66,6 +67,7 @@ __global__ void __cluster_dims__(kRefineCluster, 1, 1) __launch_bounds__(kRefine
 k_quantize_refine(const float* __restrict__ params, int n, QuantArgs q,
                   uint16_t* __restrict__ codes, float* __restrict__ dequant,
                   float* __restrict__ ranges) {
+  pdl_begin();
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   __shared__ float s_lo[kRefineThreads / 32], s_hi[kRefineThreads / 32];
@@ -151,14 +153,13 @@ cudaError_t launch_quantize(const float* params, int n, const gs2d_quant& q, uin
     a.step[r] = q.step[r];
   }
   if (n > 0 && q.refine) {
-    k_quantize_refine<<<dim3(kRefineCluster, 9), kRefineThreads, 0, s>>>(params, n, a, codes,
-                                                                         dequant, ranges);
-    return cudaGetLastError();
+    return launch_pdl(k_quantize_refine, dim3(kRefineCluster, 9), kRefineThreads, 0, s, params,
+                      n, a, codes, dequant, ranges);
   }
   const size_t want = ((size_t)9 * (n > 0 ? n : 0) + 255) / 256;
   const int blocks = (int)(want < 1 ? 1 : (want < 152 * 8 ? want : 152 * 8));
-  k_quantize<<<blocks, 256, 0, s>>>(params, n > 0 ? n : 0, a, codes, dequant, ranges);
-  return cudaGetLastError();
+  return launch_pdl(k_quantize, blocks, 256, 0, s, params, n > 0 ? n : 0, a, codes, dequant,
+                    ranges);
 }
 
 }  // namespace gs2d
