@@ -395,85 +395,87 @@ __device__ __forceinline__ void process_tile(const RenderArgs& a, const TileFram
     return;
   }
 
-  // forward (kModeFwd, kModeL2)
-  float acc[R][3];
+  if constexpr (MODE == kModeFwd || MODE == kModeL2) {
+    // forward (kModeFwd, kModeL2)
+    float acc[R][3];
 #pragma unroll
-  for (int r = 0; r < R; r++) acc[r][0] = acc[r][1] = acc[r][2] = 0.0f;
-  int staged = -1;
-  for (int b = rg.x; b < rg.y; b += S) {
-    const int cnt = min(S, rg.y - b);
-    __syncthreads();
-    stage_batch<T, S>(sm, a, f, b, cnt);
-    __syncthreads();
-    const int wn = warp_list<T, S>(sm, cnt, wid, lane, ms.wl[wid]);
-    fwd_batch<T, S>(sm, ms.wl[wid], wn, px, py, acc);
-    staged = b;
-  }
-  if constexpr (MODE == kModeFwd) {
-    if (x < f.W) {
+    for (int r = 0; r < R; r++) acc[r][0] = acc[r][1] = acc[r][2] = 0.0f;
+    int staged = -1;
+    for (int b = rg.x; b < rg.y; b += S) {
+      const int cnt = min(S, rg.y - b);
+      __syncthreads();
+      stage_batch<T, S>(sm, a, f, b, cnt);
+      __syncthreads();
+      const int wn = warp_list<T, S>(sm, cnt, wid, lane, ms.wl[wid]);
+      fwd_batch<T, S>(sm, ms.wl[wid], wn, px, py, acc);
+      staged = b;
+    }
+    if constexpr (MODE == kModeFwd) {
+      if (x < f.W) {
 #pragma unroll
-      for (int r = 0; r < R; r++) {
-        if (y0 + r < f.H) {
-          const size_t o = f.pix + (size_t)(y0 + r) * f.W + x;
+        for (int r = 0; r < R; r++) {
+          if (y0 + r < f.H) {
+            const size_t o = f.pix + (size_t)(y0 + r) * f.W + x;
+            a.img[o] = acc[r][0];
+            a.img[HW + o] = acc[r][1];
+            a.img[2 * HW + o] = acc[r][2];
+          }
+        }
+      }
+      return;
+    }
+
+    // L2 loss and dL/dC of this thread's pixels; the clip's own mean
+    const double count3 = 3.0 * (double)f.W * (double)f.H;
+    const float gscale = (float)(2.0 / count3), lscale = (float)(1.0 / count3);
+    float2 l = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (x < f.W && y0 + r < f.H) {
+        const size_t o = f.pix + (size_t)(y0 + r) * f.W + x;
+        const float t0 = a.target[o], t1 = a.target[HW + o], t2 = a.target[2 * HW + o];
+        const float d0 = acc[r][0] - t0, d1 = acc[r][1] - t1, d2 = acc[r][2] - t2;
+        const float e0 = __saturatef(acc[r][0]) - t0, e1 = __saturatef(acc[r][1]) - t1,
+                    e2 = __saturatef(acc[r][2]) - t2;
+        l.x += fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+        l.y += fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
+        g = make_float4(gscale * d0, gscale * d1, gscale * d2, 0.f);
+        if (a.img) {
           a.img[o] = acc[r][0];
           a.img[HW + o] = acc[r][1];
           a.img[2 * HW + o] = acc[r][2];
         }
       }
+      ms.g[(R * (t / T) + r) * T + t % T] = g;
     }
-    return;
-  }
-
-  // L2 loss and dL/dC of this thread's pixels; the clip's own mean
-  const double count3 = 3.0 * (double)f.W * (double)f.H;
-  const float gscale = (float)(2.0 / count3), lscale = (float)(1.0 / count3);
-  float2 l = make_float2(0.f, 0.f);
 #pragma unroll
-  for (int r = 0; r < R; r++) {
-    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (x < f.W && y0 + r < f.H) {
-      const size_t o = f.pix + (size_t)(y0 + r) * f.W + x;
-      const float t0 = a.target[o], t1 = a.target[HW + o], t2 = a.target[2 * HW + o];
-      const float d0 = acc[r][0] - t0, d1 = acc[r][1] - t1, d2 = acc[r][2] - t2;
-      const float e0 = __saturatef(acc[r][0]) - t0, e1 = __saturatef(acc[r][1]) - t1,
-                  e2 = __saturatef(acc[r][2]) - t2;
-      l.x += fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
-      l.y += fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
-      g = make_float4(gscale * d0, gscale * d1, gscale * d2, 0.f);
-      if (a.img) {
-        a.img[o] = acc[r][0];
-        a.img[HW + o] = acc[r][1];
-        a.img[2 * HW + o] = acc[r][2];
+    for (int o = 16; o > 0; o >>= 1) {
+      l.x += __shfl_xor_sync(0xffffffffu, l.x, o);
+      l.y += __shfl_xor_sync(0xffffffffu, l.y, o);
+    }
+    if (lane == 0) ms.red[wid] = l;
+    __syncthreads();
+    if (t == 0) {
+      float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int w = 0; w < G::NW; w++) {
+        s.x += ms.red[w].x;
+        s.y += ms.red[w].y;
       }
+      a.loss_part[f.tile] = make_float2(s.x * lscale, s.y * lscale);
     }
-    ms.g[(R * (t / T) + r) * T + t % T] = g;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    l.x += __shfl_xor_sync(0xffffffffu, l.x, o);
-    l.y += __shfl_xor_sync(0xffffffffu, l.y, o);
-  }
-  if (lane == 0) ms.red[wid] = l;
-  __syncthreads();
-  if (t == 0) {
-    float2 s = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int w = 0; w < G::NW; w++) {
-      s.x += ms.red[w].x;
-      s.y += ms.red[w].y;
+    // backward; the last forward batch is still staged
+    for (int b = rg.x; b < rg.y; b += S) {
+      const int cnt = min(S, rg.y - b);
+      if (b != staged) {
+        __syncthreads();
+        stage_batch<T, S>(sm, a, f, b, cnt);
+        __syncthreads();
+        staged = b;
+      }
+      bwd_batch<T, S>(sm, ms.g, cnt, ox, oy, a.partial);
     }
-    a.loss_part[f.tile] = make_float2(s.x * lscale, s.y * lscale);
-  }
-  // backward; the last forward batch is still staged
-  for (int b = rg.x; b < rg.y; b += S) {
-    const int cnt = min(S, rg.y - b);
-    if (b != staged) {
-      __syncthreads();
-      stage_batch<T, S>(sm, a, f, b, cnt);
-      __syncthreads();
-      staged = b;
-    }
-    bwd_batch<T, S>(sm, ms.g, cnt, ox, oy, a.partial);
   }
 }
 
