@@ -55,8 +55,8 @@ SMS, FP32_LANES, MUFU_LANES, SM_MAX_MHZ = 152, 128, 32, 2070.0
 # DRAM bytes (read + write) of one fused render launch (k_render, tile 32,
 # stage 128, grid) from an ncu capture of this workload, valid for the render
 # source with this sha256 (else null)
-NCU_TRAFFIC = {"bytes": 26738176, "schedule": (32, 128, 1),
-               "render_sha256": "39f2bfd3023ab627eff191019d98fead2d16792428c41b0b57d4f9d81f300d57"}
+NCU_TRAFFIC = {"bytes": 26739200, "schedule": (32, 128, 1),
+               "render_sha256": "802bf3e5e7a6c398e03641e383cc68e9798ac1c25a0bb537bb5573720f9f2095"}
 
 
 def render_traffic(schedule):
