@@ -306,20 +306,39 @@ __global__ void __launch_bounds__(256) k_sp_seed_write(SpArgs a) {
   const SpGeom g = seed_geometry(a);
   __shared__ int s_base, s_w[9];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (threadIdx.x == 0) {
+  {
+    // this block's base (counts of the blocks before it) and the total
     int b = 0, tot = 0;
-    for (int k = 0; k < (int)gridDim.x; k++) {
-      if (k < (int)blockIdx.x) b += a.blk[k];
-      tot += a.blk[k];
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+      const int c = a.blk[k];
+      b += k < (int)blockIdx.x ? c : 0;
+      tot += c;
     }
-    s_base = b;
-    if (blockIdx.x == 0) {
-      SpGeom out = g;
-      out.M = min(tot, a.n);
-      *a.geo = out;
+    for (int o = 16; o; o >>= 1) {
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
     }
+    __shared__ int s_b[8], s_t[8];
+    if (lane == 0) {
+      s_b[wid] = b;
+      s_t[wid] = tot;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int bb = 0, tt = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+        bb += s_b[w];
+        tt += s_t[w];
+      }
+      s_base = bb;
+      if (blockIdx.x == 0) {
+        SpGeom out = g;
+        out.M = min(tt, a.n);
+        *a.geo = out;
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
   const int chunk = (g.ncell + gridDim.x - 1) / gridDim.x;
   const int c0 = blockIdx.x * chunk, c1 = min(g.ncell, c0 + chunk);
   int run = s_base;
