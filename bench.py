@@ -27,6 +27,7 @@ arm times the CPU oracle on row-band samples of the same workload.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -86,6 +87,9 @@ def parse():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-quant", action="store_true")
     ap.add_argument("--quant-iters", type=int, default=100)
+    ap.add_argument("--bin-margin", type=float, default=None,
+                    help="fit-loop tile lists: widening in pixels (negative: rebuild every "
+                         "iteration); default the RasterConfig default")
     ap.add_argument("--schedule", default="",
                     help="tile/stage/launch (e.g. 32/128/grid) instead of the autotuner's pick")
     ap.add_argument("--seq-frames", type=int, default=60)
@@ -391,7 +395,6 @@ def calibrated_quantizer(dev, config, iters=100):
     """PTQ calibration on the training side: the default quantiser's ranges
     from fits (ROI initialisation, fast schedule, `iters` iterations) of four
     conferencing frames of other seeds."""
-    import dataclasses
 
     import torch
 
@@ -420,7 +423,6 @@ def measure_quant(args, dev, config, frame, mask, bg_xy, q):
     then quantised in one call.  QAT fits the same frame for the same number
     of iterations with the quantiser inside the loop (ranges refined every
     step).  Latencies are CUDA-event device times on the launching stream."""
-    import dataclasses
 
     import torch
 
@@ -577,6 +579,8 @@ def run_ours(args):
                  "config": RasterConfig(tile=int(t_), stage=int(s_), launch=la)}
     else:
         tuned = autotune([(W, H, N_GAUSS)], params0, frame.reshape(-1), reps=10, cache=False)
+    if args.bin_margin is not None:
+        tuned["config"] = dataclasses.replace(tuned["config"], bin_margin=args.bin_margin)
     rast = GaussianRasterizer(W, H, N_GAUSS, device=dev, config=tuned["config"])
     plan, ws = rast.plan, rast.ws_ptr
     params = params0.clone()
@@ -589,9 +593,12 @@ def run_ours(args):
     def fit_step(p_t):
         nat.fit_step(plan, ws, frame.data_ptr(), p_t.data_ptr(), m.data_ptr(), v.data_ptr(), sp)
 
-    # our kernels per step: prepare (project + tile counts, scans, scatter,
-    # short-list sort, long-list sort), fused render, reduction + Adam
-    launches_per_step = 5 + 1 + 1
+    # our kernels per step: projection (+ containment test of the retained
+    # lists), list rebuild counts, scans, scatter, short-list sort, long-list
+    # sort (the last four return at once while the lists hold), fused render,
+    # reduction + Adam; per-iteration binning fuses the first two
+    retained = tuned["config"].bin_margin >= 0
+    launches_per_step = (6 if retained else 5) + 1 + 1
 
     for _ in range(args.warmup):
         fit_step(params)
@@ -625,6 +632,7 @@ def run_ours(args):
     st = rast.status()
     if st != 0:
         raise RuntimeError(f"device status {nat.STATUS_NAMES.get(st, st)} during the benchmark")
+    rebuilds = rast.rebins()
     rast.prepare(params)
     pairs1, hits1 = rast.count_pairs()
 
@@ -753,7 +761,6 @@ def run_ours(args):
     if not args.no_encode:
         side = torch.cuda.Stream(dev)
         # fits from an initialiser use the fast learning-rate schedule
-        import dataclasses
         from paper_2505_09324_gb300.raster import FAST_FIT
         fast = GaussianRasterizer(W, H, N_GAUSS, device=dev,
                                   config=dataclasses.replace(tuned["config"], **FAST_FIT))
@@ -863,6 +870,9 @@ def run_ours(args):
                            "gaussians": N_GAUSS,
                            "timed_steps": f"fit iterations 1..{K} from the ROI initialisation",
                            "l2": "flushed before each timed step",
+                           "tile_lists": {"bin_margin_px": tuned["config"].bin_margin,
+                                          "rebuilt_in_timed_steps": rebuilds if retained
+                                          else K},
                            "parallelism": f"replicas{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches_per_step * K, "clocks": clocks,

@@ -79,6 +79,15 @@ typedef struct {
    * (c_r, c_g, c_b), lr_weight (w); all 1 by default (plain Adam).
    * gs2d_adam_step ignores them. */
   float lr_mu, lr_shape, lr_color, lr_weight, lr_decay;
+  /* Re-binning of the fit loop (gs2d_fit_step, gs2d_fit_step_rgb8,
+   * gs2d_fit_step_qat, gs2d_encode_frame, gs2d_encode_batch): each Gaussian is
+   * listed in the tiles its pixel box, widened by bin_margin pixels, covers,
+   * and the lists are rebuilt only in an iteration where some Gaussian's box
+   * has left its listed tiles (checked on the device every iteration).  The
+   * results are the same as binning every iteration (tiles a Gaussian does
+   * not reach contribute nothing; the widened lists need room in
+   * max_entries).  Negative: bin every iteration.  Default 4. */
+  float bin_margin;
 } gs2d_config;
 
 enum { GS2D_LAUNCH_PERSISTENT = 0, GS2D_LAUNCH_GRID = 1 };
@@ -372,6 +381,12 @@ gs2d_status gs2d_fit_step_rgb8(const gs2d_plan* plan, void* ws, const uint8_t* r
                                uint8_t* rgb_dev, float* frame_dev, const float* params_host,
                                float* params, float* adam_m, float* adam_v, float* params_out_host,
                                void* stream);
+
+/* Number of times the fit loop has rebuilt its tile lists in this workspace
+ * (see gs2d_config.bin_margin) since it was zero-filled or gs2d_fit_reset;
+ * synchronises the stream. */
+gs2d_status gs2d_fit_rebins(const gs2d_plan* plan, const void* ws, int64_t* rebins,
+                            void* stream);
 
 /* Device scratch (bytes, 256-byte aligned start) that gs2d_roi_init needs for
  * a W x H frame and n Gaussians. */

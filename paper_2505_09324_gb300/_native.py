@@ -30,6 +30,7 @@ EXPORTS = (
     "gs2d_select_changed", "gs2d_pframe_step", "gs2d_encode_pframe", "gs2d_quantize",
     "gs2d_fit_step_qat", "gs2d_code_entropy_scratch_bytes", "gs2d_code_entropy",
     "gs2d_sequence_bits", "gs2d_frame_from_rgb8", "gs2d_conv_bf16", "gs2d_fit_step_rgb8",
+    "gs2d_fit_rebins",
     "gs2d_encode_batch",
     "gs2d_autotune_ws_bytes", "gs2d_autotune",
     "gs2d_gemm_bf16", "gs2d_gemm_partial_bytes", "gs2d_cnn_input", "gs2d_im2col", "gs2d_col2im",
@@ -54,7 +55,7 @@ class Config(ctypes.Structure):
                 ("eps", ctypes.c_float), ("stage", ctypes.c_int32), ("launch", ctypes.c_int32),
                 ("lr_mu", ctypes.c_float), ("lr_shape", ctypes.c_float),
                 ("lr_color", ctypes.c_float), ("lr_weight", ctypes.c_float),
-                ("lr_decay", ctypes.c_float)]
+                ("lr_decay", ctypes.c_float), ("bin_margin", ctypes.c_float)]
 
 
 LAUNCH_PERSISTENT = 0
@@ -151,6 +152,7 @@ def load(build_if_missing: bool = False):
             "gs2d_code_entropy_scratch_bytes": (ctypes.c_size_t, []),
             "gs2d_frame_from_rgb8": (i32, [P, i32, i32, i64, P, P]),
             "gs2d_fit_step_rgb8": (i32, [pp, P, P, P, P, P, P, P, P, P, P]),
+            "gs2d_fit_rebins": (i32, [pp, P, ctypes.POINTER(i64), P]),
             "gs2d_conv_bf16": (i32, [P, i32, i32, i32, i32, i32, i32, i32, P, i32, i32, i32, P,
                                      P, i32, P, P]),
             "gs2d_code_entropy": (i32, [P, i32, ctypes.POINTER(i32), P, P, ctypes.c_size_t, P,
@@ -486,3 +488,10 @@ def fit_step_rgb8(plan: Plan, ws: int, rgb_host: int, rgb_dev: int, frame_dev: i
     check(load().gs2d_fit_step_rgb8(ctypes.byref(plan), _p(ws), _p(rgb_host), _p(rgb_dev),
                                     _p(frame_dev), _p(params_host), _p(params), _p(m), _p(v),
                                     _p(params_out_host), _p(stream)), "gs2d_fit_step_rgb8")
+
+
+def fit_rebins(plan: Plan, ws: int, stream: int) -> int:
+    out = ctypes.c_int64(0)
+    check(load().gs2d_fit_rebins(ctypes.byref(plan), _p(ws), ctypes.byref(out), _p(stream)),
+          "gs2d_fit_rebins")
+    return int(out.value)

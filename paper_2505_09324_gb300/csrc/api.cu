@@ -53,7 +53,7 @@ bool cfg_valid(const gs2d_config& c) {
          c.beta2 < 1.0f && c.eps > 0.0f && isfinite(c.eps) && c.lr_mu >= 0.0f &&
          isfinite(c.lr_mu) && c.lr_shape >= 0.0f && isfinite(c.lr_shape) && c.lr_color >= 0.0f &&
          isfinite(c.lr_color) && c.lr_weight >= 0.0f && isfinite(c.lr_weight) &&
-         c.lr_decay > 0.0f && c.lr_decay <= 1.0f;
+         c.lr_decay > 0.0f && c.lr_decay <= 1.0f && isfinite(c.bin_margin);
 }
 
 }  // namespace
@@ -81,6 +81,7 @@ void gs2d_config_default(gs2d_config* cfg) {
   cfg->launch = GS2D_LAUNCH_GRID;
   cfg->lr_mu = cfg->lr_shape = cfg->lr_color = cfg->lr_weight = 1.0f;
   cfg->lr_decay = 1.0f;
+  cfg->bin_margin = 4.0f;
 }
 
 size_t gs2d_sizeof_plan(void) { return sizeof(gs2d_plan); }
@@ -173,6 +174,7 @@ gs2d_status gs2d_plan_init_batch(gs2d_plan* plan, gs2d_clip* clips, int32_t num_
   sz[kOffActOrder] = (nt + 1) * sizeof(int);
   sz[kOffQuant] = 9 * nn * sizeof(float);
   sz[kOffGrad] = 9 * nn * sizeof(float);
+  sz[kOffLRect] = nn * sizeof(int4);
   uint64_t off = 0;
   for (int sec = 0; sec < kNumSections; sec++) {
     plan->off[sec] = off;
@@ -302,7 +304,7 @@ gs2d_status gs2d_roi_init(const float* frame, const uint8_t* mask, int32_t width
 
 static cudaError_t fit_iteration(const gs2d_plan& p, void* ws, const float* target, float* params,
                                  float* m, float* v, cudaStream_t s) {
-  cudaError_t e = launch_prepare(p, ws, params, true, s);
+  cudaError_t e = launch_prepare_fit(p, ws, params, s);
   if (e == cudaSuccess) e = launch_fit_step(p, ws, target, params, m, v, s);
   return e;
 }
@@ -410,7 +412,7 @@ gs2d_status gs2d_fit_step_rgb8(const gs2d_plan* plan, void* ws, const uint8_t* r
   // the params, projection and binning on s meanwhile
   if (e == cudaSuccess && params_host && pbytes)
     e = cudaMemcpyAsync(params, params_host, pbytes, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = launch_prepare(p, ws, params, true, s);
+  if (e == cudaSuccess) e = launch_prepare_fit(p, ws, params, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, aux->frame, 0);
   if (e == cudaSuccess) e = launch_fit_step(p, ws, frame_dev, params, adam_m, adam_v, s);
   if (e == cudaSuccess && params_out_host && pbytes)
@@ -424,6 +426,21 @@ gs2d_status gs2d_fit_reset(const gs2d_plan* plan, void* ws, float* adam_m, float
   if (st) return st;
   if (plan->n > 0 && (!adam_m || !adam_v)) return fail(GS2D_ERR_INVALID_ARG, "Adam state is NULL");
   return cuda_check(reset_fit(*plan, ws, adam_m, adam_v, (cudaStream_t)stream), "gs2d_fit_reset");
+}
+
+gs2d_status gs2d_fit_rebins(const gs2d_plan* plan, const void* ws, int64_t* rebins,
+                            void* stream) {
+  gs2d_status st = check_plan(plan, ws);
+  if (st) return st;
+  if (!rebins) return fail(GS2D_ERR_INVALID_ARG, "rebins is NULL");
+  int32_t r = 0;
+  const WsHeader* hdr = ws_ptr<WsHeader>(ws, *plan, kOffHeader);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(&r, &hdr->rebins, sizeof(r), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_check(e, "gs2d_fit_rebins");
+  *rebins = r;
+  return ok();
 }
 
 gs2d_status gs2d_encode_frame(const gs2d_plan* plan, void* ws, const float* target, float* params,

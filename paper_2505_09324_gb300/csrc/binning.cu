@@ -43,13 +43,9 @@ k_project(int n, ClipSet cs, int tile_shift, float sigma_cut, float alpha_min, f
 }
 
 // Per-tile entry counts from the rectangles (warp-cooperative: lanes share the
-// tiles of one Gaussian at a time; fire-and-forget atomics) and the block's
-// sum of per-Gaussian counts.
-__device__ __forceinline__ void count_block(int n, const int4* __restrict__ rect,
-                                           const int* __restrict__ count,
-                                           int* __restrict__ tile_cnt,
-                                           long long* __restrict__ block_sum) {
-  __shared__ int s_warp[kGB / 32];
+// tiles of one Gaussian at a time; fire-and-forget atomics).
+__device__ __forceinline__ void count_tiles_warp(int n, const int4* __restrict__ rect,
+                                                 int* __restrict__ tile_cnt) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const int4 rc = i < n ? rect[i] : make_int4(0, 0, 0, 0);
@@ -63,6 +59,14 @@ __device__ __forceinline__ void count_block(int n, const int4* __restrict__ rect
       atomicAdd(&tile_cnt[t0 + dy * stride + (j - dy * w)], 1);
     }
   }
+}
+
+// The block's sum of per-Gaussian counts.
+__device__ __forceinline__ void block_count_sum(int n, const int* __restrict__ count,
+                                                long long* __restrict__ block_sum) {
+  __shared__ int s_warp[kGB / 32];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
   int c = i < n ? count[i] : 0;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
@@ -75,10 +79,36 @@ __device__ __forceinline__ void count_block(int n, const int4* __restrict__ rect
   }
 }
 
+__device__ __forceinline__ void count_block(int n, const int4* __restrict__ rect,
+                                           const int* __restrict__ count,
+                                           int* __restrict__ tile_cnt,
+                                           long long* __restrict__ block_sum) {
+  count_tiles_warp(n, rect, tile_cnt);
+  block_count_sum(n, count, block_sum);
+}
+
+// Adam step counter, the powers beta^step and the decayed learning rate of
+// the step that begins (thread 0 of the first kernel of a fit iteration).
+__device__ __forceinline__ void adam_tick_header(WsHeader* hdr, float b1, float b2, float lr,
+                                                 float lr_decay) {
+  const int t = ++hdr->step;
+  const double p1 = t == 1 ? (double)b1 : hdr->pw1 * b1;
+  const double p2 = t == 1 ? (double)b2 : hdr->pw2 * b2;
+  hdr->pw1 = p1;
+  hdr->pw2 = p2;
+  hdr->bc1 = (float)(1.0 - p1);
+  hdr->bc2 = (float)(1.0 - p2);
+  const double pd = t == 1 ? 1.0 : hdr->pwd * lr_decay;
+  hdr->pwd = pd;
+  hdr->lr_now = (float)(lr * pd);
+}
+
 __global__ void __launch_bounds__(kGB)
 k_count_tiles(int n, const int4* __restrict__ rect, const int* __restrict__ count,
-              int* __restrict__ tile_cnt, long long* __restrict__ block_sum) {
+              int* __restrict__ tile_cnt, long long* __restrict__ block_sum,
+              WsHeader* __restrict__ hdr) {
   pdl_begin();
+  if (blockIdx.x == 0 && threadIdx.x == 0) hdr->lists_valid = 0;  // rebuilt from tight boxes
   count_block(n, rect, count, tile_cnt, block_sum);
 }
 
@@ -94,23 +124,85 @@ k_project_count(int n, ClipSet cs, int tile_shift, float sigma_cut, float alpha_
                 float b1, float b2, float lr, float lr_decay) {
   pdl_begin();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0 && adam_tick) {
-    const int t = ++hdr->step;
-    const double p1 = t == 1 ? (double)b1 : hdr->pw1 * b1;
-    const double p2 = t == 1 ? (double)b2 : hdr->pw2 * b2;
-    hdr->pw1 = p1;
-    hdr->pw2 = p2;
-    hdr->bc1 = (float)(1.0 - p1);
-    hdr->bc2 = (float)(1.0 - p2);
-    const double pd = t == 1 ? 1.0 : hdr->pwd * lr_decay;
-    hdr->pwd = pd;
-    hdr->lr_now = (float)(lr * pd);
+  if (i == 0) {
+    if (adam_tick) adam_tick_header(hdr, b1, b2, lr, lr_decay);
+    hdr->lists_valid = 0;  // the lists below are built from the tight rectangles
   }
   if (i < n)
     project_one(i, n, clip_of_gaussian(cs, i), tile_shift, sigma_cut, alpha_min, det_eps, params,
                 rec, rect, count);
   __syncwarp();
   count_block(n, rect, count, tile_cnt, block_sum);
+}
+
+// ---------------------------------------------------------------------------
+// Fit loop with retained tile lists.  Within a tile a Gaussian adds nothing
+// outside its cut-off box, so a list may hold Gaussians that do not reach the
+// tile: the render skips a (tile, Gaussian) pair whose tile lies outside the
+// Gaussian's tight rectangle, and the backward slots stay those of the tight
+// rectangles, so results are the same as with lists rebuilt every iteration.
+// Each Gaussian is listed over its rectangle widened by `margin` pixels; the
+// lists are rebuilt only in an iteration where some tight rectangle has left
+// its listed one.
+//
+// k_project_fit: records, tight rectangles and counts (the backward slots),
+// block sums of the counts, the containment test against the listed
+// rectangle (clears hdr->lists_valid on a miss) and the Adam tick.
+__global__ void __launch_bounds__(kGB)
+k_project_fit(int n, ClipSet cs, int tile_shift, float sigma_cut, float alpha_min, float det_eps,
+              const float* __restrict__ params, float4* __restrict__ rec, int4* __restrict__ rect,
+              int* __restrict__ count, long long* __restrict__ block_sum,
+              const int4* __restrict__ lrect, WsHeader* __restrict__ hdr, float b1, float b2,
+              float lr, float lr_decay) {
+  pdl_begin();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) adam_tick_header(hdr, b1, b2, lr, lr_decay);
+  if (i < n) {
+    const gs2d_clip cl = clip_of_gaussian(cs, i);
+    int tx0 = 0, ty0 = 0, tx1 = 0, ty1 = 0;
+    const bool vis = gaussian_tiles(i, n, cl, tile_shift, sigma_cut, alpha_min, det_eps, params,
+                                    0.0f, tx0, ty0, tx1, ty1);
+    const int4 rc = vis ? make_int4(cl.tile_off + ty0 * cl.tiles_x + tx0, cl.tiles_x, tx1 - tx0,
+                                    ty1 - ty0)
+                        : make_int4(0, 0, 0, 0);
+    rect[i] = rc;
+    count[i] = rc.z * rc.w;
+    write_record(i, n, vis, sigma_cut, alpha_min, params, rec);
+    if (vis) {
+      const int4 lr4 = lrect[i];
+      bool inside = lr4.z > 0;
+      if (inside) {
+        const int rel = lr4.x - cl.tile_off;
+        const int ly0 = rel / cl.tiles_x, lx0 = rel - ly0 * cl.tiles_x;
+        inside = lx0 <= tx0 && ly0 <= ty0 && tx1 <= lx0 + lr4.z && ty1 <= ly0 + lr4.w;
+      }
+      if (!inside) hdr->lists_valid = 0;
+    }
+  }
+  block_count_sum(n, count, block_sum);
+}
+
+// Rebuild step 1 (only when k_project_fit found a miss): the listed
+// rectangles, widened by `margin` pixels, and the per-tile entry counts.
+__global__ void __launch_bounds__(kGB)
+k_rebin_count(int n, ClipSet cs, int tile_shift, float sigma_cut, float alpha_min,
+              float det_eps, float margin, const float* __restrict__ params,
+              int4* __restrict__ lrect, int* __restrict__ tile_cnt, WsHeader* __restrict__ hdr) {
+  pdl_begin();
+  if (hdr->lists_valid) return;  // the same for every thread of the grid
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) hdr->rebins++;
+  if (i < n) {
+    const gs2d_clip cl = clip_of_gaussian(cs, i);
+    int tx0 = 0, ty0 = 0, tx1 = 0, ty1 = 0;
+    const bool vis = gaussian_tiles(i, n, cl, tile_shift, sigma_cut, alpha_min, det_eps, params,
+                                    margin, tx0, ty0, tx1, ty1);
+    lrect[i] = vis ? make_int4(cl.tile_off + ty0 * cl.tiles_x + tx0, cl.tiles_x, tx1 - tx0,
+                               ty1 - ty0)
+                   : make_int4(0, 0, 0, 0);
+  }
+  __syncwarp();
+  count_tiles_warp(n, lrect, tile_cnt);
 }
 
 // ---------------------------------------------------------------------------
@@ -158,7 +250,7 @@ __global__ void __launch_bounds__(kGB)
 k_bin_scan(int n, int nbg, int num_tiles, int64_t max_entries, int* __restrict__ count,
            const long long* __restrict__ block_sum, int* __restrict__ tile_cnt,
            int* __restrict__ cursor, int2* __restrict__ ranges, int* __restrict__ bucket,
-           uint32_t* __restrict__ rank, WsHeader* __restrict__ hdr) {
+           uint32_t* __restrict__ rank, WsHeader* __restrict__ hdr, int lazy) {
   pdl_begin();
   __shared__ long long warp_sum[32];
   __shared__ int s_hist[kBuckets];
@@ -181,8 +273,11 @@ k_bin_scan(int n, int nbg, int num_tiles, int64_t max_entries, int* __restrict__
     long long dummy;
     const long long ex = block_scan64(c, warp_sum, &dummy);
     if (i < n) count[i] = over ? 0 : (int)(prefix + ex);
+    if (blockIdx.x == 0 && t == 0) count[n] = over ? 0 : (int)total;
     return;
   }
+  // retained lists: only the slots (above) change
+  if (lazy && hdr->lists_valid) return;  // the same for every thread of the grid
   // tile CTAs: chunk [c0, c0 + kGB * kTileItems) of the tiles; the prefix of the
   // chunk and the total come from a strided pass over all tile counts (the
   // counts are reset later, by k_sort_short, once nothing reads them)
@@ -239,7 +334,7 @@ k_bin_scan(int n, int nbg, int num_tiles, int64_t max_entries, int* __restrict__
     hdr->entries_raw = total;
     hdr->n_entries = over ? 0 : (int)total;
     if (over) atomicCAS(&hdr->status, 0, (int)GS2D_ERR_CAPACITY);
-    count[n] = over ? 0 : (int)total;
+    if (nbg == 0) count[n] = 0;
     hdr->long_count = 0;
   }
 }
@@ -251,10 +346,11 @@ constexpr int kInFlight = 4;
 
 __global__ void __launch_bounds__(kGB)
 k_bin_scatter(int n, const int4* __restrict__ rect, const WsHeader* __restrict__ hdr,
-              int* __restrict__ cursor, uint32_t* __restrict__ list) {
+              int* __restrict__ cursor, uint32_t* __restrict__ list, int lazy) {
   pdl_begin();
   __shared__ int s_start[kGB / 32][33];
   if (hdr->entries_raw != (int64_t)hdr->n_entries) return;  // over capacity
+  if (lazy && hdr->lists_valid) return;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int g_base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31;
   const int g = g_base + lane;
@@ -358,8 +454,9 @@ __global__ void __launch_bounds__(256)
 k_sort_short(int num_tiles, const int2* __restrict__ ranges, uint32_t* __restrict__ list,
              int* __restrict__ long_tiles, int* __restrict__ tile_cnt,
              const int* __restrict__ bucket, const uint32_t* __restrict__ rank,
-             int* __restrict__ order, WsHeader* __restrict__ hdr) {
+             int* __restrict__ order, WsHeader* __restrict__ hdr, int lazy) {
   pdl_begin();
+  if (lazy && hdr->lists_valid) return;
   const int lane = threadIdx.x & 31;
   const int tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (tile >= num_tiles) return;
@@ -404,9 +501,10 @@ k_sort_short(int num_tiles, const int2* __restrict__ ranges, uint32_t* __restric
 __global__ void __launch_bounds__(1024)
 k_sort_long(int2* __restrict__ ranges, uint32_t* __restrict__ list,
             const int* __restrict__ long_tiles, int* __restrict__ bucket,
-            WsHeader* __restrict__ hdr) {
+            WsHeader* __restrict__ hdr, int lazy) {
   pdl_begin();
   extern __shared__ uint32_t s_keys[];
+  if (lazy && hdr->lists_valid) return;
   const int t = threadIdx.x;
   // the queue classes were last read by k_sort_short: clear them for the next binning
   if (blockIdx.x == 0 && t < 2 * kBuckets) bucket[t] = 0;
@@ -469,8 +567,11 @@ cudaError_t prime_binning() {
   return e;
 }
 
-// Scans, scatter and segment sorts (everything after the counts).
-static cudaError_t launch_bin_rest(const gs2d_plan& p, void* ws, cudaStream_t s) {
+// Scans, scatter and segment sorts (everything after the counts); `lists`:
+// the rectangles the lists are built from; with `lazy` the tile part returns
+// at once while hdr->lists_valid is set.
+static cudaError_t launch_bin_rest(const gs2d_plan& p, void* ws, cudaStream_t s,
+                                   const int4* lists, int lazy) {
   WsHeader* hdr = ws_ptr<WsHeader>(ws, p, kOffHeader);
   int* count = ws_ptr<int>(ws, p, kOffCount);
   int* tile_cnt = ws_ptr<int>(ws, p, kOffTileCnt);
@@ -487,16 +588,15 @@ static cudaError_t launch_bin_rest(const gs2d_plan& p, void* ws, cudaStream_t s)
   if (e == cudaSuccess)
     e = launch_pdl(k_bin_scan, nbg + nbt, kGB, 0, s, p.n, nbg, p.num_tiles, p.max_entries, count,
                    ws_ptr<long long>(ws, p, kOffBlockSum), tile_cnt, cursor, ranges, bucket,
-                   rank, hdr);
+                   rank, hdr, lazy);
   if (e == cudaSuccess && p.n > 0)
-    e = launch_pdl(k_bin_scatter, nbg, kGB, 0, s, p.n, ws_ptr<int4>(ws, p, kOffRect), hdr,
-                   cursor, list);
+    e = launch_pdl(k_bin_scatter, nbg, kGB, 0, s, p.n, lists, hdr, cursor, list, lazy);
   if (e == cudaSuccess)
     e = launch_pdl(k_sort_short, (p.num_tiles + 7) / 8, 256, 0, s, p.num_tiles, ranges, list,
-                   long_tiles, tile_cnt, bucket, rank, order, hdr);
+                   long_tiles, tile_cnt, bucket, rank, order, hdr, lazy);
   if (e == cudaSuccess)
     e = launch_pdl(k_sort_long, 152, 1024, kLongMax * sizeof(uint32_t), s, ranges, list,
-                   long_tiles, bucket, hdr);
+                   long_tiles, bucket, hdr, lazy);
   return e;
 }
 
@@ -505,9 +605,10 @@ cudaError_t launch_bin_sort(const gs2d_plan& p, void* ws, cudaStream_t s) {
   if (p.n > 0)
     e = launch_pdl(k_count_tiles, (p.n + kGB - 1) / kGB, kGB, 0, s, p.n,
                    ws_ptr<int4>(ws, p, kOffRect), ws_ptr<int>(ws, p, kOffCount),
-                   ws_ptr<int>(ws, p, kOffTileCnt), ws_ptr<long long>(ws, p, kOffBlockSum));
+                   ws_ptr<int>(ws, p, kOffTileCnt), ws_ptr<long long>(ws, p, kOffBlockSum),
+                   ws_ptr<WsHeader>(ws, p, kOffHeader));
   if (e != cudaSuccess) return e;
-  return launch_bin_rest(p, ws, s);
+  return launch_bin_rest(p, ws, s, ws_ptr<int4>(ws, p, kOffRect), 0);
 }
 
 cudaError_t launch_prepare(const gs2d_plan& p, void* ws, const float* params, bool adam_tick,
@@ -521,7 +622,29 @@ cudaError_t launch_prepare(const gs2d_plan& p, void* ws, const float* params, bo
       ws_ptr<WsHeader>(ws, p, kOffHeader), adam_tick ? 1 : 0, p.cfg.beta1, p.cfg.beta2, p.cfg.lr,
       p.cfg.lr_decay);
   if (e != cudaSuccess) return e;
-  return launch_bin_rest(p, ws, s);
+  return launch_bin_rest(p, ws, s, ws_ptr<int4>(ws, p, kOffRect), 0);
+}
+
+cudaError_t launch_prepare_fit(const gs2d_plan& p, void* ws, const float* params,
+                               cudaStream_t s) {
+  if (!fit_lists_retained(p.cfg)) return launch_prepare(p, ws, params, true, s);
+  const int blocks = (p.n + kGB - 1) / kGB;
+  WsHeader* hdr = ws_ptr<WsHeader>(ws, p, kOffHeader);
+  int4* lrect = ws_ptr<int4>(ws, p, kOffLRect);
+  const ClipSet cs = clip_set(p, ws);
+  const int shift = tile_shift_of(p.tile);
+  cudaError_t e = launch_pdl(
+      k_project_fit, blocks > 0 ? blocks : 1, kGB, 0, s, p.n, cs, shift, p.cfg.sigma_cut,
+      p.cfg.alpha_min, p.cfg.det_eps, params, ws_ptr<float4>(ws, p, kOffRec),
+      ws_ptr<int4>(ws, p, kOffRect), ws_ptr<int>(ws, p, kOffCount),
+      ws_ptr<long long>(ws, p, kOffBlockSum), (const int4*)lrect, hdr, p.cfg.beta1, p.cfg.beta2,
+      p.cfg.lr, p.cfg.lr_decay);
+  if (e == cudaSuccess)
+    e = launch_pdl(k_rebin_count, blocks > 0 ? blocks : 1, kGB, 0, s, p.n, cs, shift,
+                   p.cfg.sigma_cut, p.cfg.alpha_min, p.cfg.det_eps, p.cfg.bin_margin, params,
+                   lrect, ws_ptr<int>(ws, p, kOffTileCnt), hdr);
+  if (e != cudaSuccess) return e;
+  return launch_bin_rest(p, ws, s, lrect, 1);
 }
 
 }  // namespace gs2d

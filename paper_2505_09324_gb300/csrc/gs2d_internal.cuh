@@ -41,6 +41,7 @@ enum WsSection {
   kOffActOrder,     // int32[num_tiles + 1] P-frame: active tiles (count last)
   kOffQuant,        // float[9 n] quantisation-aware fitting: the fake-quantised parameters
   kOffGrad,         // float[9 n] gradient scratch
+  kOffLRect,        // int4[n]  fit loop: the (widened) rectangle each Gaussian is listed in
   kNumSections
 };
 static_assert(kNumSections <= 24, "gs2d_plan::off holds 24 sections");
@@ -59,7 +60,9 @@ struct WsHeader {
   int32_t done;         // render blocks that have left the queue
   double pwd;           // lr_decay^(step - 1)
   float lr_now;         // lr * lr_decay^(step - 1)
-  int32_t pad[41];
+  int32_t lists_valid;  // the fit loop's tile lists hold every Gaussian's box
+  int32_t rebins;       // times the fit loop rebuilt its lists
+  int32_t pad[39];
 };
 static_assert(sizeof(WsHeader) == 256, "header is one 256-byte block");
 
@@ -162,47 +165,57 @@ __device__ __forceinline__ void set_status(WsHeader* h, int code) {
 // The rectangle is stored as (first tile, tile-row stride, width, height) in
 // the plan's tile numbering: tile (x0 + dx, y0 + dy) of the clip is
 // first + dy * stride + dx.
-__device__ __forceinline__ void project_one(int i, int n, const gs2d_clip& cl, int tile_shift,
-                                            float sigma_cut, float alpha_min, float det_eps,
-                                            const float* __restrict__ params,
-                                            float4* __restrict__ rec, int4* __restrict__ rect,
-                                            int* __restrict__ count) {
+// Tile rectangle [tx0, tx1) x [ty0, ty1) of Gaussian i in its clip: the pixel
+// span of the bounding box of its cut-off ellipse (sigma <= sigma_cut reaches
+// sqrt(2 sigma_cut Sxx) along x and sqrt(2 sigma_cut Syy) along y: 3 sqrt(Sxx),
+// 3 sqrt(Syy) at 4.5), widened by `margin` pixels, clipped to the clip.  false
+// when the Gaussian is culled (non-finite, degenerate, too faint) or off the
+// clip.  Single-rounded FP32 operations (the oracle's rule).
+__device__ __forceinline__ bool gaussian_tiles(int i, int n, const gs2d_clip& cl, int tile_shift,
+                                               float sigma_cut, float alpha_min, float det_eps,
+                                               const float* __restrict__ params, float margin,
+                                               int& tx0, int& ty0, int& tx1, int& ty1) {
   const int W = cl.width, H = cl.height;
   const float mx = params[i], my = params[n + i];
   const float l1 = params[2 * n + i], l2 = params[3 * n + i], l3 = params[4 * n + i];
   const float cr = params[5 * n + i], cg = params[6 * n + i], cb = params[7 * n + i];
   const float w = params[8 * n + i];
-  int4 rc = make_int4(0, 0, 0, 0);
-  int cnt = 0;
   const bool finite = isfinite(mx) && isfinite(my) && isfinite(l1) && isfinite(l2) &&
                       isfinite(l3) && isfinite(cr) && isfinite(cg) && isfinite(cb) && isfinite(w);
   const float sxx = __fmul_rn(l1, l1);
   const float syy = __fadd_rn(__fmul_rn(l2, l2), __fmul_rn(l3, l3));
   const float a = __fmul_rn(l1, l3);
   const float det = __fmul_rn(a, a);
-  if (finite && (det > det_eps) && (fabsf(w) >= alpha_min)) {
-    // the ellipse sigma <= sigma_cut reaches sqrt(2 sigma_cut Sxx) along x and
-    // sqrt(2 sigma_cut Syy) along y (3 sqrt(Sxx), 3 sqrt(Syy) at 4.5)
-    const float kc = __fsqrt_rn(__fmul_rn(2.0f, sigma_cut));
-    const float rx = ceilf(__fmul_rn(kc, __fsqrt_rn(sxx)));
-    const float ry = ceilf(__fmul_rn(kc, __fsqrt_rn(syy)));
-    float fx0 = floorf(__fsub_rn(mx, rx)), fx1 = floorf(__fadd_rn(mx, rx));
-    float fy0 = floorf(__fsub_rn(my, ry)), fy1 = floorf(__fadd_rn(my, ry));
-    fx0 = fx0 < 0.0f ? 0.0f : fx0;
-    fy0 = fy0 < 0.0f ? 0.0f : fy0;
-    fx1 = fx1 > (float)(W - 1) ? (float)(W - 1) : fx1;
-    fy1 = fy1 > (float)(H - 1) ? (float)(H - 1) : fy1;
-    if (fx0 <= fx1 && fy0 <= fy1) {
-      const int tx0 = (int)fx0 >> tile_shift, ty0 = (int)fy0 >> tile_shift;
-      const int tx1 = ((int)fx1 >> tile_shift) + 1, ty1 = ((int)fy1 >> tile_shift) + 1;
-      rc = make_int4(cl.tile_off + ty0 * cl.tiles_x + tx0, cl.tiles_x, tx1 - tx0, ty1 - ty0);
-      cnt = rc.z * rc.w;
-    }
-  }
-  rect[i] = rc;
-  count[i] = cnt;
+  if (!(finite && (det > det_eps) && (fabsf(w) >= alpha_min))) return false;
+  const float kc = __fsqrt_rn(__fmul_rn(2.0f, sigma_cut));
+  const float rx = __fadd_rn(ceilf(__fmul_rn(kc, __fsqrt_rn(sxx))), margin);
+  const float ry = __fadd_rn(ceilf(__fmul_rn(kc, __fsqrt_rn(syy))), margin);
+  float fx0 = floorf(__fsub_rn(mx, rx)), fx1 = floorf(__fadd_rn(mx, rx));
+  float fy0 = floorf(__fsub_rn(my, ry)), fy1 = floorf(__fadd_rn(my, ry));
+  fx0 = fx0 < 0.0f ? 0.0f : fx0;
+  fy0 = fy0 < 0.0f ? 0.0f : fy0;
+  fx1 = fx1 > (float)(W - 1) ? (float)(W - 1) : fx1;
+  fy1 = fy1 > (float)(H - 1) ? (float)(H - 1) : fy1;
+  if (!(fx0 <= fx1 && fy0 <= fy1)) return false;
+  tx0 = (int)fx0 >> tile_shift;
+  ty0 = (int)fy0 >> tile_shift;
+  tx1 = ((int)fx1 >> tile_shift) + 1;
+  ty1 = ((int)fy1 >> tile_shift) + 1;
+  return true;
+}
+
+// The render record of Gaussian i (zeros when it is not visible).
+__device__ __forceinline__ void write_record(int i, int n, bool visible, float sigma_cut,
+                                             float alpha_min, const float* __restrict__ params,
+                                             float4* __restrict__ rec) {
   float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
-  if (cnt > 0) {
+  if (visible) {
+    const float mx = params[i], my = params[n + i];
+    const float l1 = params[2 * n + i], l2 = params[3 * n + i], l3 = params[4 * n + i];
+    const float cr = params[5 * n + i], cg = params[6 * n + i], cb = params[7 * n + i];
+    const float w = params[8 * n + i];
+    const float sxx = __fmul_rn(l1, l1);
+    const float syy = __fadd_rn(__fmul_rn(l2, l2), __fmul_rn(l3, l3));
     const float s = 0.84932180028801904272f;  // sqrt(log2(e) / 2)
     const float log2e = 1.44269504088896340736f;
     float tau2 = fminf(sigma_cut * log2e, log2f(fabsf(w) / alpha_min));
@@ -219,6 +232,22 @@ __device__ __forceinline__ void project_one(int i, int n, const gs2d_clip& cl, i
   rec[i] = r0;
   rec[n + i] = r1;
   rec[2 * n + i] = r2;
+}
+
+__device__ __forceinline__ void project_one(int i, int n, const gs2d_clip& cl, int tile_shift,
+                                            float sigma_cut, float alpha_min, float det_eps,
+                                            const float* __restrict__ params,
+                                            float4* __restrict__ rec, int4* __restrict__ rect,
+                                            int* __restrict__ count) {
+  int tx0 = 0, ty0 = 0, tx1 = 0, ty1 = 0;
+  const bool vis = gaussian_tiles(i, n, cl, tile_shift, sigma_cut, alpha_min, det_eps, params,
+                                  0.0f, tx0, ty0, tx1, ty1);
+  const int4 rc = vis ? make_int4(cl.tile_off + ty0 * cl.tiles_x + tx0, cl.tiles_x, tx1 - tx0,
+                                  ty1 - ty0)
+                      : make_int4(0, 0, 0, 0);
+  rect[i] = rc;
+  count[i] = rc.z * rc.w;
+  write_record(i, n, vis, sigma_cut, alpha_min, params, rec);
 }
 
 __host__ __device__ inline int tile_shift_of(int tile) {
@@ -288,8 +317,9 @@ cudaError_t launch_render_bwd(const gs2d_plan& p, void* ws, const float* params,
 cudaError_t launch_render_l2(const gs2d_plan& p, void* ws, const float* params,
                              const float* target, float* grads, float* img, float* loss,
                              cudaStream_t s);
-// params_eval: the values the render used, when they differ from params (the
-// chain rule is taken there; Adam updates params)
+// Follows launch_prepare_fit (it marks retained lists valid).  params_eval:
+// the values the render used, when they differ from params (the chain rule is
+// taken there; Adam updates params)
 cudaError_t launch_fit_step(const gs2d_plan& p, void* ws, const float* target, float* params,
                             float* m, float* v, cudaStream_t s,
                             const float* params_eval = nullptr);
@@ -313,6 +343,12 @@ cudaError_t launch_pframe_step(const gs2d_plan& p, void* ws, const float* target
 // corrections advance in the same launch.
 cudaError_t launch_prepare(const gs2d_plan& p, void* ws, const float* params, bool adam_tick,
                            cudaStream_t s);
+// The fit loop's projection and binning (Adam tick included): tile lists kept
+// across iterations and rebuilt only when a Gaussian leaves them
+// (cfg.bin_margin >= 0), else launch_prepare.
+inline bool fit_lists_retained(const gs2d_config& c) { return c.bin_margin >= 0.0f; }
+cudaError_t launch_prepare_fit(const gs2d_plan& p, void* ws, const float* params,
+                               cudaStream_t s);
 
 uint64_t roi_init_scratch_bytes(int W, int H, int n);
 gs2d_status roi_init(const float* frame, const uint8_t* mask, int W, int H, int n, float roi_frac,

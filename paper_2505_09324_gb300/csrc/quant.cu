@@ -200,7 +200,7 @@ extern "C" gs2d_status gs2d_fit_step_qat(const gs2d_plan* plan, void* ws, const 
   cudaStream_t s = (cudaStream_t)stream;
   float* pq = ws_ptr<float>(ws, p, kOffQuant);
   cudaError_t e = launch_quantize(params, p.n, *q, nullptr, pq, nullptr, s);
-  if (e == cudaSuccess) e = launch_prepare(p, ws, pq, true, s);
+  if (e == cudaSuccess) e = launch_prepare_fit(p, ws, pq, s);
   if (e == cudaSuccess) e = launch_fit_step(p, ws, target, params, adam_m, adam_v, s, pq);
   if (e != cudaSuccess) return set_error(GS2D_ERR_CUDA, cudaGetErrorString(e));
   return set_error(GS2D_OK, "");

@@ -90,11 +90,13 @@ k_reduce_chain_adam(int n, float* __restrict__ params, const int* __restrict__ o
                     const float4* __restrict__ partial, const WsHeader* __restrict__ hdr,
                     float* __restrict__ m, float* __restrict__ v, float4 lr_rows, float b1,
                     float b2, float eps, const uint8_t* __restrict__ select,
-                    const float* __restrict__ params_eval) {
+                    const float* __restrict__ params_eval, WsHeader* hdr_w) {
   pdl_begin();
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = gt / kRL, sub = gt % kRL;
   const bool ok = hdr->entries_raw == (int64_t)hdr->n_entries;  // else over capacity
+  // retained lists (hdr_w set): valid for the next iteration's containment test
+  if (hdr_w && gt == 0 && ok) hdr_w->lists_valid = 1;
   // a P-frame updates only the selected Gaussians (the others keep params, m, v)
   const bool on = i < n && (!select || select[i]);
   float a[kPartials], gr[9];
@@ -322,11 +324,13 @@ cudaError_t launch_fit_step(const gs2d_plan& p, void* ws, const float* target, f
   a.target = target;
   cudaError_t e = launch_render(p, kModeL2, a, s);
   if (e != cudaSuccess || p.n == 0) return e;
+  WsHeader* hdr = ws_ptr<WsHeader>(ws, p, kOffHeader);
   return launch_pdl(k_reduce_chain_adam, (p.n * kRL + 255) / 256, 256, 0, s, p.n, params,
                     ws_ptr<int>(ws, p, kOffCount),
                     reinterpret_cast<const float4*>(ws_ptr<float>(ws, p, kOffPartial)),
-                    ws_ptr<WsHeader>(ws, p, kOffHeader), m, v, lr_rows(p.cfg), p.cfg.beta1,
-                    p.cfg.beta2, p.cfg.eps, (const uint8_t*)nullptr, params_eval);
+                    (const WsHeader*)hdr, m, v, lr_rows(p.cfg), p.cfg.beta1, p.cfg.beta2,
+                    p.cfg.eps, (const uint8_t*)nullptr, params_eval,
+                    fit_lists_retained(p.cfg) ? hdr : (WsHeader*)nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -417,7 +421,7 @@ cudaError_t launch_pframe_step(const gs2d_plan& p, void* ws, const float* target
                     ws_ptr<int>(ws, p, kOffCount),
                     reinterpret_cast<const float4*>(ws_ptr<float>(ws, p, kOffPartial)),
                     ws_ptr<WsHeader>(ws, p, kOffHeader), m, v, lr_rows(p.cfg), p.cfg.beta1,
-                    p.cfg.beta2, p.cfg.eps, select, (const float*)nullptr);
+                    p.cfg.beta2, p.cfg.eps, select, (const float*)nullptr, (WsHeader*)nullptr);
 }
 
 // Runs the one-time per-device queries of the fit loop's launches (occupancy

@@ -75,6 +75,7 @@ struct TileSmem {
 struct TileFrame {
   int tile;       // global tile id
   int W, H;       // clip size
+  int tx, ty;     // tile column and row in the clip
   int ox, oy;     // pixel origin of the tile in the clip
   int64_t pix;    // first float of the clip's image
   int2 rg;        // list range
@@ -89,6 +90,8 @@ __device__ __forceinline__ TileFrame tile_frame(const RenderArgs& a, int tile) {
   f.tile = tile;
   f.W = cl.width;
   f.H = cl.height;
+  f.tx = tx;
+  f.ty = ty;
   f.ox = tx * T;
   f.oy = ty * T;
   f.pix = cl.pix_off;
@@ -115,22 +118,30 @@ __device__ __forceinline__ void stage_batch(TileSmem<S>& sm, const RenderArgs& a
     fy0 = fmaxf(fy0, 0.0f);
     fx1 = fminf(fx1, fminf((float)(T - 1), (float)(f.W - 1) - ox));
     fy1 = fminf(fy1, fminf((float)(T - 1), (float)(f.H - 1) - oy));
+    // slot: position of this tile inside the Gaussian's (tight) rectangle.
+    // Lists kept across fit iterations may hold Gaussians whose rectangle no
+    // longer covers the tile: such a pair is empty and has no slot (-1).
+    int dx = -1, dy = -1;
+    if (rc.z > 0) {
+      const int first = rc.x - (f.tile - f.ty * rc.y - f.tx);  // y0 * stride + x0 in the clip
+      const int y0 = first / rc.y;
+      dx = f.tx - (first - y0 * rc.y);
+      dy = f.ty - y0;
+    }
+    const bool covered = (unsigned)dx < (unsigned)rc.z && (unsigned)dy < (unsigned)rc.w;
     int4 bb = make_int4(1, 0, 1, 0);
     uint32_t wm = 0;
-    if (fx0 <= fx1 && fy0 <= fy1) {
+    if (covered && fx0 <= fx1 && fy0 <= fy1) {
       bb = make_int4((int)fx0, (int)fx1, (int)fy0, (int)fy1);
       const int w0 = bb.z / G::RW, w1 = bb.w / G::RW;
       wm = ((2u << w1) - 1u) & ~((1u << w0) - 1u);
     }
-    // slot: position of this tile inside the Gaussian's rectangle
-    const int rel = f.tile - rc.x;
-    const int dy = rel / rc.y, dx = rel - dy * rc.y;
     sm.r0[k] = r0;
     sm.r1[k] = r1;
     sm.cb[k] = r2.x;
     sm.bb[k] = bb;
     sm.wmask[k] = wm;
-    sm.slot[k] = off + dy * rc.z + dx;
+    sm.slot[k] = covered ? off + dy * rc.z + dx : -1;
   }
 }
 
@@ -208,7 +219,7 @@ __device__ __forceinline__ void bwd_batch(TileSmem<S>& sm, const float4* __restr
     // Gaussians whose box misses the tile: a zero record, no reduction
     const bool empty = gi >= cnt || sm.bb[gi].x > sm.bb[gi].y;
     if (__all_sync(0xffffffffu, empty)) {
-      if (gi < cnt && j < 8) partial[8 * sm.slot[gi] + j] = 0.0f;
+      if (gi < cnt && j < 8 && sm.slot[gi] >= 0) partial[8 * sm.slot[gi] + j] = 0.0f;
       continue;
     }
     float v[8];
@@ -260,7 +271,8 @@ __device__ __forceinline__ void bwd_batch(TileSmem<S>& sm, const float4* __restr
       }
     }
     const float tot = group_transpose_sum<T>(v, j);
-    if (gi < cnt && (j % G::Q) == 0) partial[8 * sm.slot[gi] + j / G::Q] = tot;
+    if (gi < cnt && (j % G::Q) == 0 && sm.slot[gi] >= 0)
+      partial[8 * sm.slot[gi] + j / G::Q] = tot;
   }
 }
 

@@ -42,6 +42,9 @@ class RasterConfig:
     lr_color: float = 1.0
     lr_weight: float = 1.0
     lr_decay: float = 1.0
+    # fit-loop tile lists: boxes widened by this many pixels, rebuilt only when
+    # a Gaussian leaves its listed tiles (negative: every iteration)
+    bin_margin: float = 4.0
 
     @classmethod
     def fast_fit(cls, **overrides):
@@ -51,7 +54,8 @@ class RasterConfig:
     def to_c(self) -> nat.Config:
         return nat.Config(self.tile, self.sigma_cut, self.alpha_min, self.det_eps, self.lr,
                           self.beta1, self.beta2, self.eps, self.stage, self.launch, self.lr_mu,
-                          self.lr_shape, self.lr_color, self.lr_weight, self.lr_decay)
+                          self.lr_shape, self.lr_color, self.lr_weight, self.lr_decay,
+                          self.bin_margin)
 
 
 # Learning-rate schedule for fitting a frame from an initialiser (the
@@ -155,6 +159,11 @@ class GaussianRasterizer:
     def count_pairs(self, stream=None):
         """(listed pairs, contributing pairs) of the current sorted list."""
         return nat.count_pairs(self.plan, self.ws_ptr, _stream(stream))
+
+    def rebins(self, stream=None) -> int:
+        """How often the fit loop rebuilt its tile lists in this workspace
+        (since the last fit reset); see RasterConfig.bin_margin."""
+        return nat.fit_rebins(self.plan, self.ws_ptr, _stream(stream))
 
     def status(self, reset: bool = False, stream=None) -> int:
         return nat.ws_status(self.plan, self.ws_ptr, reset, _stream(stream))

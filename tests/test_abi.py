@@ -46,6 +46,12 @@ def test_default_config(nat):
     assert c.tile == 16 and c.stage == 64 and c.launch == nat.LAUNCH_GRID
     assert abs(c.sigma_cut - 4.5) < 1e-7
     assert abs(c.alpha_min - 1 / 255) < 1e-9 and abs(c.lr - 1e-2) < 1e-9
+    # the Python wrapper's defaults are the library's
+    from paper_2505_09324_gb300.raster import RasterConfig
+    rc = RasterConfig().to_c()
+    for name, _ in nat.Config._fields_:
+        assert getattr(rc, name) == getattr(c, name), name
+    assert c.bin_margin == 4.0
 
 
 def test_plan_layout(nat):
@@ -53,7 +59,7 @@ def test_plan_layout(nat):
     assert (p.tiles_x, p.tiles_y, p.num_tiles) == (120, 68, 8160)
     assert p.tile_bits == 13 and p.num_clips == 1 and p.stage == 64
     assert p.max_entries == max(1 << 20, 16 * 20000) and p.pixels == 1920 * 1080
-    offs = list(p.off)[:21]
+    offs = list(p.off)[:22]
     assert all(o % 256 == 0 for o in offs)
     assert offs == sorted(offs) and p.ws_bytes > offs[-1]
     q = nat.plan_init(16, 16, 5)
@@ -92,7 +98,7 @@ def test_batch_plan_offsets(nat):
         assert (c.g_off, c.tile_off, c.pix_off) == (g, t, 3 * px)
         g, t, px = g + n, t + c.tiles_x * c.tiles_y, px + w * h
     assert p.num_tiles == t and p.pixels == px
-    offs = list(p.off)[:21]
+    offs = list(p.off)[:22]
     assert all(o % 256 == 0 for o in offs) and offs == sorted(offs)
 
 
@@ -131,6 +137,12 @@ def test_plan_rejects_bad_config(nat):
     c.sigma_cut = -1.0
     with pytest.raises(nat.Gs2dError):
         nat.plan_init(64, 64, 10, 0, c)
+    c = nat.default_config()
+    c.bin_margin = float("nan")
+    with pytest.raises(nat.Gs2dError):
+        nat.plan_init(64, 64, 10, 0, c)
+    c.bin_margin = -1.0  # per-iteration binning
+    nat.plan_init(64, 64, 10, 0, c)
 
 
 def test_calls_reject_bad_arguments_without_touching_the_gpu(nat):
