@@ -85,8 +85,9 @@ typedef struct {
    * and the lists are rebuilt only in an iteration where some Gaussian's box
    * has left its listed tiles (checked on the device every iteration).  The
    * results are the same as binning every iteration (tiles a Gaussian does
-   * not reach contribute nothing; the widened lists need room in
-   * max_entries).  Negative: bin every iteration.  Default 4. */
+   * not reach contribute nothing; a rebuild whose widened lists would not
+   * fit max_entries lists the tight boxes instead).  Negative: bin every
+   * iteration.  Default 4. */
   float bin_margin;
 } gs2d_config;
 

@@ -175,6 +175,7 @@ gs2d_status gs2d_plan_init_batch(gs2d_plan* plan, gs2d_clip* clips, int32_t num_
   sz[kOffQuant] = 9 * nn * sizeof(float);
   sz[kOffGrad] = 9 * nn * sizeof(float);
   sz[kOffLRect] = nn * sizeof(int4);
+  sz[kOffTileCnt2] = nt * sizeof(int);
   uint64_t off = 0;
   for (int sec = 0; sec < kNumSections; sec++) {
     plan->off[sec] = off;

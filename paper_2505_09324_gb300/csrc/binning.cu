@@ -183,11 +183,15 @@ k_project_fit(int n, ClipSet cs, int tile_shift, float sigma_cut, float alpha_mi
 }
 
 // Rebuild step 1 (only when k_project_fit found a miss): the listed
-// rectangles, widened by `margin` pixels, and the per-tile entry counts.
+// rectangles, widened by `margin` pixels, and the per-tile entry counts; the
+// tight rectangles are counted too (tile_cnt2), so that the scan can fall
+// back to them when the widened lists would overflow max_entries.
 __global__ void __launch_bounds__(kGB)
 k_rebin_count(int n, ClipSet cs, int tile_shift, float sigma_cut, float alpha_min,
               float det_eps, float margin, const float* __restrict__ params,
-              int4* __restrict__ lrect, int* __restrict__ tile_cnt, WsHeader* __restrict__ hdr) {
+              const int4* __restrict__ rect, int4* __restrict__ lrect,
+              int* __restrict__ tile_cnt, int* __restrict__ tile_cnt2,
+              WsHeader* __restrict__ hdr) {
   pdl_begin();
   if (hdr->lists_valid) return;  // the same for every thread of the grid
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -203,6 +207,7 @@ k_rebin_count(int n, ClipSet cs, int tile_shift, float sigma_cut, float alpha_mi
   }
   __syncwarp();
   count_tiles_warp(n, lrect, tile_cnt);
+  count_tiles_warp(n, rect, tile_cnt2);
 }
 
 // ---------------------------------------------------------------------------
@@ -250,7 +255,8 @@ __global__ void __launch_bounds__(kGB)
 k_bin_scan(int n, int nbg, int num_tiles, int64_t max_entries, int* __restrict__ count,
            const long long* __restrict__ block_sum, int* __restrict__ tile_cnt,
            int* __restrict__ cursor, int2* __restrict__ ranges, int* __restrict__ bucket,
-           uint32_t* __restrict__ rank, WsHeader* __restrict__ hdr, int lazy) {
+           uint32_t* __restrict__ rank, WsHeader* __restrict__ hdr, int lazy,
+           const int* __restrict__ tile_cnt2) {
   pdl_begin();
   __shared__ long long warp_sum[32];
   __shared__ int s_hist[kBuckets];
@@ -283,15 +289,34 @@ k_bin_scan(int n, int nbg, int num_tiles, int64_t max_entries, int* __restrict__
   // counts are reset later, by k_sort_short, once nothing reads them)
   const int tb = (int)blockIdx.x - nbg;
   const int c0 = tb * kGB * kTileItems;
-  long long tot = 0, pre = 0;
+  long long tot = 0, pre = 0, tot2 = 0, pre2 = 0;
   for (int i = t; i < num_tiles; i += kGB) {
     const int v = tile_cnt[i];
     tot += v;
     pre += i < c0 ? v : 0;
+    if (lazy) {
+      const int v2 = tile_cnt2[i];
+      tot2 += v2;
+      pre2 += i < c0 ? v2 : 0;
+    }
   }
   long long total, prefix;
   block_scan64(tot, warp_sum, &total);
   block_scan64(pre, warp_sum, &prefix);
+  // a rebuild whose widened lists overflow lists the tight rectangles instead
+  // (the same decision in every tile CTA: the totals are global)
+  bool tight = false;
+  if (lazy) {
+    long long total2, prefix2;
+    block_scan64(tot2, warp_sum, &total2);
+    block_scan64(pre2, warp_sum, &prefix2);
+    tight = total > max_entries && total2 <= max_entries;
+    if (tight) {
+      total = total2;
+      prefix = prefix2;
+      tile_cnt = const_cast<int*>(tile_cnt2);
+    }
+  }
   const bool over = total > max_entries;
   if (t < kBuckets) s_hist[t] = 0;
   __syncthreads();
@@ -336,6 +361,7 @@ k_bin_scan(int n, int nbg, int num_tiles, int64_t max_entries, int* __restrict__
     if (over) atomicCAS(&hdr->status, 0, (int)GS2D_ERR_CAPACITY);
     if (nbg == 0) count[n] = 0;
     hdr->long_count = 0;
+    hdr->lists_tight = tight ? 1 : 0;
   }
 }
 
@@ -345,8 +371,9 @@ k_bin_scan(int n, int nbg, int num_tiles, int64_t max_entries, int* __restrict__
 constexpr int kInFlight = 4;
 
 __global__ void __launch_bounds__(kGB)
-k_bin_scatter(int n, const int4* __restrict__ rect, const WsHeader* __restrict__ hdr,
-              int* __restrict__ cursor, uint32_t* __restrict__ list, int lazy) {
+k_bin_scatter(int n, const int4* __restrict__ tight_rect, int4* __restrict__ lrect,
+              const WsHeader* __restrict__ hdr, int* __restrict__ cursor,
+              uint32_t* __restrict__ list, int lazy) {
   pdl_begin();
   __shared__ int s_start[kGB / 32][33];
   if (hdr->entries_raw != (int64_t)hdr->n_entries) return;  // over capacity
@@ -354,7 +381,12 @@ k_bin_scatter(int n, const int4* __restrict__ rect, const WsHeader* __restrict__
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int g_base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31;
   const int g = g_base + lane;
+  // the rectangles listed: widened ones, or the tight ones (eager binning, or
+  // a rebuild whose widened lists overflowed: they become the listed ones)
+  const bool use_tight = !lazy || hdr->lists_tight;
+  const int4* __restrict__ rect = use_tight ? tight_rect : (const int4*)lrect;
   const int4 rc = g < n ? rect[g] : make_int4(0, 0, 0, 0);
+  if (lazy && use_tight && g < n) lrect[g] = rc;
   const int cnt = rc.z * rc.w;
   int incl = cnt;
 #pragma unroll
@@ -454,7 +486,8 @@ __global__ void __launch_bounds__(256)
 k_sort_short(int num_tiles, const int2* __restrict__ ranges, uint32_t* __restrict__ list,
              int* __restrict__ long_tiles, int* __restrict__ tile_cnt,
              const int* __restrict__ bucket, const uint32_t* __restrict__ rank,
-             int* __restrict__ order, WsHeader* __restrict__ hdr, int lazy) {
+             int* __restrict__ order, WsHeader* __restrict__ hdr, int lazy,
+             int* __restrict__ tile_cnt2) {
   pdl_begin();
   if (lazy && hdr->lists_valid) return;
   const int lane = threadIdx.x & 31;
@@ -471,6 +504,7 @@ k_sort_short(int num_tiles, const int2* __restrict__ ranges, uint32_t* __restric
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     if (lane == 0) {
       tile_cnt[tile] = 0;
+      if (lazy) tile_cnt2[tile] = 0;
       const int q = x + (int)(rk & 0x0fffffffu);
       if (q < num_tiles)
         order[q] = tile;
@@ -570,8 +604,7 @@ cudaError_t prime_binning() {
 // Scans, scatter and segment sorts (everything after the counts); `lists`:
 // the rectangles the lists are built from; with `lazy` the tile part returns
 // at once while hdr->lists_valid is set.
-static cudaError_t launch_bin_rest(const gs2d_plan& p, void* ws, cudaStream_t s,
-                                   const int4* lists, int lazy) {
+static cudaError_t launch_bin_rest(const gs2d_plan& p, void* ws, cudaStream_t s, int lazy) {
   WsHeader* hdr = ws_ptr<WsHeader>(ws, p, kOffHeader);
   int* count = ws_ptr<int>(ws, p, kOffCount);
   int* tile_cnt = ws_ptr<int>(ws, p, kOffTileCnt);
@@ -582,18 +615,20 @@ static cudaError_t launch_bin_rest(const gs2d_plan& p, void* ws, cudaStream_t s,
   int* bucket = ws_ptr<int>(ws, p, kOffBucket);
   int* order = ws_ptr<int>(ws, p, kOffOrder);
   uint32_t* rank = ws_ptr<uint32_t>(ws, p, kOffRank);
+  int* tile_cnt2 = ws_ptr<int>(ws, p, kOffTileCnt2);
   const int nbg = (p.n + kGB - 1) / kGB;
   const int nbt = (p.num_tiles + kGB * kTileItems - 1) / (kGB * kTileItems);
   cudaError_t e = prime_binning();
   if (e == cudaSuccess)
     e = launch_pdl(k_bin_scan, nbg + nbt, kGB, 0, s, p.n, nbg, p.num_tiles, p.max_entries, count,
                    ws_ptr<long long>(ws, p, kOffBlockSum), tile_cnt, cursor, ranges, bucket,
-                   rank, hdr, lazy);
+                   rank, hdr, lazy, (const int*)tile_cnt2);
   if (e == cudaSuccess && p.n > 0)
-    e = launch_pdl(k_bin_scatter, nbg, kGB, 0, s, p.n, lists, hdr, cursor, list, lazy);
+    e = launch_pdl(k_bin_scatter, nbg, kGB, 0, s, p.n, (const int4*)ws_ptr<int4>(ws, p, kOffRect),
+                   ws_ptr<int4>(ws, p, kOffLRect), hdr, cursor, list, lazy);
   if (e == cudaSuccess)
     e = launch_pdl(k_sort_short, (p.num_tiles + 7) / 8, 256, 0, s, p.num_tiles, ranges, list,
-                   long_tiles, tile_cnt, bucket, rank, order, hdr, lazy);
+                   long_tiles, tile_cnt, bucket, rank, order, hdr, lazy, tile_cnt2);
   if (e == cudaSuccess)
     e = launch_pdl(k_sort_long, 152, 1024, kLongMax * sizeof(uint32_t), s, ranges, list,
                    long_tiles, bucket, hdr, lazy);
@@ -608,7 +643,7 @@ cudaError_t launch_bin_sort(const gs2d_plan& p, void* ws, cudaStream_t s) {
                    ws_ptr<int>(ws, p, kOffTileCnt), ws_ptr<long long>(ws, p, kOffBlockSum),
                    ws_ptr<WsHeader>(ws, p, kOffHeader));
   if (e != cudaSuccess) return e;
-  return launch_bin_rest(p, ws, s, ws_ptr<int4>(ws, p, kOffRect), 0);
+  return launch_bin_rest(p, ws, s, 0);
 }
 
 cudaError_t launch_prepare(const gs2d_plan& p, void* ws, const float* params, bool adam_tick,
@@ -622,7 +657,7 @@ cudaError_t launch_prepare(const gs2d_plan& p, void* ws, const float* params, bo
       ws_ptr<WsHeader>(ws, p, kOffHeader), adam_tick ? 1 : 0, p.cfg.beta1, p.cfg.beta2, p.cfg.lr,
       p.cfg.lr_decay);
   if (e != cudaSuccess) return e;
-  return launch_bin_rest(p, ws, s, ws_ptr<int4>(ws, p, kOffRect), 0);
+  return launch_bin_rest(p, ws, s, 0);
 }
 
 cudaError_t launch_prepare_fit(const gs2d_plan& p, void* ws, const float* params,
@@ -642,9 +677,10 @@ cudaError_t launch_prepare_fit(const gs2d_plan& p, void* ws, const float* params
   if (e == cudaSuccess)
     e = launch_pdl(k_rebin_count, blocks > 0 ? blocks : 1, kGB, 0, s, p.n, cs, shift,
                    p.cfg.sigma_cut, p.cfg.alpha_min, p.cfg.det_eps, p.cfg.bin_margin, params,
-                   lrect, ws_ptr<int>(ws, p, kOffTileCnt), hdr);
+                   (const int4*)ws_ptr<int4>(ws, p, kOffRect), lrect,
+                   ws_ptr<int>(ws, p, kOffTileCnt), ws_ptr<int>(ws, p, kOffTileCnt2), hdr);
   if (e != cudaSuccess) return e;
-  return launch_bin_rest(p, ws, s, lrect, 1);
+  return launch_bin_rest(p, ws, s, 1);
 }
 
 }  // namespace gs2d

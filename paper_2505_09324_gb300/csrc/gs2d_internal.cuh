@@ -42,6 +42,8 @@ enum WsSection {
   kOffQuant,        // float[9 n] quantisation-aware fitting: the fake-quantised parameters
   kOffGrad,         // float[9 n] gradient scratch
   kOffLRect,        // int4[n]  fit loop: the (widened) rectangle each Gaussian is listed in
+  kOffTileCnt2,     // int32[num_tiles]  fit loop: tight-rectangle entries per tile (zero
+                    //                   between calls; the fallback of a list rebuild)
   kNumSections
 };
 static_assert(kNumSections <= 24, "gs2d_plan::off holds 24 sections");
@@ -62,7 +64,8 @@ struct WsHeader {
   float lr_now;         // lr * lr_decay^(step - 1)
   int32_t lists_valid;  // the fit loop's tile lists hold every Gaussian's box
   int32_t rebins;       // times the fit loop rebuilt its lists
-  int32_t pad[39];
+  int32_t lists_tight;  // the last rebuild listed tight rectangles (widened ones overflowed)
+  int32_t pad[38];
 };
 static_assert(sizeof(WsHeader) == 256, "header is one 256-byte block");
 

@@ -160,21 +160,28 @@ def test_interleaved_eager_binning_invalidates_lists(gs):
     assert outs[1][4] >= 4  # one rebuild after each interleaved prepare
 
 
-def test_widened_lists_over_capacity_are_reported(gs):
-    """A plan sized for the tight lists but not the widened ones: the fit
-    step reports GS2D_ERR_CAPACITY and leaves the parameters untouched."""
+def test_widened_lists_over_capacity_fall_back_to_tight_lists(gs):
+    """A plan sized for the tight lists but not the widened ones: each rebuild
+    lists the tight rectangles instead, with the results of per-iteration
+    binning; a plan too small for the tight lists reports GS2D_ERR_CAPACITY
+    and leaves the parameters untouched."""
     from paper_2505_09324_gb300 import _native as nat
-    W, H, n = 128, 128, 300
+    W, H, n, steps = 128, 128, 300, 12
     p0 = random_gaussians(n, W, H, seed=51, l_range=(1.0, 4.0))
     target = smooth_noise_target(W, H, seed=52)
     probe = gs.GaussianRasterizer(W, H, n, config=gs.RasterConfig(tile=8))
     probe.prepare(to_dev(p0))
     tight = probe.read_bins()["n_entries"]
+    ref = fit_steps(gs, gs.RasterConfig(tile=8, bin_margin=-1.0), p0, target, steps, W, H,
+                    max_entries=2 * tight)
+    assert ref[3].status() == 0
+    got = fit_steps(gs, gs.RasterConfig(tile=8, bin_margin=24.0), p0, target, steps, W, H,
+                    max_entries=2 * tight)
+    assert got[3].status() == 0
+    assert_same(got[:3], ref[:3])
+    assert got[3].rebins() >= 1
+    # too small for the tight lists too
     p, m, v, r = fit_steps(gs, gs.RasterConfig(tile=8, bin_margin=24.0), p0, target, 1, W, H,
-                           max_entries=tight)
+                           max_entries=tight - 1)
     assert r.status() == nat.GS2D_ERR_CAPACITY
     assert torch.equal(p, to_dev(p0))
-    # the same plan without widening fits
-    p, m, v, r = fit_steps(gs, gs.RasterConfig(tile=8, bin_margin=-1.0), p0, target, 1, W, H,
-                           max_entries=tight)
-    assert r.status() == 0 and not torch.equal(p, to_dev(p0))
