@@ -185,3 +185,35 @@ def test_widened_lists_over_capacity_fall_back_to_tight_lists(gs):
                            max_entries=tight - 1)
     assert r.status() == nat.GS2D_ERR_CAPACITY
     assert torch.equal(p, to_dev(p0))
+
+
+@pytest.mark.parametrize("tile,fast", [(8, False), (16, True), (32, False), (32, True)])
+def test_fit_step_equals_pframe_step_with_everything_selected(gs, tile, fast):
+    """The fit step (retained widened lists, every tile rendered) and the
+    P-frame step with every Gaussian selected (tight lists rebuilt each step,
+    only the tiles some Gaussian covers rendered, the masked update) must give
+    the same Gaussians and moments bit for bit, step after step, on a frame
+    of many tiles per Gaussian."""
+    from paper_2505_09324_gb300 import _native as nat
+    W, H, n, steps = 640, 360, 5000, 8
+    p0 = random_gaussians(n, W, H, seed=53, l_range=(1.0, 24.0))
+    t = to_dev(smooth_noise_target(W, H, seed=54))
+    mk = gs.RasterConfig.fast_fit if fast else gs.RasterConfig
+    r = gs.GaussianRasterizer(W, H, n, config=mk(tile=tile))
+    s = int(torch.cuda.current_stream().cuda_stream)
+    a, b = to_dev(p0), to_dev(p0)
+    ma, va, mb, vb = (torch.empty_like(a) for _ in range(4))
+    sel = torch.ones(n, dtype=torch.uint8, device="cuda")
+    nat.fit_reset(r.plan, r.ws_ptr, ma.data_ptr(), va.data_ptr(), s)
+    for _ in range(steps):
+        nat.fit_step(r.plan, r.ws_ptr, t.data_ptr(), a.data_ptr(), ma.data_ptr(), va.data_ptr(),
+                     s)
+    r2 = gs.GaussianRasterizer(W, H, n, config=mk(tile=tile))
+    nat.fit_reset(r2.plan, r2.ws_ptr, mb.data_ptr(), vb.data_ptr(), s)
+    for _ in range(steps):
+        nat.pframe_step(r2.plan, r2.ws_ptr, t.data_ptr(), b.data_ptr(), mb.data_ptr(),
+                        vb.data_ptr(), sel.data_ptr(), s)
+    torch.cuda.synchronize()
+    assert r.status() == 0 and r2.status() == 0
+    assert_same((a, ma, va), (b, mb, vb))
+    assert not torch.equal(a, to_dev(p0))
