@@ -414,6 +414,44 @@ def calibrated_quantizer(dev, config, iters=100):
     return Quantizer.calibrate(calib)
 
 
+def measure_reductions(dev, config, frame, params0, iters=300):
+    """Fit iteration time with each backward reduction at the chosen schedule:
+    per-pair records summed in a fixed order (the default, bit-reproducible)
+    and float atomics into per-Gaussian sums; CUDA events over `iters`
+    launched steps from the initialiser's output (no L2 flush: a relative
+    comparison)."""
+    import torch
+
+    from paper_2505_09324_gb300 import GaussianRasterizer
+    from paper_2505_09324_gb300 import _native as nat
+    out = {}
+    for name, red in (("slots", nat.REDUCE_SLOTS), ("atomic", nat.REDUCE_ATOMIC)):
+        r = GaussianRasterizer(W, H, N_GAUSS, device=dev,
+                               config=dataclasses.replace(config, reduce=red))
+        p = params0.clone()
+        m, v = torch.empty_like(p), torch.empty_like(p)
+        s = int(torch.cuda.current_stream(dev).cuda_stream)
+        nat.fit_reset(r.plan, r.ws_ptr, m.data_ptr(), v.data_ptr(), s)
+        step = lambda: nat.fit_step(r.plan, r.ws_ptr, frame.data_ptr(), p.data_ptr(),  # noqa
+                                    m.data_ptr(), v.data_ptr(), s)
+        for _ in range(5):
+            step()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        a.record()
+        for _ in range(iters):
+            step()
+        b.record()
+        torch.cuda.synchronize(dev)
+        if r.status() != 0:
+            raise RuntimeError(f"device status {r.status()} in the reduction comparison")
+        out[name] = {"ms_per_iter": a.elapsed_time(b) / iters,
+                     "psnr_after": r.psnr(frame, p)}
+    out["note"] = ("fit_step launched back to back from the ROI initialisation, "
+                   f"{iters} iterations per variant, L2 not flushed")
+    return out
+
+
 def measure_quant(args, dev, config, frame, mask, bg_xy, q):
     """Quantisation of the fitted Gaussians (Sec. 3.3 A; Table 3 compares the
     latency PTQ and QAT add to 1000 fitting iterations).  PTQ ranges are
@@ -846,6 +884,8 @@ def run_ours(args):
     learned = None if args.no_learned else measure_learned(dev, frame, mask, peaks)
     quant = None if args.no_quant else measure_quant(args, dev, tuned["config"], frame, mask,
                                                      bg_xy, quantizer)
+    reductions = None if args.no_encode else measure_reductions(dev, tuned["config"], frame,
+                                                                params0)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -885,7 +925,7 @@ def run_ours(args):
                 "pairs": {"listed_first": pairs0, "hits_first": hits0, "listed_last": pairs1,
                           "hits_last": hits1},
                 "encode": encode, "batch": batch, "sequence": seq, "learned_init": learned,
-                "quantisation": quant}
+                "quantisation": quant, "reductions": reductions}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

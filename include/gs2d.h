@@ -68,8 +68,8 @@ typedef struct {
   float alpha_min;   /* minimum |w| exp(-sigma), > 0 */
   float det_eps;     /* minimum det Sigma, >= 0 */
   float lr, beta1, beta2, eps; /* Adam */
-  int32_t stage;     /* Gaussians staged per shared-memory batch: 32, 64 or 128
-                        (0 means 64) */
+  int32_t stage;     /* Gaussians staged per shared-memory batch: 32, 64, 128
+                        or 256 (0 means 64) */
   int32_t launch;    /* render launch form: GS2D_LAUNCH_PERSISTENT (one wave of
                         blocks taking tiles from a queue) or GS2D_LAUNCH_GRID
                         (one block per tile, in queue order) */
@@ -89,9 +89,16 @@ typedef struct {
    * fit max_entries lists the tight boxes instead).  Negative: bin every
    * iteration.  Default 4. */
   float bin_margin;
+  /* Backward reduction to per-Gaussian sums: GS2D_REDUCE_SLOTS (default: one
+   * record per (tile, Gaussian) pair, summed per Gaussian in a fixed order,
+   * so every result is reproducible bit for bit) or GS2D_REDUCE_ATOMIC
+   * (floating-point atomic additions into per-Gaussian sums: the same sums
+   * up to the order of the additions, which varies from run to run). */
+  int32_t reduce;
 } gs2d_config;
 
 enum { GS2D_LAUNCH_PERSISTENT = 0, GS2D_LAUNCH_GRID = 1 };
+enum { GS2D_REDUCE_SLOTS = 0, GS2D_REDUCE_ATOMIC = 1 };
 
 /* One clip of a batch: a W x H frame fitted by n Gaussians.  The caller sets
  * width, height and n; gs2d_plan_init_batch fills the rest.  A batch stores
@@ -138,7 +145,7 @@ size_t gs2d_sizeof_config(void);
 /* Lays out a workspace for a W x H frame and n Gaussians with room for
  * max_entries (tile, Gaussian) pairs (0 picks max(2^20, 16 n), 64 n for tile 8).
  * cfg may be NULL (defaults).  Host only; no CUDA call.
- * Errors: W, H < 1, n < 0, tile not 8, 16 or 32, stage not 0, 32, 64 or 128,
+ * Errors: W, H < 1, n < 0, tile not 8, 16 or 32, stage not 0, 32, 64, 128 or 256,
  * unknown launch form, non-positive constants. */
 gs2d_status gs2d_plan_init(gs2d_plan* plan, int32_t width, int32_t height, int32_t n,
                            int64_t max_entries, const gs2d_config* cfg);
@@ -460,7 +467,8 @@ gs2d_status gs2d_encode_batch(const gs2d_plan* plan, void* ws, const float* targ
  * host, widths, heights and n set (the other fields are overwritten).
  * params: device 9 n_total floats; targets: device, batch image layout.
  * tiles, stages, launches: host candidate lists (tile 8, 16 or 32; stage 32,
- * 64 or 128; launch GS2D_LAUNCH_*).  ws: device scratch of
+ * 64, 128 or 256; launch GS2D_LAUNCH_*).  cfg (or the defaults) gives every
+ * other field, the backward reduction included.  ws: device scratch of
  * gs2d_autotune_ws_bytes bytes (contents are overwritten).  reps timed
  * iterations per candidate after two warm-up iterations.  ms: host,
  * num_tiles_c x num_stages x num_launches floats out (row-major: tile, then

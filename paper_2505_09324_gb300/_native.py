@@ -55,11 +55,14 @@ class Config(ctypes.Structure):
                 ("eps", ctypes.c_float), ("stage", ctypes.c_int32), ("launch", ctypes.c_int32),
                 ("lr_mu", ctypes.c_float), ("lr_shape", ctypes.c_float),
                 ("lr_color", ctypes.c_float), ("lr_weight", ctypes.c_float),
-                ("lr_decay", ctypes.c_float), ("bin_margin", ctypes.c_float)]
+                ("lr_decay", ctypes.c_float), ("bin_margin", ctypes.c_float),
+                ("reduce", ctypes.c_int32)]
 
 
 LAUNCH_PERSISTENT = 0
 LAUNCH_GRID = 1
+REDUCE_SLOTS = 0
+REDUCE_ATOMIC = 1
 
 
 class Clip(ctypes.Structure):

@@ -45,7 +45,7 @@ gs2d_status check_plan(const gs2d_plan* p, const void* ws) {
 
 bool cfg_valid(const gs2d_config& c) {
   return (c.tile == 8 || c.tile == 16 || c.tile == 32) &&
-         (c.stage == 0 || c.stage == 32 || c.stage == 64 || c.stage == 128) &&
+         (c.stage == 0 || c.stage == 32 || c.stage == 64 || c.stage == 128 || c.stage == 256) &&
          (c.launch == GS2D_LAUNCH_PERSISTENT || c.launch == GS2D_LAUNCH_GRID) &&
          c.sigma_cut > 0.0f && isfinite(c.sigma_cut) && c.alpha_min > 0.0f &&
          isfinite(c.alpha_min) && c.det_eps >= 0.0f && isfinite(c.det_eps) && c.lr > 0.0f &&
@@ -53,7 +53,8 @@ bool cfg_valid(const gs2d_config& c) {
          c.beta2 < 1.0f && c.eps > 0.0f && isfinite(c.eps) && c.lr_mu >= 0.0f &&
          isfinite(c.lr_mu) && c.lr_shape >= 0.0f && isfinite(c.lr_shape) && c.lr_color >= 0.0f &&
          isfinite(c.lr_color) && c.lr_weight >= 0.0f && isfinite(c.lr_weight) &&
-         c.lr_decay > 0.0f && c.lr_decay <= 1.0f && isfinite(c.bin_margin);
+         c.lr_decay > 0.0f && c.lr_decay <= 1.0f && isfinite(c.bin_margin) &&
+         (c.reduce == GS2D_REDUCE_SLOTS || c.reduce == GS2D_REDUCE_ATOMIC);
 }
 
 }  // namespace
@@ -82,6 +83,7 @@ void gs2d_config_default(gs2d_config* cfg) {
   cfg->lr_mu = cfg->lr_shape = cfg->lr_color = cfg->lr_weight = 1.0f;
   cfg->lr_decay = 1.0f;
   cfg->bin_margin = 4.0f;
+  cfg->reduce = GS2D_REDUCE_SLOTS;
 }
 
 size_t gs2d_sizeof_plan(void) { return sizeof(gs2d_plan); }
@@ -108,7 +110,8 @@ gs2d_status gs2d_plan_init_batch(gs2d_plan* plan, gs2d_clip* clips, int32_t num_
   gs2d_config_default(&c);
   if (cfg) c = *cfg;
   if (!cfg_valid(c))
-    return fail(GS2D_ERR_INVALID_ARG, "invalid config (tile 8, 16 or 32; stage 0, 32, 64 or 128)");
+    return fail(GS2D_ERR_INVALID_ARG,
+                "invalid config (tile 8, 16 or 32; stage 0, 32, 64, 128 or 256; reduce 0 or 1)");
   if (c.stage == 0) c.stage = kStageDefault;
   const int T = c.tile;
   int64_t n_total = 0, tiles = 0, pixels = 0;
@@ -176,6 +179,7 @@ gs2d_status gs2d_plan_init_batch(gs2d_plan* plan, gs2d_clip* clips, int32_t num_
   sz[kOffGrad] = 9 * nn * sizeof(float);
   sz[kOffLRect] = nn * sizeof(int4);
   sz[kOffTileCnt2] = nt * sizeof(int);
+  sz[kOffAcc] = 8 * nn * sizeof(float);
   uint64_t off = 0;
   for (int sec = 0; sec < kNumSections; sec++) {
     plan->off[sec] = off;

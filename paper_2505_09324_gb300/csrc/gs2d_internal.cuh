@@ -44,6 +44,8 @@ enum WsSection {
   kOffLRect,        // int4[n]  fit loop: the (widened) rectangle each Gaussian is listed in
   kOffTileCnt2,     // int32[num_tiles]  fit loop: tight-rectangle entries per tile (zero
                     //                   between calls; the fallback of a list rebuild)
+  kOffAcc,          // float[n][kPartials]  GS2D_REDUCE_ATOMIC: per-Gaussian backward sums
+                    //                      (zero between calls)
   kNumSections
 };
 static_assert(kNumSections <= 24, "gs2d_plan::off holds 24 sections");
@@ -289,6 +291,8 @@ struct RenderArgs {
   const float* frame;    // select: current frame
   float threshold;       // select: change threshold on max_c |ref - frame|
   uint8_t* selected;     // select: per-Gaussian flag out
+  float* acc;            // bwd, l2 with GS2D_REDUCE_ATOMIC: per-Gaussian sums (else NULL:
+                         // one record per pair in `partial`)
 };
 
 // One instantiation set per tile edge (render_t8.cu, render_t16.cu, render_t32.cu).

@@ -67,16 +67,44 @@ __device__ __forceinline__ bool gather_partials(const float4* __restrict__ parti
   return s1 > s0;
 }
 
+// GS2D_REDUCE_ATOMIC: the render added the Gaussian's sums up itself; every
+// lane of the group reads them, then lane 0 clears them for the next pass.
+// `any`: the Gaussian had a (tile, Gaussian) pair.  Every lane of the warp
+// must take part.
+__device__ __forceinline__ bool gather_acc(float* __restrict__ acc, const int* __restrict__ offs,
+                                           int i, bool valid, int sub, float a[kPartials]) {
+  bool any = false;
+#pragma unroll
+  for (int k = 0; k < kPartials; k++) a[k] = 0.0f;
+  float4* q = reinterpret_cast<float4*>(acc + (size_t)kPartials * i);
+  if (valid) {
+    const float4 x = q[0], y = q[1];
+    a[0] = x.x;
+    a[1] = x.y;
+    a[2] = x.z;
+    a[3] = x.w;
+    a[4] = y.x;
+    a[5] = y.y;
+    a[6] = y.z;
+    a[7] = y.w;
+    any = offs[i + 1] > offs[i];
+  }
+  __syncwarp();  // every lane of the group has read the sums
+  if (valid && sub == 0) q[0] = q[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+  return any;
+}
+
 __global__ void __launch_bounds__(256)
 k_reduce_chain(int n, const float* __restrict__ params, const int* __restrict__ offs,
                const float4* __restrict__ partial, const WsHeader* __restrict__ hdr,
-               float* __restrict__ grads) {
+               float* __restrict__ grads, float* __restrict__ acc) {
   pdl_begin();
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = gt / kRL, sub = gt % kRL;
   const bool valid = i < n && hdr->entries_raw == (int64_t)hdr->n_entries;
   float a[kPartials], gr[9];
-  const bool any = gather_partials(partial, offs, i, valid, sub, a);
+  const bool any = acc ? gather_acc(acc, offs, i, valid, sub, a)
+                       : gather_partials(partial, offs, i, valid, sub, a);
   if (i >= n) return;
   if (any) chain_grads(params, n, i, a, gr);
 #pragma unroll
@@ -90,7 +118,8 @@ k_reduce_chain_adam(int n, float* __restrict__ params, const int* __restrict__ o
                     const float4* __restrict__ partial, const WsHeader* __restrict__ hdr,
                     float* __restrict__ m, float* __restrict__ v, float4 lr_rows, float b1,
                     float b2, float eps, const uint8_t* __restrict__ select,
-                    const float* __restrict__ params_eval, WsHeader* hdr_w) {
+                    const float* __restrict__ params_eval, WsHeader* hdr_w,
+                    float* __restrict__ acc) {
   pdl_begin();
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = gt / kRL, sub = gt % kRL;
@@ -100,7 +129,10 @@ k_reduce_chain_adam(int n, float* __restrict__ params, const int* __restrict__ o
   // a P-frame updates only the selected Gaussians (the others keep params, m, v)
   const bool on = i < n && (!select || select[i]);
   float a[kPartials], gr[9];
-  const bool any = gather_partials(partial, offs, i, on && ok, sub, a);
+  // (atomic sums are read and cleared for every Gaussian: an unselected one
+  // of a rendered tile has sums too)
+  const bool any = acc ? gather_acc(acc, offs, i, i < n && ok, sub, a) && on
+                       : gather_partials(partial, offs, i, on && ok, sub, a);
   if (!ok) return;  // the same for every thread of the grid
   const bool act = on;
   // the chain rule at the parameters that were rendered (the fake-quantised
@@ -228,6 +260,11 @@ static float4 lr_rows(const gs2d_config& c) {
   return make_float4(c.lr_mu, c.lr_shape, c.lr_color, c.lr_weight);
 }
 
+// The per-Gaussian sums of GS2D_REDUCE_ATOMIC, or NULL (per-pair records).
+static float* atomic_sums(const gs2d_plan& p, void* ws) {
+  return p.cfg.reduce == GS2D_REDUCE_ATOMIC ? ws_ptr<float>(ws, p, kOffAcc) : nullptr;
+}
+
 static RenderArgs render_args(const gs2d_plan& p, void* ws) {
   RenderArgs a;
   a.clips = clip_set(p, ws);
@@ -250,6 +287,7 @@ static RenderArgs render_args(const gs2d_plan& p, void* ws) {
   a.frame = nullptr;
   a.threshold = 0.0f;
   a.selected = nullptr;
+  a.acc = atomic_sums(p, ws);
   return a;
 }
 
@@ -269,7 +307,7 @@ static cudaError_t launch_reduce(const gs2d_plan& p, void* ws, const float* para
   return launch_pdl(k_reduce_chain, (p.n * kRL + 255) / 256, 256, 0, s, p.n, params,
                     ws_ptr<int>(ws, p, kOffCount),
                     reinterpret_cast<const float4*>(ws_ptr<float>(ws, p, kOffPartial)),
-                    ws_ptr<WsHeader>(ws, p, kOffHeader), grads);
+                    ws_ptr<WsHeader>(ws, p, kOffHeader), grads, atomic_sums(p, ws));
 }
 
 cudaError_t launch_render_fwd(const gs2d_plan& p, void* ws, float* img, cudaStream_t s) {
@@ -330,7 +368,7 @@ cudaError_t launch_fit_step(const gs2d_plan& p, void* ws, const float* target, f
                     reinterpret_cast<const float4*>(ws_ptr<float>(ws, p, kOffPartial)),
                     (const WsHeader*)hdr, m, v, lr_rows(p.cfg), p.cfg.beta1, p.cfg.beta2,
                     p.cfg.eps, (const uint8_t*)nullptr, params_eval,
-                    fit_lists_retained(p.cfg) ? hdr : (WsHeader*)nullptr);
+                    fit_lists_retained(p.cfg) ? hdr : (WsHeader*)nullptr, atomic_sums(p, ws));
 }
 
 // ---------------------------------------------------------------------------
@@ -421,7 +459,8 @@ cudaError_t launch_pframe_step(const gs2d_plan& p, void* ws, const float* target
                     ws_ptr<int>(ws, p, kOffCount),
                     reinterpret_cast<const float4*>(ws_ptr<float>(ws, p, kOffPartial)),
                     ws_ptr<WsHeader>(ws, p, kOffHeader), m, v, lr_rows(p.cfg), p.cfg.beta1,
-                    p.cfg.beta2, p.cfg.eps, select, (const float*)nullptr, (WsHeader*)nullptr);
+                    p.cfg.beta2, p.cfg.eps, select, (const float*)nullptr, (WsHeader*)nullptr,
+                    atomic_sums(p, ws));
 }
 
 // Runs the one-time per-device queries of the fit loop's launches (occupancy

@@ -202,12 +202,17 @@ __device__ __forceinline__ float group_transpose_sum(const float (&v)[8], int j)
   return y;
 }
 
-// Backward over staged Gaussians [0, cnt); g (dL/dC) of the tile in s_g.
+// Backward over staged Gaussians [0, cnt) (entries batch[0 .. cnt) of the
+// tile's list); g (dL/dC) of the tile in s_g.  Each pair's eight sums go to
+// its slot of `partial`, or with `acc` (GS2D_REDUCE_ATOMIC) are added to the
+// Gaussian's sums by float atomics (pairs whose box misses the tile add
+// nothing).
 template <int T, int S>
 __device__ __forceinline__ void bwd_batch(TileSmem<S>& sm, const float4* __restrict__ s_g,
-                                          int cnt, float ox, float oy,
-                                          float* __restrict__ partial) {
+                                          int cnt, float ox, float oy, const RenderArgs& a,
+                                          int b) {
   using G = TileGeom<T>;
+  float* __restrict__ partial = a.partial;
   const int lane = threadIdx.x & 31;
   const int h = lane / T, j = lane % T;
   for (;;) {  // warps take the next GPW Gaussians as they finish (balance)
@@ -219,7 +224,7 @@ __device__ __forceinline__ void bwd_batch(TileSmem<S>& sm, const float4* __restr
     // Gaussians whose box misses the tile: a zero record, no reduction
     const bool empty = gi >= cnt || sm.bb[gi].x > sm.bb[gi].y;
     if (__all_sync(0xffffffffu, empty)) {
-      if (gi < cnt && j < 8 && sm.slot[gi] >= 0) partial[8 * sm.slot[gi] + j] = 0.0f;
+      if (!a.acc && gi < cnt && j < 8 && sm.slot[gi] >= 0) partial[8 * sm.slot[gi] + j] = 0.0f;
       continue;
     }
     float v[8];
@@ -271,17 +276,22 @@ __device__ __forceinline__ void bwd_batch(TileSmem<S>& sm, const float4* __restr
       }
     }
     const float tot = group_transpose_sum<T>(v, j);
-    if (gi < cnt && (j % G::Q) == 0 && sm.slot[gi] >= 0)
-      partial[8 * sm.slot[gi] + j / G::Q] = tot;
+    if (gi < cnt && (j % G::Q) == 0 && sm.slot[gi] >= 0) {
+      if (!a.acc)
+        partial[8 * sm.slot[gi] + j / G::Q] = tot;
+      else if (sm.bb[gi].x <= sm.bb[gi].y)
+        atomicAdd(&a.acc[(size_t)kPartials * a.list[b + gi] + j / G::Q], tot);
+    }
   }
 }
 
 // Per-mode shared memory beyond the staged batch.
-template <int T, int MODE>
+template <int T, int S, int MODE>
 struct ModeSmem {
+  static_assert(S <= 256, "per-warp list entries are 8-bit batch positions");
   static constexpr int kGrad = (MODE == kModeBwd || MODE == kModeL2) ? T * T : 1;
   float4 g[kGrad];                 // dL/dC of the tile
-  uint8_t wl[TileGeom<T>::NW][128];  // per-warp lists of the staged batch
+  uint8_t wl[TileGeom<T>::NW][S];  // per-warp lists of the staged batch
   float2 red[TileGeom<T>::NW];     // loss partials per warp
   unsigned hits;                   // kModeCount
 };
@@ -305,7 +315,7 @@ __device__ __forceinline__ int warp_list(const TileSmem<S>& sm, int cnt, int wid
 
 template <int T, int S, int MODE>
 __device__ __forceinline__ void process_tile(const RenderArgs& a, const TileFrame& f,
-                                             TileSmem<S>& sm, ModeSmem<T, MODE>& ms) {
+                                             TileSmem<S>& sm, ModeSmem<T, S, MODE>& ms) {
   using G = TileGeom<T>;
   constexpr int R = G::R;
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
@@ -333,7 +343,7 @@ __device__ __forceinline__ void process_tile(const RenderArgs& a, const TileFram
       __syncthreads();
       stage_batch<T, S>(sm, a, f, b, cnt);
       __syncthreads();
-      bwd_batch<T, S>(sm, ms.g, cnt, ox, oy, a.partial);
+      bwd_batch<T, S>(sm, ms.g, cnt, ox, oy, a, b);
     }
     return;
   }
@@ -486,7 +496,7 @@ __device__ __forceinline__ void process_tile(const RenderArgs& a, const TileFram
         __syncthreads();
         staged = b;
       }
-      bwd_batch<T, S>(sm, ms.g, cnt, ox, oy, a.partial);
+      bwd_batch<T, S>(sm, ms.g, cnt, ox, oy, a, b);
     }
   }
 }
@@ -501,7 +511,7 @@ template <int T, int S, int MODE, int LAUNCH>
 __global__ void __launch_bounds__(TileGeom<T>::NT, kMinBlocks<T>) k_render(RenderArgs a) {
   pdl_begin();
   __shared__ TileSmem<S> sm;
-  __shared__ ModeSmem<T, MODE> ms;
+  __shared__ ModeSmem<T, S, MODE> ms;
   if constexpr (LAUNCH == GS2D_LAUNCH_GRID) {
     if (a.active && (int)blockIdx.x >= *a.active) return;  // a P-frame's subset
     const int tile = a.order[blockIdx.x];
@@ -573,6 +583,7 @@ cudaError_t launch_tile(int stage, int launch, RenderMode mode, const RenderArgs
     case 32: return launch_stage<T, 32>(launch, mode, a, s);
     case 64: return launch_stage<T, 64>(launch, mode, a, s);
     case 128: return launch_stage<T, 128>(launch, mode, a, s);
+    case 256: return launch_stage<T, 256>(launch, mode, a, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -588,6 +599,7 @@ cudaError_t prime_tile(int stage, int launch) {
     case 32: g = persistent_grid((const void*)k_render<T, 32, kModeL2, P>, NT, 1); break;
     case 64: g = persistent_grid((const void*)k_render<T, 64, kModeL2, P>, NT, 1); break;
     case 128: g = persistent_grid((const void*)k_render<T, 128, kModeL2, P>, NT, 1); break;
+    case 256: g = persistent_grid((const void*)k_render<T, 256, kModeL2, P>, NT, 1); break;
     default: return cudaErrorInvalidValue;
   }
   return g > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;

@@ -23,7 +23,7 @@ class RasterConfig:
     """Constants of the rasterizer and the optimiser (project readings; the paper
     fixes none): tile 16, stage 64, sigma <= 4.5, |alpha| >= 1/255,
     det Sigma > 1e-8, Adam lr 1e-2, betas (0.9, 0.999), eps 1e-8.  tile (8, 16,
-    32), stage (32, 64, 128 Gaussians per shared-memory batch) and launch
+    32), stage (32, 64, 128, 256 Gaussians per shared-memory batch) and launch
     (persistent queue or one block per tile) choose the render schedule only."""
 
     tile: int = 16
@@ -45,6 +45,9 @@ class RasterConfig:
     # fit-loop tile lists: boxes widened by this many pixels, rebuilt only when
     # a Gaussian leaves its listed tiles (negative: every iteration)
     bin_margin: float = 4.0
+    # backward reduction: REDUCE_SLOTS (fixed order, bit-reproducible) or
+    # REDUCE_ATOMIC (float atomics; order of additions varies run to run)
+    reduce: int = nat.REDUCE_SLOTS
 
     @classmethod
     def fast_fit(cls, **overrides):
@@ -55,7 +58,7 @@ class RasterConfig:
         return nat.Config(self.tile, self.sigma_cut, self.alpha_min, self.det_eps, self.lr,
                           self.beta1, self.beta2, self.eps, self.stage, self.launch, self.lr_mu,
                           self.lr_shape, self.lr_color, self.lr_weight, self.lr_decay,
-                          self.bin_margin)
+                          self.bin_margin, self.reduce)
 
 
 # Learning-rate schedule for fitting a frame from an initialiser (the
@@ -407,31 +410,46 @@ _TUNED = {}
 
 
 def autotune(sizes, params: torch.Tensor, targets: torch.Tensor, tiles=(8, 16, 32),
-             stages=(32, 64, 128), launches=(nat.LAUNCH_PERSISTENT, nat.LAUNCH_GRID),
+             stages=(32, 64, 128, 256), launches=(nat.LAUNCH_PERSISTENT, nat.LAUNCH_GRID),
              reps: int = 5, config: RasterConfig | None = None, max_entries: int = 0,
-             stream=None, cache: bool = True):
+             stream=None, cache: bool = True, reduces=(nat.REDUCE_SLOTS,)):
     """Picks the render schedule (tile, stage, launch) for a batch
-    (gs2d_autotune).  ``params``/``targets`` in the batch layout of
-    ``BatchRasterizer(sizes)``.  Returns {"tile", "stage", "launch", "config",
-    "ms": {(tile, stage, launch): ms per fit iteration}}; the result is cached
-    per (sizes, candidates) unless ``cache`` is False."""
+    (gs2d_autotune), and the backward reduction among ``reduces``
+    (REDUCE_SLOTS only by default: the bit-reproducible one).  ``params`` /
+    ``targets`` in the batch layout of ``BatchRasterizer(sizes)``.  Returns
+    {"tile", "stage", "launch", "reduce", "config", "ms": {(tile, stage,
+    launch): ms per fit iteration}} -- keys (tile, stage, launch, reduce)
+    when several reductions are candidates; the result is cached per (sizes,
+    candidates) unless ``cache`` is False."""
     sizes = [(int(w), int(h), int(n)) for (w, h, n) in sizes]
-    key = (tuple(sizes), tuple(tiles), tuple(stages), tuple(launches), max_entries)
+    reduces = tuple(int(r) for r in reduces)
+    key = (tuple(sizes), tuple(tiles), tuple(stages), tuple(launches), max_entries, reduces)
     if cache and key in _TUNED:
         return _TUNED[key]
-    base = (config or RasterConfig()).to_c()
-    nbytes = nat.autotune_ws_bytes(sizes, list(tiles), max_entries, base)
-    if nbytes == 0:
-        raise ValueError("invalid batch or candidate tiles")
+    base_cfg = config or RasterConfig()
+    nbytes = nat.autotune_ws_bytes(sizes, list(tiles), max_entries, base_cfg.to_c())
+    if nbytes == 0 or not reduces:
+        raise ValueError("invalid batch or candidate lists")
     n_total = sum(n for (_, _, n) in sizes)
     pixels = sum(w * h for (w, h, _) in sizes)
     ws = torch.empty(nbytes, dtype=torch.uint8, device=params.device)
-    table, bt, bs, bl = nat.autotune(sizes, _check(params, "params", (9, n_total)),
+    table, best = {}, None
+    for r in reduces:
+        base = dataclasses.replace(base_cfg, reduce=r).to_c()
+        t, bt, bs, bl = nat.autotune(sizes, _check(params, "params", (9, n_total)),
                                      _check(targets, "targets", (3 * pixels,)), ws.data_ptr(),
                                      nbytes, list(tiles), list(stages), list(launches), reps,
                                      _stream(stream), max_entries, base)
-    cfg = dataclasses.replace(config or RasterConfig(), tile=bt, stage=bs, launch=bl)
-    res = {"tile": bt, "stage": bs, "launch": bl, "config": cfg, "ms": table}
+        for k, v in t.items():
+            table[k if len(reduces) == 1 else (*k, r)] = v
+        ms = t[(bt, bs, bl)]
+        if ms >= 0 and (best is None or ms < best[0]):
+            best = (ms, bt, bs, bl, r)
+    if best is None:
+        raise RuntimeError("every autotuner candidate overflowed max_entries")
+    _, bt, bs, bl, br = best
+    cfg = dataclasses.replace(base_cfg, tile=bt, stage=bs, launch=bl, reduce=br)
+    res = {"tile": bt, "stage": bs, "launch": bl, "reduce": br, "config": cfg, "ms": table}
     if cache:
         _TUNED[key] = res
     return res

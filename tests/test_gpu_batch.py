@@ -21,7 +21,7 @@ IMG_TOL = 1e-5
 GRAD_REL = 1e-3
 
 SCHEDULES = [(8, 32, 0), (8, 128, 1), (16, 32, 1), (16, 128, 0), (32, 32, 0), (32, 64, 1),
-             (32, 128, 0), (16, 64, 1)]
+             (32, 128, 0), (16, 64, 1), (8, 256, 1), (16, 256, 0), (32, 256, 1)]
 
 
 @pytest.fixture(scope="module")
@@ -248,9 +248,10 @@ def test_autotune_picks_a_measured_candidate(gs):
     res = gs.autotune(sizes, P, T, reps=3, cache=False)
     assert torch.equal(P, before)  # params untouched
     ms = res["ms"]
-    assert len(ms) == 18 and all(v > 0 for v in ms.values())
+    assert len(ms) == 24 and all(v > 0 for v in ms.values())
     assert (res["tile"], res["stage"], res["launch"]) in ms
     assert ms[(res["tile"], res["stage"], res["launch"])] == min(ms.values())
+    assert res["reduce"] == 0 and res["config"].reduce == 0  # deterministic unless asked
     # a batch planned with the chosen schedule renders like the default one
     b0 = gs.BatchRasterizer(sizes)
     b1 = gs.BatchRasterizer(sizes, config=res["config"])

@@ -241,7 +241,8 @@ def full_size_case(oracle):
             "which": which, "res": res}
 
 
-FULL_SCHEDULES = [(t, s, la) for t in (8, 16, 32) for s in (32, 64, 128) for la in (0, 1)]
+FULL_SCHEDULES = [(t, s, la) for t in (8, 16, 32) for s in (32, 64, 128) for la in (0, 1)] + [
+    (16, 256, 0), (32, 256, 1)]
 
 
 @pytest.mark.parametrize("tile,stage,launch", FULL_SCHEDULES)
