@@ -56,8 +56,8 @@ SMS, FP32_LANES, MUFU_LANES, SM_MAX_MHZ = 152, 128, 32, 2070.0
 # DRAM bytes (read + write) of one fused render launch (k_render, tile 32,
 # stage 128, grid) from an ncu capture of this workload, valid for the render
 # source with this sha256 (else null)
-NCU_TRAFFIC = {"bytes": 26832640, "schedule": (32, 128, 1),
-               "render_sha256": "db7ab23126ff65d3d305cdebb488be29f5aa90fe7516a137f30d981ac79f0dde"}
+NCU_TRAFFIC = {"bytes": 26832896, "schedule": (32, 128, 1),
+               "render_sha256": "5cb495a95b44371febe63e2d6db4aea11470d589ce7cb1f720905b80249bb138"}
 
 
 def render_traffic(schedule):
