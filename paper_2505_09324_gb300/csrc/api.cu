@@ -388,48 +388,6 @@ static cudaError_t aux_stream(AuxStream** out) {
   return cudaSuccess;
 }
 
-// The work of one gs2d_fit_step_rgb8 call, queued on s (and the auxiliary
-// stream, forked from and joined back into s).
-static cudaError_t enqueue_rgb8_step(const gs2d_plan& p, void* ws, const uint8_t* rgb_host,
-                                     uint8_t* rgb_dev, float* frame_dev,
-                                     const float* params_host, float* params, float* adam_m,
-                                     float* adam_v, float* params_out_host, cudaStream_t s,
-                                     const AuxStream& aux) {
-  const size_t rgb_bytes = (size_t)3 * p.width * p.height;
-  const size_t pbytes = (size_t)9 * p.n * sizeof(float);
-  // the frame on the auxiliary stream, after everything queued on s so far
-  // (the previous iteration's render reads frame_dev)
-  cudaError_t e = cudaEventRecord(aux.start, s);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(aux.stream, aux.start, 0);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(rgb_dev, rgb_host, rgb_bytes, cudaMemcpyHostToDevice, aux.stream);
-  if (e == cudaSuccess && gs2d_frame_from_rgb8(rgb_dev, p.width, p.height, (int64_t)3 * p.width,
-                                               frame_dev, aux.stream) != GS2D_OK)
-    e = cudaErrorLaunchFailure;
-  if (e == cudaSuccess) e = cudaEventRecord(aux.frame, aux.stream);
-  // the params, projection and binning on s meanwhile
-  if (e == cudaSuccess && params_host && pbytes)
-    e = cudaMemcpyAsync(params, params_host, pbytes, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = launch_prepare_fit(p, ws, params, s);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, aux.frame, 0);
-  if (e == cudaSuccess) e = launch_fit_step(p, ws, frame_dev, params, adam_m, adam_v, s);
-  if (e == cudaSuccess && params_out_host && pbytes)
-    e = cudaMemcpyAsync(params_out_host, params, pbytes, cudaMemcpyDeviceToHost, s);
-  return e;
-}
-
-// gs2d_fit_step_rgb8 replays its call as a CUDA graph while the plan, the
-// buffers and the stream stay the same (one launch instead of about fifteen
-// copies, events and kernel launches); one cached graph per host thread.
-struct Rgb8Graph {
-  bool valid = false;
-  int device = -1;
-  gs2d_plan plan;
-  const void* ptr[9];
-  cudaStream_t stream = nullptr;
-  cudaGraphExec_t exec = nullptr;  // NULL: capture failed, launch directly
-};
-
 gs2d_status gs2d_fit_step_rgb8(const gs2d_plan* plan, void* ws, const uint8_t* rgb_host,
                                uint8_t* rgb_dev, float* frame_dev, const float* params_host,
                                float* params, float* adam_m, float* adam_v, float* params_out_host,
@@ -441,41 +399,29 @@ gs2d_status gs2d_fit_step_rgb8(const gs2d_plan* plan, void* ws, const uint8_t* r
   if (!rgb_host || !rgb_dev || !frame_dev || (p.n > 0 && (!params || !adam_m || !adam_v)))
     return fail(GS2D_ERR_INVALID_ARG, "gs2d_fit_step_rgb8: NULL pointer");
   cudaStream_t s = (cudaStream_t)stream;
+  const size_t rgb_bytes = (size_t)3 * p.width * p.height;
+  const size_t pbytes = (size_t)9 * p.n * sizeof(float);
   AuxStream* aux = nullptr;
   cudaError_t e = aux_stream(&aux);
+  // the frame on the auxiliary stream, after everything queued on s so far
+  // (the previous iteration's render reads frame_dev)
+  if (e == cudaSuccess) e = cudaEventRecord(aux->start, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(aux->stream, aux->start, 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(rgb_dev, rgb_host, rgb_bytes, cudaMemcpyHostToDevice, aux->stream);
   if (e != cudaSuccess) return cuda_check(e, "gs2d_fit_step_rgb8");
-  static thread_local Rgb8Graph g;
-  const void* ptr[9] = {ws, rgb_host, rgb_dev, frame_dev, params_host, params, adam_m,
-                        adam_v, params_out_host};
-  const bool same = g.valid && g.device == aux->device && g.stream == s &&
-                    memcmp(&g.plan, &p, sizeof(p)) == 0 && memcmp(g.ptr, ptr, sizeof(ptr)) == 0;
-  if (!same) {
-    if (g.exec) cudaGraphExecDestroy(g.exec);
-    g = Rgb8Graph();
-    if (s != nullptr && prime_fit_launches(p) == cudaSuccess) {
-      cudaGraph_t graph = nullptr;
-      if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-        const cudaError_t ce = enqueue_rgb8_step(p, ws, rgb_host, rgb_dev, frame_dev,
-                                                 params_host, params, adam_m, adam_v,
-                                                 params_out_host, s, *aux);
-        const cudaError_t ee = cudaStreamEndCapture(s, &graph);
-        if (ce == cudaSuccess && ee == cudaSuccess && graph &&
-            cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess)
-          g.exec = nullptr;
-        if (graph) cudaGraphDestroy(graph);
-      }
-    }
-    cudaGetLastError();  // a failed capture falls back to direct launches
-    set_error(GS2D_OK, "");
-    g.valid = true;
-    g.device = aux->device;
-    g.plan = p;
-    memcpy(g.ptr, ptr, sizeof(ptr));
-    g.stream = s;
-  }
-  e = g.exec ? cudaGraphLaunch(g.exec, s)
-             : enqueue_rgb8_step(p, ws, rgb_host, rgb_dev, frame_dev, params_host, params,
-                                 adam_m, adam_v, params_out_host, s, *aux);
+  st = gs2d_frame_from_rgb8(rgb_dev, p.width, p.height, (int64_t)3 * p.width, frame_dev,
+                            aux->stream);
+  if (st) return st;
+  e = cudaEventRecord(aux->frame, aux->stream);
+  // the params, projection and binning on s meanwhile
+  if (e == cudaSuccess && params_host && pbytes)
+    e = cudaMemcpyAsync(params, params_host, pbytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = launch_prepare_fit(p, ws, params, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, aux->frame, 0);
+  if (e == cudaSuccess) e = launch_fit_step(p, ws, frame_dev, params, adam_m, adam_v, s);
+  if (e == cudaSuccess && params_out_host && pbytes)
+    e = cudaMemcpyAsync(params_out_host, params, pbytes, cudaMemcpyDeviceToHost, s);
   return cuda_check(e, "gs2d_fit_step_rgb8");
 }
 
