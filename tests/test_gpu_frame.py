@@ -103,3 +103,49 @@ def test_fit_step_rgb8_is_upload_convert_fit_download(gs):
     torch.cuda.synchronize()
     assert torch.equal(out, q.cpu()) and torch.equal(d_p, q)
     assert torch.equal(d_frame, frame)
+
+
+def test_fit_step_rgb8_on_a_stream_reads_current_host_buffers(gs):
+    """Repeated calls on a non-default stream: each must read the host
+    buffers' current contents (a new frame and the previous step's Gaussians
+    every call), also after a buffer changes."""
+    from gs2d_inputs import random_gaussians
+    from paper_2505_09324_gb300 import _native as nat
+    W, H, n, steps = 144, 80, 300, 5
+    rng = np.random.default_rng(10)
+    frames = [rng.integers(0, 256, (H, W, 3), dtype=np.uint8) for _ in range(steps)]
+    p0 = torch.from_numpy(random_gaussians(n, W, H, seed=11))
+    r = gs.GaussianRasterizer(W, H, n)
+    st = torch.cuda.Stream()
+    s = int(st.cuda_stream)
+    rgb = torch.empty((H, W, 3), dtype=torch.uint8).pin_memory()
+    h_p = p0.clone().pin_memory()
+    outs = [torch.empty_like(p0).pin_memory() for _ in range(2)]
+    d_rgb = torch.empty((H, W, 3), dtype=torch.uint8, device="cuda")
+    d_frame = torch.empty((3, H, W), device="cuda")
+    d_p = torch.empty((9, n), device="cuda")
+    m, v = torch.empty_like(d_p), torch.empty_like(d_p)
+    got = []
+    with torch.cuda.stream(st):
+        nat.fit_reset(r.plan, r.ws_ptr, m.data_ptr(), v.data_ptr(), s)
+        for k in range(steps):
+            st.synchronize()
+            rgb.copy_(torch.from_numpy(frames[k]))
+            out = outs[k // 3]  # the fourth call writes to another buffer
+            nat.fit_step_rgb8(r.plan, r.ws_ptr, rgb.data_ptr(), d_rgb.data_ptr(),
+                              d_frame.data_ptr(), h_p.data_ptr(), d_p.data_ptr(), m.data_ptr(),
+                              v.data_ptr(), out.data_ptr(), s)
+            st.synchronize()
+            got.append(out.clone())
+            h_p.copy_(out)
+    # the same iterations by parts
+    q = p0.cuda()
+    m2, v2 = torch.empty_like(q), torch.empty_like(q)
+    s0 = int(torch.cuda.current_stream().cuda_stream)
+    nat.fit_reset(r.plan, r.ws_ptr, m2.data_ptr(), v2.data_ptr(), s0)
+    for k in range(steps):
+        frame = gs.frame_from_rgb8(torch.from_numpy(frames[k]).cuda())
+        nat.fit_step(r.plan, r.ws_ptr, frame.data_ptr(), q.data_ptr(), m2.data_ptr(),
+                     v2.data_ptr(), s0)
+        torch.cuda.synchronize()
+        assert torch.equal(got[k], q.cpu()), k
