@@ -591,14 +591,8 @@ cudaError_t launch_project(const gs2d_plan& p, void* ws, const float* params, cu
                     ws_ptr<int>(ws, p, kOffCount));
 }
 
-static bool g_long_attr_set = false;
-
 cudaError_t prime_binning() {
-  if (g_long_attr_set) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(
-      k_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize, kLongMax * (int)sizeof(uint32_t));
-  if (e == cudaSuccess) g_long_attr_set = true;
-  return e;
+  return opt_in_smem((const void*)k_sort_long, kLongMax * (int)sizeof(uint32_t));
 }
 
 // Scans, scatter and segment sorts (everything after the counts); `lists`:

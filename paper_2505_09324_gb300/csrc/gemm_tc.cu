@@ -507,12 +507,7 @@ bool make_map(CUtensorMap* map, const void* base, int rows, int cols, int ld, in
 template <int BN, int ST>
 cudaError_t launch_bn_st(const CUtensorMap& ta, const CUtensorMap& tb, const TcGemmArgs& g,
                          dim3 grid, cudaStream_t s) {
-  static std::once_flag once;
-  static cudaError_t attr = cudaSuccess;
-  std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(k_gemm_bf16<BN, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                GemmShape<BN, ST>::kSmem);
-  });
+  const cudaError_t attr = opt_in_smem((const void*)k_gemm_bf16<BN, ST>, GemmShape<BN, ST>::kSmem);
   if (attr != cudaSuccess) return attr;
   k_gemm_bf16<BN, ST><<<grid, 128, GemmShape<BN, ST>::kSmem, s>>>(ta, tb, g);
   return cudaGetLastError();
@@ -521,12 +516,7 @@ cudaError_t launch_bn_st(const CUtensorMap& ta, const CUtensorMap& tb, const TcG
 template <int BN, int ST>
 cudaError_t launch_conv_st(const CUtensorMap& tb, const ConvGeom& cg, const TcGemmArgs& g,
                            dim3 grid, cudaStream_t s) {
-  static std::once_flag once;
-  static cudaError_t attr = cudaSuccess;
-  std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(k_conv_bf16<BN, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                GemmShape<BN, ST>::kSmem);
-  });
+  const cudaError_t attr = opt_in_smem((const void*)k_conv_bf16<BN, ST>, GemmShape<BN, ST>::kSmem);
   if (attr != cudaSuccess) return attr;
   k_conv_bf16<BN, ST><<<grid, 160, GemmShape<BN, ST>::kSmem, s>>>(tb, cg, g);
   return cudaGetLastError();

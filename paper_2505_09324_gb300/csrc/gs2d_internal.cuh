@@ -311,6 +311,9 @@ cudaError_t prime_binning();
 // prime_binning + the render occupancy query of the plan's fit loop.
 cudaError_t prime_fit_launches(const gs2d_plan& p);
 
+// Opt-in to `bytes` of dynamic shared memory for `kernel` on the current
+// device (once per kernel and device; thread-safe).
+cudaError_t opt_in_smem(const void* kernel, int bytes);
 // Thread blocks of a persistent launch: resident blocks per SM x SMs of the
 // current device, at most `work` blocks.
 int persistent_grid(const void* kernel, int threads, int work);

@@ -232,6 +232,20 @@ k_clip_loss(ClipSet cs, const float2* __restrict__ loss_part, float2* __restrict
 }
 
 // ---------------------------------------------------------------------------
+cudaError_t opt_in_smem(const void* kernel, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> done;  // (kernel, device) -> bytes
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = done.find({kernel, dev});
+  if (it != done.end() && it->second >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done[{kernel, dev}] = bytes;
+  return e;
+}
+
 int persistent_grid(const void* kernel, int threads, int work) {
   static std::mutex mu;
   static std::map<std::pair<const void*, int>, int> cache;  // (kernel, device) -> blocks
