@@ -612,7 +612,9 @@ gs2d_status gs2d_read_bins(const gs2d_plan* plan, const void* ws, int64_t* n_ent
  * roofline accounting): pairs = sum over tiles of (pixels of the tile inside
  * the image) x (list length), i.e. the (pixel, Gaussian) pairs a tile
  * rasterizer visits; hits = the pairs that contribute to Eq. 2 (the cut-off
- * predicate holds).  Writes host int64 values (either may be NULL).  Launches
+ * predicate holds).  After a fit step the list is the fit loop's retained
+ * one (widened rectangles: more pairs, the same hits); after gs2d_prepare
+ * or gs2d_bin_sort it is the tight one.  Writes host int64 values (either may be NULL).  Launches
  * one counting kernel and synchronises the stream. */
 gs2d_status gs2d_count_pairs(const gs2d_plan* plan, void* ws, int64_t* pairs, int64_t* hits,
                              void* stream);

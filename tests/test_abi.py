@@ -143,6 +143,15 @@ def test_plan_rejects_bad_config(nat):
         nat.plan_init(64, 64, 10, 0, c)
     c.bin_margin = -1.0  # per-iteration binning
     nat.plan_init(64, 64, 10, 0, c)
+    for reduce in (-1, 2):
+        c = nat.default_config()
+        c.reduce = reduce
+        with pytest.raises(nat.Gs2dError):
+            nat.plan_init(64, 64, 10, 0, c)
+    c = nat.default_config()
+    c.reduce, c.stage = nat.REDUCE_ATOMIC, 256
+    q = nat.plan_init(64, 64, 10, 0, c)
+    assert q.stage == 256 and q.cfg.reduce == nat.REDUCE_ATOMIC
 
 
 def test_calls_reject_bad_arguments_without_touching_the_gpu(nat):
@@ -159,6 +168,10 @@ def test_calls_reject_bad_arguments_without_touching_the_gpu(nat):
     with pytest.raises(nat.Gs2dError):
         nat.adam_step(0x1000, 0x1000, 0x1000, 0x1000, 9, 0, 0, None, 0)  # step 0
     assert "step" in nat.last_error()
+    with pytest.raises(nat.Gs2dError):
+        nat.fit_rebins(bad, 0x1000, 0)          # plan never initialised
+    with pytest.raises(nat.Gs2dError):
+        nat.fit_rebins(p, 0, 0)                 # NULL workspace
 
 
 def test_quantizer_arguments_checked_before_any_launch(nat):
