@@ -217,3 +217,35 @@ def test_fit_step_equals_pframe_step_with_everything_selected(gs, tile, fast):
     assert r.status() == 0 and r2.status() == 0
     assert_same((a, ma, va), (b, mb, vb))
     assert not torch.equal(a, to_dev(p0))
+
+
+def test_empty_gaussian_sets(gs):
+    """No Gaussians at all, with retained and with per-iteration lists; and an
+    empty clip in a batch, whose other clip must fit exactly as alone."""
+    from paper_2505_09324_gb300 import _native as nat
+    W, H = 70, 50
+    t = to_dev(smooth_noise_target(W, H, seed=55))
+    s = int(torch.cuda.current_stream().cuda_stream)
+    for margin in (-1.0, 4.0):
+        r = gs.GaussianRasterizer(W, H, 0, config=gs.RasterConfig(bin_margin=margin))
+        p = torch.zeros((9, 0), device="cuda")
+        o = r.encode_frame(t, p, 5, check_every=5)
+        assert o["status"] == 0 and o["iters"] == 5
+        m, v = torch.zeros_like(p), torch.zeros_like(p)
+        nat.fit_reset(r.plan, r.ws_ptr, m.data_ptr(), v.data_ptr(), s)
+        for _ in range(3):
+            nat.fit_step(r.plan, r.ws_ptr, t.data_ptr(), p.data_ptr(), m.data_ptr(),
+                         v.data_ptr(), s)
+        torch.cuda.synchronize()
+        assert r.status() == 0
+    w2, h2, n2, iters = 64, 48, 80, 20
+    p2 = to_dev(random_gaussians(n2, w2, h2, seed=56, l_range=(1.5, 6.0)))
+    t2 = to_dev(smooth_noise_target(w2, h2, seed=57))
+    cfg = gs.RasterConfig.fast_fit()
+    b = gs.BatchRasterizer([(W, H, 0), (w2, h2, n2)], config=cfg)
+    pp = p2.clone()
+    b.encode_batch(b.pack_images([t, t2]), pp, iters)
+    alone = p2.clone()
+    gs.GaussianRasterizer(w2, h2, n2, config=cfg).encode_frame(t2, alone, iters,
+                                                                check_every=iters)
+    assert torch.equal(pp, alone)
