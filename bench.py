@@ -120,6 +120,20 @@ def whole_job(total_ms: float, steps: int, world: int, device=None):
     return total_ms, total_ms / (steps * world)
 
 
+def shard_aggregate(ms_iter: float, hits, world: int, device=None):
+    """A sharded batch: the slowest rank's time per batched iteration and the
+    contributing pairs of all ranks."""
+    if world == 1:
+        return ms_iter, hits
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_iter], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    h = torch.tensor([float(hits)], dtype=torch.float64, device=device)
+    dist.all_reduce(h, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(h.item())
+
+
 def workload(seed):
     from gs2d_inputs import background_positions, conferencing_frame
     frame, mask = conferencing_frame(W, H, seed=seed)
@@ -190,20 +204,28 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 
-def measure_batch(args, dev):
+def measure_batch(args, dev, rank=0, world=1):
     """Batched encode of independent clips of uneven size (resolution uniform
     over 640x360 / 1280x720 / 1920x1080, Gaussian count log-uniform in
     [2000, 50000]) of the moving-subject conferencing scene: frame 0 of every
     clip from the ROI initialiser, later frames warm-started from the previous
     frame's Gaussians, `batch_iters` iterations per frame, all clips in one
-    launch per step of the path (gs2d_encode_batch, a captured CUDA graph)."""
+    launch per step of the path (gs2d_encode_batch, a captured CUDA graph).
+    With several ranks the clips are split by estimated cost (shard.py), each
+    rank fits its share, and the batch time is the slowest rank's."""
     import numpy as np
     import torch
 
     from gs2d_inputs import background_positions, clip_table, conferencing_frame, random_motion
     from paper_2505_09324_gb300 import BatchRasterizer, autotune, roi_init
+    from paper_2505_09324_gb300.shard import partition_clips, shard_loads
 
-    table = clip_table(args.batch_clips, 1000)
+    full = clip_table(args.batch_clips, 1000)
+    full_sizes = [(c["width"], c["height"], c["n"]) for c in full]
+    parts = partition_clips(full_sizes, world)
+    table = [full[i] for i in parts[rank]]
+    if not table:
+        raise RuntimeError(f"rank {rank} has no clip of the {len(full)}-clip batch")
     sizes = [(c["width"], c["height"], c["n"]) for c in table]
     motions = [random_motion(c["seed"]) for c in table]
 
@@ -249,7 +271,12 @@ def measure_batch(args, dev):
                           "psnr_min": min(psnr), "psnr_median": statistics.median(psnr),
                           "psnr_max": max(psnr)})
     ms_iter = statistics.fmean(f["ms_per_batched_iter"] for f in per_frame)
-    return {"clips": len(sizes), "gaussians": int(P.shape[1]),
+    ms_iter, hits = shard_aggregate(ms_iter, hits, world, dev)
+    sizes = full_sizes
+    return {"clips": len(full), "ranks": world,
+            "clips_per_rank": [len(p) for p in parts],
+            "estimated_load_per_rank": shard_loads(full_sizes, parts),
+            "gaussians": sum(n for (_, _, n) in full_sizes),
             "megapixels": sum(w * h for (w, h, _) in sizes) / 1e6,
             "frames_per_clip": args.batch_frames, "iters_per_frame": args.batch_iters,
             "ms_per_batched_iter": ms_iter,
@@ -870,7 +897,7 @@ def run_ours(args):
                                                            "every 25 iterations"},
                   "learned_init": learned_enc}
 
-    batch = None if args.no_batch else measure_batch(args, dev)
+    batch = None if args.no_batch else measure_batch(args, dev, rank, world)
     quantizer = None
     if not (args.no_sequence and args.no_quant):
         quantizer = calibrated_quantizer(dev, tuned["config"])
