@@ -60,6 +60,15 @@ NCU_TRAFFIC = {"bytes": 26832896, "schedule": (32, 128, 1),
                "render_sha256": "5cb495a95b44371febe63e2d6db4aea11470d589ce7cb1f720905b80249bb138"}
 
 
+def hbm_peak_gbs() -> float:
+    """Measured copy bandwidth of this machine's GPUs (GB/s), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
 def render_traffic(schedule):
     """ncu DRAM bytes of the fused render launch, if the capture was of this
     schedule (tile, stage, launch) and of the current render source."""
@@ -765,13 +774,19 @@ def run_ours(args):
                         "frac": ach / peak_fp32,
                         "call": "gs2d_render_fwd" if name == "fwd" else
                                 "gs2d_render_bwd (k_render backward + per-Gaussian reduction)"}
+    traffic = render_traffic((tuned["tile"], tuned["stage"], tuned["launch"]))
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_fp32,
                 "unit": "Top/s (FP32 pipe)", "frac": achieved / peak_fp32,
-                "traffic": render_traffic((tuned["tile"], tuned["stage"], tuned["launch"])),
+                "traffic": traffic,
                 "kernel": "gs2d_render_l2: k_render (fused forward + L2 + backward) + "
                           "k_reduce_chain",
                 "mufu_frac": MUFU_PER_HIT * hits / t_render / 1e12 / peak_mufu,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz; MUFU 32/SM/clk",
+                # the third bound: the launch's DRAM bytes (ncu) over its time,
+                # against the measured copy bandwidth
+                "hbm_frac": (traffic / t_render / 1e9 / hbm_peak_gbs()) if traffic else None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz; MUFU 32/SM/clk; "
+                               "HBM of measured (MEASURED_PEAKS.json hbm_gbs) or of fallback "
+                               "(6800 GB/s)",
                 "passes": passes}
 
     # end to end through the public API with host buffers: every step uploads
