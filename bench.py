@@ -343,20 +343,25 @@ class ClockSampler:
             self.thread.join(timeout=5)
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        rows = [r for (ts, r) in self.lines
-                if (t0 is None or ts >= t0) and (t1 is None or ts <= t1 + 0.06)]
-        if not rows and self.lines:  # region shorter than one sample period
-            rows = [min(self.lines, key=lambda x: abs(x[0] - (t1 or 0)))[1]]
-        for row in rows:
+
+        def parse(row):
             f = [x.strip() for x in row.split(",")]
             if len(f) < 9:
-                continue
+                return None
             try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
+                return float(f[1]), float(f[2]), f[5:9]
             except ValueError:
-                continue
-            for nm, val in zip(names, f[5:9]):
+                return None
+
+        samples = [(ts, p) for (ts, p) in ((ts, parse(r)) for (ts, r) in self.lines) if p]
+        rows = [p for (ts, p) in samples
+                if (t0 is None or ts >= t0) and (t1 is None or ts <= t1 + 0.06)]
+        if not rows and samples:  # region shorter than one sample period: the nearest
+            rows = [min(samples, key=lambda x: abs(x[0] - (t1 or 0)))[1]]
+        for clk, clk_max, flags in rows:
+            sm.append(clk)
+            mx.append(clk_max)
+            for nm, val in zip(names, flags):
                 if val.lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
