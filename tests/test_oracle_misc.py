@@ -71,3 +71,37 @@ def test_contributes_matches_single_gaussian_renders(oracle):
         sure = ~ambiguous[:, i]
         assert np.array_equal(nz[sure], definite[sure, i]), i
     assert not definite[:, 3].any() and not definite[:, 5].any()
+
+
+def test_subject_moves_rigidly():
+    """The subject's texture lives in object coordinates: a translation by
+    whole pixels shifts the interior of the subject exactly (the recipe's
+    rigid motion, no resampling)."""
+    from gs2d_inputs import SubjectMotion
+    W, H = 200, 120
+    mo = SubjectMotion(v=3.0, direction=0.0, omega=0.0)
+    f0, m0 = conferencing_frame(W, H, seed=4, t=0, motion=mo)
+    f2, m2 = conferencing_frame(W, H, seed=4, t=2, motion=mo)   # 6 px to the right
+    inner = np.zeros_like(m0)
+    inner[:, 6:] = m0[:, :-6] & m2[:, 6:]
+    # away from the soft edge on both frames
+    from scipy.ndimage import binary_erosion
+    inner = binary_erosion(inner, iterations=4)
+    assert inner.sum() > 1000
+    ys, xs = np.nonzero(inner)
+    np.testing.assert_allclose(f2[:, ys, xs], f0[:, ys, xs - 6], atol=2e-6)
+
+
+def test_clip_table_and_background_positions_follow_the_recipe():
+    from gs2d_inputs import background_positions, clip_table
+    t = clip_table(64, 7)
+    assert t == clip_table(64, 7)
+    assert {(c["width"], c["height"]) for c in t} <= {(640, 360), (1280, 720), (1920, 1080)}
+    assert all(2000 <= c["n"] <= 50000 for c in t)
+    ns = np.log([c["n"] for c in t])
+    assert ns.min() < np.log(6000) and ns.max() > np.log(20000)  # spread over the log range
+    _, mask = conferencing_frame(160, 96, seed=2)
+    xy = background_positions(mask, 500, seed=3)
+    assert xy.shape == (2, 500)
+    xi, yi = np.floor(xy[0]).astype(int), np.floor(xy[1]).astype(int)
+    assert not mask[yi, xi].any()  # every position on a background pixel
