@@ -258,8 +258,10 @@ gs2d_status gs2d_adam_step(float* params, const float* grads, float* m, float* v
  * fused with the Adam update of params, adam_m, adam_v (device, 9n floats
  * each).  The Adam step counter lives in the workspace header: it starts at
  * zero in a zero-filled workspace and advances by one per call;
- * gs2d_fit_reset restarts the optimiser.  target: device, the plan's image
- * layout. */
+ * gs2d_fit_reset restarts the optimiser.  The tile lists are kept from call
+ * to call while every Gaussian stays inside them (gs2d_config.bin_margin;
+ * gs2d_fit_rebins counts the rebuilds), with the results of binning every
+ * call.  target: device, the plan's image layout. */
 gs2d_status gs2d_fit_step(const gs2d_plan* plan, void* ws, const float* target, float* params,
                           float* adam_m, float* adam_v, void* stream);
 
