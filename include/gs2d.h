@@ -143,10 +143,11 @@ size_t gs2d_sizeof_plan(void);
 size_t gs2d_sizeof_config(void);
 
 /* Lays out a workspace for a W x H frame and n Gaussians with room for
- * max_entries (tile, Gaussian) pairs (0 picks max(2^20, 16 n), 64 n for tile 8).
- * cfg may be NULL (defaults).  Host only; no CUDA call.
- * Errors: W, H < 1, n < 0, tile not 8, 16 or 32, stage not 0, 32, 64, 128 or 256,
- * unknown launch form, non-positive constants. */
+ * max_entries (tile, Gaussian) pairs (0 picks max(2^20, 16 n), 64 n for tile 8,
+ * at most 2^28 - 1).  cfg may be NULL (defaults).  Host only; no CUDA call.
+ * Errors: W, H < 1 or > 65536, n < 0 or more than 2^27 Gaussians in all,
+ * max_entries < 0 or > 2^28 - 1, tile not 8, 16 or 32, stage not 0, 32, 64,
+ * 128 or 256, unknown launch form, non-positive constants. */
 gs2d_status gs2d_plan_init(gs2d_plan* plan, int32_t width, int32_t height, int32_t n,
                            int64_t max_entries, const gs2d_config* cfg);
 

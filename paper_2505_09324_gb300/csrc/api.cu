@@ -36,6 +36,12 @@ gs2d_status cuda_check(cudaError_t e, const char* what) {
 
 uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
 
+// Size limits that keep every 32-bit index of the kernels in range: the
+// parameter rows (9 n), the per-pair records (8 floats per entry) and the
+// render-queue ranks (28 bits).
+constexpr int64_t kMaxGaussians = int64_t(1) << 27;
+constexpr int64_t kMaxEntries = (int64_t(1) << 28) - 1;
+
 gs2d_status check_plan(const gs2d_plan* p, const void* ws) {
   if (!p || p->magic != kPlanMagic) return fail(GS2D_ERR_INVALID_ARG, "plan not initialised");
   if (!ws) return fail(GS2D_ERR_INVALID_ARG, "workspace is NULL");
@@ -130,14 +136,16 @@ gs2d_status gs2d_plan_init_batch(gs2d_plan* plan, gs2d_clip* clips, int32_t num_
     n_total += cl.n;
     tiles += (int64_t)cl.tiles_x * cl.tiles_y;
     pixels += (int64_t)cl.width * cl.height;
-    if (n_total > (1 << 28) || tiles > (1 << 28))
+    if (n_total > kMaxGaussians || tiles > (1 << 28))
       return fail(GS2D_ERR_INVALID_ARG, "batch too large (%lld Gaussians, %lld tiles)",
                   (long long)n_total, (long long)tiles);
   }
   if (max_entries == 0)
-    max_entries = std::max<int64_t>(1 << 20, 16 * n_total * (T == 8 ? 4 : 1));
-  if (max_entries < 1 || max_entries > (int64_t(1) << 30))
-    return fail(GS2D_ERR_INVALID_ARG, "max_entries = %lld out of range", (long long)max_entries);
+    max_entries = std::min<int64_t>(
+        kMaxEntries, std::max<int64_t>(1 << 20, 16 * n_total * (T == 8 ? 4 : 1)));
+  if (max_entries < 1 || max_entries > kMaxEntries)
+    return fail(GS2D_ERR_INVALID_ARG, "max_entries = %lld out of range (1 .. %lld)",
+                (long long)max_entries, (long long)kMaxEntries);
   // a one-clip plan is a single frame: its kernels take the clip from these
   plan->width = num_clips == 1 ? clips[0].width : 0;
   plan->height = num_clips == 1 ? clips[0].height : 0;

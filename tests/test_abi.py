@@ -67,11 +67,23 @@ def test_plan_layout(nat):
 
 
 @pytest.mark.parametrize("args", [(0, 10, 5, 0), (10, -1, 5, 0), (10, 10, -1, 0),
-                                  (10, 10, 5, -3), (10, 10, 5, 1 << 31)])
+                                  (10, 10, 5, -3), (10, 10, 5, 1 << 31), (10, 10, 5, 1 << 28),
+                                  (10, 10, (1 << 27) + 1, 0)])
 def test_plan_rejects_bad_sizes(nat, args):
     with pytest.raises(nat.Gs2dError) as e:
         nat.plan_init(*args)
     assert e.value.status == nat.GS2D_ERR_INVALID_ARG
+
+
+def test_plan_size_limits_keep_kernel_indices_in_32_bits(nat):
+    # 8 floats per entry and 9 parameter rows must stay below 2^31
+    p = nat.plan_init(64, 64, 10, (1 << 28) - 1)
+    assert 8 * p.max_entries + 7 < 1 << 31
+    big = nat.plan_init(64, 64, 1 << 27)           # the default capacity is clamped
+    assert big.max_entries == (1 << 28) - 1 and 9 * big.n < 1 << 31
+    c = nat.default_config()
+    c.tile = 8
+    assert nat.plan_init(64, 64, 1 << 27, 0, c).max_entries == (1 << 28) - 1
 
 
 @pytest.mark.parametrize("tile,stage,tiles", [(8, 32, (8, 6)), (16, 128, (4, 3)), (32, 0, (2, 2))])
