@@ -422,7 +422,9 @@ uint64_t gs2d_roi_init_scratch_bytes(int32_t width, int32_t height, int32_t n);
  * n - n_roi columns are used.  params: device, 9n floats out (region
  * Gaussians first, in seed raster order).  n_roi: host int32 out, may be NULL.
  * scratch: device, gs2d_roi_init_scratch_bytes bytes.  All work runs on the
- * device; the call synchronises the stream once at the end to return n_roi. */
+ * device; the call synchronises the stream once at the end to return n_roi.
+ * Errors: W or H < 1 or > 65536, W H > 2^30, n < 0 or > 2^27, roi_frac
+ * outside [0, 1], NULL pointers, a misaligned or short scratch. */
 gs2d_status gs2d_roi_init(const float* frame, const uint8_t* mask, int32_t width, int32_t height,
                           int32_t n, float roi_frac, const float* bg_xy, float* params,
                           int32_t* n_roi, void* scratch, uint64_t scratch_bytes, void* stream);

@@ -301,7 +301,9 @@ uint64_t gs2d_roi_init_scratch_bytes(int32_t width, int32_t height, int32_t n) {
 gs2d_status gs2d_roi_init(const float* frame, const uint8_t* mask, int32_t width, int32_t height,
                           int32_t n, float roi_frac, const float* bg_xy, float* params,
                           int32_t* n_roi, void* scratch, uint64_t scratch_bytes, void* stream) {
-  if (width < 1 || height < 1 || width > 65536 || height > 65536 || n < 0 || n > (1 << 28))
+  // (its kernels index pixels with 32-bit integers)
+  if (width < 1 || height < 1 || width > 65536 || height > 65536 ||
+      (int64_t)width * height > (int64_t(1) << 30) || n < 0 || n > kMaxGaussians)
     return fail(GS2D_ERR_INVALID_ARG, "gs2d_roi_init: sizes out of range");
   if (!(roi_frac >= 0.0f && roi_frac <= 1.0f))
     return fail(GS2D_ERR_INVALID_ARG, "gs2d_roi_init: roi_frac must be in [0, 1]");

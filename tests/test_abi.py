@@ -180,6 +180,12 @@ def test_calls_reject_bad_arguments_without_touching_the_gpu(nat):
     with pytest.raises(nat.Gs2dError):
         nat.adam_step(0x1000, 0x1000, 0x1000, 0x1000, 9, 0, 0, None, 0)  # step 0
     assert "step" in nat.last_error()
+    # a frame too large for the ROI initialiser's 32-bit pixel indices
+    lib = nat.load()
+    st = lib.gs2d_roi_init(ctypes.c_void_p(0x1000), ctypes.c_void_p(0x1000), 65536, 32768, 10,
+                           ctypes.c_float(0.7), ctypes.c_void_p(0x1000), ctypes.c_void_p(0x1000),
+                           None, ctypes.c_void_p(0x1000), ctypes.c_uint64(1 << 40), None)
+    assert st == nat.GS2D_ERR_INVALID_ARG and "sizes" in nat.last_error()
     with pytest.raises(nat.Gs2dError):
         nat.fit_rebins(bad, 0x1000, 0)          # plan never initialised
     with pytest.raises(nat.Gs2dError):
