@@ -5,43 +5,46 @@ The paper segments the region of interest into N superpixels with a K-means
 superpixel algorithm and initialises one Gaussian per segment: mean = segment
 centre, Cholesky factor from the segment covariance, colour = mean segment
 colour.  It leaves the clustering details, the covariance scale and the
-Gaussians outside the region to the reader; the readings implemented here:
+Gaussians outside the region to the reader; the readings written out here:
 
 * seeds on a square grid of step S = max(1, sqrt(A_roi / K)) (A_roi = mask
   pixels; at most one superpixel per pixel),
-  at ((i + 1/2) S, (j + 1/2) S), kept where the seed's pixel is in the mask;
-  the number of region Gaussians is the number of seeds M (at most n);
+  at ((i + 1/2) S, (j + 1/2) S), kept where the seed's pixel is in the mask,
+  numbered in raster order of the grid; the number of region Gaussians is the
+  number of seeds M (at most n);
 * I = 10 K-means iterations in (r, g, b, x, y): a mask pixel p (centre at
   (x + 1/2, y + 1/2)) joins the centre minimising
       D = |col_p - col_c|^2 + (m / S)^2 |p - c|^2,  m = 0.2,
-  among centres within S of p on both axes (ties: lowest index); a centre moves
-  to the mean colour and position of its pixels, then is clamped to within S
-  of its seed on each axis (so the candidates of p are exactly the seeds whose
-  grid cells lie within two cells of p's); a centre without pixels stays;
-* each final segment gives a Gaussian with mean = centroid, Sigma =
-  kappa (covariance of the pixel centres + I/12), kappa = 4 (I/12 completes
-  the second moment of the segment's area: b^2/12 I for a b x b block; kappa
-  widens it so that the accumulated sum of Eq. 2 over a tiling of segments is
-  flat -- on a square grid of step S with sigma = S/sqrt(3) the ripple is
-  about 2 exp(-2 pi^2 kappa / 12) ~ 0.3 %), L = chol(Sigma), colour = mean
-  colour, weight w = A / (2 pi sqrt(det Sigma)) so that the Gaussian's
-  integral equals the segment area A (the blend keeps the mean level); a
-  segment that lost all pixels keeps its seed with Sigma = kappa S^2/12 I, the
-  frame colour at the seed and w = 1;
+  among the centres within S of p on both axes (exact ties: the lowest
+  index); a centre then moves to the mean colour and the mean pixel centre of
+  its segment, clamped to within S of its seed on each axis; a centre without
+  pixels stays where it is;
+* each final segment gives a Gaussian with mean = mean pixel centre,
+  Sigma = kappa (covariance of the pixel centres + I/12), kappa = 4 (I/12
+  completes the second moment of the segment's area: b^2/12 I for a b x b
+  block; kappa widens it so that the accumulated sum of Eq. 2 over a tiling
+  of segments is flat -- on a square grid of step S with sigma = S/sqrt(3)
+  the ripple is about 2 exp(-2 pi^2 kappa / 12) ~ 0.3 %), L = chol(Sigma)
+  (Eq. 1), colour = mean colour, weight w = A / (2 pi sqrt(det Sigma)) so
+  that the Gaussian's integral equals the segment area A; a segment that lost
+  all pixels keeps its seed with Sigma = kappa S^2/12 I, the frame colour at
+  the seed and w = 1;
 * the remaining n - M Gaussians sit at caller-supplied positions bg_xy
   (random numbers are inputs), isotropic with variance kappa a / (2 pi),
   a = (background pixels) / (n - M), weight 1 / kappa (integral a), colour =
   frame at the mean.
 
-Arithmetic (a reading: the paper fixes no precision).  The assignment's
-distances and comparisons are single precision (numpy float32, each
-operation rounded once; the centres are kept as float32), the precision the
-GPU kernel decides in.  Every sum over a segment is exact: pixel-centre
-coordinates enter as the integers 2 x + 1 - 2 floor(seed) (twice the offset
-from the seed's pixel), colours as rint(c 2^20) (colours clamped to
-[-32, 32]), so counts, first and second moments are integers whose sums do
-not depend on their order; means and covariances follow from them by a fixed
-sequence of double-precision operations, rounded once to float32 at the end.
+Arithmetic: the plain definition in double precision -- distances, means and
+covariances are computed from the pixels of each segment with numpy float64
+operations.  The paper fixes no precision; an implementation that decides in
+single precision may choose either centre where two distances lie within its
+rounding error of each other (``assign`` reports the two best distances so a
+check can tell such near-ties apart).
+
+The candidate set: the clamp keeps every centre within S of its seed, so a
+centre within S of pixel p (per axis) has its seed within 2 S of p, i.e. in
+one of the 5 x 5 grid cells around p's cell.  ``assign`` therefore scans those
+cells only; that restriction is exact, not an approximation.
 """
 
 from __future__ import annotations
@@ -53,8 +56,6 @@ import numpy as np
 COMPACTNESS = 0.2
 ITERATIONS = 10
 KAPPA = 4.0  # covariance scale: keeps the additive blend of a tiling flat
-COLOUR_SCALE = float(1 << 20)
-COLOUR_LIMIT = 32.0
 
 
 def seeds(mask: np.ndarray, k_target: int, max_seeds: int | None = None):
@@ -80,120 +81,116 @@ def seeds(mask: np.ndarray, k_target: int, max_seeds: int | None = None):
     return S, np.array(pts, np.float64).reshape(-1, 2), np.array(cells, np.int64).reshape(-1, 2)
 
 
-def assign(frame, mask, centers_col, centers_xy, seed_cells, S, m=COMPACTNESS):
-    """Label map (int64 [H, W], -1 outside the mask) for the given float32
-    centres: a mask pixel joins the candidate minimising, in float32,
-    D = ((r - r_c)^2 + (g - g_c)^2) + (b - b_c)^2 + lam ((dx^2 + dy^2)),
-    lam = float32((m / S)^2), among centres with |dx|, |dy| <= float32(S);
-    candidates are visited in ascending index and only a strictly smaller D
-    replaces the best."""
-    _, h, w = frame.shape
-    label = np.full((h, w), -1, np.int64)
-    ys, xs = np.nonzero(mask)          # the mask pixels, raster order
-    if len(xs) == 0 or len(centers_xy) == 0:
-        return label
-    f32 = np.float32
-    col = frame[:, ys, xs].astype(f32)
-    PX = (xs.astype(np.float64) + 0.5).astype(f32)
-    PY = (ys.astype(np.float64) + 0.5).astype(f32)
-    S32 = f32(S)
-    lam = f32((m / S) * (m / S))
-    ccol = np.asarray(centers_col, f32)
-    cxy = np.asarray(centers_xy, f32)
-    best = np.full(len(xs), np.inf, f32)
-    lab = np.full(len(xs), -1, np.int64)
+def _candidates(xs, ys, seed_cells, S, w, h):
+    """[25, P] candidate centre indices of the pixels (x, y) (the seeds of the
+    5 x 5 cells around each pixel's cell, -1 where none), ascending per pixel."""
     gx = int(math.ceil(w / S))
     gy = int(math.ceil(h / S))
     cell_of = np.full((gy, gx), -1, np.int64)
     for idx, (i, j) in enumerate(seed_cells):
         cell_of[j, i] = idx
-    pcx = np.floor(PX.astype(np.float64) / S).astype(np.int64)
-    pcy = np.floor(PY.astype(np.float64) / S).astype(np.int64)
-    cand_lists = []
+    pcx = np.floor((xs + 0.5) / S).astype(np.int64)
+    pcy = np.floor((ys + 0.5) / S).astype(np.int64)
+    lists = []
     for dj in range(-2, 3):
         for di in range(-2, 3):
             cx, cy = pcx + di, pcy + dj
             ok = (cx >= 0) & (cx < gx) & (cy >= 0) & (cy < gy)
-            idx = np.where(ok, cell_of[np.clip(cy, 0, gy - 1), np.clip(cx, 0, gx - 1)], -1)
-            cand_lists.append(idx)
-    cand = np.stack(cand_lists, 0)  # [25, P]
-    order = np.argsort(np.where(cand < 0, np.iinfo(np.int64).max, cand), axis=0, kind="stable")
-    cand = np.take_along_axis(cand, order, 0)
+            lists.append(np.where(ok, cell_of[np.clip(cy, 0, gy - 1), np.clip(cx, 0, gx - 1)], -1))
+    cand = np.stack(lists, 0)
+    key = np.where(cand < 0, np.iinfo(np.int64).max, cand)
+    return np.take_along_axis(cand, np.argsort(key, axis=0, kind="stable"), 0)
+
+
+def assign(frame, mask, centers_col, centers_xy, seed_cells, S, m=COMPACTNESS, with_gap=False):
+    """The assignment step (double precision): label map (int64 [H, W], -1
+    outside the mask; a mask pixel with no centre within S also gets -1).
+    With ``with_gap`` also returns the smallest and the second smallest
+    distance of every pixel ([H, W] float64 each, inf where absent)."""
+    _, h, w = frame.shape
+    label = np.full((h, w), -1, np.int64)
+    d1 = np.full((h, w), np.inf)
+    d2 = np.full((h, w), np.inf)
+    ys, xs = np.nonzero(mask)          # the mask pixels, raster order
+    if len(xs) == 0 or len(centers_xy) == 0:
+        return (label, d1, d2) if with_gap else label
+    col = np.asarray(frame, np.float64)[:, ys, xs]
+    px, py = xs + 0.5, ys + 0.5
+    ccol = np.asarray(centers_col, np.float64)
+    cxy = np.asarray(centers_xy, np.float64)
+    lam = (m / S) ** 2
+    best = np.full(len(xs), np.inf)
+    second = np.full(len(xs), np.inf)
+    lab = np.full(len(xs), -1, np.int64)
+    cand = _candidates(xs, ys, seed_cells, S, w, h)
     for k in range(cand.shape[0]):
         idx = cand[k]
         valid = idx >= 0
         if not valid.any():
             break
         ii = np.where(valid, idx, 0)
-        dx = PX - cxy[ii, 0]
-        dy = PY - cxy[ii, 1]
-        within = valid & (np.abs(dx) <= S32) & (np.abs(dy) <= S32)
-        dr, dg, db = col[0] - ccol[ii, 0], col[1] - ccol[ii, 1], col[2] - ccol[ii, 2]
-        dc = (dr * dr + dg * dg) + db * db
-        d = dc + lam * (dx * dx + dy * dy)
-        take = within & (d < best)
+        dx = px - cxy[ii, 0]
+        dy = py - cxy[ii, 1]
+        within = valid & (np.abs(dx) <= S) & (np.abs(dy) <= S)
+        d = ((col[0] - ccol[ii, 0]) ** 2 + (col[1] - ccol[ii, 1]) ** 2
+             + (col[2] - ccol[ii, 2]) ** 2) + lam * (dx * dx + dy * dy)
+        d = np.where(within, d, np.inf)
+        take = d < best                # candidates ascend: ties keep the lower index
+        second = np.where(take, best, np.minimum(second, d))
         best = np.where(take, d, best)
         lab = np.where(take, idx, lab)
     label[ys, xs] = lab
-    return label
+    d1[ys, xs] = best
+    d2[ys, xs] = second
+    return (label, d1, d2) if with_gap else label
 
 
-def segment_sums(frame, label, seeds_xy):
-    """Exact integer sums per segment: count, sum of u = 2 x + 1 - 2 floor(qx),
-    of v (the same in y), of u^2, u v, v^2 and of rint(c 2^20) per channel
-    (object arrays of Python ints, [k])."""
-    _, h, w = frame.shape
-    k = len(seeds_xy)
-    sums = {key: [0] * k for key in ("n", "u", "v", "uu", "uv", "vv", "r", "g", "b")}
+def segment_means(frame, label, k):
+    """Per segment 0..k-1: pixel count, mean pixel centre (x, y) and mean
+    colour (r, g, b), plain float64 means over the segment's pixels
+    (count 0: NaN means)."""
     ys, xs = np.nonzero(label >= 0)
-    if len(xs) == 0 or k == 0:
-        return sums
     lab = label[ys, xs]
-    fx = np.floor(np.asarray(seeds_xy)[:, 0]).astype(np.int64)
-    fy = np.floor(np.asarray(seeds_xy)[:, 1]).astype(np.int64)
-    u = 2 * xs.astype(np.int64) + 1 - 2 * fx[lab]
-    v = 2 * ys.astype(np.int64) + 1 - 2 * fy[lab]
-    q = [np.rint(np.clip(frame[ch, ys, xs].astype(np.float64), -COLOUR_LIMIT, COLOUR_LIMIT)
-                 * COLOUR_SCALE).astype(np.int64) for ch in range(3)]
-    for key, vals in (("n", np.ones_like(u)), ("u", u), ("v", v), ("uu", u * u), ("uv", u * v),
-                      ("vv", v * v), ("r", q[0]), ("g", q[1]), ("b", q[2])):
-        acc = np.zeros(k, np.int64)
-        np.add.at(acc, lab, vals)      # int64: exact, order-free
-        sums[key] = [int(a) for a in acc]
-    return sums
+    cnt = np.bincount(lab, minlength=k).astype(np.float64)[:k]
+    with np.errstate(invalid="ignore", divide="ignore"):
+        mx = np.bincount(lab, weights=xs + 0.5, minlength=k)[:k] / cnt
+        my = np.bincount(lab, weights=ys + 0.5, minlength=k)[:k] / cnt
+        mc = np.stack([np.bincount(lab, weights=np.asarray(frame[ch], np.float64)[ys, xs],
+                                   minlength=k)[:k] / cnt for ch in range(3)], 1)
+    return cnt, np.stack([mx, my], 1), mc
 
 
 def update(frame, label, centers_col, centers_xy, seeds_xy, S):
-    """New float32 centres: the segment's mean position (u / (2 n) + floor(q)
-    in double) clamped to within S of the seed, and mean colour (sum /
-    (n 2^20) in double); empty segments keep their centre."""
-    sm = segment_sums(frame, label, seeds_xy)
-    new_col = np.asarray(centers_col, np.float32).copy()
-    new_xy = np.asarray(centers_xy, np.float32).copy()
-    for c in range(len(seeds_xy)):
-        n = sm["n"][c]
-        if n == 0:
-            continue
-        qx, qy = float(seeds_xy[c][0]), float(seeds_xy[c][1])
-        mx = float(sm["u"][c]) / float(2 * n) + math.floor(qx)
-        my = float(sm["v"][c]) / float(2 * n) + math.floor(qy)
-        new_xy[c, 0] = np.float32(min(max(mx, qx - S), qx + S))
-        new_xy[c, 1] = np.float32(min(max(my, qy - S), qy + S))
-        for ch, key in enumerate(("r", "g", "b")):
-            new_col[c, ch] = np.float32(float(sm[key][c]) / (float(n) * COLOUR_SCALE))
+    """The update step: every centre with pixels moves to its segment's mean
+    colour and mean pixel centre, the position clamped to within S of its
+    seed on each axis; empty segments keep their centre.  Float64 out."""
+    k = len(seeds_xy)
+    cnt, mxy, mc = segment_means(frame, label, k)
+    new_col = np.array(centers_col, np.float64, copy=True)
+    new_xy = np.array(centers_xy, np.float64, copy=True)
+    has = cnt > 0
+    q = np.asarray(seeds_xy, np.float64)
+    new_xy[has] = np.clip(mxy[has], q[has] - S, q[has] + S)
+    new_col[has] = mc[has]
     return new_col, new_xy
 
 
-def segment(frame, mask, k_target, iterations=ITERATIONS, m=COMPACTNESS, max_seeds=None):
-    """K-means superpixels of the mask: (S, seeds [M,2], labels [H,W], centres)."""
-    frame = np.asarray(frame, np.float32)
-    mask = np.asarray(mask, bool)
-    S, sxy, cells = seeds(mask, k_target, max_seeds)
+def initial_centres(frame, sxy):
+    """Centres before the first assignment: at the seeds, with the frame's
+    colour at the seed's pixel."""
     _, h, w = frame.shape
     xi = np.clip(np.floor(sxy[:, 0]).astype(np.int64), 0, w - 1)
     yi = np.clip(np.floor(sxy[:, 1]).astype(np.int64), 0, h - 1)
-    ccol = frame[:, yi, xi].T.astype(np.float32)
-    cxy = sxy.astype(np.float32)
+    return np.asarray(frame, np.float64)[:, yi, xi].T.copy(), np.array(sxy, np.float64)
+
+
+def segment(frame, mask, k_target, iterations=ITERATIONS, m=COMPACTNESS, max_seeds=None):
+    """K-means superpixels of the mask: (S, seeds [M,2], labels [H,W], centres
+    (colour [M,3], position [M,2]) used by the last assignment)."""
+    mask = np.asarray(mask, bool)
+    S, sxy, cells = seeds(mask, k_target, max_seeds)
+    _, h, w = frame.shape
+    ccol, cxy = initial_centres(frame, sxy)
     label = np.full((h, w), -1, np.int64)
     for it in range(iterations):
         label = assign(frame, mask, ccol, cxy, cells, S, m)
@@ -203,48 +200,50 @@ def segment(frame, mask, k_target, iterations=ITERATIONS, m=COMPACTNESS, max_see
 
 
 def gaussians_from_segments(frame, label, sxy, S):
-    """[9, M] float64 Gaussians from the final segments (see module doc), from
-    the exact integer sums: mean = u / (2 n) + floor(q); covariance of the
-    pixel centres (uu / n - (u / n)^2) / 4 etc. in double; Sigma = KAPPA
-    (covariance + I/12); L = chol(Sigma); colour = sum / (n 2^20); weight =
-    n / (2 pi l1 l3)."""
+    """[9, M] float64 Gaussians from the final segments (see module doc): mean
+    of the pixel centres, population covariance of the pixel centres, Sigma =
+    KAPPA (covariance + I/12), L = chol(Sigma) (Eq. 1), mean colour, weight
+    n / (2 pi sqrt(det Sigma)) = n / (2 pi l1 l3)."""
+    frame = np.asarray(frame, np.float64)
     _, h, w = frame.shape
     k = len(sxy)
     out = np.zeros((9, k), np.float64)
-    sm = segment_sums(frame, label, sxy)
-    two_pi = 2.0 * math.pi
+    ys, xs = np.nonzero(label >= 0)
+    lab = label[ys, xs]
+    order = np.argsort(lab, kind="stable")
+    lab, xs, ys = lab[order], xs[order], ys[order]
+    starts = np.searchsorted(lab, np.arange(k + 1))
     for i in range(k):
-        n = sm["n"][i]
-        if n == 0:
+        a, b = starts[i], starts[i + 1]
+        if a == b:
             xi = min(max(int(math.floor(sxy[i, 0])), 0), w - 1)
             yi = min(max(int(math.floor(sxy[i, 1])), 0), h - 1)
-            s = 2.0 * (S / math.sqrt(12.0))
+            s = math.sqrt(KAPPA * S * S / 12.0)
             out[:, i] = [sxy[i, 0], sxy[i, 1], s, 0.0, s, frame[0, yi, xi], frame[1, yi, xi],
                          frame[2, yi, xi], 1.0]
             continue
-        fn = float(n)
-        au, av = float(sm["u"][i]) / fn, float(sm["v"][i]) / fn
-        cxx = (float(sm["uu"][i]) / fn - au * au) / 4.0
-        cxy = (float(sm["uv"][i]) / fn - au * av) / 4.0
-        cyy = (float(sm["vv"][i]) / fn - av * av) / 4.0
-        vxx = cxx + 1.0 / 12.0
-        vyy = cyy + 1.0 / 12.0
-        l1 = math.sqrt(vxx)
-        l2 = cxy / l1
-        l3 = math.sqrt(vyy - l2 * l2)
-        # Sigma = KAPPA (cov + I/12): the factor sqrt(KAPPA) = 2 is exact
-        l1, l2, l3 = 2.0 * l1, 2.0 * l2, 2.0 * l3
-        out[0, i] = float(sm["u"][i]) / float(2 * n) + math.floor(sxy[i, 0])
-        out[1, i] = float(sm["v"][i]) / float(2 * n) + math.floor(sxy[i, 1])
+        px, py = xs[a:b] + 0.5, ys[a:b] + 0.5
+        n = float(b - a)
+        mx, my = px.mean(), py.mean()
+        cxx = np.mean((px - mx) ** 2)
+        cxy = np.mean((px - mx) * (py - my))
+        cyy = np.mean((py - my) ** 2)
+        sxx = KAPPA * (cxx + 1.0 / 12.0)
+        sxy_ = KAPPA * cxy
+        syy = KAPPA * (cyy + 1.0 / 12.0)
+        l1 = math.sqrt(sxx)
+        l2 = sxy_ / l1
+        l3 = math.sqrt(syy - l2 * l2)
+        out[0, i], out[1, i] = mx, my
         out[2, i], out[3, i], out[4, i] = l1, l2, l3
-        for ch, key in enumerate(("r", "g", "b")):
-            out[5 + ch, i] = float(sm[key][i]) / (fn * COLOUR_SCALE)
-        out[8, i] = fn / (two_pi * l1 * l3)
+        for ch in range(3):
+            out[5 + ch, i] = frame[ch, ys[a:b], xs[a:b]].mean()
+        out[8, i] = n / (2.0 * math.pi * l1 * l3)
     return out
 
 
 def background_gaussians(frame, mask, bg_xy, count):
-    """[9, count] isotropic Gaussians at bg_xy[:count] (variance a / (2 pi))."""
+    """[9, count] isotropic Gaussians at bg_xy[:count] (variance KAPPA a / (2 pi))."""
     _, h, w = frame.shape
     out = np.zeros((9, count), np.float64)
     if count <= 0:
@@ -258,7 +257,7 @@ def background_gaussians(frame, mask, bg_xy, count):
     out[1] = xy[:, 1]
     out[2] = s
     out[4] = s
-    out[5:8] = frame[:, yi, xi]
+    out[5:8] = np.asarray(frame, np.float64)[:, yi, xi]
     out[8] = 1.0 / KAPPA
     return out
 
@@ -273,4 +272,5 @@ def roi_init(frame, mask, n, roi_frac, bg_xy, iterations=ITERATIONS, m=COMPACTNE
     M = len(sxy)
     roi = gaussians_from_segments(frame, label, sxy, S)
     bg = background_gaussians(frame, mask, bg_xy, n - M)
-    return np.concatenate([roi, bg], axis=1), {"S": S, "seeds": sxy, "label": label, "M": M}
+    return np.concatenate([roi, bg], axis=1), {"S": S, "seeds": sxy, "label": label, "M": M,
+                                               "centres": centres}

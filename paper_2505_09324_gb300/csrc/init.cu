@@ -29,7 +29,7 @@ namespace gs2d {
 namespace {
 
 constexpr double kCompactness = 0.2;
-constexpr int kIterations = 10;
+constexpr int kIterations = kRoiIterations;
 constexpr double kKappa = 4.0;  // covariance scale: keeps the blend of a tiling flat
 constexpr double kColourScale = 1048576.0;  // 2^20
 constexpr double kColourLimit = 32.0;
@@ -417,7 +417,8 @@ uint64_t roi_init_scratch_bytes(int W, int H, int n) {
 
 gs2d_status roi_init(const float* frame, const uint8_t* mask, int W, int H, int n, float roi_frac,
                      const float* bg_xy, float* params, int32_t* n_roi, void* scratch,
-                     uint64_t scratch_bytes, cudaStream_t s, char* err, size_t err_len) {
+                     uint64_t scratch_bytes, cudaStream_t s, char* err, size_t err_len,
+                     float* cen_trace, int32_t* label_trace) {
   if (scratch_bytes < roi_init_scratch_bytes(W, H, n)) {
     snprintf(err, err_len, "gs2d_roi_init: scratch too small");
     return GS2D_ERR_INVALID_ARG;
@@ -454,7 +455,14 @@ gs2d_status roi_init(const float* frame, const uint8_t* mask, int W, int H, int 
     e = launch_pdl(k_sp_init_centres, cb, 128, 0, s, a);
     // the last assignment's sums make the Gaussians
     for (int it = 0; it < kIterations && e == cudaSuccess; it++) {
-      e = launch_pdl(k_sp_assign, pb, 256, 0, s, a);
+      // optional trace: the centres this assignment uses, the labels it makes
+      if (cen_trace)
+        e = cudaMemcpyAsync(cen_trace + (size_t)it * 5 * n, a.cen, 5ull * n * sizeof(float),
+                            cudaMemcpyDeviceToDevice, s);
+      if (e == cudaSuccess) e = launch_pdl(k_sp_assign, pb, 256, 0, s, a);
+      if (e == cudaSuccess && label_trace)
+        e = cudaMemcpyAsync(label_trace + (size_t)it * hw, a.label, hw * sizeof(int32_t),
+                            cudaMemcpyDeviceToDevice, s);
       if (e == cudaSuccess && it + 1 < kIterations) e = launch_pdl(k_sp_update, cb, 128, 0, s, a);
     }
     if (e == cudaSuccess) e = launch_pdl(k_sp_gaussians, cb, 128, 0, s, a, n, params);
