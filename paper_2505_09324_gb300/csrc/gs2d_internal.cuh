@@ -104,10 +104,10 @@ __device__ __forceinline__ gs2d_clip clip_of_tile(const ClipSet& cs, int t) {
 
 // Per-Gaussian render record, three float4 rows.
 //   r0 = (mu_x, mu_y, a1, a2)      a1 = s/l1, a2 = s/l3, s = sqrt(log2(e)/2)
-//   r1 = (k, tau2, c'_r, c'_g)     k = -l2/l3, tau2 = tau * log2(e), c' = w c
+//   r1 = (kappa, tau2, c'_r, c'_g) kappa = -(l2/l3) a1, tau2 = tau * log2(e), c' = w c
 //   r2 = (c'_b, hx, hy, 0)         half extents of the tau-ellipse (+ slack)
-// With dx = px - mu_x, dy = py - mu_y:
-//   u1 = a1 dx, u2 = a2 dy + k u1, q = u1^2 + u2^2 = sigma log2(e),
+// With dx = px - mu_x, dy = py - mu_y (Eq. 1: Sigma^-1 = L^-T L^-1):
+//   u1 = a1 dx, u2 = a2 dy + kappa dx, q = u1^2 + u2^2 = sigma log2(e),
 //   contribution c' 2^-q if q <= tau2.
 struct Rec {
   float4 r0, r1, r2;
@@ -230,8 +230,9 @@ __device__ __forceinline__ void write_record(int i, int n, bool visible, float s
     // the box stays conservative under FP32 rounding
     const float hx = sqrtf(2.0f * tau * sxx) * 1.001f + 0.0039f;
     const float hy = sqrtf(2.0f * tau * syy) * 1.001f + 0.0039f;
-    r0 = make_float4(mx, my, s / l1, s / l3);
-    r1 = make_float4(-l2 / l3, tau2, w * cr, w * cg);
+    const float a1 = s / l1;
+    r0 = make_float4(mx, my, a1, s / l3);
+    r1 = make_float4((-l2 / l3) * a1, tau2, w * cr, w * cg);
     r2 = make_float4(w * cb, hx, hy, 0.0f);
   }
   rec[i] = r0;
@@ -361,9 +362,13 @@ cudaError_t launch_prepare_fit(const gs2d_plan& p, void* ws, const float* params
                                cudaStream_t s);
 
 uint64_t roi_init_scratch_bytes(int W, int H, int n);
+// cen_trace / label_trace (device, or NULL): per K-means iteration the
+// centres the assignment used ([10][5][n]) and the labels it made ([10][H][W]).
+constexpr int kRoiIterations = 10;
 gs2d_status roi_init(const float* frame, const uint8_t* mask, int W, int H, int n, float roi_frac,
                      const float* bg_xy, float* params, int32_t* n_roi, void* scratch,
-                     uint64_t scratch_bytes, cudaStream_t s, char* err, size_t err_len);
+                     uint64_t scratch_bytes, cudaStream_t s, char* err, size_t err_len,
+                     float* cen_trace = nullptr, int32_t* label_trace = nullptr);
 
 // Records msg as the calling thread's last error (gs2d_last_error); returns st.
 gs2d_status set_error(gs2d_status st, const char* msg);

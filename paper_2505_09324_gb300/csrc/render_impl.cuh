@@ -21,17 +21,20 @@
 // inside the tile, a mask of the warps whose rows that box touches, and the
 // slot where the backward pass writes this (tile, Gaussian) pair's sums.
 //
-// sigma in Cholesky form (Eq. 1): with s = sqrt(log2(e)/2),
-//   u1 = s dx / l1,  u2 = s (dy - l2 dx / l1) / l3 = a2 dy + k u1,
-//   q = u1^2 + u2^2 = sigma log2(e),  contribution c' 2^-q if q <= tau log2(e).
-// For a fixed column dx, u1 and k u1 are constant, so each further pixel of
-// that column costs one FADD (dy), one FFMA (u2) and one FFMA (q).
+// sigma in Cholesky form (Eq. 1): with s = sqrt(log2(e)/2) and tile-local
+// offsets dx = px - mu_x, dy = py - mu_y,
+//   u1 = a1 dx,  u2 = a2 dy + kappa dx  (a1 = s / l1, a2 = s / l3,
+//   kappa = -(l2 / l3) a1),  q = u1^2 + u2^2 = sigma log2(e),
+//   contribution c' 2^-q if q <= tau log2(e).
+// For a fixed column, u1 is constant and u2 advances by a2 per row, so each
+// further pixel of that column costs one FADD (u2) and one FFMA (q).
 //
 // Forward: thread <-> one column x R-row strip (R = 2 for T = 8, else 4);
 // a warp covers a band of rows.  After each batch is staged every warp
 // compacts (by ballot) the batch's Gaussians whose box meets its band into
-// its own ascending list and walks only that list; within a strip the row
-// offset u2 advances by the constant a2 per row.  Accumulation is in ascending
+// its own ascending list; each list entry carries the Gaussian's staged
+// position and the row term a2 dy of the band's first row, so a thread's
+// setup per Gaussian is four FP32 operations.  Accumulation is in ascending
 // Gaussian index (the list order).
 //
 // Backward: the blend is recomputed from the saved lists (no per-pixel state
@@ -63,8 +66,9 @@ struct TileGeom {
 
 template <int S>
 struct TileSmem {
-  float4 r0[S], r1[S];
-  float cb[S];
+  float4 fa[S];      // (mu_x - ox, a1, kappa, a2): tile-local
+  float4 fb[S];      // (tau2, c'_r, c'_g, c'_b)
+  float my[S];       // mu_y - oy
   int4 bb[S];        // local box (x0, x1, y0, y1); x0 > x1 when empty
   int slot[S];       // partial slot of the pair
   uint32_t wmask[S]; // bit w: box touches the rows of warp w
@@ -136,39 +140,51 @@ __device__ __forceinline__ void stage_batch(TileSmem<S>& sm, const RenderArgs& a
       const int w0 = bb.z / G::RW, w1 = bb.w / G::RW;
       wm = ((2u << w1) - 1u) & ~((1u << w0) - 1u);
     }
-    sm.r0[k] = r0;
-    sm.r1[k] = r1;
-    sm.cb[k] = r2.x;
+    sm.fa[k] = make_float4(r0.x - ox, r0.z, r1.x, r0.w);
+    sm.fb[k] = make_float4(r1.y, r1.z, r1.w, r2.x);
+    sm.my[k] = r0.y - oy;
     sm.bb[k] = bb;
     sm.wmask[k] = wm;
     sm.slot[k] = covered ? off + dy * rc.z + dx : -1;
   }
 }
 
-// Forward accumulation over staged Gaussians [0, cnt) for this thread's column
-// px and rows py[0 .. R).
+// One entry of a warp's list of staged Gaussians: the row term a2 (y - mu_y)
+// at the first row of the warp's band (float bits) and the byte offset of
+// the Gaussian in the staged arrays.
+struct WarpEntry {
+  uint32_t t;
+  uint32_t off;
+};
+
+// Forward accumulation over the warp's list for this thread's column
+// (tile-local centre pxl) and rows; drow = rows between the band's first row
+// and this thread's first row.
 template <int T, int S>
-__device__ __forceinline__ void fwd_batch(const TileSmem<S>& sm, const uint8_t* __restrict__ wl,
-                                          int wn, float px, const float (&py)[TileGeom<T>::R],
+__device__ __forceinline__ void fwd_batch(const TileSmem<S>& sm, const WarpEntry* __restrict__ wl,
+                                          int wn, float pxl, float drow,
                                           float (&acc)[TileGeom<T>::R][3]) {
   constexpr int R = TileGeom<T>::R;
+  const char* fa_base = reinterpret_cast<const char*>(sm.fa);
+  const char* fb_base = reinterpret_cast<const char*>(sm.fb);
   for (int i = 0; i < wn; i++) {
-    const int j = wl[i];
-    const float4 r0 = sm.r0[j], r1 = sm.r1[j];
-    const float cb = sm.cb[j];
-    const float u1 = r0.z * (px - r0.x);
-    const float c0 = r1.x * u1;
+    const WarpEntry we = wl[i];
+    const float4 fa = *reinterpret_cast<const float4*>(fa_base + we.off);
+    const float4 fb = *reinterpret_cast<const float4*>(fb_base + we.off);
+    const float dx = pxl - fa.x;
+    const float u1 = fa.y * dx;
     const float u1sq = u1 * u1;
-    float u2 = fmaf(r0.w, py[0] - r0.y, c0);
+    float u2 = fmaf(fa.z, dx, __uint_as_float(we.t));
+    if constexpr (T != 32) u2 = fmaf(fa.w, drow, u2);
 #pragma unroll
     for (int r = 0; r < R; r++) {
-      if (r) u2 += r0.w;
+      if (r) u2 += fa.w;
       const float q = fmaf(u2, u2, u1sq);
-      if (q <= r1.y) {
+      if (q <= fb.x) {
         const float e = ex2_approx(-q);
-        acc[r][0] = fmaf(r1.z, e, acc[r][0]);
-        acc[r][1] = fmaf(r1.w, e, acc[r][1]);
-        acc[r][2] = fmaf(cb, e, acc[r][2]);
+        acc[r][0] = fmaf(fb.y, e, acc[r][0]);
+        acc[r][1] = fmaf(fb.z, e, acc[r][1]);
+        acc[r][2] = fmaf(fb.w, e, acc[r][2]);
       }
     }
   }
@@ -209,8 +225,7 @@ __device__ __forceinline__ float group_transpose_sum(const float (&v)[8], int j)
 // nothing).
 template <int T, int S>
 __device__ __forceinline__ void bwd_batch(TileSmem<S>& sm, const float4* __restrict__ s_g,
-                                          int cnt, float ox, float oy, const RenderArgs& a,
-                                          int b) {
+                                          int cnt, const RenderArgs& a, int b) {
   using G = TileGeom<T>;
   float* __restrict__ partial = a.partial;
   const int lane = threadIdx.x & 31;
@@ -240,29 +255,30 @@ __device__ __forceinline__ void bwd_batch(TileSmem<S>& sm, const float4* __restr
       const int rstep = T >> lc;
       const int y0 = bb.z + (j >> lc);
       if (bw > 0 && col <= bb.y && y0 <= bb.w) {
-        const float px = ox + (float)col + 0.5f;
-        const float4 r0 = sm.r0[gi], r1 = sm.r1[gi];
-        const float cr = r1.z, cg = r1.w, cb = sm.cb[gi];
-        const float u1 = r0.z * (px - r0.x);
-        const float c0 = r1.x * u1;
+        const float4 fa = sm.fa[gi], fb = sm.fb[gi];
+        const float dx = ((float)col + 0.5f) - fa.x;
+        const float u1 = fa.y * dx;
         const float u1sq = u1 * u1;
-        const float ustep = r0.w * (float)rstep;
-        float u2 = fmaf(r0.w, (oy + (float)y0 + 0.5f) - r0.y, c0);
+        const float ustep = fa.w * (float)rstep;
+        float u2 = fmaf(fa.w, ((float)y0 + 0.5f) - sm.my[gi], fa.z * dx);
         float ge0 = 0.f, ge1 = 0.f, ge2 = 0.f, ss = 0.f, s2 = 0.f, s22 = 0.f;
-        for (int y = y0; y <= bb.w; y += rstep, u2 += ustep) {
+        const float4* gp = s_g + y0 * T + col;
+        const float4* const gend = s_g + bb.w * T + col;
+        const int gstep = rstep * T;
+        // branch-free: a pixel outside the cut-off adds exact zeros
+#pragma unroll 2
+        for (; gp <= gend; gp += gstep, u2 += ustep) {
           const float q = fmaf(u2, u2, u1sq);
-          if (q <= r1.y) {
-            const float e = ex2_approx(-q);
-            const float4 g = s_g[y * T + col];
-            ge0 = fmaf(g.x, e, ge0);
-            ge1 = fmaf(g.y, e, ge1);
-            ge2 = fmaf(g.z, e, ge2);
-            const float Sv = fmaf(g.x, cr, fmaf(g.y, cg, g.z * cb)) * e;
-            const float su2 = Sv * u2;
-            ss += Sv;
-            s2 += su2;
-            s22 = fmaf(su2, u2, s22);
-          }
+          const float e = q <= fb.x ? ex2_approx(-q) : 0.0f;
+          const float4 g = *gp;
+          ge0 = fmaf(g.x, e, ge0);
+          ge1 = fmaf(g.y, e, ge1);
+          ge2 = fmaf(g.z, e, ge2);
+          const float Sv = fmaf(g.x, fb.y, fmaf(g.y, fb.z, g.z * fb.w)) * e;
+          const float su2 = Sv * u2;
+          ss += Sv;
+          s2 += su2;
+          s22 = fmaf(su2, u2, s22);
         }
         const float a1 = u1 * ss;
         v[0] = ge0;
@@ -288,25 +304,31 @@ __device__ __forceinline__ void bwd_batch(TileSmem<S>& sm, const float4* __restr
 // Per-mode shared memory beyond the staged batch.
 template <int T, int S, int MODE>
 struct ModeSmem {
-  static_assert(S <= 256, "per-warp list entries are 8-bit batch positions");
   static constexpr int kGrad = (MODE == kModeBwd || MODE == kModeL2) ? T * T : 1;
-  float4 g[kGrad];                 // dL/dC of the tile
-  uint8_t wl[TileGeom<T>::NW][S];  // per-warp lists of the staged batch
-  float2 red[TileGeom<T>::NW];     // loss partials per warp
-  unsigned hits;                   // kModeCount
+  static constexpr int kList = (MODE == kModeFwd || MODE == kModeL2) ? S : 1;
+  float4 g[kGrad];                       // dL/dC of the tile
+  WarpEntry wl[TileGeom<T>::NW][kList];  // per-warp lists of the staged batch
+  float2 red[TileGeom<T>::NW];         // loss partials per warp
+  unsigned hits;                       // kModeCount
 };
 
-// Warp wid's list of the staged Gaussians whose box touches its rows, in
-// ascending order; returns its length.
+// Warp wid's list of the staged Gaussians [0, cnt) whose box touches its
+// rows, in ascending order; returns its length.  pyw: tile-local centre of
+// the band's first row.
 template <int T, int S>
 __device__ __forceinline__ int warp_list(const TileSmem<S>& sm, int cnt, int wid, int lane,
-                                         uint8_t* __restrict__ wl) {
+                                         float pyw, WarpEntry* __restrict__ wl) {
   int m = 0;
   for (int base = 0; base < cnt; base += 32) {
     const int k = base + lane;
     const bool on = k < cnt && ((sm.wmask[k] >> wid) & 1u);
     const unsigned bal = __ballot_sync(0xffffffffu, on);
-    if (on) wl[m + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)k;
+    if (on) {
+      WarpEntry e;
+      e.t = __float_as_uint(sm.fa[k].w * (pyw - sm.my[k]));
+      e.off = (uint32_t)(k * sizeof(float4));
+      wl[m + __popc(bal & ((1u << lane) - 1u))] = e;
+    }
     m += __popc(bal);
   }
   __syncwarp();
@@ -320,13 +342,10 @@ __device__ __forceinline__ void process_tile(const RenderArgs& a, const TileFram
   constexpr int R = G::R;
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int x = f.ox + t % T, y0 = f.oy + R * (t / T);
-  const float px = (float)x + 0.5f;
-  float py[R];
-#pragma unroll
-  for (int r = 0; r < R; r++) py[r] = (float)(y0 + r) + 0.5f;
+  // tile-local pixel centres of this thread's column and first row
+  const float pxl = (float)(t % T) + 0.5f, pyl = (float)(R * (t / T)) + 0.5f;
   const size_t HW = (size_t)f.W * f.H;
   const int2 rg = f.rg;
-  const float ox = (float)f.ox, oy = (float)f.oy;
 
   if constexpr (MODE == kModeBwd) {
 #pragma unroll
@@ -343,7 +362,7 @@ __device__ __forceinline__ void process_tile(const RenderArgs& a, const TileFram
       __syncthreads();
       stage_batch<T, S>(sm, a, f, b, cnt);
       __syncthreads();
-      bwd_batch<T, S>(sm, ms.g, cnt, ox, oy, a, b);
+      bwd_batch<T, S>(sm, ms.g, cnt, a, b);
     }
     return;
   }
@@ -373,14 +392,14 @@ __device__ __forceinline__ void process_tile(const RenderArgs& a, const TileFram
       __syncthreads();
       if (!any) continue;
       for (int j = 0; j < cnt; j++) {
-        const float4 r0 = sm.r0[j], r1 = sm.r1[j];
-        const float u1 = r0.z * (px - r0.x);
-        const float c0 = r1.x * u1;
+        const float4 fa = sm.fa[j];
+        const float dx = pxl - fa.x, dy = pyl - sm.my[j], tau2 = sm.fb[j].x;
+        const float u1 = fa.y * dx;
         bool hit = false;
 #pragma unroll
         for (int r = 0; r < R; r++) {
-          const float u2 = fmaf(r0.w, py[r] - r0.y, c0);
-          hit |= changed[r] && fmaf(u2, u2, u1 * u1) <= r1.y;
+          const float u2 = fmaf(fa.w, dy + (float)r, fa.z * dx);
+          hit |= changed[r] && fmaf(u2, u2, u1 * u1) <= tau2;
         }
         if (hit) a.selected[a.list[b + j]] = 1;  // every writer stores 1
       }
@@ -397,12 +416,12 @@ __device__ __forceinline__ void process_tile(const RenderArgs& a, const TileFram
       stage_batch<T, S>(sm, a, f, b, cnt);
       __syncthreads();
       for (int j = 0; j < cnt && x < f.W; j++) {
-        const float4 r0 = sm.r0[j], r1 = sm.r1[j];
-        const float u1 = r0.z * (px - r0.x);
-        const float c0 = r1.x * u1;
+        const float4 fa = sm.fa[j];
+        const float dx = pxl - fa.x, dy = pyl - sm.my[j], tau2 = sm.fb[j].x;
+        const float u1 = fa.y * dx;
         for (int r = 0; r < R; r++) {
-          const float u2 = fmaf(r0.w, py[r] - r0.y, c0);
-          hits += (y0 + r < f.H) && fmaf(u2, u2, u1 * u1) <= r1.y;
+          const float u2 = fmaf(fa.w, dy + (float)r, fa.z * dx);
+          hits += (y0 + r < f.H) && fmaf(u2, u2, u1 * u1) <= tau2;
         }
       }
     }
@@ -428,8 +447,9 @@ __device__ __forceinline__ void process_tile(const RenderArgs& a, const TileFram
       __syncthreads();
       stage_batch<T, S>(sm, a, f, b, cnt);
       __syncthreads();
-      const int wn = warp_list<T, S>(sm, cnt, wid, lane, ms.wl[wid]);
-      fwd_batch<T, S>(sm, ms.wl[wid], wn, px, py, acc);
+      const int wn = warp_list<T, S>(sm, cnt, wid, lane, (float)(G::RW * wid) + 0.5f,
+                                     ms.wl[wid]);
+      fwd_batch<T, S>(sm, ms.wl[wid], wn, pxl, (float)(R * (lane / T)), acc);
       staged = b;
     }
     if constexpr (MODE == kModeFwd) {
@@ -496,7 +516,7 @@ __device__ __forceinline__ void process_tile(const RenderArgs& a, const TileFram
         __syncthreads();
         staged = b;
       }
-      bwd_batch<T, S>(sm, ms.g, cnt, ox, oy, a, b);
+      bwd_batch<T, S>(sm, ms.g, cnt, a, b);
     }
   }
 }
