@@ -194,8 +194,11 @@ gs2d_status gs2d_bin_sort(const gs2d_plan* plan, void* ws, void* stream);
 gs2d_status gs2d_prepare(const gs2d_plan* plan, void* ws, const float* params, void* stream);
 
 /* Forward render, Eq. 2.  img: device [3][H][W] output (every pixel written).
- * Needs gs2d_bin_sort first.  The render kernels are persistent: one wave of
- * thread blocks takes tiles from a queue in the order of gs2d_bin_sort. */
+ * Needs gs2d_bin_sort first.  Tiles are rendered in the queue order of
+ * gs2d_bin_sort (longest list first), by one thread block per tile
+ * (GS2D_LAUNCH_GRID, the default) or by one wave of persistent blocks that
+ * take tiles from a queue (GS2D_LAUNCH_PERSISTENT), as gs2d_config.launch
+ * says. */
 gs2d_status gs2d_render_fwd(const gs2d_plan* plan, void* ws, float* img, void* stream);
 
 /* Forward render that allocates nothing (the paper has no counterpart; this
@@ -209,8 +212,8 @@ gs2d_status gs2d_render_fwd(const gs2d_plan* plan, void* ws, float* img, void* s
  * a fixed 16 MiB array that the library reserves on every GPU that loads it,
  * held until the process exits.  Frames and Gaussian counts whose workspace
  * (with room for at least 1024 tile entries) exceeds 16 MiB are rejected with
- * GS2D_ERR_INVALID_ARG and a message; the entry capacity is whatever the rest
- * of the array holds (about 3e5 entries at 1920x1080 with 20 000 Gaussians),
+ * GS2D_ERR_INVALID_ARG and a message; the entry capacity is the largest that
+ * fits the array (about 3.5e5 entries at 1920x1080 with 20 000 Gaussians),
  * and an overflow renders zero and reports GS2D_ERR_CAPACITY through status
  * (device int32, may be NULL), written on the stream after the render.
  * Makes no cudaMalloc, cudaFree or other allocating call.  The first call on
@@ -265,6 +268,30 @@ gs2d_status gs2d_adam_step(float* params, const float* grads, float* m, float* v
  * call.  target: device, the plan's image layout. */
 gs2d_status gs2d_fit_step(const gs2d_plan* plan, void* ws, const float* target, float* params,
                           float* adam_m, float* adam_v, void* stream);
+
+/* Optimiser state of the fit loop kept in the workspace header: the Adam
+ * step counter and the running powers beta1^step, beta2^step and
+ * lr_decay^(step - 1) (kept as products, so a checkpoint holds them exactly).
+ * Together with params, adam_m and adam_v it is a checkpoint of a fit. */
+typedef struct {
+  int32_t step;
+  int32_t reserved;
+  double beta1_pow, beta2_pow, decay_pow;
+} gs2d_fit_state;
+
+/* Reads the fit loop's optimiser state (host out); synchronises the stream. */
+gs2d_status gs2d_fit_state_get(const gs2d_plan* plan, const void* ws, gs2d_fit_state* state,
+                               void* stream);
+
+/* Resumes a fit from a checkpoint: sets the optimiser state (host in, step
+ * >= 0) in the workspace, stream-ordered, and marks the tile lists unbuilt
+ * (the next gs2d_fit_step bins afresh, which gives the results of the
+ * retained lists).  With params, adam_m and adam_v restored by the caller,
+ * the following gs2d_fit_step calls give bit for bit what the interrupted
+ * fit would have.  (Checkpoint/resume is the library's; the paper has no
+ * counterpart.) */
+gs2d_status gs2d_fit_state_set(const gs2d_plan* plan, void* ws, const gs2d_fit_state* state,
+                               void* stream);
 
 /* Restarts the optimiser of gs2d_fit_step: zeroes adam_m and adam_v (device,
  * 9n floats each) and the workspace header (step counter, status word). */
@@ -333,6 +360,24 @@ typedef struct {
 gs2d_status gs2d_quantize(const float* params, int32_t n, const gs2d_quant* q, uint16_t* codes,
                           float* dequant, float* ranges, void* stream);
 
+/* Post-training calibration (Sec. 3.3 A: the quantisation parameters are
+ * fixed after fitting, from a representative set of fitted frames): for
+ * every uniform row (bits[r] in 1 ... 16; host int32 [9]) of params (device
+ * float [9][n], the frames' Gaussians side by side), the central `coverage`
+ * interval of the row's finite values, coverage in (0, 1]: lo and hi are the
+ * (1 - coverage)/2 and (1 + coverage)/2 quantiles with linear interpolation
+ * between order statistics (coverage 1: the row's minimum and maximum).  The
+ * order statistics are found on the device (a radix select on the values'
+ * order-preserving 32-bit keys); the interpolation is formed in double and
+ * rounded once.  Rows without spread (or without finite values) get
+ * hi = lo + 1; other rows get lo = hi = 0.  lo, hi: host float [9] out.
+ * scratch: device, gs2d_quant_calibrate_scratch_bytes() bytes.
+ * Synchronises the stream (an offline, training-stage step). */
+size_t gs2d_quant_calibrate_scratch_bytes(void);
+gs2d_status gs2d_quant_calibrate(const float* params, int32_t n, const int32_t* bits,
+                                 double coverage, void* scratch, size_t scratch_bytes, float* lo,
+                                 float* hi, void* stream);
+
 /* Quantisation-aware fit iteration (Sec. 3.3 A, QAT): params are
  * fake-quantised with q, the frame is rendered from the quantised values and
  * the gradient taken there, and Adam updates the float params (the
@@ -356,6 +401,18 @@ size_t gs2d_code_entropy_scratch_bytes(void);
 gs2d_status gs2d_code_entropy(const uint16_t* codes, int32_t n, const int32_t* bits,
                               const uint8_t* select, void* scratch, size_t scratch_bytes,
                               double* out_bits, void* stream);
+
+/* Coded size of one frame (Sec. 3.3 B): the sum over rows of
+ * gs2d_code_entropy's code lengths (over the selected columns when select is
+ * given), plus, when select (device uint8 [n]) is given (a P-frame), each
+ * selected Gaussian's index of ceil(log2 max(n, 2)) bits, plus, when refine
+ * != 0, the frame's own ranges (two float32 per uniform row).  out_bits:
+ * device double [1].  scratch: device, gs2d_frame_bits_scratch_bytes()
+ * bytes.  Other arguments as gs2d_code_entropy. */
+size_t gs2d_frame_bits_scratch_bytes(void);
+gs2d_status gs2d_frame_bits(const uint16_t* codes, int32_t n, const int32_t* bits,
+                            const uint8_t* select, int32_t refine, void* scratch,
+                            size_t scratch_bytes, double* out_bits, void* stream);
 
 /* Totals of a coded sequence (host arithmetic, Eq. 3-4).  counts[k] (host
  * int32 [frames]): Gaussians coded in frame k; payload_bits[k] (host double
@@ -383,11 +440,16 @@ gs2d_status gs2d_frame_from_rgb8(const uint8_t* rgb, int32_t width, int32_t heig
  * float32, gs2d_frame_from_rgb8); params_host (pinned host, 9n floats, or
  * NULL to keep the device params) is copied to params; then gs2d_fit_step;
  * then params is copied to params_out_host (pinned host, or NULL).  The
- * frame's upload and conversion run on an auxiliary stream of the calling
- * thread (created once per device) and overlap the projection and binning;
- * the render waits for them, and they wait for the work queued on `stream`
- * before the call, so the call is ordered on `stream` like the others.
- * One-clip plans only. */
+ * frame's upload and conversion run on an auxiliary stream and overlap the
+ * projection and binning; the render waits for them, and they wait for the
+ * work queued on `stream` before the call, so the call is ordered on
+ * `stream` like the others.  The auxiliary stream and its two events are
+ * the only CUDA objects the library creates: one set per host thread and
+ * device, on that thread's first call with the device current, reused by
+ * every later call and kept until the process exits.  A cudaDeviceReset
+ * destroys them without the library knowing: after one, do not call
+ * gs2d_fit_step_rgb8 on that device again in the same process.  One-clip
+ * plans only. */
 gs2d_status gs2d_fit_step_rgb8(const gs2d_plan* plan, void* ws, const uint8_t* rgb_host,
                                uint8_t* rgb_dev, float* frame_dev, const float* params_host,
                                float* params, float* adam_m, float* adam_v, float* params_out_host,
@@ -412,11 +474,14 @@ uint64_t gs2d_roi_init_scratch_bytes(int32_t width, int32_t height, int32_t n);
  * |dcol|^2 + (0.2 / S)^2 |dxy|^2 among centres within S of the pixel (centres
  * held within S of their seeds), Sigma = 4 (pixel covariance + I/12) (the
  * factor 4 keeps the additive blend of the segments flat), weight =
- * area / (2 pi sqrt(det Sigma)); distances decided in FP32, segment sums
- * exact in integers (colours quantised to 2^-20, clamped to [-32, 32]), so
- * the result is reproducible bit for bit.  The other n - n_roi Gaussians are isotropic
- * (variance = 4 x background area per Gaussian / (2 pi), weight 1/4, colour
- * of the frame) at bg_xy (random positions are inputs).
+ * area / (2 pi sqrt(det Sigma)).  Arithmetic: distances decided in FP32
+ * (centres kept as float32; where two candidates' distances lie within FP32
+ * rounding of each other either may win), segment sums exact in integers
+ * (pixel centres as 2x + 1 - 2 floor(seed); colours quantised to 2^-20,
+ * clamped to [-32, 32], so a mean colour is within 2^-21 of the plain mean),
+ * so the result is reproducible bit for bit.  The other n - n_roi Gaussians
+ * are isotropic (variance = 4 x background area per Gaussian / (2 pi),
+ * weight 1/4, colour of the frame) at bg_xy (random positions are inputs).
  * frame: device [3][H][W] float32.  mask: device [H][W] uint8 (non-zero = in
  * the region).  bg_xy: device [2][n] float32 (row x, row y); the first
  * n - n_roi columns are used.  params: device, 9n floats out (region
@@ -428,6 +493,21 @@ uint64_t gs2d_roi_init_scratch_bytes(int32_t width, int32_t height, int32_t n);
 gs2d_status gs2d_roi_init(const float* frame, const uint8_t* mask, int32_t width, int32_t height,
                           int32_t n, float roi_frac, const float* bg_xy, float* params,
                           int32_t* n_roi, void* scratch, uint64_t scratch_bytes, void* stream);
+
+/* gs2d_roi_init that also writes out the K-means iterations (Sec. 3.2 A), for
+ * inspecting or checking the segmentation step by step.  cen_trace: device
+ * float32 [10][5][n] or NULL: for iteration k the centres its assignment
+ * used, rows r, g, b, x, y of n floats (the first n_roi columns are the
+ * centres; iteration 0 holds the seeds with the frame's colour there).
+ * label_trace: device int32 [10][H][W] or NULL: for iteration k the centre
+ * each pixel joined (-1 outside the mask).  The final Gaussians come from the
+ * labels of iteration 9.  Other arguments, results and errors as
+ * gs2d_roi_init. */
+gs2d_status gs2d_roi_init_trace(const float* frame, const uint8_t* mask, int32_t width,
+                                int32_t height, int32_t n, float roi_frac, const float* bg_xy,
+                                float* params, int32_t* n_roi, void* scratch,
+                                uint64_t scratch_bytes, float* cen_trace, int32_t* label_trace,
+                                void* stream);
 
 /* Fits the plan's n Gaussians to a frame (Sec. 3.2 A: optimise N Gaussians
  * to the frame; I-frames start from an initialiser's output, P-frames from the
@@ -510,6 +590,18 @@ gs2d_status gs2d_gemm_bf16(const void* A, int32_t lda, const void* B, int32_t ld
                            void* out_bf16, int32_t ldc, int32_t splits, float* partial,
                            int32_t* status, void* stream);
 uint64_t gs2d_gemm_partial_bytes(int32_t M, int32_t N, int32_t ldc, int32_t K, int32_t splits);
+
+/* Failure-detection check of the GEMM's bounded waits (not part of the
+ * paper's method).  Launches the gs2d_gemm_bf16 kernel on one 128 x 32 x 64
+ * tile (A: device bf16 [128][64], B: device bf16 [32][64], 16-byte aligned;
+ * out: device float [128][32]) with every operand load withheld and each
+ * mbarrier wait limited to wait_ns (1 ms ... 1 s): the MMA warp's wait for
+ * the first stage runs out while no copy or MMA is in flight, so the kernel
+ * records GS2D_ERR_TIMEOUT in *status (device int32, should hold GS2D_OK),
+ * leaves out unwritten, frees its tensor memory and returns; the context
+ * stays usable.  Asynchronous on stream. */
+gs2d_status gs2d_gemm_wait_check(const void* A, const void* B, float* out, int32_t* status,
+                                 uint64_t wait_ns, void* stream);
 
 /* Network input: frames (device, B x [3][H][W] float32) and masks (device,
  * B x [H][W] uint8, or NULL = all zero) -> x (device, [B][H][W][8] BF16 NHWC:
@@ -627,6 +719,20 @@ gs2d_status gs2d_count_pairs(const gs2d_plan* plan, void* ws, int64_t* pairs, in
 /* Synchronises the stream and returns the workspace status word
  * (GS2D_OK or the first device-detected error); reset != 0 clears it. */
 gs2d_status gs2d_ws_status(const gs2d_plan* plan, void* ws, int32_t reset, void* stream);
+
+/* Throughput probes (not part of the paper's method): the issue-limited peak
+ * rates of the two pipes the render kernels are bound by, measured on the
+ * current device at its current clock, for roofline accounting.
+ * gs2d_probe_peak enqueues one launch of `blocks` blocks on `stream` that
+ * executes gs2d_probe_ops(blocks, iters) FP32 fused multiply-adds
+ * (GS2D_PROBE_FFMA) or MUFU ex2 evaluations (GS2D_PROBE_EX2) in independent
+ * dependency chains; time it with events on the stream.  sink: device, at
+ * least `blocks` floats (one result per block, so no work is dead code).
+ * gs2d_probe_ops returns 0 for blocks or iters < 1. */
+enum { GS2D_PROBE_FFMA = 0, GS2D_PROBE_EX2 = 1 };
+int64_t gs2d_probe_ops(int32_t blocks, int32_t iters);
+gs2d_status gs2d_probe_peak(int32_t kind, int32_t blocks, int32_t iters, float* sink,
+                            void* stream);
 
 /* Message for the calling thread's last error ("" if none).  Copies at most
  * len - 1 characters and a terminating NUL into buf (host). */

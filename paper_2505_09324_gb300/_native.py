@@ -30,14 +30,17 @@ EXPORTS = (
     "gs2d_select_changed", "gs2d_pframe_step", "gs2d_encode_pframe", "gs2d_quantize",
     "gs2d_fit_step_qat", "gs2d_code_entropy_scratch_bytes", "gs2d_code_entropy",
     "gs2d_sequence_bits", "gs2d_frame_from_rgb8", "gs2d_conv_bf16", "gs2d_fit_step_rgb8",
-    "gs2d_fit_rebins",
+    "gs2d_fit_rebins", "gs2d_fit_state_get", "gs2d_fit_state_set",
     "gs2d_encode_batch",
     "gs2d_autotune_ws_bytes", "gs2d_autotune",
     "gs2d_gemm_bf16", "gs2d_gemm_partial_bytes", "gs2d_cnn_input", "gs2d_im2col", "gs2d_col2im",
     "gs2d_transpose_bf16", "gs2d_relu_bwd", "gs2d_cast_weights", "gs2d_head_decode",
     "gs2d_head_smem_bytes", "gs2d_head_decode_bwd", "gs2d_chamfer", "gs2d_chamfer_scratch_bytes",
     "gs2d_read_bins", "gs2d_count_pairs", "gs2d_ws_status",
-    "gs2d_roi_init_scratch_bytes", "gs2d_roi_init",
+    "gs2d_roi_init_scratch_bytes", "gs2d_roi_init", "gs2d_roi_init_trace",
+    "gs2d_probe_ops", "gs2d_probe_peak", "gs2d_gemm_wait_check",
+    "gs2d_quant_calibrate_scratch_bytes", "gs2d_quant_calibrate",
+    "gs2d_frame_bits_scratch_bytes", "gs2d_frame_bits",
     "gs2d_last_error",
 )
 
@@ -70,6 +73,12 @@ class Clip(ctypes.Structure):
                 ("tiles_x", ctypes.c_int32), ("tiles_y", ctypes.c_int32),
                 ("g_off", ctypes.c_int32), ("tile_off", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("pix_off", ctypes.c_int64)]
+
+
+class FitState(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("beta1_pow", ctypes.c_double), ("beta2_pow", ctypes.c_double),
+                ("decay_pow", ctypes.c_double)]
 
 
 class Quant(ctypes.Structure):
@@ -156,6 +165,8 @@ def load(build_if_missing: bool = False):
             "gs2d_frame_from_rgb8": (i32, [P, i32, i32, i64, P, P]),
             "gs2d_fit_step_rgb8": (i32, [pp, P, P, P, P, P, P, P, P, P, P]),
             "gs2d_fit_rebins": (i32, [pp, P, ctypes.POINTER(i64), P]),
+            "gs2d_fit_state_get": (i32, [pp, P, ctypes.POINTER(FitState), P]),
+            "gs2d_fit_state_set": (i32, [pp, P, ctypes.POINTER(FitState), P]),
             "gs2d_conv_bf16": (i32, [P, i32, i32, i32, i32, i32, i32, i32, P, i32, i32, i32, P,
                                      P, i32, P, P]),
             "gs2d_code_entropy": (i32, [P, i32, ctypes.POINTER(i32), P, P, ctypes.c_size_t, P,
@@ -168,7 +179,19 @@ def load(build_if_missing: bool = False):
             "gs2d_roi_init_scratch_bytes": (ctypes.c_uint64, [i32, i32, i32]),
             "gs2d_roi_init": (i32, [P, P, i32, i32, i32, f32, P, P, ctypes.POINTER(i32), P,
                                     ctypes.c_uint64, P]),
+            "gs2d_roi_init_trace": (i32, [P, P, i32, i32, i32, f32, P, P, ctypes.POINTER(i32),
+                                          P, ctypes.c_uint64, P, P, P]),
             "gs2d_last_error": (i32, [ctypes.c_char_p, ctypes.c_size_t]),
+            "gs2d_probe_ops": (i64, [i32, i32]),
+            "gs2d_probe_peak": (i32, [i32, i32, i32, P, P]),
+            "gs2d_gemm_wait_check": (i32, [P, P, P, P, ctypes.c_uint64, P]),
+            "gs2d_quant_calibrate_scratch_bytes": (ctypes.c_size_t, []),
+            "gs2d_frame_bits_scratch_bytes": (ctypes.c_size_t, []),
+            "gs2d_frame_bits": (i32, [P, i32, ctypes.POINTER(i32), P, i32, P, ctypes.c_size_t, P,
+                                      P]),
+            "gs2d_quant_calibrate": (i32, [P, i32, ctypes.POINTER(i32), ctypes.c_double, P,
+                                           ctypes.c_size_t,
+                                           ctypes.POINTER(f32), ctypes.POINTER(f32), P]),
             "gs2d_gemm_bf16": (i32, [P, i32, P, i32, i32, i32, i32, P, i32, P, P, i32, i32, P, P,
                                      P]),
             "gs2d_gemm_partial_bytes": (ctypes.c_uint64, [i32, i32, i32, i32, i32]),
@@ -498,3 +521,37 @@ def fit_rebins(plan: Plan, ws: int, stream: int) -> int:
     check(load().gs2d_fit_rebins(ctypes.byref(plan), _p(ws), ctypes.byref(out), _p(stream)),
           "gs2d_fit_rebins")
     return int(out.value)
+
+
+PROBE_FFMA = 0
+PROBE_EX2 = 1
+
+
+def probe_ops(blocks: int, iters: int) -> int:
+    return int(load().gs2d_probe_ops(blocks, iters))
+
+
+def probe_peak(kind: int, blocks: int, iters: int, sink: int, stream: int):
+    check(load().gs2d_probe_peak(kind, blocks, iters, _p(sink), _p(stream)), "gs2d_probe_peak")
+
+
+def fit_state_get(plan: Plan, ws: int, stream: int) -> FitState:
+    st = FitState()
+    check(load().gs2d_fit_state_get(ctypes.byref(plan), _p(ws), ctypes.byref(st), _p(stream)),
+          "gs2d_fit_state_get")
+    return st
+
+
+def fit_state_set(plan: Plan, ws: int, st: FitState, stream: int):
+    check(load().gs2d_fit_state_set(ctypes.byref(plan), _p(ws), ctypes.byref(st), _p(stream)),
+          "gs2d_fit_state_set")
+
+
+def quant_calibrate(params: int, n: int, bits, coverage: float, scratch: int,
+                    scratch_bytes: int, stream: int):
+    """gs2d_quant_calibrate: (lo, hi) lists of 9 floats."""
+    b = (ctypes.c_int32 * 9)(*[int(x) for x in bits])
+    lo, hi = (ctypes.c_float * 9)(), (ctypes.c_float * 9)()
+    check(load().gs2d_quant_calibrate(_p(params), n, b, float(coverage), _p(scratch),
+                                      scratch_bytes, lo, hi, _p(stream)), "gs2d_quant_calibrate")
+    return list(lo), list(hi)

@@ -298,23 +298,42 @@ uint64_t gs2d_roi_init_scratch_bytes(int32_t width, int32_t height, int32_t n) {
   return roi_init_scratch_bytes(width, height, n);
 }
 
-gs2d_status gs2d_roi_init(const float* frame, const uint8_t* mask, int32_t width, int32_t height,
-                          int32_t n, float roi_frac, const float* bg_xy, float* params,
-                          int32_t* n_roi, void* scratch, uint64_t scratch_bytes, void* stream) {
+static gs2d_status roi_init_checked(const float* frame, const uint8_t* mask, int32_t width,
+                                    int32_t height, int32_t n, float roi_frac, const float* bg_xy,
+                                    float* params, int32_t* n_roi, void* scratch,
+                                    uint64_t scratch_bytes, void* stream, float* cen_trace,
+                                    int32_t* label_trace, const char* what) {
   // (its kernels index pixels with 32-bit integers)
   if (width < 1 || height < 1 || width > 65536 || height > 65536 ||
       (int64_t)width * height > (int64_t(1) << 30) || n < 0 || n > kMaxGaussians)
-    return fail(GS2D_ERR_INVALID_ARG, "gs2d_roi_init: sizes out of range");
+    return fail(GS2D_ERR_INVALID_ARG, "%s: sizes out of range", what);
   if (!(roi_frac >= 0.0f && roi_frac <= 1.0f))
-    return fail(GS2D_ERR_INVALID_ARG, "gs2d_roi_init: roi_frac must be in [0, 1]");
+    return fail(GS2D_ERR_INVALID_ARG, "%s: roi_frac must be in [0, 1]", what);
   if (!frame || !mask || (n > 0 && (!params || !bg_xy)) || !scratch)
-    return fail(GS2D_ERR_INVALID_ARG, "gs2d_roi_init: NULL pointer");
+    return fail(GS2D_ERR_INVALID_ARG, "%s: NULL pointer", what);
   if ((uintptr_t)scratch % 256) return fail(GS2D_ERR_INVALID_ARG, "scratch not 256-byte aligned");
   char msg[256] = "";
   const gs2d_status st = roi_init(frame, mask, width, height, n, roi_frac, bg_xy, params, n_roi,
-                                  scratch, scratch_bytes, (cudaStream_t)stream, msg, sizeof(msg));
+                                  scratch, scratch_bytes, (cudaStream_t)stream, msg, sizeof(msg),
+                                  cen_trace, label_trace);
   if (st != GS2D_OK) return fail(st, "%s", msg);
   return ok();
+}
+
+gs2d_status gs2d_roi_init(const float* frame, const uint8_t* mask, int32_t width, int32_t height,
+                          int32_t n, float roi_frac, const float* bg_xy, float* params,
+                          int32_t* n_roi, void* scratch, uint64_t scratch_bytes, void* stream) {
+  return roi_init_checked(frame, mask, width, height, n, roi_frac, bg_xy, params, n_roi, scratch,
+                          scratch_bytes, stream, nullptr, nullptr, "gs2d_roi_init");
+}
+
+gs2d_status gs2d_roi_init_trace(const float* frame, const uint8_t* mask, int32_t width,
+                                int32_t height, int32_t n, float roi_frac, const float* bg_xy,
+                                float* params, int32_t* n_roi, void* scratch,
+                                uint64_t scratch_bytes, float* cen_trace, int32_t* label_trace,
+                                void* stream) {
+  return roi_init_checked(frame, mask, width, height, n, roi_frac, bg_xy, params, n_roi, scratch,
+                          scratch_bytes, stream, cen_trace, label_trace, "gs2d_roi_init_trace");
 }
 
 static cudaError_t fit_iteration(const gs2d_plan& p, void* ws, const float* target, float* params,
@@ -372,29 +391,28 @@ gs2d_status gs2d_fit_step(const gs2d_plan* plan, void* ws, const float* target, 
 
 // An auxiliary stream per host thread and device for the frame's upload, so
 // that it overlaps the projection and binning (which need only the params).
+// Created on the thread's first call on that device (one non-blocking stream
+// and two events) and kept for the life of the process.
 struct AuxStream {
-  int device = -1;
   cudaStream_t stream = nullptr;
   cudaEvent_t start = nullptr, frame = nullptr;
 };
+constexpr int kAuxDevices = 64;
 
 static cudaError_t aux_stream(AuxStream** out) {
-  static thread_local AuxStream aux;
+  static thread_local AuxStream aux[kAuxDevices];
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (aux.device != dev) {
-    if (aux.stream) {  // another device: start over (the old handles belong to it)
-      aux.stream = nullptr;
-      aux.start = aux.frame = nullptr;
-    }
-    e = cudaStreamCreateWithFlags(&aux.stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&aux.start, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&aux.frame, cudaEventDisableTiming);
+  if (dev < 0 || dev >= kAuxDevices) return cudaErrorInvalidDevice;
+  AuxStream& a = aux[dev];
+  if (!a.stream) {
+    e = cudaStreamCreateWithFlags(&a.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.start, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.frame, cudaEventDisableTiming);
     if (e != cudaSuccess) return e;
-    aux.device = dev;
   }
-  *out = &aux;
+  *out = &a;
   return cudaSuccess;
 }
 
@@ -441,6 +459,47 @@ gs2d_status gs2d_fit_reset(const gs2d_plan* plan, void* ws, float* adam_m, float
   if (st) return st;
   if (plan->n > 0 && (!adam_m || !adam_v)) return fail(GS2D_ERR_INVALID_ARG, "Adam state is NULL");
   return cuda_check(reset_fit(*plan, ws, adam_m, adam_v, (cudaStream_t)stream), "gs2d_fit_reset");
+}
+
+// Sets the optimiser state of the fit loop in the workspace header (a
+// checkpoint's values) and marks the tile lists as not yet built.
+__global__ void k_set_fit_state(WsHeader* __restrict__ hdr, int32_t step, double pw1, double pw2,
+                                double pwd) {
+  hdr->step = step;
+  hdr->pw1 = pw1;
+  hdr->pw2 = pw2;
+  hdr->pwd = pwd;
+  hdr->lists_valid = 0;
+}
+
+gs2d_status gs2d_fit_state_get(const gs2d_plan* plan, const void* ws, gs2d_fit_state* state,
+                               void* stream) {
+  gs2d_status st = check_plan(plan, ws);
+  if (st) return st;
+  if (!state) return fail(GS2D_ERR_INVALID_ARG, "state is NULL");
+  WsHeader h;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(&h, ws_ptr<WsHeader>(ws, *plan, kOffHeader), sizeof(h),
+                                  cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_check(e, "gs2d_fit_state_get");
+  memset(state, 0, sizeof(*state));
+  state->step = h.step;
+  state->beta1_pow = h.pw1;
+  state->beta2_pow = h.pw2;
+  state->decay_pow = h.pwd;
+  return ok();
+}
+
+gs2d_status gs2d_fit_state_set(const gs2d_plan* plan, void* ws, const gs2d_fit_state* state,
+                               void* stream) {
+  gs2d_status st = check_plan(plan, ws);
+  if (st) return st;
+  if (!state || state->step < 0) return fail(GS2D_ERR_INVALID_ARG, "state is NULL or step < 0");
+  k_set_fit_state<<<1, 1, 0, (cudaStream_t)stream>>>(ws_ptr<WsHeader>(ws, *plan, kOffHeader),
+                                                     state->step, state->beta1_pow,
+                                                     state->beta2_pow, state->decay_pow);
+  return cuda_check(cudaGetLastError(), "gs2d_fit_state_set");
 }
 
 gs2d_status gs2d_fit_rebins(const gs2d_plan* plan, const void* ws, int64_t* rebins,

@@ -133,3 +133,54 @@ extern "C" gs2d_status gs2d_sequence_bits(const int32_t* counts, const double* p
   *out = r;
   return set_error(GS2D_OK, "");
 }
+
+// ---------------------------------------------------------------------------
+// Coded size of one frame (Sec. 3.3 B): the rows' ideal code lengths, plus
+// for a P-frame the index of every selected Gaussian (ceil(log2 n) bits),
+// plus the per-frame ranges of a quantiser that refines them per frame
+// (two float32 per uniform row).
+namespace gs2d {
+namespace {
+
+__global__ void k_frame_bits(const double* __restrict__ rows, const uint32_t* __restrict__ hist,
+                             int index_bits, int range_bits, double* __restrict__ out) {
+  double t = 0.0;
+  for (int r = 0; r < 9; r++) t += rows[r];
+  const double m = (double)hist[(size_t)9 * kBins];  // selected columns
+  out[0] = t + m * (double)index_bits + (double)range_bits;
+}
+
+}  // namespace
+}  // namespace gs2d
+
+extern "C" size_t gs2d_frame_bits_scratch_bytes(void) {
+  return gs2d_code_entropy_scratch_bytes() + 16 * sizeof(double);
+}
+
+extern "C" gs2d_status gs2d_frame_bits(const uint16_t* codes, int32_t n, const int32_t* bits,
+                                       const uint8_t* select, int32_t refine, void* scratch,
+                                       size_t scratch_bytes, double* out_bits, void* stream) {
+  if (!scratch || scratch_bytes < gs2d_frame_bits_scratch_bytes() || !out_bits || !bits)
+    return set_error(GS2D_ERR_INVALID_ARG, "gs2d_frame_bits: arguments");
+  const size_t eb = gs2d_code_entropy_scratch_bytes();
+  double* rows = reinterpret_cast<double*>(static_cast<char*>(scratch) +
+                                           ((eb + 15) & ~size_t(15)));
+  gs2d_status st = gs2d_code_entropy(codes, n, bits, select, scratch, eb, rows, stream);
+  if (st != GS2D_OK) return st;
+  int index_bits = 0;
+  if (select) {
+    int64_t span = 1;
+    while (span < (int64_t)(n > 2 ? n : 2)) {
+      span <<= 1;
+      index_bits++;
+    }
+  }
+  int uniform = 0;
+  for (int r = 0; r < 9; r++) uniform += bits[r] > 0;
+  const int range_bits = refine ? 64 * uniform : 0;
+  k_frame_bits<<<1, 1, 0, (cudaStream_t)stream>>>(
+      rows, static_cast<const uint32_t*>(scratch), index_bits, range_bits, out_bits);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(GS2D_ERR_CUDA, cudaGetErrorString(e));
+  return set_error(GS2D_OK, "");
+}

@@ -56,6 +56,39 @@ extern "C" gs2d_status gs2d_gemm_bf16(const void* A, int32_t lda, const void* B,
   return set_error(GS2D_OK, "");
 }
 
+extern "C" gs2d_status gs2d_gemm_wait_check(const void* A, const void* B, float* out,
+                                            int32_t* status, uint64_t wait_ns, void* stream) {
+  if (!A || !B || !out || !status || ((uintptr_t)A & 15) || ((uintptr_t)B & 15))
+    return set_error(GS2D_ERR_INVALID_ARG, "gs2d_gemm_wait_check: NULL or misaligned pointer");
+  if (wait_ns < 1000000ull || wait_ns > 1000000000ull)
+    return set_error(GS2D_ERR_INVALID_ARG, "gs2d_gemm_wait_check: wait_ns outside [1 ms, 1 s]");
+  TcGemmProblem pr;
+  pr.A = static_cast<const __nv_bfloat16*>(A);
+  pr.lda = 64;
+  pr.B = static_cast<const __nv_bfloat16*>(B);
+  pr.ldb = 64;
+  pr.M = 128;
+  pr.N = 32;
+  pr.K = 64;
+  pr.out_f32 = out;
+  pr.out_bf16 = nullptr;
+  pr.ldc = 32;
+  pr.bias = nullptr;
+  pr.relu = 0;
+  pr.splits = 1;
+  pr.partial = nullptr;
+  pr.status = status;
+  pr.wait_ns = wait_ns;
+  pr.withhold_loads = 1;
+  const cudaError_t e = tc_gemm(pr, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    char msg[200];
+    snprintf(msg, sizeof(msg), "gs2d_gemm_wait_check: %s", cudaGetErrorString(e));
+    return set_error(GS2D_ERR_CUDA, msg);
+  }
+  return set_error(GS2D_OK, "");
+}
+
 extern "C" gs2d_status gs2d_conv_bf16(const void* x, int32_t B, int32_t Hi, int32_t Wi,
                                       int32_t C, int32_t ks, int32_t stride, int32_t pad,
                                       const void* W, int32_t ldk, int32_t N, int32_t relu,

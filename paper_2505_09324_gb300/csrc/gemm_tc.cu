@@ -17,9 +17,12 @@
 // Long K is split over gridDim.z (split-K): each split writes an FP32 partial
 // tile and k_splitk_reduce sums the splits in a fixed order (deterministic).
 //
-// Every wait on an mbarrier is bounded in time (%globaltimer, 1 s): on a
-// timeout the kernel records GS2D_ERR_TIMEOUT in the caller's status word,
-// skips the rest of its work, still frees its tensor memory and returns.
+// Every wait on an mbarrier is bounded in time (%globaltimer, 1 s unless the
+// launch asks for less): on a timeout the kernel records GS2D_ERR_TIMEOUT in
+// the caller's status word, skips the rest of its work, still frees its tensor
+// memory and returns.  gs2d_gemm_wait_check exercises that path: its launch
+// withholds every load, so the first wait on a stage runs out while no TMA
+// copy or MMA is in flight.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdio.h>
@@ -71,14 +74,17 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
   return done != 0;
 }
 
-// Waits for the phase of the given parity to complete; false after kWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Waits for the phase of the given parity to complete; false after limit_ns
+// (kWaitNs when 0).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          uint64_t limit_ns = 0) {
   if (mbar_test(bar, parity)) return true;
+  const uint64_t limit = limit_ns ? limit_ns : kWaitNs;
   const uint64_t t0 = global_ns();
   for (;;) {
     for (int i = 0; i < 64; i++)
       if (mbar_test(bar, parity)) return true;
-    if (global_ns() - t0 > kWaitNs) return false;
+    if (global_ns() - t0 > limit) return false;
   }
 }
 
@@ -244,11 +250,11 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUte
   const uint32_t tmem = s_tmem;
 
   if (warp == 0 && lane == 0) {
-    // producer
-    for (int i = 0; i < nk; i++) {
+    // producer (a failure-detection launch withholds every load)
+    for (int i = 0; i < nk && !g.withhold_loads; i++) {
       const int s = i % kStages;
       const uint32_t ph = (uint32_t)(i / kStages) & 1u;
-      if (!mbar_wait(&empty[s], ph ^ 1u)) {  // the preceding phase: free at first
+      if (!mbar_wait(&empty[s], ph ^ 1u, g.wait_ns)) {  // the preceding phase: free at first
         s_fail = 1;
         break;
       }
@@ -264,7 +270,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUte
     for (int i = 0; i < nk; i++) {
       const int s = i % kStages;
       const uint32_t ph = (uint32_t)(i / kStages) & 1u;
-      if (!mbar_wait(&full[s], ph)) {
+      if (!mbar_wait(&full[s], ph, g.wait_ns)) {
         s_fail = 1;
         break;
       }
@@ -282,7 +288,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUte
   __syncwarp();
 
   // epilogue: warp w holds accumulator rows 32 w ... 32 w + 31
-  const bool ready = mbar_wait(&accum, 0);
+  const bool ready = mbar_wait(&accum, 0, g.wait_ns);
   tc_fence_after();
   if (!ready) s_fail = 1;
   __syncthreads();
@@ -580,6 +586,8 @@ cudaError_t tc_gemm(const TcGemmProblem& pr, cudaStream_t s) {
   g.bias = pr.bias;
   g.relu = pr.relu;
   g.status = pr.status;
+  g.wait_ns = pr.wait_ns;
+  g.withhold_loads = pr.withhold_loads;
   g.split_stride = (size_t)pr.M * pr.ldc;
   if (splits == 1) {
     g.out_f32 = pr.out_f32;
@@ -646,6 +654,8 @@ cudaError_t tc_conv(const TcConvProblem& pr, cudaStream_t s) {
   g.bias = nullptr;
   g.relu = pr.relu;
   g.status = pr.status;
+  g.wait_ns = 0;
+  g.withhold_loads = 0;
   const dim3 grid((M + kBM - 1) / kBM, (pr.N + bn - 1) / bn, 1);
   switch (bn) {
     case 32: return launch_conv<32>(tb, cg, g, grid, s);

@@ -7,9 +7,9 @@
 // CUDA graph is being captured, where allocation calls are not allowed.
 // gs2d_render_fwd_noalloc serves them: the caller passes only the parameters
 // and the output image; every intermediate buffer (projected records, tile
-// counts, the radix-sort keys and their ping-pong copies, the histograms, the
-// tile ranges) lives in one file-scope device array of fixed size that the
-// library reserves when it is loaded.  The paper has no counterpart; this is an
+// rectangles and counts, the scans' offsets, the per-tile Gaussian lists, the
+// tile ranges and the render queue) lives in one file-scope device array of
+// fixed size that the library reserves when it is loaded.  The paper has no counterpart; this is an
 // integration convenience.
 #include <mutex>
 #include <stdio.h>
@@ -63,29 +63,28 @@ extern "C" gs2d_status gs2d_render_fwd_noalloc(const float* params, int32_t n, i
   if (!img) return set_error(GS2D_ERR_INVALID_ARG, "gs2d_render_fwd_noalloc: img is NULL");
   if (n > 0 && !params)
     return set_error(GS2D_ERR_INVALID_ARG, "gs2d_render_fwd_noalloc: params is NULL");
-  // Lay out a workspace with the largest entry capacity that fits the array.
+  // Lay out a workspace with the largest entry capacity that fits the array:
+  // the workspace size grows with max_entries (monotonically, in 256-byte
+  // steps), so bisect on it.
   gs2d_plan plan;
-  gs2d_status st = gs2d_plan_init(&plan, width, height, n, 1, cfg);
-  if (st != GS2D_OK) return st;
-  const uint64_t fixed = plan.ws_bytes;  // every section, with room for one entry
-  const uint64_t per_entry = 4 * sizeof(uint32_t) + kPartials * sizeof(float);
   const int64_t min_entries = 1024;
-  if (fixed + min_entries * per_entry > kNoallocBytes) {
+  gs2d_status st = gs2d_plan_init(&plan, width, height, n, min_entries, cfg);
+  if (st != GS2D_OK) return st;
+  if (plan.ws_bytes > kNoallocBytes) {
     snprintf(msg, sizeof(msg),
              "gs2d_render_fwd_noalloc: %d Gaussians on a %d x %d frame need more than the "
              "%llu-byte static scratch; use a caller-allocated workspace (gs2d_plan_init)",
              n, width, height, (unsigned long long)kNoallocBytes);
     return set_error(GS2D_ERR_INVALID_ARG, msg);
   }
-  int64_t max_entries = (int64_t)((kNoallocBytes - fixed) / per_entry);
-  do {
-    st = gs2d_plan_init(&plan, width, height, n, max_entries, cfg);
-    if (st != GS2D_OK) return st;
-    if (plan.ws_bytes <= kNoallocBytes) break;
-    max_entries -= 64;
-  } while (max_entries >= min_entries);
-  if (plan.ws_bytes > kNoallocBytes)
-    return set_error(GS2D_ERR_INVALID_ARG, "gs2d_render_fwd_noalloc: layout exceeds the scratch");
+  int64_t lo = min_entries, hi = (int64_t)(kNoallocBytes / sizeof(uint32_t)) + 1;  // lo fits
+  while (hi - lo > 1) {
+    const int64_t mid = lo + (hi - lo) / 2;
+    st = gs2d_plan_init(&plan, width, height, n, mid, cfg);
+    if (st == GS2D_OK && plan.ws_bytes <= kNoallocBytes) lo = mid; else hi = mid;
+  }
+  st = gs2d_plan_init(&plan, width, height, n, lo, cfg);
+  if (st != GS2D_OK) return st;
   void* ws = nullptr;
   cudaError_t e = scratch_address(&ws);
   cudaStream_t s = (cudaStream_t)stream;

@@ -205,3 +205,155 @@ extern "C" gs2d_status gs2d_fit_step_qat(const gs2d_plan* plan, void* ws, const 
   if (e != cudaSuccess) return set_error(GS2D_ERR_CUDA, cudaGetErrorString(e));
   return set_error(GS2D_OK, "");
 }
+
+// ---------------------------------------------------------------------------
+// Post-training calibration (Sec. 3.3 A: the quantisation parameters are
+// fixed from representative fitted frames): order statistics of every row's
+// finite values by a radix select on order-preserving 32-bit keys.
+namespace gs2d {
+namespace {
+
+constexpr int kCalSlots = 4;  // ranks per row: floor and ceiling of two positions
+
+__device__ __forceinline__ uint32_t order_key(float x) {
+  const uint32_t u = __float_as_uint(x);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ float key_value(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// Finite values per row (block r).
+__global__ void __launch_bounds__(256)
+k_cal_count(const float* __restrict__ params, int n, long long* __restrict__ count) {
+  __shared__ long long s_c[8];
+  long long c = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) c += isfinite(params[(size_t)blockIdx.x * n + i]);
+  for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) s_c[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long t = 0;
+    for (int w = 0; w < 8; w++) t += s_c[w];
+    count[blockIdx.x] = t;
+  }
+}
+
+// Block (r, slot): the rank[r][slot]-th smallest (0-based) finite value of
+// row r, found digit by digit (8 bits at a time, most significant first):
+// each pass histograms the keys that match the digits found so far and keeps
+// the bucket holding the rank.  rank < 0: no value (NaN out).
+__global__ void __launch_bounds__(512)
+k_cal_select(const float* __restrict__ params, int n, const long long* __restrict__ rank,
+             float* __restrict__ out) {
+  __shared__ unsigned hist[256];
+  __shared__ uint32_t s_prefix, s_mask;
+  __shared__ long long s_k;
+  const int r = blockIdx.x / kCalSlots;
+  const long long k0 = rank[blockIdx.x];
+  if (k0 < 0) {
+    if (threadIdx.x == 0) out[blockIdx.x] = __int_as_float(0x7fc00000);
+    return;
+  }
+  if (threadIdx.x == 0) {
+    s_prefix = 0u;
+    s_mask = 0u;
+    s_k = k0;
+  }
+  const float* row = params + (size_t)r * n;
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0u;
+    __syncthreads();
+    const uint32_t prefix = s_prefix, mask = s_mask;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const float x = row[i];
+      if (!isfinite(x)) continue;
+      const uint32_t key = order_key(x);
+      if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long k = s_k;
+      int b = 0;
+      while (b < 255 && k >= (long long)hist[b]) k -= hist[b++];
+      s_k = k;
+      s_prefix = prefix | ((uint32_t)b << shift);
+      s_mask = mask | (255u << shift);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = key_value(s_prefix);
+}
+
+}  // namespace
+}  // namespace gs2d
+
+// numpy's linear quantile interpolation between order statistics a and b.
+static double lerp_quantile(double a, double b, double t) {
+  const double d = b - a;
+  return t >= 0.5 ? b - d * (1.0 - t) : a + d * t;
+}
+
+extern "C" gs2d_status gs2d_quant_calibrate(const float* params, int32_t n, const int32_t* bits,
+                                            double coverage, void* scratch, size_t scratch_bytes,
+                                            float* lo, float* hi, void* stream) {
+  if (n < 0 || !bits || !lo || !hi || !scratch || scratch_bytes < gs2d_quant_calibrate_scratch_bytes() ||
+      (n > 0 && !params) || !(coverage > 0.0 && coverage <= 1.0))
+    return set_error(GS2D_ERR_INVALID_ARG, "gs2d_quant_calibrate: arguments");
+  for (int r = 0; r < 9; r++)
+    if (!(bits[r] == -16 || (bits[r] >= 0 && bits[r] <= 16)))
+      return set_error(GS2D_ERR_INVALID_ARG, "gs2d_quant_calibrate: bits");
+  cudaStream_t s = (cudaStream_t)stream;
+  long long* d_count = static_cast<long long*>(scratch);
+  long long* d_rank = d_count + 16;
+  float* d_val = reinterpret_cast<float*>(d_rank + 9 * kCalSlots);
+  long long count[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  cudaError_t e = cudaSuccess;
+  if (n > 0) {
+    k_cal_count<<<9, 256, 0, s>>>(params, n, d_count);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(count, d_count, sizeof(count), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  // positions of the central `coverage` interval (numpy's default method)
+  const double q = (1.0 - coverage) / 2.0;
+  long long rank[9 * kCalSlots];
+  double frac[9][2];
+  for (int r = 0; r < 9; r++) {
+    const long long N = bits[r] > 0 ? count[r] : 0;
+    for (int j = 0; j < 2; j++) {
+      const double h = (double)(N - 1) * (j == 0 ? q : 1.0 - q);
+      const long long f = N > 0 ? (long long)floor(h) : -1;
+      rank[r * kCalSlots + 2 * j] = f;
+      rank[r * kCalSlots + 2 * j + 1] = N > 0 ? (f + 1 < N ? f + 1 : N - 1) : -1;
+      frac[r][j] = N > 0 ? h - (double)f : 0.0;
+    }
+  }
+  float val[9 * kCalSlots];
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_rank, rank, sizeof(rank), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && n > 0) {
+    k_cal_select<<<9 * kCalSlots, 512, 0, s>>>(params, n, d_rank, d_val);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && n > 0)
+    e = cudaMemcpyAsync(val, d_val, sizeof(val), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return set_error(GS2D_ERR_CUDA, cudaGetErrorString(e));
+  for (int r = 0; r < 9; r++) {
+    double a = 0.0, b = 1.0;
+    if (bits[r] > 0 && n > 0 && count[r] > 0) {
+      a = lerp_quantile(val[r * kCalSlots], val[r * kCalSlots + 1], frac[r][0]);
+      b = lerp_quantile(val[r * kCalSlots + 2], val[r * kCalSlots + 3], frac[r][1]);
+      if (!(b > a)) b = a + 1.0;
+    }
+    lo[r] = (float)a;
+    hi[r] = (float)b;
+  }
+  return set_error(GS2D_OK, "");
+}
+
+extern "C" size_t gs2d_quant_calibrate_scratch_bytes(void) {
+  return 16 * sizeof(long long) + 9 * kCalSlots * (sizeof(long long) + sizeof(float));
+}

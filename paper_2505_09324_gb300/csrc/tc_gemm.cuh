@@ -16,6 +16,8 @@ struct TcGemmArgs {
   const float* bias;       // [N] or NULL
   int relu;
   int* status;             // device status word (GS2D_ERR_TIMEOUT) or NULL
+  unsigned long long wait_ns;  // limit of every mbarrier wait
+  int withhold_loads;      // failure-detection check: the producer issues no load
 };
 
 struct TcGemmProblem {
@@ -32,6 +34,8 @@ struct TcGemmProblem {
   int splits;              // split-K factor (1: none)
   float* partial;          // splits x M x ldc floats when splits > 1
   int* status;
+  unsigned long long wait_ns = 0;  // mbarrier wait limit (0: one second)
+  int withhold_loads = 0;  // failure-detection check only (see gs2d_gemm_wait_check)
 };
 
 // Implicit-GEMM convolution: Z[p][n] = sum_k col(X)[p][k] W[n][k] with col the

@@ -24,8 +24,6 @@ Cholesky factor, 8-bit colour and weight: 94 bits per Gaussian, within
 
 from __future__ import annotations
 
-import math
-
 import numpy as np
 import torch
 
@@ -57,24 +55,25 @@ class Quantizer:
         self.c = nat.make_quant(bits, self.lo, self.hi, refine)
 
     @classmethod
-    def calibrate(cls, param_sets, bits=DEFAULT_BITS, coverage: float = 1.0):
+    def calibrate(cls, param_sets, bits=DEFAULT_BITS, coverage: float = 1.0, stream=None):
         """PTQ calibration (Sec. 3.3 A): the range of every uniform row is the
         central ``coverage`` quantile interval of that row over the fitted
-        frames in ``param_sets`` ([9, n] tensors or arrays); the default is
-        the whole span (clipping the tails, at 99.9 %, cost 1.6 dB on fitted
-        1080p frames: the largest Gaussians matter).  A training-stage step
-        that runs once per codec, not per frame."""
-        rows = [np.asarray(p.detach().cpu() if isinstance(p, torch.Tensor) else p,
-                           np.float32).reshape(9, -1) for p in param_sets]
-        allp = np.concatenate(rows, axis=1).astype(np.float64)
-        lo, hi = [0.0] * 9, [0.0] * 9
-        q = (1.0 - coverage) / 2.0
-        for r in range(9):
-            if int(bits[r]) > 0:
-                x = allp[r][np.isfinite(allp[r])]
-                lo[r], hi[r] = np.quantile(x, q), np.quantile(x, 1.0 - q)
-                if not hi[r] > lo[r]:
-                    hi[r] = lo[r] + 1.0
+        frames in ``param_sets`` ([9, n] tensors or arrays), found on the
+        device (gs2d_quant_calibrate); the default is the whole span (clipping
+        the tails, at 99.9 %, cost 1.6 dB on fitted 1080p frames: the largest
+        Gaussians matter).  A training-stage step that runs once per codec,
+        not per frame; it synchronises the stream."""
+        dev = next((p.device for p in param_sets
+                    if isinstance(p, torch.Tensor) and p.is_cuda), torch.device("cuda"))
+        rows = [(p.detach() if isinstance(p, torch.Tensor) else torch.from_numpy(
+            np.ascontiguousarray(p, np.float32))).to(dev, torch.float32).reshape(9, -1)
+            for p in param_sets]
+        allp = torch.cat(rows, dim=1).contiguous()
+        nbytes = int(nat.load().gs2d_quant_calibrate_scratch_bytes())
+        scratch = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        s = torch.cuda.current_stream(dev) if stream is None else stream
+        lo, hi = nat.quant_calibrate(allp.data_ptr(), allp.shape[1], bits, coverage,
+                                     scratch.data_ptr(), nbytes, int(s.cuda_stream))
         return cls(bits, lo, hi)
 
     @property
@@ -130,19 +129,27 @@ def code_bits(codes: torch.Tensor, bits, select: torch.Tensor | None = None,
 
 def frame_bits(quantizer: Quantizer, params: torch.Tensor, select: torch.Tensor | None = None,
                stream=None) -> float:
-    """Coded size of a frame (host float; synchronises): the entropy-coded
-    codes of all Gaussians (an I-frame) or of the selected ones, each with
-    its index of ceil(log2 n) bits (a P-frame), plus the frame's ranges
-    (two float32 per uniform row) when the quantiser refines them per frame."""
+    """Coded size of a frame (gs2d_frame_bits; host float, synchronises):
+    the entropy-coded codes of all Gaussians (an I-frame) or of the selected
+    ones, each with its index of ceil(log2 n) bits (a P-frame), plus the
+    frame's ranges (two float32 per uniform row) when the quantiser refines
+    them per frame."""
     codes, _, _ = quantizer.quantize(params, values=False, stream=stream)
-    bits = float(code_bits(codes, quantizer.bits, select, stream).sum().item())
     n = params.shape[1]
-    if select is not None:
-        m = int(select.sum().item())
-        bits += m * math.ceil(math.log2(max(n, 2)))
-    if quantizer.refine:
-        bits += 64 * sum(b > 0 for b in quantizer.bits)
-    return bits
+    dev = params.device
+    nbytes = int(nat.load().gs2d_frame_bits_scratch_bytes())
+    key = (dev, "frame")
+    buf = _scratch.get(key)
+    if buf is None or buf.numel() < nbytes:
+        buf = _scratch[key] = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    out = torch.empty(1, dtype=torch.float64, device=dev)
+    s = torch.cuda.current_stream(dev) if stream is None else stream
+    b = (nat.ctypes.c_int32 * 9)(*quantizer.bits)
+    nat.check(nat.load().gs2d_frame_bits(
+        nat._p(codes.data_ptr()), n, b, nat._p(0 if select is None else select.data_ptr()),
+        int(quantizer.refine), nat._p(buf.data_ptr()), nbytes, nat._p(out.data_ptr()),
+        nat._p(int(s.cuda_stream))), "gs2d_frame_bits")
+    return float(out.item())
 
 
 def sequence_bits(counts, payload_bits, gop: int) -> dict:

@@ -190,6 +190,8 @@ class GaussianRasterizer:
             adam_state = (torch.empty_like(params), torch.empty_like(params))
         m, v = adam_state
         shape = (9, self.n)
+        # the P-frame loop re-bins the workspace every iteration
+        self.version += 1
         return nat.encode_pframe(self.plan, self.ws_ptr,
                                  _check(target, "target", self.image_shape()),
                                  _check(params, "params", shape), _check(m, "adam_m", shape),
@@ -204,6 +206,8 @@ class GaussianRasterizer:
         if adam_state is None:
             adam_state = (torch.empty_like(params), torch.empty_like(params))
         m, v = adam_state
+        # the fit loop re-bins the workspace (lists of other parameters)
+        self.version += 1
         st, done, final, trace = nat.encode_frame(
             self.plan, self.ws_ptr, _check(target, "target", self.image_shape()),
             _check(params, "params", (9, self.n)), _check(m, "adam_m", (9, self.n)),
@@ -236,6 +240,45 @@ class GaussianRasterizer:
         return {"psnr": self.psnr(target, params, stream), "psnr_q": self.psnr(target, values,
                                                                                stream),
                 "codes": codes, "values": values, "ranges": ranges}
+
+    def fit_step(self, target: torch.Tensor, params: torch.Tensor, adam_state, stream=None):
+        """One fit iteration (gs2d_fit_step) on params and the Adam moments
+        (m, v) in place; the step counter lives in the workspace."""
+        m, v = adam_state
+        shape = (9, self.n)
+        nat.fit_step(self.plan, self.ws_ptr, _check(target, "target", self.image_shape()),
+                     _check(params, "params", shape), _check(m, "adam_m", shape),
+                     _check(v, "adam_v", shape), _stream(stream))
+        self.version += 1
+
+    def fit_reset(self, adam_state, stream=None):
+        """Restarts the fit's optimiser (gs2d_fit_reset)."""
+        m, v = adam_state
+        nat.fit_reset(self.plan, self.ws_ptr, _check(m, "adam_m", (9, self.n)),
+                      _check(v, "adam_v", (9, self.n)), _stream(stream))
+
+    def fit_checkpoint(self, params: torch.Tensor, adam_state, stream=None) -> dict:
+        """A checkpoint of a fit in progress: host copies of params and the
+        Adam moments and the optimiser state of the workspace
+        (gs2d_fit_state_get; synchronises the stream)."""
+        st = nat.fit_state_get(self.plan, self.ws_ptr, _stream(stream))
+        m, v = adam_state
+        return {"params": params.detach().cpu().clone(), "m": m.cpu().clone(),
+                "v": v.cpu().clone(), "step": int(st.step), "beta1_pow": st.beta1_pow,
+                "beta2_pow": st.beta2_pow, "decay_pow": st.decay_pow}
+
+    def fit_restore(self, ckpt: dict, params: torch.Tensor, adam_state, stream=None):
+        """Resumes from fit_checkpoint's output: copies params and the moments
+        back into the given device tensors and sets the workspace's optimiser
+        state (gs2d_fit_state_set); the next fit_step continues the fit."""
+        m, v = adam_state
+        params.copy_(ckpt["params"])
+        m.copy_(ckpt["m"])
+        v.copy_(ckpt["v"])
+        st = nat.FitState(int(ckpt["step"]), 0, float(ckpt["beta1_pow"]),
+                          float(ckpt["beta2_pow"]), float(ckpt["decay_pow"]))
+        nat.fit_state_set(self.plan, self.ws_ptr, st, _stream(stream))
+        self.version += 1
 
     def psnr(self, target: torch.Tensor, params: torch.Tensor, stream=None) -> float:
         """PSNR of the clamped render of ``params`` against ``target``
@@ -312,6 +355,19 @@ def roi_init(frame: torch.Tensor, mask: torch.Tensor, n: int, roi_frac: float,
     """Region-of-interest superpixel initialiser (gs2d_roi_init).  frame:
     [3, H, W] float32, mask: [H, W] uint8/bool, bg_xy: [2, n] float32 random
     background positions.  Returns (params [9, n], n_roi)."""
+    return _roi_init(frame, mask, n, roi_frac, bg_xy, stream, trace=False)[:2]
+
+
+def roi_init_trace(frame: torch.Tensor, mask: torch.Tensor, n: int, roi_frac: float,
+                   bg_xy: torch.Tensor, stream=None):
+    """roi_init with the K-means iterations written out
+    (gs2d_roi_init_trace): (params [9, n], n_roi, centres [10, 5, n] (r, g,
+    b, x, y rows; the first n_roi columns used) each assignment used,
+    labels [10, H, W] int32 each assignment made)."""
+    return _roi_init(frame, mask, n, roi_frac, bg_xy, stream, trace=True)
+
+
+def _roi_init(frame, mask, n, roi_frac, bg_xy, stream, trace):
     _, h, w = frame.shape
     f = _check(frame, "frame", (3, h, w))
     if mask.dtype == torch.bool:
@@ -322,11 +378,18 @@ def roi_init(frame: torch.Tensor, mask: torch.Tensor, n: int, roi_frac: float,
     nbytes = int(nat.load().gs2d_roi_init_scratch_bytes(w, h, n))
     scratch = torch.empty(nbytes, dtype=torch.uint8, device=frame.device)
     n_roi = nat.ctypes.c_int32(0)
-    nat.check(nat.load().gs2d_roi_init(
-        nat._p(f), nat._p(mk), w, h, n, float(roi_frac), nat._p(bg), nat._p(params.data_ptr()),
-        nat.ctypes.byref(n_roi), nat._p(scratch.data_ptr()), nbytes, nat._p(_stream(stream))),
-        "gs2d_roi_init")
-    return params, int(n_roi.value)
+    args = (nat._p(f), nat._p(mk), w, h, n, float(roi_frac), nat._p(bg),
+            nat._p(params.data_ptr()), nat.ctypes.byref(n_roi), nat._p(scratch.data_ptr()),
+            nbytes)
+    if not trace:
+        nat.check(nat.load().gs2d_roi_init(*args, nat._p(_stream(stream))), "gs2d_roi_init")
+        return params, int(n_roi.value), None, None
+    cen = torch.empty((10, 5, n), device=frame.device)
+    lab = torch.empty((10, h, w), dtype=torch.int32, device=frame.device)
+    nat.check(nat.load().gs2d_roi_init_trace(*args, nat._p(cen.data_ptr()),
+                                             nat._p(lab.data_ptr()), nat._p(_stream(stream))),
+              "gs2d_roi_init_trace")
+    return params, int(n_roi.value), cen, lab
 
 
 def adam_step(params: torch.Tensor, grads: torch.Tensor, m: torch.Tensor, v: torch.Tensor,
@@ -400,6 +463,7 @@ class BatchRasterizer(GaussianRasterizer):
             adam_state = (torch.empty_like(params), torch.empty_like(params))
         m, v = adam_state
         shape = (9, self.n)
+        self.version += 1  # the fit loop re-bins the workspace
         return nat.encode_batch(self.plan, self.ws_ptr, _check(targets, "targets",
                                                                 self.image_shape()),
                                 _check(params, "params", shape), _check(m, "adam_m", shape),

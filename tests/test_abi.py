@@ -215,8 +215,7 @@ def test_quantizer_spec_host_side():
     import numpy as np
     from paper_2505_09324_gb300.quant import HALF, Quantizer
     bits = (HALF, HALF, 8, 8, 8, 8, 8, 8, 8)
-    q = Quantizer.calibrate([np.tile(np.linspace(-1, 1, 1001, dtype=np.float32), (9, 1))],
-                            bits, coverage=1.0)
+    q = Quantizer(bits, [-1.0] * 9, [1.0] * 9)
     assert q.bits_per_gaussian == 32 + 7 * 8
     assert q.lo[2] == -1.0 and q.hi[2] == 1.0
     assert q.c.scale[2] == np.float32(255 / 2) and q.c.step[2] == np.float32(2 / 255)

@@ -102,3 +102,49 @@ def test_backward_rebins_after_workspace_reuse(crop):
     tp2 = torch.from_numpy(p).cuda().requires_grad_(True)
     rasterize(tp2, r2).sum().backward()
     np.testing.assert_array_equal(tp.grad.cpu().numpy(), tp2.grad.cpu().numpy())
+
+
+@pytest.mark.parametrize("fit", ["encode_frame", "encode_pframe"])
+def test_backward_rebins_after_a_fit_on_the_rasterizer(crop, oracle, fit):
+    """A fit loop on the rasterizer between forward and backward re-bins the
+    workspace for other parameters; the backward must notice and re-bin, and
+    its gradient must still be the oracle's."""
+    from paper_2505_09324_gb300 import GaussianRasterizer
+    from paper_2505_09324_gb300.autograd import rasterize
+    p, target, W, H = crop
+    r = GaussianRasterizer(W, H, p.shape[1])
+    tp = torch.from_numpy(p).cuda().requires_grad_(True)
+    T = torch.from_numpy(target).cuda()
+    img = rasterize(tp, r)
+    q = torch.from_numpy(p).cuda()
+    q[0] += 2.5  # moved Gaussians: other tile lists
+    if fit == "encode_frame":
+        r.encode_frame(T, q, 5, check_every=5)
+    else:
+        sel = torch.ones(p.shape[1], dtype=torch.uint8, device="cuda")
+        r.prepare(q)
+        r.encode_pframe(T, q, sel, 5)
+    loss = ((img - T) ** 2).mean()
+    loss.backward()
+    res = oracle.loss_and_grad(p, target)
+    g = tp.grad.cpu().numpy().astype(np.float64)
+    ref, unc = res["grad"], res["grad_unc"]
+    rms = np.sqrt(np.mean(ref * ref, axis=1, keepdims=True))
+    assert np.all(np.abs(g - ref) <= 1e-3 * np.abs(ref) + 1e-3 * rms + unc)
+
+
+def test_check_status_raises_on_capacity_overflow(crop):
+    """With check_status, a plan too small for the tile entries raises instead
+    of returning the zero image the kernels leave behind."""
+    from paper_2505_09324_gb300 import GaussianRasterizer
+    from paper_2505_09324_gb300 import _native as nat
+    from paper_2505_09324_gb300.autograd import rasterize
+    p, target, W, H = crop
+    r = GaussianRasterizer(W, H, p.shape[1], max_entries=8)
+    tp = torch.from_numpy(p).cuda()
+    img = rasterize(tp, r)  # default: no status read, a zero image
+    assert float(img.abs().max()) == 0.0
+    assert r.status() == nat.GS2D_ERR_CAPACITY
+    r2 = GaussianRasterizer(W, H, p.shape[1], max_entries=8)
+    with pytest.raises(nat.Gs2dError):
+        rasterize(tp, r2, check_status=True)

@@ -93,3 +93,16 @@ def test_selective_sequence_accounting(gs):
         assert got[key] == pytest.approx(ref[key], rel=1e-12)
     assert got["i_frames"] == 3 and got["p_frames"] == 6
     assert 0 < got["savings"] < got["p_bits"]
+
+
+def test_frame_bits_i_frame_and_refined_ranges(gs):
+    """gs2d_frame_bits on an I-frame (no selection: no index bits) with a
+    quantiser that refines its ranges per frame (two float32 per uniform row
+    ride along) against the oracle's code lengths."""
+    from paper_2505_09324_gb300.quant import frame_bits
+    p = random_gaussians(3000, 640, 360, seed=9)
+    q = gs.Quantizer(refine=True)
+    got = frame_bits(q, torch.from_numpy(p).cuda())
+    oc, _, _ = Q.quantize(p, q.bits, refine=True)
+    ref = B.code_entropy_bits(oc, q.bits).sum() + 64 * sum(b > 0 for b in q.bits)
+    assert got == pytest.approx(ref, rel=1e-12)

@@ -176,3 +176,35 @@ def test_qat_raises_the_quantised_quality_of_a_fit(gs):
     out = r.encode_frame_qat(target, qat, 300, q)
     assert psnr_ptq < psnr_float - 0.5          # 5-bit codes cost quality
     assert out["psnr_q"] > psnr_ptq + 1.0, (psnr_float, psnr_ptq, out["psnr_q"])
+
+
+@pytest.mark.parametrize("coverage", [1.0, 0.999, 0.5])
+def test_ptq_calibration_is_the_quantile_interval(gs, coverage):
+    """gs2d_quant_calibrate (order statistics by a device radix select,
+    interpolated in double) against numpy's quantile of the finite values of
+    every uniform row over several frames, non-finite values, duplicates and
+    negative zeros included; a constant row gets hi = lo + 1."""
+    rng = np.random.default_rng(3)
+    sets = []
+    for k, n in enumerate((5000, 1, 777)):
+        p = rng.normal(0.0, 10.0 ** (k - 1), (9, n)).astype(np.float32)
+        sets.append(p)
+    sets[0][2, :50] = np.nan
+    sets[0][3, :7] = np.inf
+    sets[0][4, :9] = -np.inf
+    sets[2][5, :100] = 0.25          # duplicates
+    sets[2][6, :10] = -0.0
+    for s in sets:
+        s[7] = 3.5                    # a constant row
+    bits = (8, 8, 8, 8, 8, 8, 8, 8, Q.HALF)
+    q = gs.Quantizer.calibrate([torch.from_numpy(s).cuda() for s in sets], bits, coverage)
+    allp = np.concatenate(sets, axis=1).astype(np.float64)
+    lo_q = (1.0 - coverage) / 2.0
+    for r in range(9):
+        if bits[r] <= 0:
+            continue
+        x = allp[r][np.isfinite(allp[r])]
+        lo, hi = np.quantile(x, lo_q), np.quantile(x, 1.0 - lo_q)
+        if not hi > lo:
+            hi = lo + 1.0
+        assert q.lo[r] == float(np.float32(lo)) and q.hi[r] == float(np.float32(hi)), r

@@ -70,3 +70,24 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(nat):
                                      None, None)
     assert rc == nat.GS2D_ERR_INVALID_ARG
     assert "static scratch" in nat.last_error()
+
+
+@pytest.mark.gpu
+def test_noalloc_reports_capacity_overflow_then_recovers(nat):
+    """Tile entries beyond the scratch's entry capacity: the call renders zero
+    and reports GS2D_ERR_CAPACITY through its status word; the next call, which
+    fits, must not see that status (the header is cleared per call) and must
+    match the workspace render again."""
+    torch = pytest.importorskip("torch")
+    W, H = 512, 512
+    p = random_gaussians(1000, W, H, seed=4)
+    p[2] = 150.0  # every Gaussian covers the whole frame: ~1e6 (tile, Gaussian) entries
+    p[3] = 0.0
+    p[4] = 150.0
+    got, status = noalloc_render(nat, torch, p, W, H)
+    assert status == nat.GS2D_ERR_CAPACITY
+    assert float(np.abs(got).max()) == 0.0
+    q = random_gaussians(300, 100, 70, seed=11)
+    got, status = noalloc_render(nat, torch, q, 100, 70)
+    assert status == nat.GS2D_OK
+    np.testing.assert_allclose(got, workspace_render(torch, q, 100, 70), rtol=0, atol=IMG_TOL)
