@@ -512,10 +512,18 @@ gs2d_status gs2d_roi_init_trace(const float* frame, const uint8_t* mask, int32_t
 /* Fits the plan's n Gaussians to a frame (Sec. 3.2 A: optimise N Gaussians
  * to the frame; I-frames start from an initialiser's output, P-frames from the
  * previous frame's Gaussians).  Runs up to `iters` iterations of
- * project -> bin_sort -> render_l2 -> adam_step, replayed as a captured CUDA
- * graph on non-default streams (plain launches on the legacy default stream).
- * Every check_every iterations (>= 1) the PSNR of the clamped render is read
- * back; the loop stops once it reaches target_psnr (<= 0 disables the test).
+ * project -> bin_sort -> render_l2 -> adam_step.  Every check_every
+ * iterations (>= 1, and after the last) the PSNR of the clamped render is
+ * taken; the loop stops once it reaches target_psnr (<= 0 disables the test)
+ * or a kernel records an error.  On a non-default stream the device drives
+ * the loop: the whole fit is one CUDA graph whose WHILE node repeats one
+ * iteration and a control kernel that counts iterations, takes the PSNR
+ * checks and ends the loop, with one host read at the end (the trace is kept
+ * in the workspace's gradient scratch, so it needs iters / check_every + 1
+ * <= 9n).  Otherwise (the legacy default stream, a longer trace, or a driver
+ * that declines the graph) the host replays one captured iteration, or
+ * launches it plainly on the legacy stream, and reads the PSNR back at each
+ * check.  Both give the same results bit for bit.
  * target: device [3][H][W].  params: device 9n floats, in: start, out: fitted.
  * adam_m, adam_v: device 9n floats each, zeroed by this call (the optimiser
  * state restarts per frame).  psnr_trace: host, NULL or room for

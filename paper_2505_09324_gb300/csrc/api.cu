@@ -517,6 +517,119 @@ gs2d_status gs2d_fit_rebins(const gs2d_plan* plan, const void* ws, int64_t* rebi
   return ok();
 }
 
+// Device-driven fit loop: the body of a conditional WHILE graph node is one
+// fit iteration followed by this kernel.  It counts the iteration; every
+// check_every iterations (and at the last) it sums the render's per-tile loss
+// partials, writes the PSNR of the clamped image to the trace and clears the
+// loop condition once the target is met, the cap is reached or a kernel has
+// recorded an error.  The host reads the header and the trace once, at the
+// end.
+struct LoopArgs {
+  int num_tiles, iters, check_every;
+  float target_psnr;
+  const float2* loss_part;
+  WsHeader* hdr;
+  float* trace;  // device, one float per check
+  cudaGraphConditionalHandle handle;
+};
+
+__global__ void __launch_bounds__(1024) k_loop_control(LoopArgs a) {
+  pdl_begin();
+  __shared__ int s_it;
+  __shared__ double s_a[32], s_b[32];
+  if (threadIdx.x == 0) s_it = ++a.hdr->loop_iter;
+  __syncthreads();
+  const int it = s_it;
+  if (it % a.check_every != 0 && it < a.iters) return;
+  double x = 0.0, y = 0.0;
+  for (int t = threadIdx.x; t < a.num_tiles; t += blockDim.x) {
+    x += a.loss_part[t].x;
+    y += a.loss_part[t].y;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    x += __shfl_xor_sync(0xffffffffu, x, o);
+    y += __shfl_xor_sync(0xffffffffu, y, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_a[wid] = x;
+    s_b[wid] = y;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double sa = 0.0, sb = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+    sa += s_a[w];
+    sb += s_b[w];
+  }
+  a.hdr->loss[0] = (float)sa;
+  a.hdr->loss[1] = (float)sb;
+  const double mse = (double)a.hdr->loss[1];
+  const float psnr = mse > 0.0 ? (float)(10.0 * log10(1.0 / mse)) : INFINITY;
+  a.trace[a.hdr->loop_checks++] = psnr;
+  const bool stop = it >= a.iters || a.hdr->status != 0 ||
+                    (a.target_psnr > 0.0f && psnr >= a.target_psnr);
+  if (stop) cudaGraphSetConditional(a.handle, 0u);
+}
+
+// The whole fit loop as one executable graph: a WHILE node whose body is one
+// fit iteration and k_loop_control; NULL when the stream cannot be captured,
+// the trace does not fit the gradient scratch or the driver declines the
+// graph (the caller then drives the loop from the host).
+static cudaGraphExec_t capture_fit_loop(const gs2d_plan& p, void* ws, const float* target,
+                                        float* params, float* m, float* v, int iters,
+                                        int check_every, float target_psnr, cudaStream_t s) {
+  const int checks = iters / check_every + 1;
+  if (s == nullptr || iters <= 0 || (size_t)checks > (size_t)9 * p.n ||
+      prime_fit_launches(p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphConditionalHandle handle;
+  cudaError_t e = cudaGraphCreate(&graph, 0);
+  if (e == cudaSuccess)
+    e = cudaGraphConditionalHandleCreate(&handle, graph, 1u, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams cp = {};
+  cudaGraphNode_t node = nullptr;
+  if (e == cudaSuccess) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+  }
+  if (e == cudaSuccess) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t ce = fit_iteration(p, ws, target, params, m, v, s);
+      if (ce == cudaSuccess) {
+        LoopArgs la;
+        la.num_tiles = p.num_tiles;
+        la.iters = iters;
+        la.check_every = check_every;
+        la.target_psnr = target_psnr;
+        la.loss_part = ws_ptr<float2>(ws, p, kOffLossPart);
+        la.hdr = ws_ptr<WsHeader>(ws, p, kOffHeader);
+        la.trace = ws_ptr<float>(ws, p, kOffGrad);
+        la.handle = handle;
+        ce = launch_pdl(k_loop_control, 1, 1024, 0, s, la);
+      }
+      cudaGraph_t captured = nullptr;
+      const cudaError_t ee = cudaStreamEndCapture(s, &captured);
+      e = ce != cudaSuccess ? ce : ee;
+    }
+  }
+  if (e == cudaSuccess && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();
+  return exec;
+}
+
 gs2d_status gs2d_encode_frame(const gs2d_plan* plan, void* ws, const float* target, float* params,
                               float* adam_m, float* adam_v, int32_t iters, float target_psnr,
                               int32_t check_every, float* psnr_trace, int32_t* iters_done,
@@ -535,6 +648,34 @@ gs2d_status gs2d_encode_frame(const gs2d_plan* plan, void* ws, const float* targ
   cudaError_t e = reset_fit(p, ws, adam_m, adam_v, s);
   if (e != cudaSuccess) return cuda_check(e, "gs2d_encode_frame: reset");
   WsHeader* hdr = ws_ptr<WsHeader>(ws, p, kOffHeader);
+  // the device drives the loop (one graph launch, one read at the end) ...
+  cudaGraphExec_t loop = capture_fit_loop(p, ws, target, params, adam_m, adam_v, iters,
+                                          check_every, target_psnr, s);
+  if (loop) {
+    e = cudaGraphLaunch(loop, s);
+    WsHeader h;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, hdr, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaGraphExecDestroy(loop);
+    if (e != cudaSuccess) return cuda_check(e, "gs2d_encode_frame");
+    const int checks = h.loop_checks;
+    float last = 0.0f;
+    if (checks > 0) {
+      e = cudaMemcpy(&last, ws_ptr<float>(ws, p, kOffGrad) + (checks - 1), sizeof(float),
+                     cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess && psnr_trace)
+        e = cudaMemcpy(psnr_trace, ws_ptr<float>(ws, p, kOffGrad), (size_t)checks * sizeof(float),
+                       cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_check(e, "gs2d_encode_frame: trace");
+    }
+    if (iters_done) *iters_done = h.loop_iter;
+    if (final_psnr) *final_psnr = last;
+    if (h.status != 0)
+      return fail((gs2d_status)h.status, "device status %d after %d iterations", h.status,
+                  h.loop_iter);
+    return ok();
+  }
+  // ... or, where that graph is unavailable, the host polls every check_every
   cudaGraphExec_t exec = capture_fit(p, ws, target, params, adam_m, adam_v, iters, s);
 
   int done = 0, checks = 0;

@@ -67,7 +67,9 @@ struct WsHeader {
   int32_t lists_valid;  // the fit loop's tile lists hold every Gaussian's box
   int32_t rebins;       // times the fit loop rebuilt its lists
   int32_t lists_tight;  // the last rebuild listed tight rectangles (widened ones overflowed)
-  int32_t pad[38];
+  int32_t loop_iter;    // device-driven fit loop: iterations run
+  int32_t loop_checks;  // device-driven fit loop: PSNR checks made
+  int32_t pad[36];
 };
 static_assert(sizeof(WsHeader) == 256, "header is one 256-byte block");
 

@@ -372,3 +372,39 @@ def test_fast_schedule_tracks_oracle_trajectory(gs, oracle):
     assert l_ref < 0.2 * l_0
     scale = np.abs(p).max(axis=1, keepdims=True) + 1e-3
     assert np.median(np.abs(got - p) / scale) < 1e-3
+
+
+@pytest.mark.parametrize("mode,check_every", [("cap", 7), ("early", 5), ("never", 10)])
+def test_device_driven_loop_equals_host_driven_loop(gs, mode, check_every):
+    """On a non-default stream gs2d_encode_frame runs the whole fit loop as one
+    graph whose WHILE node the device stops (PSNR checked on the device every
+    check_every iterations, one host read at the end); on the legacy default
+    stream the host drives it.  Both give the same Gaussians bit for bit, the
+    same iteration count and the same PSNR trace: with no target (the cap,
+    not a multiple of check_every), a target met at the third check, and one
+    never met."""
+    W, H, n, iters = 96, 80, 120, 53
+    p0 = to_dev(random_gaussians(n, W, H, seed=27, l_range=(2.0, 6.0)))
+    target = to_dev(smooth_noise_target(W, H, seed=28))
+
+    def run(name, target_psnr):
+        r = gs.GaussianRasterizer(W, H, n)
+        p = p0.clone()
+        s = torch.cuda.default_stream() if name == "host" else torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            o = r.encode_frame(target, p, iters, target_psnr=target_psnr,
+                               check_every=check_every, stream=s)
+        s.synchronize()
+        return p, o
+
+    goal = {"cap": 0.0, "never": 99.0}.get(mode)
+    if goal is None:
+        goal = run("host", 0.0)[1]["trace"][2]  # reached at the third check
+    (ph, oh), (pd, od) = run("host", goal), run("device", goal)
+    assert oh["status"] == od["status"] == 0
+    assert oh["iters"] == od["iters"] and oh["trace"] == od["trace"] and oh["psnr"] == od["psnr"]
+    assert torch.equal(ph, pd)
+    if mode == "early":
+        assert od["iters"] <= 3 * check_every and od["psnr"] >= goal
+    else:
+        assert od["iters"] == iters and len(od["trace"]) == -(-iters // check_every)
