@@ -46,18 +46,43 @@ METRIC = "fwd+bwd ms/iter @1080p,20k Gaussians; encode s/frame to 35 dB PSNR vs 
 UNIT = "ms/iter"
 WORKLOAD = ("1920x1080 RGB FP32 synthetic conferencing frame (seed 1), 20000 Gaussians from "
             "the ROI superpixel initialiser (70% target in the subject), L2 loss, Adam lr 1e-2")
-# FP32-pipe operations and MUFU ex2 per contributing (pixel, Gaussian) pair of the
-# fused fit kernel: forward 8 (sigma + predicate) + 3 (accumulate); backward 8
-# (recompute) + 3 (colour sums) + 4 (dL/dsigma) + 7 (quadratic-form moments).
-OPS_FWD, OPS_BWD = 11, 22
-OPS_PER_HIT = OPS_FWD + OPS_BWD
-MUFU_PER_HIT = 2
-SMS, FP32_LANES, MUFU_LANES, SM_MAX_MHZ = 152, 128, 32, 2070.0
+# Algorithmic work of the render passes (what the tiled method itself must
+# do; the dense W x H x N pairs it skips are not counted).  Per listed
+# (pixel, Gaussian) pair of the tight 16-pixel tile lists: 8 FP32-pipe
+# operations (2 sub and 5 mul/FMA for sigma in base 2, 1 compare against the
+# cut-off) and one MUFU ex2, in each pass; per contributing pair 3 more FMAs
+# in the forward (the colour accumulation) and about 20 in the backward (the
+# nine partials).  The stricter count beside it takes contributing pairs
+# only: forward 8 + 3 = 11, backward 8 + 3 + 4 + 7 = 22 (recompute, colour
+# sums, dL/dsigma, quadratic-form moments).
+OPS_PER_PAIR, OPS_HIT_FWD, OPS_HIT_BWD = 8, 3, 20
+STRICT_FWD, STRICT_BWD = 11, 22
+MUFU_PER_PAIR = 1
+# Bytes the HBM-bound steps must move per unit (the workspace layout's
+# records; each read or written once):
+#   projection: 36 B parameters in; 48 B render record, 16 B tile rectangle,
+#     4 B tile count out, per Gaussian;
+#   binning + sort: per Gaussian 16 B rectangle + 4 B count in, 4 B offset out;
+#     per (tile, Gaussian) entry 4 B list write + 8 B for the per-tile index
+#     sort (read + write); per tile 8 B range + 4 B queue slot + 4 B count;
+#   Adam: 28 B per parameter (p, g, m, v in; p, m, v out).
+BYTES_PROJECT_G = 36 + 48 + 16 + 4
+BYTES_BIN_G, BYTES_BIN_E, BYTES_BIN_T = 16 + 4 + 4, 4 + 8, 8 + 4 + 4
+BYTES_ADAM_P = 28
+# The paper's own encode-time result (Table 1; RTX 3090 Ti, VCD clips at 360p,
+# 1000 Gaussians, to 30 dB): superpixel initialisation 750 iterations, 100 ms
+# init, 1.5 s in total, against GaussianImage's random initialisation with
+# 8733 iterations and 13.1 s: -88 %.
+PAPER_ENCODE = {"reduction": 1.0 - 1.5 / 13.1, "superpixel_s": 1.5, "random_init_s": 13.1,
+                "superpixel_iters": 750, "random_init_iters": 8733, "target_db": 30.0,
+                "gaussians": 1000, "resolution": "640x360",
+                "hardware": "RTX 3090 Ti + Threadripper 3960X",
+                "source": "Table 1 (encode time to 30 dB); abstract: -88 %"}
 # DRAM bytes (read + write) of one fused render launch (k_render, tile 32,
 # stage 128, grid) from an ncu capture of this workload, valid for the render
 # source with this sha256 (else null)
-NCU_TRAFFIC = {"bytes": 26832896, "schedule": (32, 128, 1),
-               "render_sha256": "5cb495a95b44371febe63e2d6db4aea11470d589ce7cb1f720905b80249bb138"}
+NCU_TRAFFIC = {"bytes": 26836224, "schedule": (32, 128, 1),
+               "render_sha256": "4e5b099f6bca4bcae99dff9622978e0c215a19696df27bb96fad98d84882224a"}
 
 
 def hbm_peak_gbs() -> float:
@@ -67,6 +92,24 @@ def hbm_peak_gbs() -> float:
             return float(json.load(f)["hbm_gbs"])
     except (OSError, KeyError, ValueError):
         return 6800.0
+
+
+def render_work(pairs16: float, hits: float) -> dict:
+    """FP32-pipe operations of the forward, backward and fused render passes
+    by the per-pair count (pairs16: listed pairs of tight 16-pixel tile lists)
+    and by the strict per-contributing-pair count, and MUFU ex2 per pass."""
+    fwd = OPS_PER_PAIR * pairs16 + OPS_HIT_FWD * hits
+    bwd = OPS_PER_PAIR * pairs16 + OPS_HIT_BWD * hits
+    return {"fwd": fwd, "bwd": bwd, "fused": fwd + bwd,
+            "fwd_strict": STRICT_FWD * hits, "bwd_strict": STRICT_BWD * hits,
+            "fused_strict": (STRICT_FWD + STRICT_BWD) * hits,
+            "mufu_per_pass": MUFU_PER_PAIR * pairs16}
+
+
+def binning_bytes(n: int, entries: int, tiles: int) -> dict:
+    """Bytes the projection and the binning + sort must move (see above)."""
+    return {"project": BYTES_PROJECT_G * n,
+            "bin_sort": BYTES_BIN_G * n + BYTES_BIN_E * entries + BYTES_BIN_T * tiles}
 
 
 def render_traffic(schedule):
@@ -106,7 +149,7 @@ def parse():
     ap.add_argument("--seq-threshold", type=float, default=0.02)
     ap.add_argument("--seq-gop", type=int, default=4)
     ap.add_argument("--batch-clips", type=int, default=32)
-    ap.add_argument("--batch-frames", type=int, default=2)
+    ap.add_argument("--batch-frames", type=int, default=8)
     ap.add_argument("--batch-iters", type=int, default=300)
     return ap.parse_args()
 
@@ -213,7 +256,7 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 
-def measure_batch(args, dev, rank=0, world=1):
+def measure_batch(args, dev, rank=0, world=1, peak_fp32=None):
     """Batched encode of independent clips of uneven size (resolution uniform
     over 640x360 / 1280x720 / 1920x1080, Gaussian count log-uniform in
     [2000, 50000]) of the moving-subject conferencing scene: frame 0 of every
@@ -262,6 +305,12 @@ def measure_batch(args, dev, rank=0, world=1):
     b = BatchRasterizer(sizes, config=tuned["config"], device=dev)
     b.prepare(P)
     pairs, hits = b.count_pairs()
+    # listed pairs of tight 16-pixel tile lists: the per-pair work count
+    from paper_2505_09324_gb300 import RasterConfig as _RC
+    b16 = BatchRasterizer(sizes, config=_RC(tile=16), device=dev)
+    b16.prepare(P)
+    pairs16, _ = b16.count_pairs()
+    del b16
     side = torch.cuda.Stream(dev)
     adam = (torch.empty_like(P), torch.empty_like(P))
     per_frame = []
@@ -281,7 +330,16 @@ def measure_batch(args, dev, rank=0, world=1):
                           "psnr_max": max(psnr)})
     ms_iter = statistics.fmean(f["ms_per_batched_iter"] for f in per_frame)
     ms_iter, hits = shard_aggregate(ms_iter, hits, world, dev)
+    _, pairs16 = shard_aggregate(ms_iter, pairs16, world, dev)
     sizes = full_sizes
+    work = render_work(pairs16, hits)["fused"]
+    ach = work / (ms_iter * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": ach, "peak": peak_fp32, "unit": "Top/s (FP32 pipe)",
+            "frac": ach / peak_fp32 if peak_fp32 else None,
+            "note": "render work (8 FP32 ops per listed pair of tight 16-px lists + 23 per "
+                    "contributing pair, at the first frame's initialisation) over the whole "
+                    "batched iteration (binning, fused render, reduction + Adam) from the "
+                    "graph-replay wall clock"}
     return {"clips": len(full), "ranks": world,
             "clips_per_rank": [len(p) for p in parts],
             "estimated_load_per_rank": shard_loads(full_sizes, parts),
@@ -291,6 +349,7 @@ def measure_batch(args, dev, rank=0, world=1):
             "ms_per_batched_iter": ms_iter,
             "frame_iters_per_s": len(sizes) * 1e3 / ms_iter,
             "contributing_pairs_per_s": hits * 1e3 / ms_iter, "pairs_at_init": [pairs, hits],
+            "pairs16_at_init": pairs16, "roofline": roof,
             "roi_init_s_all_clips": init_s,
             "schedule": {"tile": tuned["tile"], "stage": tuned["stage"],
                          "launch": ["persistent", "grid"][tuned["launch"]]},
@@ -571,6 +630,44 @@ def measure_quant(args, dev, config, frame, mask, bg_xy, q):
                       "steps launched one by one (no graph)"}
 
 
+def measure_device_peaks(dev, local):
+    """Issue-limited peaks of the FP32 pipe (fused multiply-adds) and of MUFU
+    ex2 on this device at its current clock (gs2d_probe_peak, CUDA events on
+    the launching stream, median of 7 launches of about 2 ms), with the SM
+    clock sampled meanwhile so that the per-SM per-clock rates can be read
+    off; the SM count comes from the device."""
+    import torch
+
+    from paper_2505_09324_gb300 import _native as nat
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = 8 * sms  # 2048 threads per SM
+    sink = torch.empty(blocks, device=dev)
+    s = int(torch.cuda.current_stream(dev).cuda_stream)
+    out = {"sms": sms}
+    for name, kind, iters in (("ffma", nat.PROBE_FFMA, 2500), ("ex2", nat.PROBE_EX2, 600)):
+        nat.probe_peak(kind, blocks, 20, sink.data_ptr(), s)
+        torch.cuda.synchronize(dev)
+        sampler = ClockSampler(local)
+        sampler.start()
+        time.sleep(0.2)
+        t0 = time.perf_counter()
+        times = []
+        for _ in range(7):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            nat.probe_peak(kind, blocks, iters, sink.data_ptr(), s)
+            b.record()
+            torch.cuda.synchronize(dev)
+            times.append(a.elapsed_time(b))
+        clk = sampler.stop(t0, time.perf_counter())
+        rate = nat.probe_ops(blocks, iters) / (statistics.median(times) * 1e-3)  # ops/s
+        mhz = clk.get("sm_mhz")
+        out[name] = {"tops": rate / 1e12, "ms": statistics.median(times),
+                     "per_sm_per_clk": rate / (sms * mhz * 1e6) if mhz else None,
+                     "sm_mhz": mhz}
+    return out
+
+
 def measure_learned(dev, frame, mask, peaks):
     """Inference of the learned initialiser (Sec. 3.2 B regressor) for a batch
     of 8 frames of the benchmark size: frame + mask -> 20k Gaussians per frame.
@@ -605,13 +702,50 @@ def measure_learned(dev, frame, mask, peaks):
         cout = 9 * net.cfg.slots if li == net.L else co
         flops += 2 * B * h * w * cout * (ks * ks * ci + 1)
     tflops = flops / ms / 1e9
+    # the bytes every layer must move once: the frame and mask in, the 8-channel
+    # BF16 input out; each convolution's input and weights in, its output out
+    # (BF16, the head FP32); the decoded Gaussians out
+    nbytes = B * (H * W * (3 * 4 + 1) + H * W * 8 * 2)
+    for li, (ci, co, ks, ldk) in enumerate(net.layers):
+        hi_, wi_ = net.sizes[li] if li < net.L else net.sizes[-1]
+        ho_, wo_ = net.sizes[li + 1] if li < net.L else net.sizes[-1]
+        nbytes += B * hi_ * wi_ * ci * 2 + co * ldk * 2
+        nbytes += B * ho_ * wo_ * co * (4 if li == net.L else 2)
+    nbytes += B * 9 * net.n * 4
     peak = peaks.get("bf16_tflops")
     return {"batch": B, "ms_per_batch": ms, "ms_per_frame": ms / B, "params": net.num_params(),
             "gflop_per_frame": flops / B / 1e9,
             "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak,
                          "unit": "TFLOP/s (BF16)", "frac": tflops / peak if peak else None,
                          "peak_source": peaks.get("source"),
-                         "note": "whole forward (implicit-GEMM convolutions, head selection) timed; convolution FLOPs only"}}
+                         "note": "whole forward (implicit-GEMM convolutions, head selection) timed; convolution FLOPs only"},
+            "hbm": {"bytes_per_batch": nbytes, "gbs": nbytes / ms / 1e6,
+                    "frac": nbytes / ms / 1e6 / hbm_peak_gbs(),
+                    "note": "each layer's input, weights and output once, over the same time: "
+                            "the early layers (few channels, many pixels) are bandwidth-heavy, "
+                            "the late ones (deep K, few pixels) latency-bound"}}
+
+
+def measure_learned_training(lam: float = 1e-5, epochs: int = 6):
+    """A short training run of the learned initialiser on a small
+    configuration (320 x 192, 480 Gaussians, 24 frames fitted to 35 dB by the
+    ROI-initialised encoder, batch 4): the per-epoch render MSE and Chamfer
+    distance (px^2) to the encoder's fitted means, i.e. how the fitted pairs
+    enter the training at the shipped weight lam."""
+    from paper_2505_09324_gb300.learned import (LearnedInitializer, NetConfig, make_dataset,
+                                                train)
+    W2, H2, n2, B2 = 320, 192, 480, 4
+    t0 = time.perf_counter()
+    data = make_dataset(W2, H2, n2, list(range(500, 524)), cap=600)
+    net = LearnedInitializer(W2, H2, n2, B2, NetConfig(channels=(8, 32, 64, 64, 128, 128),
+                                                       slots=10, lr=2e-3, chamfer_lambda=lam),
+                             seed=2)
+    hist = train(net, data, epochs=epochs, seed=1)
+    return {"config": f"{W2}x{H2}, {n2} Gaussians, {len(data.iters)} frames, batch {B2}, "
+                      f"chamfer_lambda {lam}",
+            "render_mse_per_frame": [h["render_mse_per_frame"] for h in hist],
+            "chamfer_px2": [h["chamfer"] for h in hist],
+            "seconds": time.perf_counter() - t0}
 
 
 def run_ours(args):
@@ -684,6 +818,12 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     # the timed steps are iterations 1..K of the fit from the initialiser's output
     params.copy_(params0)
+    # listed pairs of tight 16-pixel tile lists (the per-pair work count) at
+    # the first and the last timed state
+    from paper_2505_09324_gb300 import RasterConfig as _RC
+    r16 = GaussianRasterizer(W, H, N_GAUSS, device=dev, config=_RC(tile=16))
+    r16.prepare(params)
+    p16_0, h16_0 = r16.count_pairs()
     rast.prepare(params)
     pairs0, hits0 = rast.count_pairs()
     nat.fit_reset(plan, ws, m.data_ptr(), v.data_ptr(), sp)
@@ -712,8 +852,12 @@ def run_ours(args):
     if st != 0:
         raise RuntimeError(f"device status {nat.STATUS_NAMES.get(st, st)} during the benchmark")
     rebuilds = rast.rebins()
+    r16.prepare(params)
+    p16_1, h16_1 = r16.count_pairs()
     rast.prepare(params)
     pairs1, hits1 = rast.count_pairs()
+    entries1 = nat.read_bins(plan, ws, sp, max_keys=0, want_keys=False, want_ranges=False,
+                             want_counts=False)["n_entries"]
 
     # the forward and the backward pass alone, at this state (L2 flushed each time)
     img = torch.empty_like(frame)
@@ -740,59 +884,93 @@ def run_ours(args):
 
     per = {"step": [e[0].elapsed_time(e[1]) for e in ev]}
     # diagnostic split of a step at the final state (untimed for the value):
-    # gs2d_prepare, gs2d_render_l2 (render + reduction to gradients), Adam
-    for k in ("prepare", "render_l2", "adam"):
+    # gs2d_project, gs2d_bin_sort, gs2d_render_l2 (render + reduction to
+    # gradients), Adam; L2 flushed before each
+    for k in ("project", "bin_sort", "render_l2", "adam"):
         per[k] = []
     for r in range(25):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
         flush.zero_()
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         e[0].record(stream)
-        nat.prepare(plan, ws, params.data_ptr(), sp)
+        nat.project(plan, ws, params.data_ptr(), sp)
         e[1].record(stream)
-        nat.render_l2(plan, ws, params.data_ptr(), frame.data_ptr(), grads.data_ptr(), 0, 0, sp)
+        flush.zero_()
         e[2].record(stream)
+        nat.bin_sort(plan, ws, sp)
+        e[3].record(stream)
+        flush.zero_()
+        e[4].record(stream)
+        nat.render_l2(plan, ws, params.data_ptr(), frame.data_ptr(), grads.data_ptr(), 0, 0, sp)
+        e[5].record(stream)
+        flush.zero_()
+        e[6].record(stream)
         nat.adam_step(params.data_ptr(), grads.data_ptr(), m.data_ptr(), v.data_ptr(),
                       params.numel(), 1000 + r, 0, None, sp)
-        e[3].record(stream)
+        e[7].record(stream)
         torch.cuda.synchronize(dev)
         if r >= 5:
-            per["prepare"].append(e[0].elapsed_time(e[1]))
-            per["render_l2"].append(e[1].elapsed_time(e[2]))
-            per["adam"].append(e[2].elapsed_time(e[3]))
+            per["project"].append(e[0].elapsed_time(e[1]))
+            per["bin_sort"].append(e[2].elapsed_time(e[3]))
+            per["render_l2"].append(e[4].elapsed_time(e[5]))
+            per["adam"].append(e[6].elapsed_time(e[7]))
     total_ms, value = whole_job(sum(per["step"]), K, world, dev)
     ms_per_step = total_ms / K
 
-    # roofline of the dominant call (fused forward + loss + backward + reduction);
-    # the work per step changes along the fit: use the mean of the contributing
-    # pairs at the first and the last timed step
+    # roofline of the dominant call (fused forward + loss + backward +
+    # reduction) against the peaks measured on this device: the work per step
+    # changes along the fit, so the mean of the first and the last timed state
+    peaks_dev = measure_device_peaks(dev, local)
+    peak_fp32 = peaks_dev["ffma"]["tops"]
+    peak_mufu = peaks_dev["ex2"]["tops"]
     t_render = statistics.fmean(per["render_l2"]) * 1e-3
-    hits = 0.5 * (hits0 + hits1)
-    f_hz = SM_MAX_MHZ * 1e6
-    peak_fp32 = SMS * FP32_LANES * f_hz / 1e12
-    peak_mufu = SMS * MUFU_LANES * f_hz / 1e12
-    achieved = OPS_PER_HIT * hits / t_render / 1e12
+    w_mean = render_work(0.5 * (p16_0 + p16_1), 0.5 * (hits0 + hits1))
+    w_last = render_work(p16_1, hits1)
+    achieved = w_mean["fused"] / t_render / 1e12
     passes = {}
-    for name, ops in (("fwd", OPS_FWD), ("bwd", OPS_BWD)):
+    for name in ("fwd", "bwd"):
         t_s = statistics.fmean(sep[name]) * 1e-3
-        ach = ops * hits1 / t_s / 1e12
-        passes[name] = {"ms": t_s * 1e3, "ops_per_hit": ops, "achieved": ach,
-                        "frac": ach / peak_fp32,
+        ach = w_last[name] / t_s / 1e12
+        ach_s = w_last[name + "_strict"] / t_s / 1e12
+        passes[name] = {"ms": t_s * 1e3, "achieved": ach, "frac": ach / peak_fp32,
+                        "achieved_per_hit_count": ach_s, "frac_per_hit_count": ach_s / peak_fp32,
+                        "mufu_frac": w_last["mufu_per_pass"] / t_s / 1e12 / peak_mufu,
                         "call": "gs2d_render_fwd" if name == "fwd" else
                                 "gs2d_render_bwd (k_render backward + per-Gaussian reduction)"}
     traffic = render_traffic((tuned["tile"], tuned["stage"], tuned["launch"]))
+    hbm = hbm_peak_gbs()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_fp32,
                 "unit": "Top/s (FP32 pipe)", "frac": achieved / peak_fp32,
                 "traffic": traffic,
                 "kernel": "gs2d_render_l2: k_render (fused forward + L2 + backward) + "
                           "k_reduce_chain",
-                "mufu_frac": MUFU_PER_HIT * hits / t_render / 1e12 / peak_mufu,
+                "work": "8 FP32 ops per listed pair of tight 16-px tile lists + 3 (fwd) / 20 "
+                        "(bwd) per contributing pair; frac_per_hit_count: 11 + 22 per "
+                        "contributing pair only",
+                "frac_per_hit_count": w_mean["fused_strict"] / t_render / 1e12 / peak_fp32,
+                "mufu_frac": 2 * w_mean["mufu_per_pass"] / t_render / 1e12 / peak_mufu,
                 # the third bound: the launch's DRAM bytes (ncu) over its time,
                 # against the measured copy bandwidth
-                "hbm_frac": (traffic / t_render / 1e9 / hbm_peak_gbs()) if traffic else None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz; MUFU 32/SM/clk; "
-                               "HBM of measured (MEASURED_PEAKS.json hbm_gbs) or of fallback "
-                               "(6800 GB/s)",
-                "passes": passes}
+                "hbm_frac": (traffic / t_render / 1e9 / hbm) if traffic else None,
+                "peak_source": "of measured: FP32 and ex2 peaks by gs2d_probe_peak on this "
+                               "device (field device_peaks); HBM of measured "
+                               "(MEASURED_PEAKS.json hbm_gbs) or of fallback (6800 GB/s)",
+                "device_peaks": peaks_dev,
+                "passes": passes,
+                "pairs16": {"first": p16_0, "last": p16_1, "hits_first": h16_0,
+                            "hits_last": h16_1}}
+    # the HBM-bound steps: algorithmic bytes over their time (L2 flushed first)
+    nbytes = binning_bytes(N_GAUSS, entries1, int(plan.num_tiles))
+    nbytes["adam"] = BYTES_ADAM_P * params.numel()
+    hbm_steps = {}
+    for k2 in ("project", "bin_sort", "adam"):
+        t_k = statistics.fmean(per[k2]) * 1e-3
+        hbm_steps[k2] = {"ms": t_k * 1e3, "bytes": nbytes[k2], "gbs": nbytes[k2] / t_k / 1e9,
+                         "frac": nbytes[k2] / t_k / 1e9 / hbm}
+    hbm_steps["note"] = ("eager gs2d_project / gs2d_bin_sort / gs2d_adam_step at the final "
+                         f"state ({N_GAUSS} Gaussians, {entries1} tile entries, "
+                         f"{int(plan.num_tiles)} tiles): a few MB each, so launch latency "
+                         "and dependent-kernel chains bound them, not HBM bandwidth")
+    hbm_steps["peak_gbs"] = hbm
 
     # end to end through the public API with host buffers: every step uploads
     # the frame as the 8-bit RGB a decoder delivers (converted on the device
@@ -850,18 +1028,19 @@ def run_ours(args):
         fast = GaussianRasterizer(W, H, N_GAUSS, device=dev,
                                   config=dataclasses.replace(tuned["config"], **FAST_FIT))
 
-        def encode_from(p_start, r_enc=fast, every=5):
+        def encode_from(p_start, r_enc=fast, every=5, target=None, cap=None):
+            target = args.target_psnr if target is None else target
+            cap = args.encode_iters if cap is None else cap
             p_enc = p_start.clone()
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             with torch.cuda.stream(side):
-                out = r_enc.encode_frame(frame, p_enc, args.encode_iters,
-                                         target_psnr=args.target_psnr, check_every=every,
-                                         stream=side)
+                out = r_enc.encode_frame(frame, p_enc, cap, target_psnr=target,
+                                         check_every=every, stream=side)
             side.synchronize()
             secs = time.perf_counter() - t0
             return {"seconds": secs, "iters": out["iters"], "psnr": out["psnr"],
-                    "reached": out["psnr"] >= args.target_psnr,
+                    "reached": out["psnr"] >= target,
                     "ms_per_iter_graph": 1e3 * secs / max(out["iters"], 1),
                     "status": out["status"]}
 
@@ -903,7 +1082,30 @@ def run_ours(args):
         p_rand = torch.from_numpy(random_gaussians(N_GAUSS, W, H, seed=SEED + 20)).to(dev)
         rnd = encode_from(p_rand)
         rnd_plain_schedule = encode_from(p_rand, rast, 25)
+        # a target that separates the initialisers: the PSNR the plain
+        # ROI-initialised encoder (plain Adam) reaches at its iteration cap;
+        # every initialiser under both schedules then runs to it (cap 5x)
+        plain_cap = encode_from(params0, rast, args.encode_iters, target=0.0)
+        star = plain_cap["psnr"]
+        inits = {"random": (p_rand, 0.0), "roi": (params0, init_s)}
+        if net is not None:
+            inits["learned"] = (p_learn, learned_enc["init_s"])
+        to_star = {"target_psnr": star, "cap_iters": 5 * args.encode_iters,
+                   "psnr_checks_every": 10,
+                   "plain_roi_at_cap": plain_cap,
+                   "note": "target = PSNR of the ROI-initialised fit with plain Adam after "
+                           f"{args.encode_iters} iterations; s_per_frame includes the "
+                           "initialiser's time"}
+        for sched_name, r_enc in (("plain_adam", rast), ("fast", fast)):
+            to_star[sched_name] = {}
+            for init_name, (p_i, t_init) in inits.items():
+                res = encode_from(p_i, r_enc, 10, target=star, cap=5 * args.encode_iters)
+                res["psnr_at_init"] = r_enc.psnr(frame, p_i)
+                res["init_s"] = t_init
+                res["s_per_frame"] = t_init + res["seconds"]
+                to_star[sched_name][init_name] = res
         encode = {"target_psnr": args.target_psnr, "cap_iters": args.encode_iters,
+                  "paper": PAPER_ENCODE, "to_plain_roi_psnr_at_cap": to_star,
                   "schedule": {"lr": tuned["config"].lr, **FAST_FIT,
                                "psnr_checks_every": 5},
                   "roi_init_plain_adam": {**roi_plain_schedule,
@@ -917,7 +1119,7 @@ def run_ours(args):
                                                            "every 25 iterations"},
                   "learned_init": learned_enc}
 
-    batch = None if args.no_batch else measure_batch(args, dev, rank, world)
+    batch = None if args.no_batch else measure_batch(args, dev, rank, world, peak_fp32)
     quantizer = None
     if not (args.no_sequence and args.no_quant):
         quantizer = calibrated_quantizer(dev, tuned["config"])
@@ -929,6 +1131,8 @@ def run_ours(args):
     except OSError:
         peaks = {"bf16_tflops": 1900.0, "source": "of fallback (1.9 PFLOP/s bf16 burst)"}
     learned = None if args.no_learned else measure_learned(dev, frame, mask, peaks)
+    if learned is not None:
+        learned["training_trajectory"] = measure_learned_training()
     quant = None if args.no_quant else measure_quant(args, dev, tuned["config"], frame, mask,
                                                      bg_xy, quantizer)
     reductions = None if args.no_encode else measure_reductions(dev, tuned["config"], frame,
@@ -961,7 +1165,7 @@ def run_ours(args):
                                           "rebuilt_in_timed_steps": rebuilds if retained
                                           else K},
                            "parallelism": f"replicas{world}"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "hbm_steps": hbm_steps, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches_per_step * K, "clocks": clocks,
                 "wall_s_timed_region": wall,
                 "kernels_ms": {k2: statistics.fmean(vv) for k2, vv in per.items()},
