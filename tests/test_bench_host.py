@@ -63,3 +63,28 @@ def test_hbm_peak_measured_or_fallback(bench, monkeypatch, tmp_path):
     assert bench.hbm_peak_gbs() == 6800.0
     (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 7000.5}))
     assert bench.hbm_peak_gbs() == 7000.5
+
+
+def test_render_work_counts(bench):
+    """The per-listed-pair count (8 FP32 operations per listed pair of tight
+    16-px lists in each pass, 3 / 20 more per contributing pair) and the
+    strict count (11 / 22 per contributing pair), and one ex2 per listed pair
+    and pass."""
+    w = bench.render_work(1000, 300)
+    assert w["fwd"] == 8 * 1000 + 3 * 300 and w["bwd"] == 8 * 1000 + 20 * 300
+    assert w["fused"] == w["fwd"] + w["bwd"]
+    assert w["fwd_strict"] == 11 * 300 and w["bwd_strict"] == 22 * 300
+    assert w["fused_strict"] == 33 * 300 and w["mufu_per_pass"] == 1000
+
+
+def test_binning_bytes(bench):
+    b = bench.binning_bytes(n=20000, entries=100000, tiles=2040)
+    assert b["project"] == (36 + 48 + 16 + 4) * 20000
+    assert b["bin_sort"] == 24 * 20000 + 12 * 100000 + 16 * 2040
+
+
+def test_paper_encode_reference(bench):
+    """Table 1's numbers behind the quoted -88 %."""
+    p = bench.PAPER_ENCODE
+    assert p["superpixel_s"] == 1.5 and p["random_init_s"] == 13.1
+    assert abs(p["reduction"] - 0.885) < 1e-3  # the paper rounds it to 88 %
