@@ -639,6 +639,22 @@ gs2d_status gs2d_conv_bf16(const void* x, int32_t B, int32_t Hi, int32_t Wi, int
                            int32_t N, int32_t relu, float* out_f32, void* out_bf16, int32_t ldc,
                            int32_t* status, void* stream);
 
+/* The first convolution of the learned initialiser straight from the frames:
+ * out = gs2d_conv_bf16 of gs2d_cnn_input(frames, masks) (C = 8: R, G, B, mask
+ * != 0, four zeros), the same sums in the same order, bit for bit, without the
+ * 8-channel image in memory (paper section 3.2 B).  frames: device float
+ * [B][3][H][W]; masks: device uint8 [B][H][W] or NULL (channel 3 zero); both
+ * 16-byte aligned.  Wt: device BF16 [N][ldk], ldk a multiple of 8, >= 8 ks^2
+ * + 1 (the bias in column 8 ks^2) and <= 192.  Requires W a multiple of 16,
+ * ks <= 3, 127 stride + ks <= 257 (stride 1 or 2) and N <= 128, else
+ * GS2D_ERR_INVALID_ARG.  relu, out_f32 / out_bf16, ldc and status as
+ * gs2d_conv_bf16. */
+gs2d_status gs2d_conv_frame_bf16(const float* frames, const uint8_t* masks, int32_t B, int32_t H,
+                                 int32_t W, int32_t ks, int32_t stride, int32_t pad,
+                                 const void* Wt, int32_t ldk, int32_t N, int32_t relu,
+                                 float* out_f32, void* out_bf16, int32_t ldc, int32_t* status,
+                                 void* stream);
+
 /* Gradient of gs2d_im2col: dx[b][iy][ix][ci] = sum over the taps that read
  * (iy, ix) of dcol (device, float32 [B Ho Wo][ldk]), multiplied by (act > 0)
  * when act (device, [B][Hi][Wi][C] BF16, the ReLU output fed to the im2col) is

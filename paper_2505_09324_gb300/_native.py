@@ -33,7 +33,8 @@ EXPORTS = (
     "gs2d_fit_rebins", "gs2d_fit_state_get", "gs2d_fit_state_set",
     "gs2d_encode_batch",
     "gs2d_autotune_ws_bytes", "gs2d_autotune",
-    "gs2d_gemm_bf16", "gs2d_gemm_partial_bytes", "gs2d_cnn_input", "gs2d_im2col", "gs2d_col2im",
+    "gs2d_gemm_bf16", "gs2d_gemm_partial_bytes", "gs2d_cnn_input", "gs2d_conv_frame_bf16",
+    "gs2d_im2col", "gs2d_col2im",
     "gs2d_transpose_bf16", "gs2d_relu_bwd", "gs2d_cast_weights", "gs2d_head_decode",
     "gs2d_head_smem_bytes", "gs2d_head_decode_bwd", "gs2d_chamfer", "gs2d_chamfer_scratch_bytes",
     "gs2d_read_bins", "gs2d_count_pairs", "gs2d_ws_status",
@@ -196,6 +197,8 @@ def load(build_if_missing: bool = False):
                                      P]),
             "gs2d_gemm_partial_bytes": (ctypes.c_uint64, [i32, i32, i32, i32, i32]),
             "gs2d_cnn_input": (i32, [P, P, i32, i32, i32, P, P]),
+            "gs2d_conv_frame_bf16": (i32, [P, P, i32, i32, i32, i32, i32, i32, P, i32, i32, i32, P,
+                                           P, i32, P, P]),
             "gs2d_im2col": (i32, [P, i32, i32, i32, i32, i32, i32, i32, P, i32, P]),
             "gs2d_col2im": (i32, [P, i32, i32, i32, i32, i32, i32, i32, i32, P, P, P]),
             "gs2d_transpose_bf16": (i32, [P, i32, i32, i32, P, i32, P]),

@@ -129,6 +129,50 @@ extern "C" gs2d_status gs2d_conv_bf16(const void* x, int32_t B, int32_t Hi, int3
   return set_error(GS2D_OK, "");
 }
 
+extern "C" gs2d_status gs2d_conv_frame_bf16(const float* frames, const uint8_t* masks,
+                                            int32_t B, int32_t H, int32_t W, int32_t ks,
+                                            int32_t stride, int32_t pad, const void* Wt,
+                                            int32_t ldk, int32_t N, int32_t relu, float* out_f32,
+                                            void* out_bf16, int32_t ldc, int32_t* status,
+                                            void* stream) {
+  if (B < 0 || H < 1 || W < 1 || ks < 1 || stride < 1 || pad < 0 || N < 0 || ldk % 8 ||
+      ldk < ks * ks * 8 + 1 || ldk > 192 || ldc < N)
+    return set_error(GS2D_ERR_INVALID_ARG, "gs2d_conv_frame_bf16: sizes");
+  const int Ho = (H + 2 * pad - ks) / stride + 1, Wo = (W + 2 * pad - ks) / stride + 1;
+  if (Ho < 1 || Wo < 1) return set_error(GS2D_ERR_INVALID_ARG, "gs2d_conv_frame_bf16: empty output");
+  if (B == 0 || N == 0) return set_error(GS2D_OK, "");
+  if (!frame_conv_supported(W, ks, stride, N))
+    return set_error(GS2D_ERR_INVALID_ARG,
+                     "gs2d_conv_frame_bf16: W a multiple of 16, ks <= 3, stride <= 2, N <= 128");
+  if (!frames || !Wt || ((out_f32 == nullptr) == (out_bf16 == nullptr)) ||
+      ((uintptr_t)frames & 15) || ((uintptr_t)masks & 15) || ((uintptr_t)Wt & 15))
+    return set_error(GS2D_ERR_INVALID_ARG, "gs2d_conv_frame_bf16: operands");
+  TcFrameConvProblem pr;
+  pr.frames = frames;
+  pr.masks = masks;
+  pr.B = B;
+  pr.H = H;
+  pr.W = W;
+  pr.ks = ks;
+  pr.stride = stride;
+  pr.pad = pad;
+  pr.W_ = static_cast<const __nv_bfloat16*>(Wt);
+  pr.ldk = ldk;
+  pr.N = N;
+  pr.relu = relu;
+  pr.out_f32 = out_f32;
+  pr.out_bf16 = static_cast<__nv_bfloat16*>(out_bf16);
+  pr.ldc = ldc;
+  pr.status = status;
+  const cudaError_t e = tc_conv_frame(pr, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    char msg[200];
+    snprintf(msg, sizeof(msg), "gs2d_conv_frame_bf16: %s", cudaGetErrorString(e));
+    return set_error(GS2D_ERR_CUDA, msg);
+  }
+  return set_error(GS2D_OK, "");
+}
+
 // ---------------------------------------------------------------------------
 // Convolution helpers.  Activations are NHWC BF16 ([B][H][W][C], C a multiple
 // of 8); a ks x ks convolution is the GEMM  Z = col(X) . W^T  with

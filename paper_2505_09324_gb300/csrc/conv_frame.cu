@@ -1,0 +1,403 @@
+// The learned initialiser's first convolution straight from the float frame
+// and its ROI mask (paper section 3.2 B): gs2d_cnn_input (8-channel BF16 NHWC:
+// R, G, B, mask, four zeros) followed by gs2d_conv_bf16 in one persistent
+// tcgen05 kernel, so the 8-channel image is never written out or read back.
+//
+// A tile is 128 consecutive output pixels of one output row; the CTA takes
+// tiles j = 0, 1, ... of its share in turn.  Per tile:
+//   warp 0, one lane   four TMA loads of the tile's three input rows: the
+//                      colour planes (256 + 8 floats per row and plane from a
+//                      16-byte boundary) and the mask (256 + 16 bytes per
+//                      row), into a ring of raw stages;
+//   warps 10-25        two groups of eight warps, group j % 2, build the
+//                      tile's im2col rows in shared memory: one thread per
+//                      (row, input row ky) converts the ks pixels of its taps
+//                      to 16-byte chunks (R, G, B, mask as BF16, four zeros)
+//                      and stores them in the 128-byte-swizzled K-major
+//                      layout a TMA box of the im2col operand would have; the
+//                      tile's k-tiles (64 K each) take consecutive stages of
+//                      a second ring, whose bias and zero chunks, the same
+//                      for every tile, are written once.  After a barrier of
+//                      the group its first thread issues the tile's MMAs
+//                      (128 x BN x 16 per K slice, weights resident in shared
+//                      memory) into TMEM accumulator j % 4;
+//   warps 2-9          two groups of four warps, group j % 2, run the
+//                      epilogue (tcgen05.ld, ReLU, BF16 stores).
+// Two tiles are built and two drained at a time: a single warp per role
+// left each tile's work waiting on its own instruction latency.
+// The operands and the MMA sequence are those of gs2d_im2col + gs2d_gemm_bf16
+// on gs2d_cnn_input's output, so the result is the same bit for bit.  Every
+// mbarrier wait is bounded in time (GS2D_ERR_TIMEOUT in the status word); a
+// group leaves its loop only together, after its barrier.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "gs2d_internal.cuh"
+#include "tc_gemm.cuh"
+#include "tc_ptx.cuh"
+
+namespace gs2d {
+namespace {
+
+constexpr int kEpiWarp0 = 2;           // warps 2-9: two epilogue groups of four
+constexpr int kXfWarp0 = 10;           // warps 10-25: two im2col groups of eight
+constexpr int kGroups = 2;
+constexpr int kXfGroupWarps = 8;
+constexpr int kFrThreads = (kXfWarp0 + kGroups * kXfGroupWarps) * 32;  // 832
+constexpr int kRawStages = 4;
+constexpr int kAStages = 6;
+constexpr int kAcc = 4;
+constexpr int kRawRows = 3;            // input rows per tile (ks <= 3)
+// raw stage: floats [plane][row][256] + [plane][row][8], mask [row][256] +
+// [row][16], each box at a 128-byte boundary
+constexpr int kRawTail = 9 * 256 * 4;                // 9216
+constexpr int kRawMask = kRawTail + 512;             // 9728
+constexpr int kRawMaskTail = kRawMask + 3 * 256;     // 10496
+constexpr int kRawBytes = 11264;
+constexpr int kStageA = kBM * kBK * 2;  // 16 KB
+
+struct FrameArgs {
+  int B, H, W, Ho, Wo, ks, stride, pad;
+  int N, ldc, relu, has_mask;
+  int segs, tiles, nk;
+  float* out_f32;
+  __nv_bfloat16* out_bf16;
+  int* status;
+};
+
+__device__ __forceinline__ bool failed(const int* flag) {
+  return *reinterpret_cast<const volatile int*>(flag) != 0;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+// Barrier of one im2col group (named barriers 1 and 2; 0 is __syncthreads)
+// that returns the OR of every participating thread's v.
+__device__ __forceinline__ bool group_sync_or(int grp, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n"
+      " bar.red.or.pred p, %2, %3, q;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(1 + grp), "n"(kXfGroupWarps * 32)
+      : "memory");
+  return r != 0;
+}
+
+// Shared-memory offsets (from the 1024-aligned base): A ring, raw ring,
+// resident weights.
+struct FrameSmem {
+  static constexpr int kA = 0;
+  static constexpr int kRaw = kAStages * kStageA;
+  static constexpr int kB = kRaw + kRawStages * kRawBytes;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(kFrThreads, 1)
+k_conv_frame(const __grid_constant__ CUtensorMap tf256, const __grid_constant__ CUtensorMap tf8,
+             const __grid_constant__ CUtensorMap tm256, const __grid_constant__ CUtensorMap tm16,
+             const __grid_constant__ CUtensorMap tb, FrameArgs g) {
+  constexpr int kAccStride = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+  constexpr int kCols = kAcc * kAccStride;
+  constexpr int kTmemCols = kCols <= 128 ? 128 : kCols <= 256 ? 256 : 512;
+  constexpr int kBBytes = BN * kBK * 2;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t raw_full[kRawStages], raw_empty[kRawStages];
+  __shared__ __align__(8) uint64_t a_empty[kAStages];
+  __shared__ __align__(8) uint64_t acc_full[kAcc], acc_empty[kAcc], bres_full;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail;
+  // 1024-aligned, and kept in the shared window so that accesses compile to
+  // shared-memory instructions
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nk = g.nk;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kRawStages; s++) {
+      mbar_init(&raw_full[s], 1);
+      mbar_init(&raw_empty[s], kXfGroupWarps);
+    }
+    for (int s = 0; s < kAStages; s++) mbar_init(&a_empty[s], 1);
+    for (int a = 0; a < kAcc; a++) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], 4);
+    }
+    mbar_init(&bres_full, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // the chunks past the taps (the bias column's 1, then zeros): stage s
+  // always holds k-tile s % nk (nk divides the ring), so they are written once
+  for (int q = threadIdx.x; q < kAStages * 8 * kBM; q += blockDim.x) {
+    const int st = q / (8 * kBM), c = (q / kBM) & 7, r = q % kBM;
+    const int tap = (st % nk) * 8 + c;
+    if (tap >= g.ks * g.ks)
+      *reinterpret_cast<uint4*>(smem + FrameSmem::kA + st * kStageA + r * 128 +
+                                ((c ^ (r & 7)) << 4)) =
+          make_uint4(tap == g.ks * g.ks ? 0x3F80u : 0u, 0u, 0u, 0u);
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s_tmem)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer: the weights once, then each tile's raw input rows
+      mbar_expect_tx(&bres_full, (uint32_t)(nk * kBBytes));
+      for (int i = 0; i < nk; i++)
+        tma_load_2d(smem + FrameSmem::kB + i * kBBytes, &tb, &bres_full, i * kBK, 0);
+      const uint32_t bytes =
+          (uint32_t)(kRawRows * (3 * (256 + 8) * 4 + (g.has_mask ? 256 + 16 : 0)));
+      uint32_t j = 0;
+      for (int t = blockIdx.x; t < g.tiles && !failed(&s_fail); t += gridDim.x, j++) {
+        const int row = t / g.segs, seg = t - row * g.segs;
+        const int b = row / g.Ho, oy = row - b * g.Ho;
+        const int x0 = seg * kBM * g.stride - g.pad, y0 = oy * g.stride - g.pad;
+        const int xa = x0 & ~3, xm = x0 & ~15;  // 16-byte boundaries (floor)
+        const int s = (int)(j % kRawStages);
+        if (!mbar_wait(&raw_empty[s], ((j / kRawStages) & 1u) ^ 1u)) {
+          s_fail = 1;
+          break;
+        }
+        uint8_t* st = smem + FrameSmem::kRaw + s * kRawBytes;
+        mbar_expect_tx(&raw_full[s], bytes);
+        tma_load_4d(st, &tf256, &raw_full[s], xa, y0, 0, b);
+        tma_load_4d(st + kRawTail, &tf8, &raw_full[s], xa + 256, y0, 0, b);
+        if (g.has_mask) {
+          tma_load_3d(st + kRawMask, &tm256, &raw_full[s], xm, y0, b);
+          tma_load_3d(st + kRawMaskTail, &tm16, &raw_full[s], xm + 256, y0, b);
+        }
+      }
+    }
+  } else if (warp >= kEpiWarp0 && warp < kXfWarp0) {
+    // epilogue group e takes tiles j = e, e + 2, ...; warp w reads TMEM lanes
+    // 32 (w % 4) ... (its accumulator rows)
+    const int e = (warp - kEpiWarp0) >> 2;
+    const int quarter = warp & 3, r = quarter * 32 + lane;
+    const bool vec_ok =
+        (g.ldc % 8) == 0 &&
+        ((reinterpret_cast<uintptr_t>(g.out_bf16 ? (const void*)g.out_bf16
+                                                 : (const void*)g.out_f32) &
+          15) == 0);
+    uint32_t j = (uint32_t)e;
+    for (int t = blockIdx.x + e * gridDim.x; t < g.tiles; t += kGroups * gridDim.x, j += kGroups) {
+      const int a = (int)(j % kAcc);
+      if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[a], (j / kAcc) & 1u))) {
+        s_fail = 1;
+        break;
+      }
+      tc_fence_after();
+      const int row = t / g.segs, seg = t - row * g.segs;
+      const int ox = seg * kBM + r;
+      const size_t o = ((size_t)row * g.Wo + ox) * g.ldc;
+      const uint32_t taddr =
+          tmem + (uint32_t)(a * kAccStride) + ((uint32_t)(quarter * 32) << 16);
+      store_acc_row<BN>(taddr, ox < g.Wo, o, g.N, g.relu, vec_ok, g.out_f32, g.out_bf16);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[a]);
+    }
+  } else if (warp >= kXfWarp0) {
+    // im2col group x takes tiles j = x, x + 2, ...: one thread per (tile row
+    // r, input row ky) writes the ks chunks of taps (ky, 0 ... ks - 1) of row
+    // r, all loads first (consecutive threads take consecutive rows:
+    // stride-apart words on the loads, the 16-byte stores spread over the
+    // swizzle); then the group's first thread issues the tile's MMAs
+    const int x = (warp - kXfWarp0) / kXfGroupWarps;
+    const int xt = threadIdx.x - (kXfWarp0 + x * kXfGroupWarps) * 32;  // 0 ... 255
+    constexpr uint32_t idesc = idesc_bf16(kBM, BN);
+    if (xt == 0 && !mbar_wait(&bres_full, 0)) s_fail = 1;
+    uint32_t j = (uint32_t)x;
+    for (int t = blockIdx.x + x * gridDim.x; t < g.tiles; t += kGroups * gridDim.x, j += kGroups) {
+      const uint32_t aj = j * (uint32_t)nk;  // the tile's k-tiles: stages aj, aj + 1, ...
+      const int rs = (int)(j % kRawStages);
+      bool ok = __all_sync(0xffffffffu, mbar_wait(&raw_full[rs], (j / kRawStages) & 1u));
+      for (int i = 0; i < nk && ok; i++) {
+        const uint32_t q = aj + (uint32_t)i;
+        ok = __all_sync(0xffffffffu,
+                        mbar_wait(&a_empty[q % kAStages], ((q / kAStages) & 1u) ^ 1u));
+      }
+      if (ok) {
+        const int row = t / g.segs, seg = t - row * g.segs;
+        const int x0 = seg * kBM * g.stride - g.pad;
+        const int fa = x0 - (x0 & ~3), fm = x0 - (x0 & ~15);  // x0 within the raw rows
+        const uint8_t* raw = smem + FrameSmem::kRaw + rs * kRawBytes;
+        const float* rf = reinterpret_cast<const float*>(raw);
+        const float* rt = reinterpret_cast<const float*>(raw + kRawTail);
+        for (int q = xt; q < g.ks * kBM; q += kXfGroupWarps * 32) {
+          const int ky = q >> 7, r = q & (kBM - 1);
+          const float* fr = rf + ky * 256;
+          const float* ft = rt + ky * 8;
+          const uint8_t* mr = raw + kRawMask + ky * 256;
+          const uint8_t* mt = raw + kRawMaskTail + ky * 16;
+          float c3[kRawRows][3];
+          uint8_t mb[kRawRows];
+#pragma unroll
+          for (int kx = 0; kx < kRawRows; kx++) {
+            const int d = r * g.stride + kx, f = fa + d, h = fm + d;
+            const bool on = kx < g.ks;
+#pragma unroll
+            for (int p = 0; p < 3; p++)
+              c3[kx][p] = !on ? 0.0f : f < 256 ? fr[p * 768 + f] : ft[p * 24 + f - 256];
+            mb[kx] = !on || !g.has_mask ? 0 : h < 256 ? mr[h] : mt[h - 256];
+          }
+#pragma unroll
+          for (int kx = 0; kx < kRawRows; kx++) {
+            if (kx >= g.ks) break;
+            const __nv_bfloat162 rg = __floats2bfloat162_rn(c3[kx][0], c3[kx][1]);
+            const __nv_bfloat162 bm = __floats2bfloat162_rn(c3[kx][2], mb[kx] ? 1.0f : 0.0f);
+            const int tap = ky * g.ks + kx, c = tap & 7;
+            uint8_t* A =
+                smem + FrameSmem::kA + ((aj + (uint32_t)(tap >> 3)) % kAStages) * kStageA;
+            *reinterpret_cast<uint4*>(A + r * 128 + ((c ^ (r & 7)) << 4)) =
+                make_uint4(*reinterpret_cast<const uint32_t*>(&rg),
+                           *reinterpret_cast<const uint32_t*>(&bm), 0u, 0u);
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&raw_empty[rs]);
+      // the whole group stops together: the barrier ORs every thread's view
+      if (group_sync_or(x, !ok || failed(&s_fail))) {
+        s_fail = 1;
+        break;
+      }
+      if (xt == 0) {
+        const int a = (int)(j % kAcc);
+        if (!mbar_wait(&acc_empty[a], ((j / kAcc) & 1u) ^ 1u)) {
+          s_fail = 1;
+        } else {
+          tc_fence_after();
+          const uint32_t d = tmem + (uint32_t)(a * kAccStride);
+          for (int i = 0; i < nk; i++) {
+            const int s = (int)((aj + (uint32_t)i) % kAStages);
+            const uint64_t ad = sw128_desc(smem_u32(smem + FrameSmem::kA + s * kStageA));
+            const uint64_t bd = sw128_desc(smem_u32(smem + FrameSmem::kB + i * kBBytes));
+#pragma unroll
+            for (int kk = 0; kk < kBK / 16; kk++)
+              mma_bf16(d, ad + 2 * kk, bd + 2 * kk, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(&a_empty[s]);
+          }
+          mma_commit(&acc_full[a]);
+        }
+      }
+    }
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols));
+  if (threadIdx.x == 0 && s_fail && g.status) atomicCAS(g.status, 0, (int)GS2D_ERR_TIMEOUT);
+}
+
+// Tensor map of a dim-4 float tensor [B][3][H][W] (box w pixels x 3 rows x 3
+// planes) or of a dim-3 byte tensor [B][H][W] (box w pixels x 3 rows); zeros
+// out of range.
+bool make_row_map(CUtensorMap* map, const void* base, bool bytes, int B, int H, int W, int w) {
+  EncodeTiled fn = tensor_map_encoder();
+  if (!fn) return false;
+  const cuuint64_t es = bytes ? 1 : 4;
+  const cuuint64_t dims4[4] = {(cuuint64_t)W, (cuuint64_t)H, 3, (cuuint64_t)B};
+  const cuuint64_t str4[3] = {W * es, (cuuint64_t)H * W * es, (cuuint64_t)3 * H * W * es};
+  const cuuint64_t dims3[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+  const cuuint64_t str3[2] = {W * es, (cuuint64_t)H * W * es};
+  const cuuint32_t box[4] = {(cuuint32_t)w, kRawRows, bytes ? 1u : 3u, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return fn(map, bytes ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+            bytes ? 3 : 4, const_cast<void*>(base), bytes ? dims3 : dims4, bytes ? str3 : str4,
+            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN>
+cudaError_t launch_frame(const CUtensorMap (&maps)[5], const FrameArgs& g, int smem,
+                         cudaStream_t s) {
+  const cudaError_t attr = opt_in_smem((const void*)k_conv_frame<BN>, smem);
+  if (attr != cudaSuccess) return attr;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 1;
+  const int grid = std::max(1, std::min(g.tiles, sms));
+  k_conv_frame<BN><<<grid, kFrThreads, smem, s>>>(maps[0], maps[1], maps[2], maps[3], maps[4],
+                                                   g);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool frame_conv_supported(int W, int ks, int stride, int N) {
+  return W % 16 == 0 && ks >= 1 && ks <= kRawRows && stride >= 1 &&
+         kBM * stride - stride + ks <= 257 && N >= 1 && N <= 128;
+}
+
+cudaError_t tc_conv_frame(const TcFrameConvProblem& pr, cudaStream_t s) {
+  const int Ho = (pr.H + 2 * pr.pad - pr.ks) / pr.stride + 1;
+  const int Wo = (pr.W + 2 * pr.pad - pr.ks) / pr.stride + 1;
+  if (pr.B <= 0 || Ho <= 0 || Wo <= 0 || pr.N <= 0) return cudaSuccess;
+  if (!frame_conv_supported(pr.W, pr.ks, pr.stride, pr.N) || pr.ldk % 8 ||
+      pr.ldk < pr.ks * pr.ks * 8 + 1 || kAStages % ((pr.ldk + kBK - 1) / kBK) != 0 || (reinterpret_cast<uintptr_t>(pr.frames) & 15) ||
+      (reinterpret_cast<uintptr_t>(pr.masks) & 15) || (reinterpret_cast<uintptr_t>(pr.W_) & 15))
+    return cudaErrorInvalidValue;
+  const int bn = tc_gemm_bn(pr.N);
+  FrameArgs g;
+  g.B = pr.B;
+  g.H = pr.H;
+  g.W = pr.W;
+  g.Ho = Ho;
+  g.Wo = Wo;
+  g.ks = pr.ks;
+  g.stride = pr.stride;
+  g.pad = pr.pad;
+  g.N = pr.N;
+  g.ldc = pr.ldc;
+  g.relu = pr.relu;
+  g.has_mask = pr.masks ? 1 : 0;
+  g.segs = (Wo + kBM - 1) / kBM;
+  g.tiles = pr.B * Ho * g.segs;
+  g.nk = (pr.ldk + kBK - 1) / kBK;
+  g.out_f32 = pr.out_f32;
+  g.out_bf16 = pr.out_bf16;
+  g.status = pr.status;
+  const int smem = FrameSmem::kB + g.nk * bn * kBK * 2 + 1024;
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  CUtensorMap maps[5];
+  // without a mask the mask maps are never used: encode them over the frames
+  const void* mbase = pr.masks ? (const void*)pr.masks : (const void*)pr.frames;
+  if (!make_row_map(&maps[0], pr.frames, false, pr.B, pr.H, pr.W, 256) ||
+      !make_row_map(&maps[1], pr.frames, false, pr.B, pr.H, pr.W, 8) ||
+      !make_row_map(&maps[2], mbase, true, pr.B, pr.H, pr.W, 256) ||
+      !make_row_map(&maps[3], mbase, true, pr.B, pr.H, pr.W, 16) ||
+      !make_map(&maps[4], pr.W_, pr.N, pr.ldk, pr.ldk, bn))
+    return cudaErrorInvalidValue;
+  switch (bn) {
+    case 32: return launch_frame<32>(maps, g, smem, s);
+    case 64: return launch_frame<64>(maps, g, smem, s);
+    case 96: return launch_frame<96>(maps, g, smem, s);
+    default: return launch_frame<128>(maps, g, smem, s);
+  }
+}
+
+}  // namespace gs2d

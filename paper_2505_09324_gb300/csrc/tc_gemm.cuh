@@ -5,6 +5,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
+#include <stdint.h>
 
 namespace gs2d {
 
@@ -53,8 +54,32 @@ struct TcConvProblem {
   int* status;
 };
 
+// The first convolution straight from float frames [B][3][H][W] and masks
+// [B][H][W] (or NULL): im2col of the 8-channel BF16 input (R, G, B, mask != 0,
+// zeros) formed on the fly; csrc/conv_frame.cu.
+struct TcFrameConvProblem {
+  const float* frames;
+  const uint8_t* masks;
+  int B, H, W, ks, stride, pad;
+  const __nv_bfloat16* W_;  // [N][ldk], ldk >= ks^2 8 + 1
+  int ldk, N;
+  int relu;
+  float* out_f32;
+  __nv_bfloat16* out_bf16;
+  int ldc;
+  int* status;
+};
+
 cudaError_t tc_gemm(const TcGemmProblem& pr, cudaStream_t s);
 cudaError_t tc_conv(const TcConvProblem& pr, cudaStream_t s);
+// The persistent TMA-tap convolution (csrc/conv_tap.cu): C of 16, 32 or a
+// multiple of 64, stride 1 or 2, N <= 256, output rows of 64 pixels or more.
+bool tap_conv_supported(const TcConvProblem& pr);
+cudaError_t tap_conv(const TcConvProblem& pr, cudaStream_t s);
+// W a multiple of 16, ks <= 3, the 128-pixel window within 257 input pixels,
+// N <= 128.
+bool frame_conv_supported(int W, int ks, int stride, int N);
+cudaError_t tc_conv_frame(const TcFrameConvProblem& pr, cudaStream_t s);
 int tc_gemm_bn(int n);
 size_t tc_gemm_partial_floats(int M, int N, int ldc, int K, int splits);
 

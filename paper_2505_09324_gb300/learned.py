@@ -143,8 +143,10 @@ class LearnedInitializer:
         """frames: [B, 3, H, W] float32 CUDA; masks: [B, H, W] uint8 or None.
         Returns the Gaussians, [9, B n] float32 (frame b in columns b n ...).
         keep_col=False (inference) runs the convolutions as implicit GEMMs
-        (gs2d_conv_bf16, the same result bit for bit) and keeps no complete
-        set of im2col operands, which backward() needs."""
+        (gs2d_conv_bf16; the first one, gs2d_conv_frame_bf16, straight from
+        the frames when W is a multiple of 16; the same result bit for bit)
+        and keeps neither the im2col operands nor the 8-channel input, which
+        backward() needs."""
         B, s = self.B, self._s()
         if tuple(frames.shape) != (B, 3, self.H, self.W) or frames.dtype != torch.float32:
             raise ValueError("frames must be [B, 3, H, W] float32")
@@ -153,10 +155,21 @@ class LearnedInitializer:
         if masks is not None:
             masks = masks.to(torch.uint8).contiguous()
             mptr = masks.data_ptr()
-        nat.call("gs2d_cnn_input", frames.data_ptr(), mptr, B, self.H, self.W,
-                 self.x[0].data_ptr(), s)
         st = self.status.data_ptr()
+        ci0, co0, ks0, ldk0 = self.layers[0]
+        first = 0
+        if not keep_col and self.W % 16 == 0 and ks0 == 3 and co0 <= 128 and self.L > 0:
+            # the first convolution straight from the frames and masks (the
+            # 8-channel input never written; the same result bit for bit)
+            nat.call("gs2d_conv_frame_bf16", frames.data_ptr(), mptr, B, self.H, self.W, 3, 2,
+                     1, self.wb[0].data_ptr(), ldk0, co0, 1, 0, self.x[1].data_ptr(), co0, st, s)
+            first = 1
+        else:
+            nat.call("gs2d_cnn_input", frames.data_ptr(), mptr, B, self.H, self.W,
+                     self.x[0].data_ptr(), s)
         for li, (ci, co, ks, ldk) in enumerate(self.layers):
+            if li < first:
+                continue
             src = self.x[li]
             hi, wi = self.sizes[li] if li < self.L else self.sizes[-1]
             stride, pad = (2, 1) if ks == 3 else (1, 0)

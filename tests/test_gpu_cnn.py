@@ -265,7 +265,16 @@ def test_chamfer_loss_and_gradient(nat):
     (1, 24, 30, 32, 64, 3, 2, 1, "bf16"),
     (2, 12, 9, 256, 384, 3, 2, 1, "bf16"),   # N over two 192-column tiles, 37 k-tiles
     (3, 7, 11, 384, 90, 1, 1, 0, "f32"),     # the head: 1 x 1, N = 90, FP32 out
-    (1, 135, 240, 64, 128, 3, 2, 1, "bf16")])
+    # output rows of 64 pixels or more and C of 16, 32 or 64 j: the
+    # persistent kernel with TMA tap loads (128-pixel row segments, the last
+    # one ragged); C = 8 stays with the gathering kernel
+    (1, 135, 240, 64, 128, 3, 2, 1, "bf16"),  # 128-byte blocks, weights streamed
+    (2, 40, 300, 8, 32, 3, 2, 1, "bf16"),     # C = 8, wide rows: the gathering kernel
+    (1, 30, 260, 16, 48, 3, 2, 1, "bf16"),    # 32-byte swizzle, N below the tile
+    (2, 24, 200, 32, 64, 3, 2, 1, "bf16"),    # 64-byte swizzle, weights resident
+    (1, 17, 150, 128, 256, 3, 2, 1, "bf16"),  # two chunks per tap, N = 256
+    (1, 9, 70, 64, 90, 1, 1, 0, "f32"),       # stride 1, a k-tile of bias and zeros only
+    (1, 8, 140, 8, 32, 3, 1, 1, "bf16")])     # stride 1, C = 8
 def test_implicit_conv_equals_im2col_gemm(nat, B, H, W, ci, co, ks, st, pad, out):
     """gs2d_conv_bf16 gathers the im2col tiles itself: its output equals
     gs2d_im2col + gs2d_gemm_bf16 bit for bit, and the oracle's convolution
@@ -303,6 +312,62 @@ def test_implicit_conv_equals_im2col_gemm(nat, B, H, W, ci, co, ks, st, pad, out
     got = (to_np_bf16(z) if out == "bf16" else z.cpu().numpy()).astype(np.float64)
     tol = REL * scale + (np.abs(ref) * 2.0 ** -8 if relu else 0.0) + 1e-30
     assert np.all(np.abs(got - ref) <= tol)
+
+
+@pytest.mark.parametrize("B,H,W,ks,st,pad,co,with_mask,out", [
+    (2, 37, 304, 3, 2, 1, 32, True, "bf16"),    # two row segments, the last ragged
+    (1, 20, 160, 3, 1, 1, 64, False, "bf16"),   # stride 1, no mask (channel 3 zero)
+    (3, 9, 272, 1, 1, 0, 90, True, "f32"),      # 1 x 1: one k-tile, N = 90, FP32 out
+    (1, 1080, 1920, 3, 2, 1, 32, True, "bf16")])  # the network's first layer at 1080p
+def test_conv_frame_equals_input_then_conv(nat, B, H, W, ks, st, pad, co, with_mask, out):
+    """gs2d_conv_frame_bf16 forms the 8-channel input of each im2col row from
+    the float frame and the mask itself: its output equals gs2d_cnn_input +
+    gs2d_conv_bf16 bit for bit."""
+    g = np.random.Generator(np.random.PCG64(11 * co + H + ks))
+    frames = torch.from_numpy(g.normal(0.5, 0.4, size=(B, 3, H, W)).astype(np.float32)).cuda()
+    masks = None
+    if with_mask:
+        masks = torch.from_numpy(g.choice(np.array([0, 1, 7], np.uint8), size=(B, H, W))).cuda()
+    ldk = -(-(ks * ks * 8 + 1) // 8) * 8
+    w = np.zeros((co, ldk), np.float32)
+    w[:, :ks * ks * 8 + 1] = g.normal(size=(co, ks * ks * 8 + 1)) / np.sqrt(ks * ks * 8)
+    d_w = bf16_dev(cnn.bf16_round(w))
+    Ho, Wo = cnn.out_size(H, ks, st, pad), cnn.out_size(W, ks, st, pad)
+    P = B * Ho * Wo
+    dt = torch.bfloat16 if out == "bf16" else torch.float32
+    relu = 1 if out == "bf16" else 0
+    x = torch.empty((B, H, W, 8), dtype=torch.bfloat16, device="cuda")
+    z_ref = torch.empty((P, co), dtype=dt, device="cuda")
+    z = torch.full((P, co), 7.0, dtype=dt, device="cuda")
+    st_ = torch.zeros(1, dtype=torch.int32, device="cuda")
+    mptr = masks.data_ptr() if masks is not None else 0
+
+    def outs(t):
+        return (t.data_ptr() if out == "f32" else 0, t.data_ptr() if out == "bf16" else 0)
+
+    nat.call("gs2d_cnn_input", frames.data_ptr(), mptr, B, H, W, x.data_ptr(), 0)
+    nat.call("gs2d_conv_bf16", x.data_ptr(), B, H, W, 8, ks, st, pad, d_w.data_ptr(), ldk, co,
+             relu, *outs(z_ref), co, st_.data_ptr(), 0)
+    nat.call("gs2d_conv_frame_bf16", frames.data_ptr(), mptr, B, H, W, ks, st, pad,
+             d_w.data_ptr(), ldk, co, relu, *outs(z), co, st_.data_ptr(), 0)
+    torch.cuda.synchronize()
+    assert int(st_.item()) == 0
+    assert torch.equal(z, z_ref)
+
+
+def test_conv_frame_bad_arguments(nat):
+    d = torch.zeros(1 << 16, dtype=torch.float32, device="cuda")
+    w = torch.zeros(32 * 80, dtype=torch.bfloat16, device="cuda")
+    o = torch.zeros(1 << 16, dtype=torch.bfloat16, device="cuda")
+    with pytest.raises(nat.Gs2dError):   # W not a multiple of 16
+        nat.call("gs2d_conv_frame_bf16", d.data_ptr(), 0, 1, 8, 40, 3, 2, 1, w.data_ptr(), 80,
+                 32, 1, 0, o.data_ptr(), 32, 0, 0)
+    with pytest.raises(nat.Gs2dError):   # N above 128
+        nat.call("gs2d_conv_frame_bf16", d.data_ptr(), 0, 1, 8, 32, 3, 2, 1, w.data_ptr(), 80,
+                 160, 1, 0, o.data_ptr(), 160, 0, 0)
+    with pytest.raises(nat.Gs2dError):   # no room for the bias column
+        nat.call("gs2d_conv_frame_bf16", d.data_ptr(), 0, 1, 8, 32, 3, 2, 1, w.data_ptr(), 72,
+                 32, 1, 0, o.data_ptr(), 32, 0, 0)
 
 
 def test_implicit_conv_bad_arguments(nat):
