@@ -702,14 +702,19 @@ def measure_learned(dev, frame, mask, peaks):
         cout = 9 * net.cfg.slots if li == net.L else co
         flops += 2 * B * h * w * cout * (ks * ks * ci + 1)
     tflops = flops / ms / 1e9
-    # the bytes every layer must move once: the frame and mask in, the 8-channel
-    # BF16 input out; each convolution's input and weights in, its output out
-    # (BF16, the head FP32); the decoded Gaussians out
-    nbytes = B * (H * W * (3 * 4 + 1) + H * W * 8 * 2)
+    # the bytes every layer must move once: the frame and mask in; each
+    # convolution's input and weights in, its output out (BF16, the head
+    # FP32); the decoded Gaussians out.  The first convolution reads the frame
+    # and mask itself (gs2d_conv_frame_bf16, W a multiple of 16); otherwise the
+    # 8-channel BF16 input is written and read back as well
+    fused_first = W % 16 == 0
+    nbytes = B * H * W * (3 * 4 + 1) + (0 if fused_first else B * H * W * 8 * 2)
     for li, (ci, co, ks, ldk) in enumerate(net.layers):
         hi_, wi_ = net.sizes[li] if li < net.L else net.sizes[-1]
         ho_, wo_ = net.sizes[li + 1] if li < net.L else net.sizes[-1]
-        nbytes += B * hi_ * wi_ * ci * 2 + co * ldk * 2
+        if not (li == 0 and fused_first):
+            nbytes += B * hi_ * wi_ * ci * 2
+        nbytes += co * ldk * 2
         nbytes += B * ho_ * wo_ * co * (4 if li == net.L else 2)
     nbytes += B * 9 * net.n * 4
     peak = peaks.get("bf16_tflops")
