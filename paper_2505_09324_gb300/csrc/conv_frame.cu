@@ -9,7 +9,7 @@
 //                      colour planes (256 + 8 floats per row and plane from a
 //                      16-byte boundary) and the mask (256 + 16 bytes per
 //                      row), into a ring of raw stages;
-//   warps 10-25        two groups of eight warps, group j % 2, build the
+//   warps 10-27        three groups of six warps, group j % 3, build the
 //                      tile's im2col rows in shared memory: one thread per
 //                      (row, input row ky) converts the ks pixels of its taps
 //                      to 16-byte chunks (R, G, B, mask as BF16, four zeros)
@@ -23,7 +23,7 @@
 //                      memory) into TMEM accumulator j % 4;
 //   warps 2-9          two groups of four warps, group j % 2, run the
 //                      epilogue (tcgen05.ld, ReLU, BF16 stores).
-// Two tiles are built and two drained at a time: a single warp per role
+// Three tiles are built and two drained at a time: a single warp per role
 // left each tile's work waiting on its own instruction latency.
 // The operands and the MMA sequence are those of gs2d_im2col + gs2d_gemm_bf16
 // on gs2d_cnn_input's output, so the result is the same bit for bit.  Every
@@ -42,11 +42,12 @@ namespace gs2d {
 namespace {
 
 constexpr int kEpiWarp0 = 2;           // warps 2-9: two epilogue groups of four
-constexpr int kXfWarp0 = 10;           // warps 10-25: two im2col groups of eight
-constexpr int kGroups = 2;
-constexpr int kXfGroupWarps = 8;
-constexpr int kFrThreads = (kXfWarp0 + kGroups * kXfGroupWarps) * 32;  // 832
-constexpr int kRawStages = 4;
+constexpr int kEpiGroups = 2;
+constexpr int kXfWarp0 = 10;           // warps 10-27: three im2col groups of six
+constexpr int kXfGroups = 3;
+constexpr int kXfGroupWarps = 6;
+constexpr int kFrThreads = (kXfWarp0 + kXfGroups * kXfGroupWarps) * 32;  // 896
+constexpr int kRawStages = 6;
 constexpr int kAStages = 6;
 constexpr int kAcc = 4;
 constexpr int kRawRows = 3;            // input rows per tile (ks <= 3)
@@ -80,7 +81,7 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
-// Barrier of one im2col group (named barriers 1 and 2; 0 is __syncthreads)
+// Barrier of one im2col group (named barriers 1-3; 0 is __syncthreads)
 // that returns the OR of every participating thread's v.
 __device__ __forceinline__ bool group_sync_or(int grp, bool v) {
   uint32_t r;
@@ -198,7 +199,8 @@ k_conv_frame(const __grid_constant__ CUtensorMap tf256, const __grid_constant__ 
                                                  : (const void*)g.out_f32) &
           15) == 0);
     uint32_t j = (uint32_t)e;
-    for (int t = blockIdx.x + e * gridDim.x; t < g.tiles; t += kGroups * gridDim.x, j += kGroups) {
+    for (int t = blockIdx.x + e * gridDim.x; t < g.tiles;
+         t += kEpiGroups * gridDim.x, j += kEpiGroups) {
       const int a = (int)(j % kAcc);
       if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[a], (j / kAcc) & 1u))) {
         s_fail = 1;
@@ -216,17 +218,18 @@ k_conv_frame(const __grid_constant__ CUtensorMap tf256, const __grid_constant__ 
       if (lane == 0) mbar_arrive(&acc_empty[a]);
     }
   } else if (warp >= kXfWarp0) {
-    // im2col group x takes tiles j = x, x + 2, ...: one thread per (tile row
+    // im2col group x takes tiles j = x, x + 3, ...: one thread per (tile row
     // r, input row ky) writes the ks chunks of taps (ky, 0 ... ks - 1) of row
     // r, all loads first (consecutive threads take consecutive rows:
     // stride-apart words on the loads, the 16-byte stores spread over the
     // swizzle); then the group's first thread issues the tile's MMAs
     const int x = (warp - kXfWarp0) / kXfGroupWarps;
-    const int xt = threadIdx.x - (kXfWarp0 + x * kXfGroupWarps) * 32;  // 0 ... 255
+    const int xt = threadIdx.x - (kXfWarp0 + x * kXfGroupWarps) * 32;  // 0 ... 191
     constexpr uint32_t idesc = idesc_bf16(kBM, BN);
     if (xt == 0 && !mbar_wait(&bres_full, 0)) s_fail = 1;
     uint32_t j = (uint32_t)x;
-    for (int t = blockIdx.x + x * gridDim.x; t < g.tiles; t += kGroups * gridDim.x, j += kGroups) {
+    for (int t = blockIdx.x + x * gridDim.x; t < g.tiles;
+         t += kXfGroups * gridDim.x, j += kXfGroups) {
       const uint32_t aj = j * (uint32_t)nk;  // the tile's k-tiles: stages aj, aj + 1, ...
       const int rs = (int)(j % kRawStages);
       bool ok = __all_sync(0xffffffffu, mbar_wait(&raw_full[rs], (j / kRawStages) & 1u));

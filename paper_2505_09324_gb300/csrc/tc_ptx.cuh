@@ -39,10 +39,14 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// One test of the phase; a thread whose phase is not complete may be
+// suspended for up to 20 us (the suspend-time hint) and is resumed when it
+// completes, so that waiting warps do not spin on the issue slots of the
+// working ones.
 __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
   uint32_t done;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 20000;\n"
       " selp.u32 %0, 1, 0, p;\n}"
       : "=r"(done)
       : "r"(smem_u32(bar)), "r"(parity)
@@ -126,18 +130,45 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
       : "memory");
 }
 
+// tcgen05.ld of 16 or 32 consecutive accumulator columns of the warp's 32
+// TMEM lanes, with the wait in the same statement so that no use of the
+// registers can be scheduled before the data has arrived.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-      "%11, %12, %13, %14, %15}, [%16];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {"
+      "%0, %1, %2, %3, %4, %5, %6, %7, "
+      "%8, %9, %10, %11, %12, %13, %14, %15"
+      "}, [%16];\n"
+      "tcgen05.wait::ld.sync.aligned;"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
         "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      : "r"(taddr)
+      : "memory");
 #pragma unroll
   for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {"
+      "%0, %1, %2, %3, %4, %5, %6, %7, "
+      "%8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, "
+      "%24, %25, %26, %27, %28, %29, %30, %31"
+      "}, [%32];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ void tc_fence_before() {
@@ -156,36 +187,46 @@ template <int BN>
 __device__ __forceinline__ void store_acc_row(uint32_t taddr, bool valid, size_t o, int N,
                                               int relu, bool vec_ok, float* out_f32,
                                               __nv_bfloat16* out_bf16) {
+  // 32 columns per load where the tile allows (one wait per 32 columns)
+  constexpr int kW = BN % 32 == 0 ? 32 : 16;
 #pragma unroll 1
-  for (int c = 0; c < BN; c += 16) {
-    float v[16];
-    tmem_ld16(taddr + (uint32_t)c, v);
+  for (int c0 = 0; c0 < BN; c0 += kW) {
+    float w[kW];
+    if constexpr (kW == 32)
+      tmem_ld32(taddr + (uint32_t)c0, w);
+    else
+      tmem_ld16(taddr + (uint32_t)c0, w);
     if (!valid) continue;
 #pragma unroll
-    for (int j = 0; j < 16; j++)
-      if (relu) v[j] = fmaxf(v[j], 0.0f);
-    if (vec_ok && c + 16 <= N) {
-      if (out_bf16) {
-        __align__(16) __nv_bfloat162 h[8];
+    for (int j = 0; j < kW; j++)
+      if (relu) w[j] = fmaxf(w[j], 0.0f);
 #pragma unroll
-        for (int j = 0; j < 8; j++) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-        uint4* dst = reinterpret_cast<uint4*>(out_bf16 + o + c);
-        dst[0] = reinterpret_cast<const uint4*>(h)[0];
-        dst[1] = reinterpret_cast<const uint4*>(h)[1];
+    for (int q = 0; q < kW; q += 16) {
+      const int c = c0 + q;
+      const float* v = w + q;
+      if (vec_ok && c + 16 <= N) {
+        if (out_bf16) {
+          __align__(16) __nv_bfloat162 hv[8];
+#pragma unroll
+          for (int j = 0; j < 8; j++) hv[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+          uint4* dst = reinterpret_cast<uint4*>(out_bf16 + o + c);
+          dst[0] = reinterpret_cast<const uint4*>(hv)[0];
+          dst[1] = reinterpret_cast<const uint4*>(hv)[1];
+        } else {
+          float4* dst = reinterpret_cast<float4*>(out_f32 + o + c);
+#pragma unroll
+          for (int j = 0; j < 4; j++)
+            dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        }
       } else {
-        float4* dst = reinterpret_cast<float4*>(out_f32 + o + c);
 #pragma unroll
-        for (int j = 0; j < 4; j++)
-          dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < 16; j++) {
-        if (c + j < N) {
-          if (out_bf16)
-            out_bf16[o + c + j] = __float2bfloat16_rn(v[j]);
-          else
-            out_f32[o + c + j] = v[j];
+        for (int j = 0; j < 16; j++) {
+          if (c + j < N) {
+            if (out_bf16)
+              out_bf16[o + c + j] = __float2bfloat16_rn(v[j]);
+            else
+              out_f32[o + c + j] = v[j];
+          }
         }
       }
     }
