@@ -430,7 +430,8 @@ gs2d_status gs2d_sequence_bits(const int32_t* counts, const double* payload_bits
 /* Frame input (the video frame a fit targets, Sec. 3.2): 8-bit interleaved
  * RGB (device, row y at rgb + y * row_bytes, pixel x at 3 * x; row_bytes >=
  * 3 * width) to the planar float32 frame [3][H][W] (device) with value c /
- * 255 correctly rounded.  Stream-ordered; nothing is allocated. */
+ * 255 correctly rounded; height at most 65535.  Stream-ordered; nothing is
+ * allocated. */
 gs2d_status gs2d_frame_from_rgb8(const uint8_t* rgb, int32_t width, int32_t height,
                                  int64_t row_bytes, float* frame, void* stream);
 

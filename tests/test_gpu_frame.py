@@ -19,7 +19,7 @@ def gs():
     return pkg
 
 
-@pytest.mark.parametrize("W,H", [(1, 1), (37, 5), (641, 359), (1920, 1080)])
+@pytest.mark.parametrize("W,H", [(1, 1), (37, 5), (641, 359), (1000, 7), (1920, 1080)])
 def test_rgb8_to_planar_bit_exact(gs, W, H):
     rng = np.random.default_rng(W * 7 + H)
     rgb = rng.integers(0, 256, (H, W, 3), dtype=np.uint8)
@@ -29,9 +29,10 @@ def test_rgb8_to_planar_bit_exact(gs, W, H):
     assert got[0, 0, 0] == np.float32(rgb[0, 0, 0]) / np.float32(255)
 
 
-def test_rgb8_padded_rows(gs):
+@pytest.mark.parametrize("pad", [61, 64])   # odd rows: byte loads; 4-byte rows: word loads
+def test_rgb8_padded_rows(gs, pad):
     from paper_2505_09324_gb300 import _native as nat
-    W, H, pad = 100, 33, 61
+    W, H = 100, 33
     rng = np.random.default_rng(3)
     buf = rng.integers(0, 256, (H, 3 * W + pad), dtype=np.uint8)
     d = torch.from_numpy(buf).cuda()
@@ -52,6 +53,8 @@ def test_rgb8_empty_and_bad_arguments(gs):
     out = torch.empty((3, 4, 4), device="cuda")
     with pytest.raises(nat.Gs2dError):
         nat.frame_from_rgb8(d.data_ptr(), 4, 4, 11, out.data_ptr(), s)  # row too short
+    with pytest.raises(nat.Gs2dError):                         # taller than 65535 rows
+        nat.frame_from_rgb8(d.data_ptr(), 1, 65536, 3, out.data_ptr(), s)
 
 
 def test_fit_on_converted_frame(gs):
