@@ -436,9 +436,11 @@ gs2d_status gs2d_frame_from_rgb8(const uint8_t* rgb, int32_t width, int32_t heig
                                  int64_t row_bytes, float* frame, void* stream);
 
 /* One fit iteration end to end, as an encoder on the host drives it: the
- * 8-bit RGB frame (pinned host, H x W x 3, packed rows) is copied to rgb_dev
- * (device, 3 W H bytes) and converted into frame_dev (device [3][H][W]
- * float32, gs2d_frame_from_rgb8); params_host (pinned host, 9n floats, or
+ * 8-bit RGB frame (host, H x W x 3, packed rows) is converted into frame_dev
+ * (device [3][H][W] float32, as gs2d_frame_from_rgb8): read over the host
+ * link by the conversion itself when rgb_host is pinned memory the device can
+ * address (cudaHostAlloc / cudaHostRegister), else first copied to rgb_dev
+ * (device, 3 W H bytes); params_host (pinned host, 9n floats, or
  * NULL to keep the device params) is copied to params; then gs2d_fit_step;
  * then params is copied to params_out_host (pinned host, or NULL).  The
  * frame's upload and conversion run on an auxiliary stream and overlap the

@@ -435,10 +435,21 @@ gs2d_status gs2d_fit_step_rgb8(const gs2d_plan* plan, void* ws, const uint8_t* r
   // (the previous iteration's render reads frame_dev)
   if (e == cudaSuccess) e = cudaEventRecord(aux->start, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(aux->stream, aux->start, 0);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(rgb_dev, rgb_host, rgb_bytes, cudaMemcpyHostToDevice, aux->stream);
+  // pinned host memory the device can address: the conversion reads it over
+  // the host link itself, one pass instead of a copy and then a conversion;
+  // other host memory goes through rgb_dev
+  const uint8_t* src = rgb_dev;
+  cudaPointerAttributes pa;
+  if (cudaPointerGetAttributes(&pa, rgb_host) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+      pa.devicePointer) {
+    src = static_cast<const uint8_t*>(pa.devicePointer);
+  } else {
+    cudaGetLastError();
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(rgb_dev, rgb_host, rgb_bytes, cudaMemcpyHostToDevice, aux->stream);
+  }
   if (e != cudaSuccess) return cuda_check(e, "gs2d_fit_step_rgb8");
-  st = gs2d_frame_from_rgb8(rgb_dev, p.width, p.height, (int64_t)3 * p.width, frame_dev,
+  st = gs2d_frame_from_rgb8(src, p.width, p.height, (int64_t)3 * p.width, frame_dev,
                             aux->stream);
   if (st) return st;
   e = cudaEventRecord(aux->frame, aux->stream);

@@ -73,13 +73,18 @@ def test_fit_on_converted_frame(gs):
     assert torch.equal(a, b)
 
 
-def test_fit_step_rgb8_is_upload_convert_fit_download(gs):
-    """The one-call end-to-end iteration from host buffers equals its parts."""
+@pytest.mark.parametrize("pinned", [True, False])
+def test_fit_step_rgb8_is_upload_convert_fit_download(gs, pinned):
+    """The one-call end-to-end iteration from host buffers equals its parts:
+    with a pinned frame the conversion reads it over the host link itself,
+    with a pageable one it goes through the device staging buffer."""
     from gs2d_inputs import random_gaussians
     from paper_2505_09324_gb300 import _native as nat
     W, H, n = 160, 96, 400
     rng = np.random.default_rng(8)
-    rgb = torch.from_numpy(rng.integers(0, 256, (H, W, 3), dtype=np.uint8)).pin_memory()
+    rgb = torch.from_numpy(rng.integers(0, 256, (H, W, 3), dtype=np.uint8))
+    if pinned:
+        rgb = rgb.pin_memory()
     p0 = torch.from_numpy(random_gaussians(n, W, H, seed=9)).pin_memory()
     out = torch.empty_like(p0).pin_memory()
     r = gs.GaussianRasterizer(W, H, n)
