@@ -442,7 +442,9 @@ gs2d_status gs2d_frame_from_rgb8(const uint8_t* rgb, int32_t width, int32_t heig
  * address (cudaHostAlloc / cudaHostRegister), else first copied to rgb_dev
  * (device, 3 W H bytes); params_host (pinned host, 9n floats, or
  * NULL to keep the device params) is copied to params; then gs2d_fit_step;
- * then params is copied to params_out_host (pinned host, or NULL).  The
+ * params after the step also go to params_out_host (host, or NULL): stored
+ * there by the Adam kernel itself when it is pinned memory the device can
+ * address, else copied after it.  The
  * frame's upload and conversion run on an auxiliary stream and overlap the
  * projection and binning; the render waits for them, and they wait for the
  * work queued on `stream` before the call, so the call is ordered on

@@ -458,8 +458,19 @@ gs2d_status gs2d_fit_step_rgb8(const gs2d_plan* plan, void* ws, const uint8_t* r
     e = cudaMemcpyAsync(params, params_host, pbytes, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = launch_prepare_fit(p, ws, params, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, aux->frame, 0);
-  if (e == cudaSuccess) e = launch_fit_step(p, ws, frame_dev, params, adam_m, adam_v, s);
-  if (e == cudaSuccess && params_out_host && pbytes)
+  // pinned output the device can address: the Adam kernel stores the new
+  // parameters there as well, in place of a download after it
+  float* host_out = nullptr;
+  if (params_out_host && pbytes) {
+    if (cudaPointerGetAttributes(&pa, params_out_host) == cudaSuccess &&
+        pa.type == cudaMemoryTypeHost && pa.devicePointer)
+      host_out = static_cast<float*>(pa.devicePointer);
+    else
+      cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = launch_fit_step(p, ws, frame_dev, params, adam_m, adam_v, s, nullptr, host_out);
+  if (e == cudaSuccess && params_out_host && pbytes && !host_out)
     e = cudaMemcpyAsync(params_out_host, params, pbytes, cudaMemcpyDeviceToHost, s);
   return cuda_check(e, "gs2d_fit_step_rgb8");
 }

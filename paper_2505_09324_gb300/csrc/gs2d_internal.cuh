@@ -332,10 +332,11 @@ cudaError_t launch_render_l2(const gs2d_plan& p, void* ws, const float* params,
                              cudaStream_t s);
 // Follows launch_prepare_fit (it marks retained lists valid).  params_eval:
 // the values the render used, when they differ from params (the chain rule is
-// taken there; Adam updates params)
+// taken there; Adam updates params).  host_out: a device view of pinned host
+// memory that receives the parameters after the step, or NULL.
 cudaError_t launch_fit_step(const gs2d_plan& p, void* ws, const float* target, float* params,
                             float* m, float* v, cudaStream_t s,
-                            const float* params_eval = nullptr);
+                            const float* params_eval = nullptr, float* host_out = nullptr);
 cudaError_t launch_adam(float* params, const float* grads, float* m, float* v, int64_t count,
                         int32_t step, const uint8_t* mask, const gs2d_config& cfg,
                         cudaStream_t s);

@@ -112,14 +112,16 @@ k_reduce_chain(int n, const float* __restrict__ params, const int* __restrict__ 
 }
 
 // Fit loop: reduction + chain + Adam on the Gaussian's nine parameters (lane
-// `sub` of the group updates rows sub, sub + kRL, ...).
+// `sub` of the group updates rows sub, sub + kRL, ...).  host_out (device
+// view of pinned host memory, or NULL): every Gaussian's parameters after
+// the step are also stored there, so that no separate download is needed.
 __global__ void __launch_bounds__(256)
 k_reduce_chain_adam(int n, float* __restrict__ params, const int* __restrict__ offs,
                     const float4* __restrict__ partial, const WsHeader* __restrict__ hdr,
                     float* __restrict__ m, float* __restrict__ v, float4 lr_rows, float b1,
                     float b2, float eps, const uint8_t* __restrict__ select,
                     const float* __restrict__ params_eval, WsHeader* hdr_w,
-                    float* __restrict__ acc) {
+                    float* __restrict__ acc, float* __restrict__ host_out) {
   pdl_begin();
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = gt / kRL, sub = gt % kRL;
@@ -133,8 +135,8 @@ k_reduce_chain_adam(int n, float* __restrict__ params, const int* __restrict__ o
   // of a rendered tile has sums too)
   const bool any = acc ? gather_acc(acc, offs, i, i < n && ok, sub, a) && on
                        : gather_partials(partial, offs, i, on && ok, sub, a);
-  if (!ok) return;  // the same for every thread of the grid
-  const bool act = on;
+  // (ok is the same for every thread of the grid)
+  const bool act = on && ok;
   // the chain rule at the parameters that were rendered (the fake-quantised
   // ones of quantisation-aware fitting; the same array otherwise)
   if (act && any)
@@ -142,20 +144,25 @@ k_reduce_chain_adam(int n, float* __restrict__ params, const int* __restrict__ o
   else
     for (int r = 0; r < 9; r++) gr[r] = 0.0f;
   __syncwarp();  // every lane of the group has read the parameters
-  if (!act) return;
+  if (i >= n) return;
   const float ibc1 = 1.0f / hdr->bc1, ibc2 = 1.0f / hdr->bc2;
   const float lr_now = hdr->lr_now;  // lr * lr_decay^(step - 1)
 #pragma unroll
   for (int r = sub; r < 9; r += kRL) {
     const size_t k = (size_t)r * n + i;
-    const float lr = lr_now * (r < 2 ? lr_rows.x : (r < 5 ? lr_rows.y : (r < 8 ? lr_rows.z
-                                                                            : lr_rows.w)));
-    const float g = gr[r];
-    const float mm = fmaf(b1, m[k], (1.0f - b1) * g);
-    const float vv = fmaf(b2, v[k], (1.0f - b2) * g * g);
-    m[k] = mm;
-    v[k] = vv;
-    params[k] -= lr * (mm * ibc1) / (sqrtf(vv * ibc2) + eps);
+    float p = params[k];
+    if (act) {
+      const float lr = lr_now * (r < 2 ? lr_rows.x : (r < 5 ? lr_rows.y : (r < 8 ? lr_rows.z
+                                                                              : lr_rows.w)));
+      const float g = gr[r];
+      const float mm = fmaf(b1, m[k], (1.0f - b1) * g);
+      const float vv = fmaf(b2, v[k], (1.0f - b2) * g * g);
+      m[k] = mm;
+      v[k] = vv;
+      p -= lr * (mm * ibc1) / (sqrtf(vv * ibc2) + eps);
+      params[k] = p;
+    }
+    if (host_out) host_out[k] = p;
   }
 }
 
@@ -371,7 +378,8 @@ cudaError_t launch_count_pairs(const gs2d_plan& p, void* ws, cudaStream_t s) {
 // One fit iteration after projection and binning (which advanced the Adam
 // step counter): fused render + loss + backward, then reduction + chain + Adam.
 cudaError_t launch_fit_step(const gs2d_plan& p, void* ws, const float* target, float* params,
-                            float* m, float* v, cudaStream_t s, const float* params_eval) {
+                            float* m, float* v, cudaStream_t s, const float* params_eval,
+                            float* host_out) {
   RenderArgs a = render_args(p, ws);
   a.target = target;
   cudaError_t e = launch_render(p, kModeL2, a, s);
@@ -382,7 +390,8 @@ cudaError_t launch_fit_step(const gs2d_plan& p, void* ws, const float* target, f
                     reinterpret_cast<const float4*>(ws_ptr<float>(ws, p, kOffPartial)),
                     (const WsHeader*)hdr, m, v, lr_rows(p.cfg), p.cfg.beta1, p.cfg.beta2,
                     p.cfg.eps, (const uint8_t*)nullptr, params_eval,
-                    fit_lists_retained(p.cfg) ? hdr : (WsHeader*)nullptr, atomic_sums(p, ws));
+                    fit_lists_retained(p.cfg) ? hdr : (WsHeader*)nullptr, atomic_sums(p, ws),
+                    host_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -474,7 +483,7 @@ cudaError_t launch_pframe_step(const gs2d_plan& p, void* ws, const float* target
                     reinterpret_cast<const float4*>(ws_ptr<float>(ws, p, kOffPartial)),
                     ws_ptr<WsHeader>(ws, p, kOffHeader), m, v, lr_rows(p.cfg), p.cfg.beta1,
                     p.cfg.beta2, p.cfg.eps, select, (const float*)nullptr, (WsHeader*)nullptr,
-                    atomic_sums(p, ws));
+                    atomic_sums(p, ws), (float*)nullptr);
 }
 
 // Runs the one-time per-device queries of the fit loop's launches (occupancy
