@@ -34,7 +34,7 @@ EXPORTS = (
     "gs2d_encode_batch",
     "gs2d_autotune_ws_bytes", "gs2d_autotune",
     "gs2d_gemm_bf16", "gs2d_gemm_partial_bytes", "gs2d_cnn_input", "gs2d_conv_frame_bf16",
-    "gs2d_im2col", "gs2d_col2im",
+    "gs2d_conv_wait_check", "gs2d_im2col", "gs2d_col2im",
     "gs2d_transpose_bf16", "gs2d_relu_bwd", "gs2d_cast_weights", "gs2d_head_decode",
     "gs2d_head_smem_bytes", "gs2d_head_decode_bwd", "gs2d_chamfer", "gs2d_chamfer_scratch_bytes",
     "gs2d_read_bins", "gs2d_count_pairs", "gs2d_ws_status",
@@ -197,6 +197,7 @@ def load(build_if_missing: bool = False):
                                      P]),
             "gs2d_gemm_partial_bytes": (ctypes.c_uint64, [i32, i32, i32, i32, i32]),
             "gs2d_cnn_input": (i32, [P, P, i32, i32, i32, P, P]),
+            "gs2d_conv_wait_check": (i32, [i32, P, P, P, P, ctypes.c_uint64, P]),
             "gs2d_conv_frame_bf16": (i32, [P, P, i32, i32, i32, i32, i32, i32, P, i32, i32, i32, P,
                                            P, i32, P, P]),
             "gs2d_im2col": (i32, [P, i32, i32, i32, i32, i32, i32, i32, P, i32, P]),
@@ -528,6 +529,8 @@ def fit_rebins(plan: Plan, ws: int, stream: int) -> int:
 
 PROBE_FFMA = 0
 PROBE_EX2 = 1
+CHECK_CONV_FRAME = 0
+CHECK_CONV_TAP = 1
 
 
 def probe_ops(blocks: int, iters: int) -> int:

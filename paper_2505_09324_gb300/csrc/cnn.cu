@@ -89,6 +89,66 @@ extern "C" gs2d_status gs2d_gemm_wait_check(const void* A, const void* B, float*
   return set_error(GS2D_OK, "");
 }
 
+extern "C" gs2d_status gs2d_conv_wait_check(int32_t kernel, const void* x, const void* W,
+                                            void* out, int32_t* status, uint64_t wait_ns,
+                                            void* stream) {
+  if ((kernel != GS2D_CHECK_CONV_FRAME && kernel != GS2D_CHECK_CONV_TAP) || !x || !W || !out ||
+      !status || ((uintptr_t)x & 15) || ((uintptr_t)W & 15) || ((uintptr_t)out & 15))
+    return set_error(GS2D_ERR_INVALID_ARG, "gs2d_conv_wait_check: kernel, NULL or misaligned");
+  if (wait_ns < 1000000ull || wait_ns > 1000000000ull)
+    return set_error(GS2D_ERR_INVALID_ARG, "gs2d_conv_wait_check: wait_ns outside [1 ms, 1 s]");
+  cudaError_t e;
+  if (kernel == GS2D_CHECK_CONV_FRAME) {  // 1 x 3 x 16 x 256 frame -> 8 x 128 x 32
+    TcFrameConvProblem pr;
+    pr.frames = static_cast<const float*>(x);
+    pr.masks = nullptr;
+    pr.B = 1;
+    pr.H = 16;
+    pr.W = 256;
+    pr.ks = 3;
+    pr.stride = 2;
+    pr.pad = 1;
+    pr.W_ = static_cast<const __nv_bfloat16*>(W);
+    pr.ldk = 80;
+    pr.N = 32;
+    pr.relu = 1;
+    pr.out_f32 = nullptr;
+    pr.out_bf16 = static_cast<__nv_bfloat16*>(out);
+    pr.ldc = 32;
+    pr.status = status;
+    pr.wait_ns = wait_ns;
+    pr.withhold_loads = 1;
+    e = tc_conv_frame(pr, (cudaStream_t)stream);
+  } else {  // 1 x 16 x 256 x 32 activation -> 8 x 128 x 64
+    TcConvProblem pr;
+    pr.x = static_cast<const __nv_bfloat16*>(x);
+    pr.B = 1;
+    pr.Hi = 16;
+    pr.Wi = 256;
+    pr.C = 32;
+    pr.ks = 3;
+    pr.stride = 2;
+    pr.pad = 1;
+    pr.W = static_cast<const __nv_bfloat16*>(W);
+    pr.ldk = 296;
+    pr.N = 64;
+    pr.relu = 1;
+    pr.out_f32 = nullptr;
+    pr.out_bf16 = static_cast<__nv_bfloat16*>(out);
+    pr.ldc = 64;
+    pr.status = status;
+    pr.wait_ns = wait_ns;
+    pr.withhold_loads = 1;
+    e = tap_conv(pr, (cudaStream_t)stream);
+  }
+  if (e != cudaSuccess) {
+    char msg[200];
+    snprintf(msg, sizeof(msg), "gs2d_conv_wait_check: %s", cudaGetErrorString(e));
+    return set_error(GS2D_ERR_CUDA, msg);
+  }
+  return set_error(GS2D_OK, "");
+}
+
 extern "C" gs2d_status gs2d_conv_bf16(const void* x, int32_t B, int32_t Hi, int32_t Wi,
                                       int32_t C, int32_t ks, int32_t stride, int32_t pad,
                                       const void* W, int32_t ldk, int32_t N, int32_t relu,

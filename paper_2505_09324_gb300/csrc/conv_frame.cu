@@ -63,6 +63,8 @@ struct FrameArgs {
   int B, H, W, Ho, Wo, ks, stride, pad;
   int N, ldc, relu, has_mask;
   int segs, tiles, nk;
+  unsigned long long wait_ns;       // limit of every mbarrier wait (0: one second)
+  int withhold;                     // failure-detection check: the producer issues no load
   float* out_f32;
   __nv_bfloat16* out_bf16;
   int* status;
@@ -160,7 +162,7 @@ k_conv_frame(const __grid_constant__ CUtensorMap tf256, const __grid_constant__ 
   const uint32_t tmem = s_tmem;
 
   if (warp == 0) {
-    if (lane == 0) {
+    if (lane == 0 && !g.withhold) {  // a failure-detection launch issues no load
       // producer: the weights once, then each tile's raw input rows
       mbar_expect_tx(&bres_full, (uint32_t)(nk * kBBytes));
       for (int i = 0; i < nk; i++)
@@ -174,7 +176,7 @@ k_conv_frame(const __grid_constant__ CUtensorMap tf256, const __grid_constant__ 
         const int x0 = seg * kBM * g.stride - g.pad, y0 = oy * g.stride - g.pad;
         const int xa = x0 & ~3, xm = x0 & ~15;  // 16-byte boundaries (floor)
         const int s = (int)(j % kRawStages);
-        if (!mbar_wait(&raw_empty[s], ((j / kRawStages) & 1u) ^ 1u)) {
+        if (!mbar_wait(&raw_empty[s], ((j / kRawStages) & 1u) ^ 1u, g.wait_ns)) {
           s_fail = 1;
           break;
         }
@@ -202,7 +204,7 @@ k_conv_frame(const __grid_constant__ CUtensorMap tf256, const __grid_constant__ 
     for (int t = blockIdx.x + e * gridDim.x; t < g.tiles;
          t += kEpiGroups * gridDim.x, j += kEpiGroups) {
       const int a = (int)(j % kAcc);
-      if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[a], (j / kAcc) & 1u))) {
+      if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[a], (j / kAcc) & 1u, g.wait_ns))) {
         s_fail = 1;
         break;
       }
@@ -226,17 +228,18 @@ k_conv_frame(const __grid_constant__ CUtensorMap tf256, const __grid_constant__ 
     const int x = (warp - kXfWarp0) / kXfGroupWarps;
     const int xt = threadIdx.x - (kXfWarp0 + x * kXfGroupWarps) * 32;  // 0 ... 191
     constexpr uint32_t idesc = idesc_bf16(kBM, BN);
-    if (xt == 0 && !mbar_wait(&bres_full, 0)) s_fail = 1;
+    if (xt == 0 && !mbar_wait(&bres_full, 0, g.wait_ns)) s_fail = 1;
     uint32_t j = (uint32_t)x;
     for (int t = blockIdx.x + x * gridDim.x; t < g.tiles;
          t += kXfGroups * gridDim.x, j += kXfGroups) {
       const uint32_t aj = j * (uint32_t)nk;  // the tile's k-tiles: stages aj, aj + 1, ...
       const int rs = (int)(j % kRawStages);
-      bool ok = __all_sync(0xffffffffu, mbar_wait(&raw_full[rs], (j / kRawStages) & 1u));
+      bool ok =
+          __all_sync(0xffffffffu, mbar_wait(&raw_full[rs], (j / kRawStages) & 1u, g.wait_ns));
       for (int i = 0; i < nk && ok; i++) {
         const uint32_t q = aj + (uint32_t)i;
-        ok = __all_sync(0xffffffffu,
-                        mbar_wait(&a_empty[q % kAStages], ((q / kAStages) & 1u) ^ 1u));
+        ok = __all_sync(0xffffffffu, mbar_wait(&a_empty[q % kAStages],
+                                               ((q / kAStages) & 1u) ^ 1u, g.wait_ns));
       }
       if (ok) {
         const int row = t / g.segs, seg = t - row * g.segs;
@@ -286,7 +289,7 @@ k_conv_frame(const __grid_constant__ CUtensorMap tf256, const __grid_constant__ 
       }
       if (xt == 0) {
         const int a = (int)(j % kAcc);
-        if (!mbar_wait(&acc_empty[a], ((j / kAcc) & 1u) ^ 1u)) {
+        if (!mbar_wait(&acc_empty[a], ((j / kAcc) & 1u) ^ 1u, g.wait_ns)) {
           s_fail = 1;
         } else {
           tc_fence_after();
@@ -384,6 +387,8 @@ cudaError_t tc_conv_frame(const TcFrameConvProblem& pr, cudaStream_t s) {
   g.out_f32 = pr.out_f32;
   g.out_bf16 = pr.out_bf16;
   g.status = pr.status;
+  g.wait_ns = pr.wait_ns;
+  g.withhold = pr.withhold_loads;
   const int smem = FrameSmem::kB + g.nk * bn * kBK * 2 + 1024;
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   CUtensorMap maps[5];

@@ -60,6 +60,8 @@ struct TapArgs {
   int stage_bytes;                  // A (+ the weights' box if streamed)
   int b_off;                        // the weights' box within a stage (streamed)
   int ring_off, bres_off;           // offsets of the stage ring and the resident weights
+  unsigned long long wait_ns;       // limit of every mbarrier wait (0: one second)
+  int withhold;                     // failure-detection check: the producer issues no load
   float* out_f32;
   __nv_bfloat16* out_bf16;
   int* status;
@@ -136,7 +138,7 @@ k_conv_tap(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUten
   const uint32_t tmem = s_tmem;
 
   if (warp == 0) {
-    if (lane == 0) {
+    if (lane == 0 && !g.withhold) {  // a failure-detection launch issues no load
       // producer
       if (g.resident_b) {
         mbar_expect_tx(&bres_full, (uint32_t)(nk * Sh::kBBytes));
@@ -153,7 +155,7 @@ k_conv_tap(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUten
         for (int i = 0; i < nk; i++, it++) {
           const int s = (int)(it % (uint32_t)ST);
           const uint32_t ph = (it / (uint32_t)ST) & 1u;
-          if (!mbar_wait(&empty[s], ph ^ 1u)) {
+          if (!mbar_wait(&empty[s], ph ^ 1u, g.wait_ns)) {
             s_fail = 1;
             break;
           }
@@ -180,13 +182,13 @@ k_conv_tap(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUten
     if (lane == 0) {
       // MMA issuer
       constexpr uint32_t idesc = idesc_bf16(kBM, BN);
-      if (g.resident_b && !mbar_wait(&bres_full, 0)) s_fail = 1;
+      if (g.resident_b && !mbar_wait(&bres_full, 0, g.wait_ns)) s_fail = 1;
       const uint32_t cst_s = smem_u32(cst);
       uint32_t it = 0, at = 0;
       for (int t = blockIdx.x; t < g.tiles && !failed(&s_fail); t += gridDim.x, at++) {
         const int a = (int)(at % (uint32_t)Sh::kAcc);
         const uint32_t aph = (at / (uint32_t)Sh::kAcc) & 1u;
-        if (!mbar_wait(&acc_empty[a], aph ^ 1u)) {
+        if (!mbar_wait(&acc_empty[a], aph ^ 1u, g.wait_ns)) {
           s_fail = 1;
           break;
         }
@@ -195,7 +197,7 @@ k_conv_tap(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUten
         for (int i = 0; i < nk; i++, it++) {
           const int s = (int)(it % (uint32_t)ST);
           const uint32_t ph = (it / (uint32_t)ST) & 1u;
-          if (!mbar_wait(&full[s], ph)) {
+          if (!mbar_wait(&full[s], ph, g.wait_ns)) {
             s_fail = 1;
             break;
           }
@@ -237,7 +239,7 @@ k_conv_tap(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUten
       const uint32_t aph = (at / (uint32_t)Sh::kAcc) & 1u;
       // tcgen05.ld is warp-collective: the warp goes on only if every lane saw
       // the accumulator complete
-      if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[a], aph))) {
+      if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[a], aph, g.wait_ns))) {
         s_fail = 1;
         break;
       }
@@ -360,6 +362,8 @@ cudaError_t tap_conv(const TcConvProblem& pr, cudaStream_t s) {
   g.out_f32 = pr.out_f32;
   g.out_bf16 = pr.out_bf16;
   g.status = pr.status;
+  g.wait_ns = pr.wait_ns;
+  g.withhold = pr.withhold_loads;
   const int smem = tap_plan(bn, g.nk, &g);
   if (smem <= 0) return cudaErrorInvalidValue;
   CUtensorMap ta, tb;

@@ -52,6 +52,8 @@ struct TcConvProblem {
   __nv_bfloat16* out_bf16;
   int ldc;
   int* status;
+  unsigned long long wait_ns = 0;  // mbarrier wait limit (0: one second)
+  int withhold_loads = 0;  // failure-detection check only (see gs2d_conv_wait_check)
 };
 
 // The first convolution straight from float frames [B][3][H][W] and masks
@@ -68,6 +70,8 @@ struct TcFrameConvProblem {
   __nv_bfloat16* out_bf16;
   int ldc;
   int* status;
+  unsigned long long wait_ns = 0;  // mbarrier wait limit (0: one second)
+  int withhold_loads = 0;  // failure-detection check only (see gs2d_conv_wait_check)
 };
 
 cudaError_t tc_gemm(const TcGemmProblem& pr, cudaStream_t s);

@@ -63,6 +63,56 @@ def test_gemm_wait_runs_out_and_reports_timeout(nat):
     assert float((C - ref).abs().max()) <= 2e-5 * float((A.float().abs() @ B.float().abs().T).max())
 
 
+
+@pytest.mark.parametrize("kernel", ["frame", "tap"])
+def test_conv_wait_runs_out_and_reports_timeout(nat, kernel):
+    """The persistent convolutions with every load withheld: each role's
+    first wait runs out, the groups that share a named barrier leave it
+    together, and the kernel reports GS2D_ERR_TIMEOUT without writing its
+    output; then the same convolution, loads issued, is right."""
+    lib = nat.load()
+    g = torch.Generator(device="cpu").manual_seed(1)
+    if kernel == "frame":
+        which, ldk, co = nat.CHECK_CONV_FRAME, 80, 32
+        x = torch.rand(1, 3, 16, 256, generator=g).cuda()
+    else:
+        which, ldk, co = nat.CHECK_CONV_TAP, 296, 64
+        x = torch.randn(1, 16, 256, 32, generator=g).to(torch.bfloat16).cuda()
+    w = (torch.randn(co, ldk, generator=g) * 0.1).to(torch.bfloat16).cuda()
+    out = torch.full((8 * 128, co), 7.0, dtype=torch.bfloat16, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc = lib.gs2d_conv_wait_check(which, ctypes.c_void_p(x.data_ptr()),
+                                  ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                  ctypes.c_void_p(status.data_ptr()), 20_000_000,
+                                  ctypes.c_void_p(stream))
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    nat.check(rc, "gs2d_conv_wait_check")
+    assert int(status.item()) == nat.GS2D_ERR_TIMEOUT
+    assert dt >= 0.02                       # the waits ran to their limit
+    assert bool(torch.all(out == 7.0))      # nothing was stored
+    # the context is still usable: the same convolution with its loads
+    status.zero_()
+    if kernel == "frame":
+        nat.call("gs2d_conv_frame_bf16", x.data_ptr(), 0, 1, 16, 256, 3, 2, 1, w.data_ptr(), ldk,
+                 co, 1, 0, out.data_ptr(), co, status.data_ptr(), stream)
+        xin = torch.empty((1, 16, 256, 8), dtype=torch.bfloat16, device="cuda")
+        nat.call("gs2d_cnn_input", x.data_ptr(), 0, 1, 16, 256, xin.data_ptr(), stream)
+        cin = 8
+    else:
+        nat.call("gs2d_conv_bf16", x.data_ptr(), 1, 16, 256, 32, 3, 2, 1, w.data_ptr(), ldk, co,
+                 1, 0, out.data_ptr(), co, status.data_ptr(), stream)
+        xin, cin = x, 32
+    col = torch.empty((8 * 128, ldk), dtype=torch.bfloat16, device="cuda")
+    nat.call("gs2d_im2col", xin.data_ptr(), 1, 16, 256, cin, 3, 2, 1, col.data_ptr(), ldk, stream)
+    ref = torch.relu(col.float() @ w.float().T)
+    torch.cuda.synchronize()
+    assert int(status.item()) == nat.GS2D_OK
+    assert float((out.float() - ref).abs().max()) <= 1e-2 * float(ref.abs().max()) + 1e-6
+
 def test_wait_check_rejects_bad_arguments(nat):
     lib = nat.load()
     rc = lib.gs2d_gemm_wait_check(None, None, None, None, 20_000_000, None)
