@@ -12,12 +12,14 @@
 //   warps 10-27        three groups of six warps, group j % 3, build the
 //                      tile's im2col rows in shared memory: one thread per
 //                      (row, input row ky) converts the ks pixels of its taps
-//                      to 16-byte chunks (R, G, B, mask as BF16, four zeros)
-//                      and stores them in the 128-byte-swizzled K-major
-//                      layout a TMA box of the im2col operand would have; the
-//                      tile's k-tiles (64 K each) take consecutive stages of
-//                      a second ring, whose bias and zero chunks, the same
-//                      for every tile, are written once.  After a barrier of
+//                      to 16-byte chunks (R, G, B, mask as BF16, four zeros;
+//                      with 3 x 3 taps at stride 2 the third pixel comes from
+//                      the next lane) and stores them in the 128-byte-swizzled
+//                      K-major layout a TMA box of the im2col operand would
+//                      have; the tile's k-tiles (64 K each) take consecutive
+//                      stages of a second ring, whose bias and zero chunks,
+//                      the same for every tile, are written once.  After a
+//                      barrier of
 //                      the group its first thread issues the tile's MMAs
 //                      (128 x BN x 16 per K slice, weights resident in shared
 //                      memory) into TMEM accumulator j % 4;
@@ -222,9 +224,9 @@ k_conv_frame(const __grid_constant__ CUtensorMap tf256, const __grid_constant__ 
   } else if (warp >= kXfWarp0) {
     // im2col group x takes tiles j = x, x + 3, ...: one thread per (tile row
     // r, input row ky) writes the ks chunks of taps (ky, 0 ... ks - 1) of row
-    // r, all loads first (consecutive threads take consecutive rows:
-    // stride-apart words on the loads, the 16-byte stores spread over the
-    // swizzle); then the group's first thread issues the tile's MMAs
+    // r (consecutive threads take consecutive rows: stride-apart words on the
+    // loads, the 16-byte stores spread over the swizzle); then the group's
+    // first thread issues the tile's MMAs
     const int x = (warp - kXfWarp0) / kXfGroupWarps;
     const int xt = threadIdx.x - (kXfWarp0 + x * kXfGroupWarps) * 32;  // 0 ... 191
     constexpr uint32_t idesc = idesc_bf16(kBM, BN);
@@ -248,34 +250,48 @@ k_conv_frame(const __grid_constant__ CUtensorMap tf256, const __grid_constant__ 
         const uint8_t* raw = smem + FrameSmem::kRaw + rs * kRawBytes;
         const float* rf = reinterpret_cast<const float*>(raw);
         const float* rt = reinterpret_cast<const float*>(raw + kRawTail);
-        for (int q = xt; q < g.ks * kBM; q += kXfGroupWarps * 32) {
-          const int ky = q >> 7, r = q & (kBM - 1);
+        // the 16-byte chunk of window pixel d of input row ky: R, G, B, mask
+        // as BF16, four zeros
+        auto chunk = [&](int ky, int d) {
+          const int f = fa + d, h = fm + d;
           const float* fr = rf + ky * 256;
           const float* ft = rt + ky * 8;
-          const uint8_t* mr = raw + kRawMask + ky * 256;
-          const uint8_t* mt = raw + kRawMaskTail + ky * 16;
-          float c3[kRawRows][3];
-          uint8_t mb[kRawRows];
+          float c3[3];
 #pragma unroll
-          for (int kx = 0; kx < kRawRows; kx++) {
-            const int d = r * g.stride + kx, f = fa + d, h = fm + d;
-            const bool on = kx < g.ks;
-#pragma unroll
-            for (int p = 0; p < 3; p++)
-              c3[kx][p] = !on ? 0.0f : f < 256 ? fr[p * 768 + f] : ft[p * 24 + f - 256];
-            mb[kx] = !on || !g.has_mask ? 0 : h < 256 ? mr[h] : mt[h - 256];
+          for (int p = 0; p < 3; p++) c3[p] = f < 256 ? fr[p * 768 + f] : ft[p * 24 + f - 256];
+          const uint8_t mb = !g.has_mask                ? 0
+                             : h < 256                   ? raw[kRawMask + ky * 256 + h]
+                                                         : raw[kRawMaskTail + ky * 16 + h - 256];
+          const __nv_bfloat162 rg = __floats2bfloat162_rn(c3[0], c3[1]);
+          const __nv_bfloat162 bm = __floats2bfloat162_rn(c3[2], mb ? 1.0f : 0.0f);
+          return make_uint2(*reinterpret_cast<const uint32_t*>(&rg),
+                            *reinterpret_cast<const uint32_t*>(&bm));
+        };
+        auto store = [&](int ky, int kx, int r, uint2 v) {
+          const int tap = ky * g.ks + kx, c = tap & 7;
+          uint8_t* A = smem + FrameSmem::kA + ((aj + (uint32_t)(tap >> 3)) % kAStages) * kStageA;
+          *reinterpret_cast<uint4*>(A + r * 128 + ((c ^ (r & 7)) << 4)) =
+              make_uint4(v.x, v.y, 0u, 0u);
+        };
+        if (g.stride == 2 && g.ks == 3) {
+          // 3 x 3, stride 2: the kx = 2 pixel of row r is the kx = 0 pixel of
+          // row r + 1, taken from the next lane (a warp's lanes hold
+          // consecutive rows of one ky); each pixel is converted once
+          for (int q = xt; q < 3 * kBM; q += kXfGroupWarps * 32) {
+            const int ky = q >> 7, r = q & (kBM - 1);
+            const uint2 v0 = chunk(ky, 2 * r), v1 = chunk(ky, 2 * r + 1);
+            uint2 v2;
+            v2.x = __shfl_down_sync(0xffffffffu, v0.x, 1);
+            v2.y = __shfl_down_sync(0xffffffffu, v0.y, 1);
+            if (lane == 31) v2 = chunk(ky, 2 * r + 2);
+            store(ky, 0, r, v0);
+            store(ky, 1, r, v1);
+            store(ky, 2, r, v2);
           }
-#pragma unroll
-          for (int kx = 0; kx < kRawRows; kx++) {
-            if (kx >= g.ks) break;
-            const __nv_bfloat162 rg = __floats2bfloat162_rn(c3[kx][0], c3[kx][1]);
-            const __nv_bfloat162 bm = __floats2bfloat162_rn(c3[kx][2], mb[kx] ? 1.0f : 0.0f);
-            const int tap = ky * g.ks + kx, c = tap & 7;
-            uint8_t* A =
-                smem + FrameSmem::kA + ((aj + (uint32_t)(tap >> 3)) % kAStages) * kStageA;
-            *reinterpret_cast<uint4*>(A + r * 128 + ((c ^ (r & 7)) << 4)) =
-                make_uint4(*reinterpret_cast<const uint32_t*>(&rg),
-                           *reinterpret_cast<const uint32_t*>(&bm), 0u, 0u);
+        } else {
+          for (int q = xt; q < g.ks * kBM; q += kXfGroupWarps * 32) {
+            const int ky = q >> 7, r = q & (kBM - 1);
+            for (int kx = 0; kx < g.ks; kx++) store(ky, kx, r, chunk(ky, r * g.stride + kx));
           }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
