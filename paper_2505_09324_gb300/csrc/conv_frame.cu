@@ -19,10 +19,9 @@
 //                      have; the tile's k-tiles (64 K each) take consecutive
 //                      stages of a second ring, whose bias and zero chunks,
 //                      the same for every tile, are written once.  After a
-//                      barrier of
-//                      the group its first thread issues the tile's MMAs
-//                      (128 x BN x 16 per K slice, weights resident in shared
-//                      memory) into TMEM accumulator j % 4;
+//                      barrier of the group its first thread issues the
+//                      tile's MMAs (128 x BN x 16 per K slice, weights
+//                      resident in shared memory) into TMEM accumulator j % 4;
 //   warps 2-9          two groups of four warps, group j % 2, run the
 //                      epilogue (tcgen05.ld, ReLU, BF16 stores).
 // Three tiles are built and two drained at a time: a single warp per role
