@@ -23,11 +23,13 @@
 // kernel of csrc/gemm_tc.cu.
 //
 // Roles: warp 0 (one lane) issues the TMA loads into an ST-deep ring of
-// k-tile stages; warp 1 (one lane) issues the MMAs into one of NACC TMEM
-// accumulators; warps 2-5 read a finished accumulator (tcgen05.ld), apply
+// k-tile stages; warp 1 (one lane) issues the MMAs into TMEM accumulators
+// (two or four); warps 2-5 read a finished accumulator (tcgen05.ld), apply
 // ReLU, convert and store while the next tile accumulates.  The weights stay
-// in shared memory when they fit (the narrow early layers), else each stage
-// also brings the k-tile's weight box.  Every mbarrier wait is bounded in
+// in shared memory when they fit (the narrow early layers); else each stage
+// also brings the k-tile's weight box, and serves two of the CTA's tiles
+// with it (their A boxes side by side, one accumulator each), which halves
+// the weight traffic out of L2.  Every mbarrier wait is bounded in
 // time; a timeout records GS2D_ERR_TIMEOUT in the caller's status word.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -57,6 +59,7 @@ struct TapArgs {
   int segs, tiles, nk;
   int cw, cpt, blocks_real, kbias;  // channels per block, blocks per tap, tap blocks, bias k
   int stages, resident_b;
+  int per;                          // output tiles per weight load: 2 when streamed
   int stage_bytes;                  // A (+ the weights' box if streamed)
   int b_off;                        // the weights' box within a stage (streamed)
   int ring_off, bres_off;           // offsets of the stage ring and the resident weights
@@ -69,7 +72,7 @@ struct TapArgs {
 
 template <int BN>
 struct TapShape {
-  static constexpr int kAcc = BN <= 64 ? 4 : 2;
+  static constexpr int kAcc = BN <= 128 ? 4 : 2;
   static constexpr int kAccStride = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
   static constexpr int kCols = kAcc * kAccStride;
   static constexpr int kTmemCols =
@@ -148,10 +151,17 @@ k_conv_tap(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUten
       const int bpk = kBK / g.cw;  // k-blocks per k-tile
       const int block_bytes = kBM * g.cw * 2;
       uint32_t it = 0;
-      for (int t = blockIdx.x; t < g.tiles && !failed(&s_fail); t += gridDim.x) {
-        const int row = t / g.segs, seg = t - row * g.segs;
-        const int b = row / g.Ho, oy = row - b * g.Ho;
-        const int x0 = seg * kBM * g.stride - g.pad, y0 = oy * g.stride - g.pad;
+      // a unit: this CTA's next g.per tiles, which share each weight box
+      for (int t0 = blockIdx.x; t0 < g.tiles && !failed(&s_fail); t0 += g.per * gridDim.x) {
+        const int nt = g.per == 2 && t0 + (int)gridDim.x < g.tiles ? 2 : 1;
+        int ub[2], ux0[2], uy0[2];
+        for (int k = 0; k < nt; k++) {
+          const int t = t0 + k * (int)gridDim.x;
+          const int row = t / g.segs, seg = t - row * g.segs;
+          ub[k] = row / g.Ho;
+          ux0[k] = seg * kBM * g.stride - g.pad;
+          uy0[k] = (row - ub[k] * g.Ho) * g.stride - g.pad;
+        }
         for (int i = 0; i < nk; i++, it++) {
           const int s = (int)(it % (uint32_t)ST);
           const uint32_t ph = (it / (uint32_t)ST) & 1u;
@@ -162,17 +172,20 @@ k_conv_tap(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUten
           uint8_t* st = ring + s * g.stage_bytes;
           const int q0 = i * bpk;
           const int nl = max(0, min(bpk, g.blocks_real - q0));
-          const uint32_t bytes =
-              (uint32_t)(nl * block_bytes) + (g.resident_b ? 0u : (uint32_t)Sh::kBBytes);
+          const uint32_t bytes = (uint32_t)(nt * nl * block_bytes) +
+                                 (g.resident_b ? 0u : (uint32_t)Sh::kBBytes);
           if (bytes == 0) {
             mbar_arrive(&full[s]);
             continue;
           }
           mbar_expect_tx(&full[s], bytes);
-          for (int j = 0; j < nl; j++) {
-            const int q = q0 + j, tap = q / g.cpt;
-            const int ch = (q - tap * g.cpt) * g.cw, ky = tap / g.ks, kx = tap - ky * g.ks;
-            tma_load_4d(st + j * block_bytes, &ta, &full[s], ch, x0 + kx, y0 + ky, b);
+          for (int k = 0; k < nt; k++) {
+            for (int j = 0; j < nl; j++) {
+              const int q = q0 + j, tap = q / g.cpt;
+              const int ch = (q - tap * g.cpt) * g.cw, ky = tap / g.ks, kx = tap - ky * g.ks;
+              tma_load_4d(st + k * kABytes + j * block_bytes, &ta, &full[s], ch, ux0[k] + kx,
+                          uy0[k] + ky, ub[k]);
+            }
           }
           if (!g.resident_b) tma_load_2d(st + g.b_off, &tb, &full[s], i * kBK, 0);
         }
@@ -184,16 +197,22 @@ k_conv_tap(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUten
       constexpr uint32_t idesc = idesc_bf16(kBM, BN);
       if (g.resident_b && !mbar_wait(&bres_full, 0, g.wait_ns)) s_fail = 1;
       const uint32_t cst_s = smem_u32(cst);
-      uint32_t it = 0, at = 0;
-      for (int t = blockIdx.x; t < g.tiles && !failed(&s_fail); t += gridDim.x, at++) {
-        const int a = (int)(at % (uint32_t)Sh::kAcc);
-        const uint32_t aph = (at / (uint32_t)Sh::kAcc) & 1u;
-        if (!mbar_wait(&acc_empty[a], aph ^ 1u, g.wait_ns)) {
+      uint32_t it = 0, at = 0;  // k-tiles and accumulators used so far
+      for (int t0 = blockIdx.x; t0 < g.tiles && !failed(&s_fail); t0 += g.per * gridDim.x) {
+        const int nt = g.per == 2 && t0 + (int)gridDim.x < g.tiles ? 2 : 1;
+        uint32_t d[2];
+        bool ok = true;
+        for (int k = 0; k < nt && ok; k++) {
+          const uint32_t ak = at + (uint32_t)k;
+          const int a = (int)(ak % (uint32_t)Sh::kAcc);
+          ok = mbar_wait(&acc_empty[a], ((ak / (uint32_t)Sh::kAcc) & 1u) ^ 1u, g.wait_ns);
+          d[k] = tmem + (uint32_t)(a * Sh::kAccStride);
+        }
+        if (!ok) {
           s_fail = 1;
           break;
         }
         tc_fence_after();
-        const uint32_t d = tmem + (uint32_t)(a * Sh::kAccStride);
         for (int i = 0; i < nk; i++, it++) {
           const int s = (int)(it % (uint32_t)ST);
           const uint32_t ph = (it / (uint32_t)ST) & 1u;
@@ -206,23 +225,27 @@ k_conv_tap(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUten
           const uint32_t b_s =
               g.resident_b ? smem_u32(smem + g.bres_off + i * Sh::kBBytes) : a_s + g.b_off;
           const uint64_t bd = sw128_desc(b_s);
+          for (int k = 0; k < nt; k++) {
 #pragma unroll
-          for (int kk = 0; kk < kBK / 16; kk++) {
-            const int k = i * kBK + kk * 16;
-            uint64_t ad;
-            if (k < g.kbias) {
-              ad = tap_desc(a_s, kk, g.cw);
-            } else if (k == g.kbias) {
-              ad = kmajor_desc(cst_s, 2048u, 128u, 0u);
-            } else {
-              ad = kmajor_desc(cst_s + 2048u, 2048u, 128u, 0u);
+            for (int kk = 0; kk < kBK / 16; kk++) {
+              const int kq = i * kBK + kk * 16;
+              uint64_t ad;
+              if (kq < g.kbias) {
+                ad = tap_desc(a_s + (uint32_t)(k * kABytes), kk, g.cw);
+              } else if (kq == g.kbias) {
+                ad = kmajor_desc(cst_s, 2048u, 128u, 0u);
+              } else {
+                ad = kmajor_desc(cst_s + 2048u, 2048u, 128u, 0u);
+              }
+              mma_bf16(d[k], ad, bd + 2 * kk, idesc, (i > 0 || kk > 0) ? 1u : 0u);
             }
-            mma_bf16(d, ad, bd + 2 * kk, idesc, (i > 0 || kk > 0) ? 1u : 0u);
           }
           mma_commit(&empty[s]);
         }
         if (failed(&s_fail)) break;
-        mma_commit(&acc_full[a]);
+        for (int k = 0; k < nt; k++)
+          mma_commit(&acc_full[(at + (uint32_t)k) % (uint32_t)Sh::kAcc]);
+        at += (uint32_t)nt;
       }
     }
   } else {
@@ -234,26 +257,32 @@ k_conv_tap(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUten
                                                  : (const void*)g.out_f32) &
           15) == 0);
     uint32_t at = 0;
-    for (int t = blockIdx.x; t < g.tiles; t += gridDim.x, at++) {
-      const int a = (int)(at % (uint32_t)Sh::kAcc);
-      const uint32_t aph = (at / (uint32_t)Sh::kAcc) & 1u;
-      // tcgen05.ld is warp-collective: the warp goes on only if every lane saw
-      // the accumulator complete
-      if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[a], aph, g.wait_ns))) {
-        s_fail = 1;
-        break;
+    bool ok = true;
+    for (int t0 = blockIdx.x; t0 < g.tiles && ok; t0 += g.per * gridDim.x) {
+      const int nt = g.per == 2 && t0 + (int)gridDim.x < g.tiles ? 2 : 1;
+      for (int k = 0; k < nt; k++, at++) {
+        const int t = t0 + k * (int)gridDim.x;
+        const int a = (int)(at % (uint32_t)Sh::kAcc);
+        const uint32_t aph = (at / (uint32_t)Sh::kAcc) & 1u;
+        // tcgen05.ld is warp-collective: the warp goes on only if every lane
+        // saw the accumulator complete
+        if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[a], aph, g.wait_ns))) {
+          s_fail = 1;
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const int row = t / g.segs, seg = t - row * g.segs;
+        const int ox = seg * kBM + r;
+        const bool valid = ox < g.Wo;
+        const size_t o = ((size_t)row * g.Wo + ox) * g.ldc;
+        const uint32_t taddr =
+            tmem + (uint32_t)(a * Sh::kAccStride) + ((uint32_t)(quarter * 32) << 16);
+        store_acc_row<BN>(taddr, valid, o, g.N, g.relu, vec_ok, g.out_f32, g.out_bf16);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[a]);
       }
-      tc_fence_after();
-      const int row = t / g.segs, seg = t - row * g.segs;
-      const int ox = seg * kBM + r;
-      const bool valid = ox < g.Wo;
-      const size_t o = ((size_t)row * g.Wo + ox) * g.ldc;
-      const uint32_t taddr =
-          tmem + (uint32_t)(a * Sh::kAccStride) + ((uint32_t)(quarter * 32) << 16);
-      store_acc_row<BN>(taddr, valid, o, g.N, g.relu, vec_ok, g.out_f32, g.out_bf16);
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty[a]);
     }
   }
   __syncwarp();
@@ -302,7 +331,8 @@ int sm_count() {
 int tap_plan(int bn, int nk, TapArgs* g) {
   const int kb = bn * kBK * 2;
   g->resident_b = nk * kb <= 64 * 1024 ? 1 : 0;
-  g->b_off = kABytes;
+  g->per = g->resident_b ? 1 : 2;  // streamed weights: each box serves two tiles
+  g->b_off = g->per * kABytes;
   g->stage_bytes = g->b_off + (g->resident_b ? 0 : kb);
   const int bres = g->resident_b ? nk * kb : 0;
   const int fixed = kCstRegion + bres + 1024;  // + alignment slack

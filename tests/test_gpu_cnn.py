@@ -273,6 +273,10 @@ def test_chamfer_loss_and_gradient(nat):
     (1, 30, 260, 16, 48, 3, 2, 1, "bf16"),    # 32-byte swizzle, N below the tile
     (2, 24, 200, 32, 64, 3, 2, 1, "bf16"),    # 64-byte swizzle, weights resident
     (1, 17, 150, 128, 256, 3, 2, 1, "bf16"),  # two chunks per tap, N = 256
+    # more tiles than CTAs with streamed weights: two tiles per weight box
+    # in some CTAs, one in the others
+    (2, 160, 256, 64, 128, 3, 2, 1, "bf16"),
+    (2, 200, 130, 128, 256, 3, 2, 1, "bf16"),
     (1, 9, 70, 64, 90, 1, 1, 0, "f32"),       # stride 1, a k-tile of bias and zeros only
     (1, 8, 140, 8, 32, 3, 1, 1, "bf16")])     # stride 1, C = 8
 def test_implicit_conv_equals_im2col_gemm(nat, B, H, W, ci, co, ks, st, pad, out):
