@@ -59,7 +59,7 @@ struct TapArgs {
   int segs, tiles, nk;
   int cw, cpt, blocks_real, kbias;  // channels per block, blocks per tap, tap blocks, bias k
   int stages, resident_b;
-  int per;                          // output tiles per weight load: 2 when streamed
+  int per;                          // output tiles per weight load (2 when streamed)
   int stage_bytes;                  // A (+ the weights' box if streamed)
   int b_off;                        // the weights' box within a stage (streamed)
   int ring_off, bres_off;           // offsets of the stage ring and the resident weights
@@ -94,7 +94,7 @@ __device__ __forceinline__ uint64_t tap_desc(uint32_t a_s, int kk, int cw) {
   }
 }
 
-template <int BN>
+template <int BN, int PER>
 __global__ void __launch_bounds__(kTapThreads, 1)
 k_conv_tap(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
            TapArgs g) {
@@ -151,9 +151,9 @@ k_conv_tap(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUten
       const int bpk = kBK / g.cw;  // k-blocks per k-tile
       const int block_bytes = kBM * g.cw * 2;
       uint32_t it = 0;
-      // a unit: this CTA's next g.per tiles, which share each weight box
-      for (int t0 = blockIdx.x; t0 < g.tiles && !failed(&s_fail); t0 += g.per * gridDim.x) {
-        const int nt = g.per == 2 && t0 + (int)gridDim.x < g.tiles ? 2 : 1;
+      // a unit: this CTA's next PER tiles, which share each weight box
+      for (int t0 = blockIdx.x; t0 < g.tiles && !failed(&s_fail); t0 += PER * gridDim.x) {
+        const int nt = PER == 2 && t0 + (int)gridDim.x < g.tiles ? 2 : 1;
         int ub[2], ux0[2], uy0[2];
         for (int k = 0; k < nt; k++) {
           const int t = t0 + k * (int)gridDim.x;
@@ -198,8 +198,8 @@ k_conv_tap(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUten
       if (g.resident_b && !mbar_wait(&bres_full, 0, g.wait_ns)) s_fail = 1;
       const uint32_t cst_s = smem_u32(cst);
       uint32_t it = 0, at = 0;  // k-tiles and accumulators used so far
-      for (int t0 = blockIdx.x; t0 < g.tiles && !failed(&s_fail); t0 += g.per * gridDim.x) {
-        const int nt = g.per == 2 && t0 + (int)gridDim.x < g.tiles ? 2 : 1;
+      for (int t0 = blockIdx.x; t0 < g.tiles && !failed(&s_fail); t0 += PER * gridDim.x) {
+        const int nt = PER == 2 && t0 + (int)gridDim.x < g.tiles ? 2 : 1;
         uint32_t d[2];
         bool ok = true;
         for (int k = 0; k < nt && ok; k++) {
@@ -258,8 +258,8 @@ k_conv_tap(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUten
           15) == 0);
     uint32_t at = 0;
     bool ok = true;
-    for (int t0 = blockIdx.x; t0 < g.tiles && ok; t0 += g.per * gridDim.x) {
-      const int nt = g.per == 2 && t0 + (int)gridDim.x < g.tiles ? 2 : 1;
+    for (int t0 = blockIdx.x; t0 < g.tiles && ok; t0 += PER * gridDim.x) {
+      const int nt = PER == 2 && t0 + (int)gridDim.x < g.tiles ? 2 : 1;
       for (int k = 0; k < nt; k++, at++) {
         const int t = t0 + k * (int)gridDim.x;
         const int a = (int)(at % (uint32_t)Sh::kAcc);
@@ -344,15 +344,22 @@ int tap_plan(int bn, int nk, TapArgs* g) {
   return g->bres_off + bres + 1024;
 }
 
-template <int BN>
-cudaError_t launch_tap(const CUtensorMap& ta, const CUtensorMap& tb, const TapArgs& g, int smem,
-                       cudaStream_t s) {
-  const cudaError_t attr = opt_in_smem((const void*)k_conv_tap<BN>, smem);
+template <int BN, int PER>
+cudaError_t launch_tap_per(const CUtensorMap& ta, const CUtensorMap& tb, const TapArgs& g,
+                           int smem, cudaStream_t s) {
+  const cudaError_t attr = opt_in_smem((const void*)k_conv_tap<BN, PER>, smem);
   if (attr != cudaSuccess) return attr;
   const int sms = sm_count();
   const int grid = std::max(1, std::min(g.tiles, sms > 0 ? sms : 1));
-  k_conv_tap<BN><<<grid, kTapThreads, smem, s>>>(ta, tb, g);
+  k_conv_tap<BN, PER><<<grid, kTapThreads, smem, s>>>(ta, tb, g);
   return cudaGetLastError();
+}
+
+template <int BN>
+cudaError_t launch_tap(const CUtensorMap& ta, const CUtensorMap& tb, const TapArgs& g, int smem,
+                       cudaStream_t s) {
+  return g.per == 2 ? launch_tap_per<BN, 2>(ta, tb, g, smem, s)
+                    : launch_tap_per<BN, 1>(ta, tb, g, smem, s);
 }
 
 }  // namespace
