@@ -374,6 +374,51 @@ def test_conv_frame_bad_arguments(nat):
                  32, 1, 0, o.data_ptr(), 32, 0, 0)
 
 
+@pytest.mark.parametrize("H,W,ci,co", [(540, 960, 32, 64), (270, 480, 64, 128),
+                                        (135, 240, 128, 256)])
+def test_tap_conv_network_layers_full_size(nat, H, W, ci, co):
+    """Layers 2-4 of the learned initialiser at 1080p (two frames), in the
+    launch configuration the forward uses: the TMA-tap kernel equals
+    im2col + GEMM bit for bit everywhere, and 256 sampled outputs equal the
+    oracle's convolution of their receptive fields within the GEMM bar."""
+    B, ks, st, pad = 2, 3, 2, 1
+    g = np.random.Generator(np.random.PCG64(5 * co + H))
+    ldk = -(-(ks * ks * ci + 1) // 8) * 8
+    x = cnn.bf16_round(g.normal(size=(B, H, W, ci)).astype(np.float32))
+    w = np.zeros((co, ldk), np.float32)
+    w[:, :ks * ks * ci + 1] = g.normal(size=(co, ks * ks * ci + 1)) / np.sqrt(ks * ks * ci)
+    w = cnn.bf16_round(w)
+    Ho, Wo = cnn.out_size(H, ks, st, pad), cnn.out_size(W, ks, st, pad)
+    P = B * Ho * Wo
+    d_x, d_w = bf16_dev(x), bf16_dev(w)
+    z = torch.empty((P, co), dtype=torch.bfloat16, device="cuda")
+    z_ref = torch.empty_like(z)
+    col = torch.empty((P, ldk), dtype=torch.bfloat16, device="cuda")
+    st_ = torch.zeros(1, dtype=torch.int32, device="cuda")
+    nat.call("gs2d_conv_bf16", d_x.data_ptr(), B, H, W, ci, ks, st, pad, d_w.data_ptr(), ldk, co,
+             0, 0, z.data_ptr(), co, st_.data_ptr(), 0)
+    nat.call("gs2d_im2col", d_x.data_ptr(), B, H, W, ci, ks, st, pad, col.data_ptr(), ldk, 0)
+    nat.gemm_bf16(col.data_ptr(), ldk, d_w.data_ptr(), ldk, P, co, ldk, 0, False, 0,
+                  z_ref.data_ptr(), co, 1, 0, st_.data_ptr(), 0)
+    torch.cuda.synchronize()
+    assert int(st_.item()) == 0
+    assert torch.equal(z, z_ref)
+    got = to_np_bf16(z).reshape(B, Ho, Wo, co)
+    for _ in range(256):
+        b, oy, ox = int(g.integers(B)), int(g.integers(Ho)), int(g.integers(Wo))
+        patch = np.zeros((1, ks, ks, ci), np.float32)   # the receptive field, zero outside
+        for ky in range(ks):
+            for kx in range(ks):
+                iy, ix = oy * st - pad + ky, ox * st - pad + kx
+                if 0 <= iy < H and 0 <= ix < W:
+                    patch[0, ky, kx] = x[b, iy, ix]
+        ref = cnn.conv(patch, w[:, :ks * ks * ci + 1], ks, 1, 0)[0, 0, 0]
+        scale = cnn.gemm_abs(cnn.im2col(patch, ks, 1, 0, ldk), w)[0]
+        # one BF16 rounding of the FP32 sum on top of the GEMM bar
+        tol = REL * scale + np.abs(ref) * 2.0 ** -8 + 1e-30
+        assert np.all(np.abs(got[b, oy, ox] - ref) <= tol), (b, oy, ox)
+
+
 def test_implicit_conv_bad_arguments(nat):
     d = torch.zeros(64, dtype=torch.bfloat16, device="cuda")
     with pytest.raises(nat.Gs2dError):   # C not a multiple of 8
