@@ -107,7 +107,7 @@ k_conv_tap(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUten
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ST = g.stages, nk = g.nk;
+  const int ST = g.stages;
   uint8_t* cst = smem;  // constant block at the start
   uint8_t* ring = smem + g.ring_off;
 
@@ -142,18 +142,26 @@ k_conv_tap(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUten
 
   if (warp == 0) {
     if (lane == 0 && !g.withhold) {  // a failure-detection launch issues no load
-      // producer
-      if (g.resident_b) {
+      // producer: the launch's fields held in registers, the stage and the
+      // tap position advanced incrementally (a lone thread: every
+      // instruction of its loop is on the pipeline's critical path)
+      const int nk = g.nk, tiles = g.tiles, cw = g.cw, cpt = g.cpt, ks = g.ks;
+      const int blocks_real = g.blocks_real, stage_bytes = g.stage_bytes;
+      const bool resident = g.resident_b != 0;
+      const unsigned long long wait_ns = g.wait_ns;
+      if (resident) {
         mbar_expect_tx(&bres_full, (uint32_t)(nk * Sh::kBBytes));
         for (int i = 0; i < nk; i++)
           tma_load_2d(smem + g.bres_off + i * Sh::kBBytes, &tb, &bres_full, i * kBK, 0);
       }
-      const int bpk = kBK / g.cw;  // k-blocks per k-tile
-      const int block_bytes = kBM * g.cw * 2;
-      uint32_t it = 0;
+      const int bpk = kBK / cw;  // k-blocks per k-tile
+      const int block_bytes = kBM * cw * 2;
+      int s = 0;
+      uint32_t ph = 0;
+      bool ok = true;
       // a unit: this CTA's next PER tiles, which share each weight box
-      for (int t0 = blockIdx.x; t0 < g.tiles && !failed(&s_fail); t0 += PER * gridDim.x) {
-        const int nt = PER == 2 && t0 + (int)gridDim.x < g.tiles ? 2 : 1;
+      for (int t0 = blockIdx.x; t0 < tiles && ok && !failed(&s_fail); t0 += PER * gridDim.x) {
+        const int nt = PER == 2 && t0 + (int)gridDim.x < tiles ? 2 : 1;
         int ub[2], ux0[2], uy0[2];
         for (int k = 0; k < nt; k++) {
           const int t = t0 + k * (int)gridDim.x;
@@ -162,91 +170,125 @@ k_conv_tap(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUten
           ux0[k] = seg * kBM * g.stride - g.pad;
           uy0[k] = (row - ub[k] * g.Ho) * g.stride - g.pad;
         }
-        for (int i = 0; i < nk; i++, it++) {
-          const int s = (int)(it % (uint32_t)ST);
-          const uint32_t ph = (it / (uint32_t)ST) & 1u;
-          if (!mbar_wait(&empty[s], ph ^ 1u, g.wait_ns)) {
-            s_fail = 1;
+        int qc = 0, qx = 0, qy = 0;  // chunk and tap (ky, kx) of the k-tile's first block
+        for (int i = 0; i < nk; i++) {
+          if (!mbar_wait(&empty[s], ph ^ 1u, wait_ns)) {
+            ok = false;
             break;
           }
-          uint8_t* st = ring + s * g.stage_bytes;
-          const int q0 = i * bpk;
-          const int nl = max(0, min(bpk, g.blocks_real - q0));
-          const uint32_t bytes = (uint32_t)(nt * nl * block_bytes) +
-                                 (g.resident_b ? 0u : (uint32_t)Sh::kBBytes);
+          uint8_t* st = ring + s * stage_bytes;
+          const int nl = max(0, min(bpk, blocks_real - i * bpk));
+          const uint32_t bytes =
+              (uint32_t)(nt * nl * block_bytes) + (resident ? 0u : (uint32_t)Sh::kBBytes);
           if (bytes == 0) {
             mbar_arrive(&full[s]);
-            continue;
+          } else {
+            mbar_expect_tx(&full[s], bytes);
+            for (int k = 0; k < nt; k++) {
+              int c = qc, x = qx, y = qy;
+              for (int j = 0; j < nl; j++) {
+                tma_load_4d(st + k * kABytes + j * block_bytes, &ta, &full[s], c * cw,
+                            ux0[k] + x, uy0[k] + y, ub[k]);
+                if (++c == cpt) {
+                  c = 0;
+                  if (++x == ks) {
+                    x = 0;
+                    ++y;
+                  }
+                }
+              }
+            }
+            if (!resident) tma_load_2d(st + g.b_off, &tb, &full[s], i * kBK, 0);
           }
-          mbar_expect_tx(&full[s], bytes);
-          for (int k = 0; k < nt; k++) {
-            for (int j = 0; j < nl; j++) {
-              const int q = q0 + j, tap = q / g.cpt;
-              const int ch = (q - tap * g.cpt) * g.cw, ky = tap / g.ks, kx = tap - ky * g.ks;
-              tma_load_4d(st + k * kABytes + j * block_bytes, &ta, &full[s], ch, ux0[k] + kx,
-                          uy0[k] + ky, ub[k]);
+          for (int j = 0; j < nl; j++) {
+            if (++qc == cpt) {
+              qc = 0;
+              if (++qx == ks) {
+                qx = 0;
+                ++qy;
+              }
             }
           }
-          if (!g.resident_b) tma_load_2d(st + g.b_off, &tb, &full[s], i * kBK, 0);
+          if (++s == ST) {
+            s = 0;
+            ph ^= 1u;
+          }
         }
       }
+      if (!ok) s_fail = 1;
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // MMA issuer
+      // MMA issuer: the descriptors of stage 0 built once, each K = 16 slice's
+      // as a fixed offset of them (the start address field counts 16 bytes)
       constexpr uint32_t idesc = idesc_bf16(kBM, BN);
-      if (g.resident_b && !mbar_wait(&bres_full, 0, g.wait_ns)) s_fail = 1;
-      const uint32_t cst_s = smem_u32(cst);
-      uint32_t it = 0, at = 0;  // k-tiles and accumulators used so far
-      for (int t0 = blockIdx.x; t0 < g.tiles && !failed(&s_fail); t0 += PER * gridDim.x) {
-        const int nt = PER == 2 && t0 + (int)gridDim.x < g.tiles ? 2 : 1;
+      const int nk = g.nk, tiles = g.tiles, kbias = g.kbias, cw = g.cw;
+      const bool resident = g.resident_b != 0;
+      const unsigned long long wait_ns = g.wait_ns;
+      if (resident && !mbar_wait(&bres_full, 0, wait_ns)) s_fail = 1;
+      const uint32_t cst_s = smem_u32(cst), ring_s = smem_u32(ring);
+      uint64_t adesc[kBK / 16];
+#pragma unroll
+      for (int kk = 0; kk < kBK / 16; kk++) adesc[kk] = tap_desc(ring_s, kk, cw);
+      const uint64_t bdesc0 =
+          sw128_desc(resident ? smem_u32(smem + g.bres_off) : ring_s + (uint32_t)g.b_off);
+      const uint64_t bias_d = kmajor_desc(cst_s, 2048u, 128u, 0u);
+      const uint64_t zero_d = kmajor_desc(cst_s + 2048u, 2048u, 128u, 0u);
+      const uint64_t stage_d = (uint64_t)(g.stage_bytes >> 4);
+      constexpr uint64_t tile_d = kABytes >> 4, bk_d = Sh::kBBytes >> 4;
+      const int kfull = kbias / kBK;  // k-tiles of tap slices only
+      int s = 0;
+      uint32_t ph = 0, at = 0;  // stage, its phase; accumulators used so far
+      bool ok = true;
+      for (int t0 = blockIdx.x; t0 < tiles && ok && !failed(&s_fail); t0 += PER * gridDim.x) {
+        const int nt = PER == 2 && t0 + (int)gridDim.x < tiles ? 2 : 1;
         uint32_t d[2];
-        bool ok = true;
         for (int k = 0; k < nt && ok; k++) {
           const uint32_t ak = at + (uint32_t)k;
           const int a = (int)(ak % (uint32_t)Sh::kAcc);
-          ok = mbar_wait(&acc_empty[a], ((ak / (uint32_t)Sh::kAcc) & 1u) ^ 1u, g.wait_ns);
+          ok = mbar_wait(&acc_empty[a], ((ak / (uint32_t)Sh::kAcc) & 1u) ^ 1u, wait_ns);
           d[k] = tmem + (uint32_t)(a * Sh::kAccStride);
         }
-        if (!ok) {
-          s_fail = 1;
-          break;
-        }
+        if (!ok) break;
         tc_fence_after();
-        for (int i = 0; i < nk; i++, it++) {
-          const int s = (int)(it % (uint32_t)ST);
-          const uint32_t ph = (it / (uint32_t)ST) & 1u;
-          if (!mbar_wait(&full[s], ph, g.wait_ns)) {
-            s_fail = 1;
+        for (int i = 0; i < nk; i++) {
+          if (!mbar_wait(&full[s], ph, wait_ns)) {
+            ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t a_s = smem_u32(ring + s * g.stage_bytes);
-          const uint32_t b_s =
-              g.resident_b ? smem_u32(smem + g.bres_off + i * Sh::kBBytes) : a_s + g.b_off;
-          const uint64_t bd = sw128_desc(b_s);
-          for (int k = 0; k < nt; k++) {
+          const uint64_t so = (uint64_t)s * stage_d;
+          const uint64_t bd = bdesc0 + (resident ? (uint64_t)i * bk_d : so);
+          if (i < kfull) {
+            for (int k = 0; k < nt; k++) {
+              const uint64_t ko = so + (uint64_t)k * tile_d;
 #pragma unroll
-            for (int kk = 0; kk < kBK / 16; kk++) {
-              const int kq = i * kBK + kk * 16;
-              uint64_t ad;
-              if (kq < g.kbias) {
-                ad = tap_desc(a_s + (uint32_t)(k * kABytes), kk, g.cw);
-              } else if (kq == g.kbias) {
-                ad = kmajor_desc(cst_s, 2048u, 128u, 0u);
-              } else {
-                ad = kmajor_desc(cst_s + 2048u, 2048u, 128u, 0u);
+              for (int kk = 0; kk < kBK / 16; kk++)
+                mma_bf16(d[k], adesc[kk] + ko, bd + 2 * kk, idesc, (i | kk) ? 1u : 0u);
+            }
+          } else {  // the k-tile of the bias slice: taps, bias, zeros
+            for (int k = 0; k < nt; k++) {
+              const uint64_t ko = so + (uint64_t)k * tile_d;
+#pragma unroll
+              for (int kk = 0; kk < kBK / 16; kk++) {
+                const int kq = i * kBK + kk * 16;
+                const uint64_t ad = kq < kbias ? adesc[kk] + ko : kq == kbias ? bias_d : zero_d;
+                mma_bf16(d[k], ad, bd + 2 * kk, idesc, (i | kk) ? 1u : 0u);
               }
-              mma_bf16(d[k], ad, bd + 2 * kk, idesc, (i > 0 || kk > 0) ? 1u : 0u);
             }
           }
           mma_commit(&empty[s]);
+          if (++s == ST) {
+            s = 0;
+            ph ^= 1u;
+          }
         }
-        if (failed(&s_fail)) break;
+        if (!ok) break;
         for (int k = 0; k < nt; k++)
           mma_commit(&acc_full[(at + (uint32_t)k) % (uint32_t)Sh::kAcc]);
         at += (uint32_t)nt;
       }
+      if (!ok) s_fail = 1;
     }
   } else {
     // epilogue: warp w reads TMEM lanes 32 (w % 4) ... (its accumulator rows)

@@ -278,7 +278,13 @@ def test_chamfer_loss_and_gradient(nat):
     (2, 160, 256, 64, 128, 3, 2, 1, "bf16"),
     (2, 200, 130, 128, 256, 3, 2, 1, "bf16"),
     (1, 9, 70, 64, 90, 1, 1, 0, "f32"),       # stride 1, a k-tile of bias and zeros only
-    (1, 8, 140, 8, 32, 3, 1, 1, "bf16")])     # stride 1, C = 8
+    (1, 8, 140, 8, 32, 3, 1, 1, "bf16"),      # stride 1, C = 8
+    (1, 9, 600, 32, 64, 3, 2, 1, "bf16"),     # three row segments, the last ragged
+    (2, 11, 400, 64, 32, 3, 2, 1, "f32"),     # C = 64 with resident weights, odd height
+    (1, 21, 259, 32, 64, 3, 2, 1, "bf16"),    # odd width
+    (2, 19, 261, 64, 128, 3, 2, 1, "bf16"),   # odd width, weights streamed
+    (1, 12, 200, 16, 32, 5, 2, 4, "bf16"),    # 5 x 5, pad 4: taps start 4 pixels left of the image
+    (1, 20, 258, 32, 32, 3, 2, 0, "f32")])    # no padding
 def test_implicit_conv_equals_im2col_gemm(nat, B, H, W, ci, co, ks, st, pad, out):
     """gs2d_conv_bf16 gathers the im2col tiles itself: its output equals
     gs2d_im2col + gs2d_gemm_bf16 bit for bit, and the oracle's convolution
