@@ -616,18 +616,19 @@ uint64_t gs2d_gemm_partial_bytes(int32_t M, int32_t N, int32_t ldc, int32_t K, i
 gs2d_status gs2d_gemm_wait_check(const void* A, const void* B, float* out, int32_t* status,
                                  uint64_t wait_ns, void* stream);
 
-/* The same check for the two persistent convolution kernels.  kernel:
+/* The same check for the persistent convolution kernels.  kernel:
  * GS2D_CHECK_CONV_FRAME (gs2d_conv_frame_bf16's kernel; x: device float
  * frame [1][3][16][256], W: device bf16 [32][80], out: device bf16
- * [8 x 128][32]) or GS2D_CHECK_CONV_TAP (the TMA-tap kernel of
- * gs2d_conv_bf16; x: device bf16 NHWC [1][16][256][32], W: device bf16
- * [64][296], out: device bf16 [8 x 128][64]); all 16-byte aligned.  Every
+ * [8 x 128][32]), GS2D_CHECK_CONV_TAP (the TMA-tap kernel of gs2d_conv_bf16)
+ * or GS2D_CHECK_CONV_ROWS (its row-box kernel), both with x: device bf16
+ * NHWC [1][16][256][32], W: device bf16 [64][296], out: device bf16
+ * [8 x 128][64]; all 16-byte aligned.  Every
  * load is withheld and each wait limited to wait_ns (1 ms ... 1 s): every
  * role's first wait runs out with no copy or MMA in flight, the groups that
  * share a named barrier leave together, the kernel records GS2D_ERR_TIMEOUT
  * in *status, leaves out unwritten, frees its tensor memory and returns.
  * Asynchronous on stream. */
-enum { GS2D_CHECK_CONV_FRAME = 0, GS2D_CHECK_CONV_TAP = 1 };
+enum { GS2D_CHECK_CONV_FRAME = 0, GS2D_CHECK_CONV_TAP = 1, GS2D_CHECK_CONV_ROWS = 2 };
 gs2d_status gs2d_conv_wait_check(int32_t kernel, const void* x, const void* W, void* out,
                                  int32_t* status, uint64_t wait_ns, void* stream);
 

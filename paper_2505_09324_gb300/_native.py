@@ -531,6 +531,7 @@ PROBE_FFMA = 0
 PROBE_EX2 = 1
 CHECK_CONV_FRAME = 0
 CHECK_CONV_TAP = 1
+CHECK_CONV_ROWS = 2
 
 
 def probe_ops(blocks: int, iters: int) -> int:

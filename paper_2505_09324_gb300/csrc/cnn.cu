@@ -92,7 +92,8 @@ extern "C" gs2d_status gs2d_gemm_wait_check(const void* A, const void* B, float*
 extern "C" gs2d_status gs2d_conv_wait_check(int32_t kernel, const void* x, const void* W,
                                             void* out, int32_t* status, uint64_t wait_ns,
                                             void* stream) {
-  if ((kernel != GS2D_CHECK_CONV_FRAME && kernel != GS2D_CHECK_CONV_TAP) || !x || !W || !out ||
+  if ((kernel != GS2D_CHECK_CONV_FRAME && kernel != GS2D_CHECK_CONV_TAP &&
+       kernel != GS2D_CHECK_CONV_ROWS) || !x || !W || !out ||
       !status || ((uintptr_t)x & 15) || ((uintptr_t)W & 15) || ((uintptr_t)out & 15))
     return set_error(GS2D_ERR_INVALID_ARG, "gs2d_conv_wait_check: kernel, NULL or misaligned");
   if (wait_ns < 1000000ull || wait_ns > 1000000000ull)
@@ -139,7 +140,8 @@ extern "C" gs2d_status gs2d_conv_wait_check(int32_t kernel, const void* x, const
     pr.status = status;
     pr.wait_ns = wait_ns;
     pr.withhold_loads = 1;
-    e = tap_conv(pr, (cudaStream_t)stream);
+    e = kernel == GS2D_CHECK_CONV_TAP ? tap_conv(pr, (cudaStream_t)stream)
+                                      : rows_conv(pr, (cudaStream_t)stream);
   }
   if (e != cudaSuccess) {
     char msg[200];

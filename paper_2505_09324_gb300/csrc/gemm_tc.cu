@@ -512,7 +512,9 @@ cudaError_t tc_conv(const TcConvProblem& pr, cudaStream_t s) {
   if (pr.C % 8 || pr.ldk % 8 || pr.ldk < pr.ks * pr.ks * pr.C + 1 ||
       (reinterpret_cast<uintptr_t>(pr.x) & 15) || (reinterpret_cast<uintptr_t>(pr.W) & 15))
     return cudaErrorInvalidValue;
-  // wide output rows: the persistent kernel with TMA tap loads (same result)
+  // wide output rows: the persistent kernels with TMA row or tap loads
+  // (same result)
+  if (rows_conv_supported(pr)) return rows_conv(pr, s);
   if (tap_conv_supported(pr)) return tap_conv(pr, s);
   const int bn = tc_gemm_bn(pr.N);
   CUtensorMap tb;

@@ -80,6 +80,11 @@ cudaError_t tc_conv(const TcConvProblem& pr, cudaStream_t s);
 // multiple of 64, stride 1 or 2, N <= 256, output rows of 64 pixels or more.
 bool tap_conv_supported(const TcConvProblem& pr);
 cudaError_t tap_conv(const TcConvProblem& pr, cudaStream_t s);
+// The persistent row-box convolution (csrc/conv_rows.cu): 3 x 3, stride 2,
+// pad 1, an even input width, C of 32 or 64, N <= 256, output rows of 64
+// pixels or more, within its shared-memory plan.
+bool rows_conv_supported(const TcConvProblem& pr);
+cudaError_t rows_conv(const TcConvProblem& pr, cudaStream_t s);
 // W a multiple of 16, ks <= 3, the 128-pixel window within 257 input pixels,
 // N <= 128.
 bool frame_conv_supported(int W, int ks, int stride, int N);

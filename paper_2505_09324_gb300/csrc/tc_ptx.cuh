@@ -1,6 +1,7 @@
 // Inline-PTX building blocks of the tcgen05 kernels (csrc/gemm_tc.cu,
-// csrc/conv_tap.cu): mbarriers with time-bounded waits, TMA tensor loads,
-// shared-memory matrix descriptors, tcgen05.mma / commit / ld and the
+// csrc/conv_tap.cu, csrc/conv_rows.cu, csrc/conv_frame.cu): mbarriers with
+// time-bounded waits, TMA tensor loads, shared-memory matrix descriptors,
+// tcgen05.mma / commit / ld and the
 // tcgen05 thread-sync fences.
 #pragma once
 
@@ -88,6 +89,17 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// 5D tiled TMA load (coordinates innermost first) completing on a barrier.
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1, int c2, int c3, int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2),
+      "r"(c3), "r"(c4)
+      : "memory");
+}
+
 // Shared-memory matrix descriptor of a K-major operand, descriptor version 1:
 // start address, leading byte offset (between the 16-byte core-matrix
 // columns along K; used by the unswizzled layout only), stride byte offset
@@ -121,6 +133,20 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+// The same with each descriptor as its two 32-bit words: a K-major
+// descriptor's start address sits in the low word (14 bits, in 16-byte units,
+// no carry out of it below 256 KB of shared memory), so operand offsets are
+// 32-bit additions.
+__device__ __forceinline__ void mma_bf16_w(uint32_t d_tmem, uint32_t a_lo, uint32_t a_hi,
+                                           uint32_t b_lo, uint32_t b_hi, uint32_t idesc,
+                                           uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n .reg .b64 da, db;\n setp.ne.b32 p, %6, 0;\n"
+      " mov.b64 da, {%1, %2};\n mov.b64 db, {%3, %4};\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, p;\n}" ::"r"(d_tmem),
+      "r"(a_lo), "r"(a_hi), "r"(b_lo), "r"(b_hi), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {

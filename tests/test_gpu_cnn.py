@@ -281,6 +281,8 @@ def test_chamfer_loss_and_gradient(nat):
     (1, 8, 140, 8, 32, 3, 1, 1, "bf16"),      # stride 1, C = 8
     (1, 9, 600, 32, 64, 3, 2, 1, "bf16"),     # three row segments, the last ragged
     (2, 11, 400, 64, 32, 3, 2, 1, "f32"),     # C = 64 with resident weights, odd height
+    (1, 10, 300, 32, 160, 3, 2, 1, "bf16"),   # C = 32, weights streamed: k-tiles across input rows
+    (1, 12, 260, 128, 96, 3, 2, 1, "f32"),    # C = 128, N = 96
     (1, 21, 259, 32, 64, 3, 2, 1, "bf16"),    # odd width
     (2, 19, 261, 64, 128, 3, 2, 1, "bf16"),   # odd width, weights streamed
     (1, 12, 200, 16, 32, 5, 2, 4, "bf16"),    # 5 x 5, pad 4: taps start 4 pixels left of the image

@@ -64,7 +64,7 @@ def test_gemm_wait_runs_out_and_reports_timeout(nat):
 
 
 
-@pytest.mark.parametrize("kernel", ["frame", "tap"])
+@pytest.mark.parametrize("kernel", ["frame", "tap", "rows"])
 def test_conv_wait_runs_out_and_reports_timeout(nat, kernel):
     """The persistent convolutions with every load withheld: each role's
     first wait runs out, the groups that share a named barrier leave it
@@ -76,7 +76,7 @@ def test_conv_wait_runs_out_and_reports_timeout(nat, kernel):
         which, ldk, co = nat.CHECK_CONV_FRAME, 80, 32
         x = torch.rand(1, 3, 16, 256, generator=g).cuda()
     else:
-        which, ldk, co = nat.CHECK_CONV_TAP, 296, 64
+        which, ldk, co = nat.CHECK_CONV_TAP if kernel == "tap" else nat.CHECK_CONV_ROWS, 296, 64
         x = torch.randn(1, 16, 256, 32, generator=g).to(torch.bfloat16).cuda()
     w = (torch.randn(co, ldk, generator=g) * 0.1).to(torch.bfloat16).cuda()
     out = torch.full((8 * 128, co), 7.0, dtype=torch.bfloat16, device="cuda")
