@@ -59,6 +59,12 @@ constexpr int kRawMask = kRawTail + 512;             // 9728
 constexpr int kRawMaskTail = kRawMask + 3 * 256;     // 10496
 constexpr int kRawBytes = 11264;
 constexpr int kStageA = kBM * kBK * 2;  // 16 KB
+// 3 x 3 at stride 2 (the network's first layer): a tile's operand as six
+// arrays of 16-byte pixel records, the even and the odd window pixels of
+// each input row (129 records each), two buffers per group
+constexpr int kParArr = 129 * 16;
+constexpr int kParBuf = 6 * kParArr + 32;  // 12416
+constexpr int kCstBytes = 6144;            // bias rows (2 KB), then 4 KB of zeros
 
 struct FrameArgs {
   int B, H, W, Ho, Wo, ks, stride, pad;
@@ -97,15 +103,17 @@ __device__ __forceinline__ bool group_sync_or(int grp, bool v) {
   return r != 0;
 }
 
-// Shared-memory offsets (from the 1024-aligned base): A ring, raw ring,
-// resident weights.
+// Shared-memory offsets (from the 1024-aligned base): A ring (or the
+// groups' record buffers and the constant block), raw ring, resident weights.
+template <bool PAR>
 struct FrameSmem {
   static constexpr int kA = 0;
-  static constexpr int kRaw = kAStages * kStageA;
+  static constexpr int kCst = PAR ? (kXfGroups * 2 * kParBuf + 1023) / 1024 * 1024 : 0;
+  static constexpr int kRaw = PAR ? kCst + 8192 : kAStages * kStageA;
   static constexpr int kB = kRaw + kRawStages * kRawBytes;
 };
 
-template <int BN>
+template <int BN, bool PAR>
 __global__ void __launch_bounds__(kFrThreads, 1)
 k_conv_frame(const __grid_constant__ CUtensorMap tf256, const __grid_constant__ CUtensorMap tf8,
              const __grid_constant__ CUtensorMap tm256, const __grid_constant__ CUtensorMap tm16,
@@ -114,6 +122,7 @@ k_conv_frame(const __grid_constant__ CUtensorMap tf256, const __grid_constant__ 
   constexpr int kCols = kAcc * kAccStride;
   constexpr int kTmemCols = kCols <= 128 ? 128 : kCols <= 256 ? 256 : 512;
   constexpr int kBBytes = BN * kBK * 2;
+  using Sm = FrameSmem<PAR>;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t raw_full[kRawStages], raw_empty[kRawStages];
   __shared__ __align__(8) uint64_t a_empty[kAStages];
@@ -140,15 +149,23 @@ k_conv_frame(const __grid_constant__ CUtensorMap tf256, const __grid_constant__ 
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  if constexpr (PAR) {
+    // constant block: 128 rows of 16 bytes with bf16 1.0 first (the bias
+    // column), then 4 KB of zeros
+    for (int i = threadIdx.x; i < kCstBytes / 16; i += blockDim.x)
+      reinterpret_cast<uint4*>(smem + Sm::kCst)[i] =
+          make_uint4(i < kBM ? 0x3F80u : 0u, 0u, 0u, 0u);
+  } else {
   // the chunks past the taps (the bias column's 1, then zeros): stage s
   // always holds k-tile s % nk (nk divides the ring), so they are written once
   for (int q = threadIdx.x; q < kAStages * 8 * kBM; q += blockDim.x) {
     const int st = q / (8 * kBM), c = (q / kBM) & 7, r = q % kBM;
     const int tap = (st % nk) * 8 + c;
     if (tap >= g.ks * g.ks)
-      *reinterpret_cast<uint4*>(smem + FrameSmem::kA + st * kStageA + r * 128 +
+      *reinterpret_cast<uint4*>(smem + Sm::kA + st * kStageA + r * 128 +
                                 ((c ^ (r & 7)) << 4)) =
           make_uint4(tap == g.ks * g.ks ? 0x3F80u : 0u, 0u, 0u, 0u);
+  }
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   if (warp == 0) {
@@ -167,7 +184,7 @@ k_conv_frame(const __grid_constant__ CUtensorMap tf256, const __grid_constant__ 
       // producer: the weights once, then each tile's raw input rows
       mbar_expect_tx(&bres_full, (uint32_t)(nk * kBBytes));
       for (int i = 0; i < nk; i++)
-        tma_load_2d(smem + FrameSmem::kB + i * kBBytes, &tb, &bres_full, i * kBK, 0);
+        tma_load_2d(smem + Sm::kB + i * kBBytes, &tb, &bres_full, i * kBK, 0);
       const uint32_t bytes =
           (uint32_t)(kRawRows * (3 * (256 + 8) * 4 + (g.has_mask ? 256 + 16 : 0)));
       uint32_t j = 0;
@@ -181,7 +198,7 @@ k_conv_frame(const __grid_constant__ CUtensorMap tf256, const __grid_constant__ 
           s_fail = 1;
           break;
         }
-        uint8_t* st = smem + FrameSmem::kRaw + s * kRawBytes;
+        uint8_t* st = smem + Sm::kRaw + s * kRawBytes;
         mbar_expect_tx(&raw_full[s], bytes);
         tma_load_4d(st, &tf256, &raw_full[s], xa, y0, 0, b);
         tma_load_4d(st + kRawTail, &tf8, &raw_full[s], xa + 256, y0, 0, b);
@@ -220,7 +237,99 @@ k_conv_frame(const __grid_constant__ CUtensorMap tf256, const __grid_constant__ 
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[a]);
     }
-  } else if (warp >= kXfWarp0) {
+  } else if (PAR && warp >= kXfWarp0) {
+    // 3 x 3, stride 2.  Group x takes tiles j = x, x + 3, ... into its two
+    // record buffers in turn.  Window pixel d (input x0 + d, d = 0 ... 256) of
+    // input row ky is converted once, to a 16-byte record (R, G, B, mask as
+    // BF16, four zeros), stored in O_ky[d / 2] (d even) or E_ky[d / 2] (d odd).
+    // Output pixel m reads window pixels 2m + kx, so its taps are O_ky[m],
+    // E_ky[m], O_ky[m + 1]: each tap's operand is an array (or one record
+    // further), 128 consecutive 16-byte rows, the unswizzled K-major layout
+    // (8-row groups 128 bytes apart).  A K = 16 slice joins two taps (the
+    // second 8 channels at the descriptor's leading-dimension offset from
+    // the first); the arrays lie in the order O_0, E_0, E_1, O_1, O_2, E_2
+    // and the constant block above them, so that every such offset is
+    // positive.  Slice 4 joins tap (2, 2) and the bias row, the slices past
+    // it are zeros: the MMA sequence of the GEMM over the im2col operand.
+    const int x = (warp - kXfWarp0) / kXfGroupWarps;
+    const int xt = threadIdx.x - (kXfWarp0 + x * kXfGroupWarps) * 32;  // 0 ... 191
+    constexpr uint32_t idesc = idesc_bf16(kBM, BN);
+    constexpr uint32_t S = kParArr;
+    const uint32_t cst_s = smem_u32(smem + Sm::kCst);
+    if (xt == 0 && !mbar_wait(&bres_full, 0, g.wait_ns)) s_fail = 1;
+    uint32_t j = (uint32_t)x, jj = 0;  // CTA tile index; the group's own count
+    for (int t = blockIdx.x + x * gridDim.x; t < g.tiles;
+         t += kXfGroups * gridDim.x, j += kXfGroups, jj++) {
+      const int rs = (int)(j % kRawStages);
+      const int ab = x * 2 + (int)(jj & 1u);  // the record buffer, its barrier
+      uint8_t* buf = smem + Sm::kA + ab * kParBuf;
+      bool ok =
+          __all_sync(0xffffffffu, mbar_wait(&raw_full[rs], (j / kRawStages) & 1u, g.wait_ns));
+      // the buffer's last MMAs (the group's tile jj - 2) have completed
+      ok = ok && __all_sync(0xffffffffu,
+                            mbar_wait(&a_empty[ab], ((jj >> 1) & 1u) ^ 1u, g.wait_ns));
+      if (ok) {
+        const int row = t / g.segs, seg = t - row * g.segs;
+        const int x0 = seg * kBM * 2 - g.pad;
+        const int fa = x0 - (x0 & ~3), fm = x0 - (x0 & ~15);  // x0 within the raw rows
+        const uint8_t* raw = smem + Sm::kRaw + rs * kRawBytes;
+        const float* rf = reinterpret_cast<const float*>(raw);
+        const float* rt = reinterpret_cast<const float*>(raw + kRawTail);
+        for (int q = xt; q < 3 * 257; q += kXfGroupWarps * 32) {
+          const int ky = q >= 514 ? 2 : q >= 257 ? 1 : 0;
+          const int d = q - ky * 257, f = fa + d, h = fm + d;
+          // colour planes: the 256-float box, or the 8-float box past it
+          const bool main = f < 256;
+          const float* p = main ? rf + ky * 256 + f : rt + ky * 8 + (f - 256);
+          const int ps = main ? 768 : 24;  // plane stride
+          const float c0 = p[0], c1 = p[ps], c2 = p[2 * ps];
+          const uint8_t mb = !g.has_mask ? 0
+                             : h < 256    ? raw[kRawMask + ky * 256 + h]
+                                          : raw[kRawMaskTail + ky * 16 + h - 256];
+          const __nv_bfloat162 rg = __floats2bfloat162_rn(c0, c1);
+          const __nv_bfloat162 bm = __floats2bfloat162_rn(c2, mb ? 1.0f : 0.0f);
+          const int arr = ky * 2 + ((d & 1) ^ (ky == 1 ? 1 : 0));  // O_0 E_0 | E_1 O_1 | O_2 E_2
+          *reinterpret_cast<uint4*>(buf + arr * kParArr + (d >> 1) * 16) =
+              make_uint4(*reinterpret_cast<const uint32_t*>(&rg),
+                         *reinterpret_cast<const uint32_t*>(&bm), 0u, 0u);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&raw_empty[rs]);
+      // the whole group stops together: the barrier ORs every thread's view
+      if (group_sync_or(x, !ok || failed(&s_fail))) {
+        s_fail = 1;
+        break;
+      }
+      if (xt == 0) {
+        const int a = (int)(j % kAcc);
+        if (!mbar_wait(&acc_empty[a], ((j / kAcc) & 1u) ^ 1u, g.wait_ns)) {
+          s_fail = 1;
+        } else {
+          tc_fence_after();
+          const uint32_t d = tmem + (uint32_t)(a * kAccStride);
+          const uint32_t bs = smem_u32(buf);
+          // the weights' K = 16 slice q: k-tile q / 4, 32 bytes per slice
+          const uint64_t bd0 = sw128_desc(smem_u32(smem + Sm::kB));
+          auto bq = [&](int q) {
+            return bd0 + (uint64_t)((q >> 2) * (kBBytes >> 4)) + 2u * (uint32_t)(q & 3);
+          };
+          // slices 0 ... 4: (start, leading-dimension offset) as above
+          mma_bf16(d, kmajor_desc(bs, S, 128u, 0u), bq(0), idesc, 0u);
+          mma_bf16(d, kmajor_desc(bs + 16u, 3u * S - 16u, 128u, 0u), bq(1), idesc, 1u);
+          mma_bf16(d, kmajor_desc(bs + 2u * S, S + 16u, 128u, 0u), bq(2), idesc, 1u);
+          mma_bf16(d, kmajor_desc(bs + 4u * S, S, 128u, 0u), bq(3), idesc, 1u);
+          mma_bf16(d, kmajor_desc(bs + 4u * S + 16u, cst_s - (bs + 4u * S + 16u), 128u, 0u),
+                   bq(4), idesc, 1u);
+          const uint64_t zd = kmajor_desc(cst_s + 2048u, 2048u, 128u, 0u);
+          for (int q = 5; q < 4 * nk; q++) mma_bf16(d, zd, bq(q), idesc, 1u);
+          mma_commit(&a_empty[ab]);
+          mma_commit(&acc_full[a]);
+        }
+      }
+    }
+  } else if (!PAR && warp >= kXfWarp0) {
     // im2col group x takes tiles j = x, x + 3, ...: one thread per (tile row
     // r, input row ky) writes the ks chunks of taps (ky, 0 ... ks - 1) of row
     // r (consecutive threads take consecutive rows: stride-apart words on the
@@ -246,7 +355,7 @@ k_conv_frame(const __grid_constant__ CUtensorMap tf256, const __grid_constant__ 
         const int row = t / g.segs, seg = t - row * g.segs;
         const int x0 = seg * kBM * g.stride - g.pad;
         const int fa = x0 - (x0 & ~3), fm = x0 - (x0 & ~15);  // x0 within the raw rows
-        const uint8_t* raw = smem + FrameSmem::kRaw + rs * kRawBytes;
+        const uint8_t* raw = smem + Sm::kRaw + rs * kRawBytes;
         const float* rf = reinterpret_cast<const float*>(raw);
         const float* rt = reinterpret_cast<const float*>(raw + kRawTail);
         // the 16-byte chunk of window pixel d of input row ky: R, G, B, mask
@@ -268,7 +377,7 @@ k_conv_frame(const __grid_constant__ CUtensorMap tf256, const __grid_constant__ 
         };
         auto store = [&](int ky, int kx, int r, uint2 v) {
           const int tap = ky * g.ks + kx, c = tap & 7;
-          uint8_t* A = smem + FrameSmem::kA + ((aj + (uint32_t)(tap >> 3)) % kAStages) * kStageA;
+          uint8_t* A = smem + Sm::kA + ((aj + (uint32_t)(tap >> 3)) % kAStages) * kStageA;
           *reinterpret_cast<uint4*>(A + r * 128 + ((c ^ (r & 7)) << 4)) =
               make_uint4(v.x, v.y, 0u, 0u);
         };
@@ -311,8 +420,8 @@ k_conv_frame(const __grid_constant__ CUtensorMap tf256, const __grid_constant__ 
           const uint32_t d = tmem + (uint32_t)(a * kAccStride);
           for (int i = 0; i < nk; i++) {
             const int s = (int)((aj + (uint32_t)i) % kAStages);
-            const uint64_t ad = sw128_desc(smem_u32(smem + FrameSmem::kA + s * kStageA));
-            const uint64_t bd = sw128_desc(smem_u32(smem + FrameSmem::kB + i * kBBytes));
+            const uint64_t ad = sw128_desc(smem_u32(smem + Sm::kA + s * kStageA));
+            const uint64_t bd = sw128_desc(smem_u32(smem + Sm::kB + i * kBBytes));
 #pragma unroll
             for (int kk = 0; kk < kBK / 16; kk++)
               mma_bf16(d, ad + 2 * kk, bd + 2 * kk, idesc, (i > 0 || kk > 0) ? 1u : 0u);
@@ -352,18 +461,18 @@ bool make_row_map(CUtensorMap* map, const void* base, bool bytes, int B, int H, 
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN>
+template <int BN, bool PAR>
 cudaError_t launch_frame(const CUtensorMap (&maps)[5], const FrameArgs& g, int smem,
                          cudaStream_t s) {
-  const cudaError_t attr = opt_in_smem((const void*)k_conv_frame<BN>, smem);
+  const cudaError_t attr = opt_in_smem((const void*)k_conv_frame<BN, PAR>, smem);
   if (attr != cudaSuccess) return attr;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     sms = 1;
   const int grid = std::max(1, std::min(g.tiles, sms));
-  k_conv_frame<BN><<<grid, kFrThreads, smem, s>>>(maps[0], maps[1], maps[2], maps[3], maps[4],
-                                                   g);
+  k_conv_frame<BN, PAR><<<grid, kFrThreads, smem, s>>>(maps[0], maps[1], maps[2], maps[3],
+                                                        maps[4], g);
   return cudaGetLastError();
 }
 
@@ -379,7 +488,7 @@ cudaError_t tc_conv_frame(const TcFrameConvProblem& pr, cudaStream_t s) {
   const int Wo = (pr.W + 2 * pr.pad - pr.ks) / pr.stride + 1;
   if (pr.B <= 0 || Ho <= 0 || Wo <= 0 || pr.N <= 0) return cudaSuccess;
   if (!frame_conv_supported(pr.W, pr.ks, pr.stride, pr.N) || pr.ldk % 8 ||
-      pr.ldk < pr.ks * pr.ks * 8 + 1 || kAStages % ((pr.ldk + kBK - 1) / kBK) != 0 || (reinterpret_cast<uintptr_t>(pr.frames) & 15) ||
+      pr.ldk < pr.ks * pr.ks * 8 + 1 || (reinterpret_cast<uintptr_t>(pr.frames) & 15) ||
       (reinterpret_cast<uintptr_t>(pr.masks) & 15) || (reinterpret_cast<uintptr_t>(pr.W_) & 15))
     return cudaErrorInvalidValue;
   const int bn = tc_gemm_bn(pr.N);
@@ -404,7 +513,11 @@ cudaError_t tc_conv_frame(const TcFrameConvProblem& pr, cudaStream_t s) {
   g.status = pr.status;
   g.wait_ns = pr.wait_ns;
   g.withhold = pr.withhold_loads;
-  const int smem = FrameSmem::kB + g.nk * bn * kBK * 2 + 1024;
+  // 3 x 3 at stride 2: the record layout; else im2col rows in a ring whose
+  // stage s always holds k-tile s % nk
+  const bool par = pr.ks == 3 && pr.stride == 2;
+  if (!par && kAStages % g.nk != 0) return cudaErrorInvalidValue;
+  const int smem = (par ? FrameSmem<true>::kB : FrameSmem<false>::kB) + g.nk * bn * kBK * 2 + 1024;
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   CUtensorMap maps[5];
   // without a mask the mask maps are never used: encode them over the frames
@@ -415,11 +528,19 @@ cudaError_t tc_conv_frame(const TcFrameConvProblem& pr, cudaStream_t s) {
       !make_row_map(&maps[3], mbase, true, pr.B, pr.H, pr.W, 16) ||
       !make_map(&maps[4], pr.W_, pr.N, pr.ldk, pr.ldk, bn))
     return cudaErrorInvalidValue;
+  if (par) {
+    switch (bn) {
+      case 32: return launch_frame<32, true>(maps, g, smem, s);
+      case 64: return launch_frame<64, true>(maps, g, smem, s);
+      case 96: return launch_frame<96, true>(maps, g, smem, s);
+      default: return launch_frame<128, true>(maps, g, smem, s);
+    }
+  }
   switch (bn) {
-    case 32: return launch_frame<32>(maps, g, smem, s);
-    case 64: return launch_frame<64>(maps, g, smem, s);
-    case 96: return launch_frame<96>(maps, g, smem, s);
-    default: return launch_frame<128>(maps, g, smem, s);
+    case 32: return launch_frame<32, false>(maps, g, smem, s);
+    case 64: return launch_frame<64, false>(maps, g, smem, s);
+    case 96: return launch_frame<96, false>(maps, g, smem, s);
+    default: return launch_frame<128, false>(maps, g, smem, s);
   }
 }
 
