@@ -3,25 +3,28 @@
 // R, G, B, mask, four zeros) followed by gs2d_conv_bf16 in one persistent
 // tcgen05 kernel, so the 8-channel image is never written out or read back.
 //
-// A tile is 128 consecutive output pixels of one output row; the CTA takes
-// tiles j = 0, 1, ... of its share in turn.  Per tile:
-//   warp 0, one lane   four TMA loads of the tile's three input rows: the
-//                      colour planes (256 + 8 floats per row and plane from a
-//                      16-byte boundary) and the mask (256 + 16 bytes per
-//                      row), into a ring of raw stages;
+// A tile is 128 (120 for 3 x 3 at stride 2) consecutive output pixels of
+// one output row; the CTA takes tiles j = 0, 1, ... of its share in turn.
+// Per tile:
+//   warp 0, one lane   TMA loads of the tile's three input rows into a ring of
+//                      raw stages: the colour planes (256 floats per row and
+//                      plane from a 16-byte boundary, for 128-pixel tiles 8
+//                      more in a second box) and the mask (256 bytes, and 16
+//                      more);
 //   warps 10-27        three groups of six warps, group j % 3, build the
-//                      tile's im2col rows in shared memory: one thread per
-//                      (row, input row ky) converts the ks pixels of its taps
-//                      to 16-byte chunks (R, G, B, mask as BF16, four zeros;
-//                      with 3 x 3 taps at stride 2 the third pixel comes from
-//                      the next lane) and stores them in the 128-byte-swizzled
-//                      K-major layout a TMA box of the im2col operand would
-//                      have; the tile's k-tiles (64 K each) take consecutive
-//                      stages of a second ring, whose bias and zero chunks,
-//                      the same for every tile, are written once.  After a
-//                      barrier of the group its first thread issues the
-//                      tile's MMAs (128 x BN x 16 per K slice, weights
-//                      resident in shared memory) into TMEM accumulator j % 4;
+//                      tile's operand in shared memory, then the group's
+//                      first thread issues the tile's MMAs (128 x BN x 16 per
+//                      K slice, weights resident) into TMEM accumulator j % 4:
+//                      3 x 3 at stride 2: each window pixel converted once to
+//                      a 16-byte record (R, G, B, mask as BF16, four zeros)
+//                      in arrays of the odd and even pixels of each input
+//                      row, the taps joined by the MMA descriptors (see the
+//                      record-mode group below);
+//                      else: one thread per (row, input row ky) writes its
+//                      taps' records into the 128-byte-swizzled K-major
+//                      layout a TMA box of the im2col operand would have, the
+//                      tile's k-tiles (64 K each) in consecutive stages of a
+//                      second ring whose bias and zero chunks are written once;
 //   warps 2-9          two groups of four warps, group j % 2, run the
 //                      epilogue (tcgen05.ld, ReLU, BF16 stores).
 // Three tiles are built and two drained at a time: a single warp per role
@@ -122,6 +125,10 @@ k_conv_frame(const __grid_constant__ CUtensorMap tf256, const __grid_constant__ 
   constexpr int kCols = kAcc * kAccStride;
   constexpr int kTmemCols = kCols <= 128 ? 128 : kCols <= 256 ? 256 : 512;
   constexpr int kBBytes = BN * kBK * 2;
+  // output pixels per tile: 120 in record mode, so that the 241 input pixels
+  // of a row, from a 16-byte boundary, fit one 256-element TMA box (colour
+  // planes and mask alike); 128 otherwise
+  constexpr int kTW = PAR ? 120 : kBM;
   using Sm = FrameSmem<PAR>;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t raw_full[kRawStages], raw_empty[kRawStages];
@@ -186,12 +193,13 @@ k_conv_frame(const __grid_constant__ CUtensorMap tf256, const __grid_constant__ 
       for (int i = 0; i < nk; i++)
         tma_load_2d(smem + Sm::kB + i * kBBytes, &tb, &bres_full, i * kBK, 0);
       const uint32_t bytes =
-          (uint32_t)(kRawRows * (3 * (256 + 8) * 4 + (g.has_mask ? 256 + 16 : 0)));
+          PAR ? (uint32_t)(kRawRows * (3 * 256 * 4 + (g.has_mask ? 256 : 0)))
+              : (uint32_t)(kRawRows * (3 * (256 + 8) * 4 + (g.has_mask ? 256 + 16 : 0)));
       uint32_t j = 0;
       for (int t = blockIdx.x; t < g.tiles && !failed(&s_fail); t += gridDim.x, j++) {
         const int row = t / g.segs, seg = t - row * g.segs;
         const int b = row / g.Ho, oy = row - b * g.Ho;
-        const int x0 = seg * kBM * g.stride - g.pad, y0 = oy * g.stride - g.pad;
+        const int x0 = seg * kTW * g.stride - g.pad, y0 = oy * g.stride - g.pad;
         const int xa = x0 & ~3, xm = x0 & ~15;  // 16-byte boundaries (floor)
         const int s = (int)(j % kRawStages);
         if (!mbar_wait(&raw_empty[s], ((j / kRawStages) & 1u) ^ 1u, g.wait_ns)) {
@@ -201,10 +209,10 @@ k_conv_frame(const __grid_constant__ CUtensorMap tf256, const __grid_constant__ 
         uint8_t* st = smem + Sm::kRaw + s * kRawBytes;
         mbar_expect_tx(&raw_full[s], bytes);
         tma_load_4d(st, &tf256, &raw_full[s], xa, y0, 0, b);
-        tma_load_4d(st + kRawTail, &tf8, &raw_full[s], xa + 256, y0, 0, b);
+        if (!PAR) tma_load_4d(st + kRawTail, &tf8, &raw_full[s], xa + 256, y0, 0, b);
         if (g.has_mask) {
           tma_load_3d(st + kRawMask, &tm256, &raw_full[s], xm, y0, b);
-          tma_load_3d(st + kRawMaskTail, &tm16, &raw_full[s], xm + 256, y0, b);
+          if (!PAR) tma_load_3d(st + kRawMaskTail, &tm16, &raw_full[s], xm + 256, y0, b);
         }
       }
     }
@@ -228,23 +236,25 @@ k_conv_frame(const __grid_constant__ CUtensorMap tf256, const __grid_constant__ 
       }
       tc_fence_after();
       const int row = t / g.segs, seg = t - row * g.segs;
-      const int ox = seg * kBM + r;
+      const int ox = seg * kTW + r;
       const size_t o = ((size_t)row * g.Wo + ox) * g.ldc;
       const uint32_t taddr =
           tmem + (uint32_t)(a * kAccStride) + ((uint32_t)(quarter * 32) << 16);
-      store_acc_row<BN>(taddr, ox < g.Wo, o, g.N, g.relu, vec_ok, g.out_f32, g.out_bf16);
+      store_acc_row<BN>(taddr, r < kTW && ox < g.Wo, o, g.N, g.relu, vec_ok, g.out_f32,
+                        g.out_bf16);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[a]);
     }
   } else if (PAR && warp >= kXfWarp0) {
     // 3 x 3, stride 2.  Group x takes tiles j = x, x + 3, ... into its two
-    // record buffers in turn.  Window pixel d (input x0 + d, d = 0 ... 256) of
+    // record buffers in turn.  Window pixel d (input x0 + d, d = 0 ... 240) of
     // input row ky is converted once, to a 16-byte record (R, G, B, mask as
     // BF16, four zeros), stored in O_ky[d / 2] (d even) or E_ky[d / 2] (d odd).
     // Output pixel m reads window pixels 2m + kx, so its taps are O_ky[m],
     // E_ky[m], O_ky[m + 1]: each tap's operand is an array (or one record
-    // further), 128 consecutive 16-byte rows, the unswizzled K-major layout
+    // further), 128 consecutive 16-byte rows (the last 8 unused: a tile has
+    // 120 output pixels), the unswizzled K-major layout
     // (8-row groups 128 bytes apart).  A K = 16 slice joins two taps (the
     // second 8 channels at the descriptor's leading-dimension offset from
     // the first); the arrays lie in the order O_0, E_0, E_1, O_1, O_2, E_2
@@ -270,22 +280,17 @@ k_conv_frame(const __grid_constant__ CUtensorMap tf256, const __grid_constant__ 
                             mbar_wait(&a_empty[ab], ((jj >> 1) & 1u) ^ 1u, g.wait_ns));
       if (ok) {
         const int row = t / g.segs, seg = t - row * g.segs;
-        const int x0 = seg * kBM * 2 - g.pad;
+        const int x0 = seg * kTW * 2 - g.pad;
         const int fa = x0 - (x0 & ~3), fm = x0 - (x0 & ~15);  // x0 within the raw rows
         const uint8_t* raw = smem + Sm::kRaw + rs * kRawBytes;
         const float* rf = reinterpret_cast<const float*>(raw);
-        const float* rt = reinterpret_cast<const float*>(raw + kRawTail);
-        for (int q = xt; q < 3 * 257; q += kXfGroupWarps * 32) {
-          const int ky = q >= 514 ? 2 : q >= 257 ? 1 : 0;
-          const int d = q - ky * 257, f = fa + d, h = fm + d;
-          // colour planes: the 256-float box, or the 8-float box past it
-          const bool main = f < 256;
-          const float* p = main ? rf + ky * 256 + f : rt + ky * 8 + (f - 256);
-          const int ps = main ? 768 : 24;  // plane stride
-          const float c0 = p[0], c1 = p[ps], c2 = p[2 * ps];
-          const uint8_t mb = !g.has_mask ? 0
-                             : h < 256    ? raw[kRawMask + ky * 256 + h]
-                                          : raw[kRawMaskTail + ky * 16 + h - 256];
+        constexpr int kWin = 2 * kTW + 1;  // window pixels per input row
+        for (int q = xt; q < 3 * kWin; q += kXfGroupWarps * 32) {
+          const int ky = q >= 2 * kWin ? 2 : q >= kWin ? 1 : 0;
+          const int d = q - ky * kWin, f = fa + d, h = fm + d;  // f, h < 256
+          const float* p = rf + ky * 256 + f;  // planes 768 floats apart
+          const float c0 = p[0], c1 = p[768], c2 = p[2 * 768];
+          const uint8_t mb = g.has_mask ? raw[kRawMask + ky * 256 + h] : 0;
           const __nv_bfloat162 rg = __floats2bfloat162_rn(c0, c1);
           const __nv_bfloat162 bm = __floats2bfloat162_rn(c2, mb ? 1.0f : 0.0f);
           const int arr = ky * 2 + ((d & 1) ^ (ky == 1 ? 1 : 0));  // O_0 E_0 | E_1 O_1 | O_2 E_2
@@ -505,7 +510,11 @@ cudaError_t tc_conv_frame(const TcFrameConvProblem& pr, cudaStream_t s) {
   g.ldc = pr.ldc;
   g.relu = pr.relu;
   g.has_mask = pr.masks ? 1 : 0;
-  g.segs = (Wo + kBM - 1) / kBM;
+  // 3 x 3 at stride 2: the record layout, 120-pixel tiles; else im2col rows
+  // in a ring whose stage s always holds k-tile s % nk, 128-pixel tiles
+  const bool par = pr.ks == 3 && pr.stride == 2;
+  const int tw = par ? 120 : kBM;
+  g.segs = (Wo + tw - 1) / tw;
   g.tiles = pr.B * Ho * g.segs;
   g.nk = (pr.ldk + kBK - 1) / kBK;
   g.out_f32 = pr.out_f32;
@@ -513,9 +522,6 @@ cudaError_t tc_conv_frame(const TcFrameConvProblem& pr, cudaStream_t s) {
   g.status = pr.status;
   g.wait_ns = pr.wait_ns;
   g.withhold = pr.withhold_loads;
-  // 3 x 3 at stride 2: the record layout; else im2col rows in a ring whose
-  // stage s always holds k-tile s % nk
-  const bool par = pr.ks == 3 && pr.stride == 2;
   if (!par && kAStages % g.nk != 0) return cudaErrorInvalidValue;
   const int smem = (par ? FrameSmem<true>::kB : FrameSmem<false>::kB) + g.nk * bn * kBK * 2 + 1024;
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
