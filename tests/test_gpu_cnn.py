@@ -335,12 +335,23 @@ def test_conv_frame_equals_input_then_conv(nat, B, H, W, ks, st, pad, co, with_m
     """gs2d_conv_frame_bf16 forms the 8-channel input of each im2col row from
     the float frame and the mask itself: its output equals gs2d_cnn_input +
     gs2d_conv_bf16 bit for bit."""
+    _frame_vs_parts(nat, B, H, W, ks, st, pad, co, with_mask, out)
+
+
+@pytest.mark.parametrize("ks,st", [(3, 2), (3, 1)])
+def test_conv_frame_three_k_tiles(nat, ks, st):
+    """A padded weight row (ldk 136: three k-tiles, zero slices past the bias)
+    in both operand layouts."""
+    _frame_vs_parts(nat, 1, 23, 272, ks, st, 1, 32, True, "bf16", ldk_extra=56)
+
+
+def _frame_vs_parts(nat, B, H, W, ks, st, pad, co, with_mask, out, ldk_extra=0):
     g = np.random.Generator(np.random.PCG64(11 * co + H + ks))
     frames = torch.from_numpy(g.normal(0.5, 0.4, size=(B, 3, H, W)).astype(np.float32)).cuda()
     masks = None
     if with_mask:
         masks = torch.from_numpy(g.choice(np.array([0, 1, 7], np.uint8), size=(B, H, W))).cuda()
-    ldk = -(-(ks * ks * 8 + 1) // 8) * 8
+    ldk = -(-(ks * ks * 8 + 1) // 8) * 8 + ldk_extra
     w = np.zeros((co, ldk), np.float32)
     w[:, :ks * ks * 8 + 1] = g.normal(size=(co, ks * ks * 8 + 1)) / np.sqrt(ks * ks * 8)
     d_w = bf16_dev(cnn.bf16_round(w))
