@@ -1,6 +1,9 @@
 // Implicit-GEMM convolution fed by TMA tap loads: the learned initialiser's
 // wide 3 x 3 stride-2 layers (paper section 3.2 B) as a persistent tcgen05
-// kernel, one CTA per SM.
+// kernel, one CTA per SM.  At 1080p it runs layer 4 (C = 128); the 3 x 3,
+// stride-2, pad-1 layers with C = 32 or 64 and an even width go to the
+// row-box kernel of csrc/conv_rows.cu (fewer, larger TMA boxes), and this
+// kernel keeps every other supported shape.
 //
 //   Z[p][n] = sum_k col(X)[p][k] W[n][k],   k = (ky ks + kx) C + ci,
 //   a column of ones at k = ks^2 C carrying the bias, zeros beyond.
@@ -29,8 +32,12 @@
 // in shared memory when they fit (the narrow early layers); else each stage
 // also brings the k-tile's weight box, and serves two of the CTA's tiles
 // with it (their A boxes side by side, one accumulator each), which halves
-// the weight traffic out of L2.  Every mbarrier wait is bounded in
-// time; a timeout records GS2D_ERR_TIMEOUT in the caller's status word.
+// the weight traffic out of L2.  The producer and the MMA issuer are lone
+// threads whose every dependent instruction costs about ten cycles, so they
+// keep the launch's fields in registers, advance stage and tap counters by
+// increments and add precomputed descriptor offsets.  Every mbarrier wait is
+// bounded in time; a timeout records GS2D_ERR_TIMEOUT in the caller's status
+// word.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
