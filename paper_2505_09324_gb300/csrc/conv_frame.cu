@@ -65,8 +65,12 @@ constexpr int kStageA = kBM * kBK * 2;  // 16 KB
 // 3 x 3 at stride 2 (the network's first layer): a tile's operand as six
 // arrays of 16-byte pixel records, the even and the odd window pixels of
 // each input row (129 records each), two buffers per group
-constexpr int kParArr = 129 * 16;
-constexpr int kParBuf = 6 * kParArr + 32;  // 12416
+// Arrays of 129 records, 2112 bytes apart: an odd and an even record of the
+// same index (stored by adjacent lanes) then fall 64 bytes apart in the
+// banks, so a quarter-warp's 16-byte stores do not conflict (at 2064 bytes
+// apart half of the build's shared-memory wavefronts were conflicts).
+constexpr int kParArr = 2112;
+constexpr int kParBuf = 6 * kParArr + 32;  // 12704
 constexpr int kCstBytes = 6144;            // bias rows (2 KB), then 4 KB of zeros
 
 struct FrameArgs {
