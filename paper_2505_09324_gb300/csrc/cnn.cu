@@ -263,27 +263,34 @@ __global__ void k_cnn_input(int B, int H, int W, const float* __restrict__ frame
 }
 
 // One thread per (output pixel, 8-wide chunk of k).
+// One thread per 16-byte chunk of col (consecutive threads, consecutive
+// chunks of a row: coalesced stores).  I is the index type: 32-bit whenever
+// the chunk count fits, since 64-bit divisions are long emulated sequences
+// and this kernel is a few divisions per 16 bytes moved.
+template <typename I>
 __global__ void k_im2col(int B, int Hi, int Wi, int C, int Ho, int Wo, int ks, int stride,
                          int pad, int ldk, const bf16* __restrict__ x, bf16* __restrict__ col) {
-  const int chunks = ldk / 8, kk = ks * ks * C;
-  const size_t total = (size_t)B * Ho * Wo * chunks;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
-       t += (size_t)gridDim.x * blockDim.x) {
-    const size_t p = t / chunks;
-    const int c = (int)(t % chunks), k0 = 8 * c;
-    const int b = (int)(p / ((size_t)Ho * Wo));
-    const int r = (int)(p % ((size_t)Ho * Wo));
-    const int oy = r / Wo, ox = r % Wo;
+  const I chunks = (I)(ldk / 8), hw = (I)Ho * (I)Wo;
+  const int kk = ks * ks * C;
+  const I total = (I)B * hw * chunks;
+  for (I t = (I)blockIdx.x * (I)blockDim.x + (I)threadIdx.x; t < total;
+       t += (I)gridDim.x * (I)blockDim.x) {
+    const I p = t / chunks;
+    const int c = (int)(t - p * chunks), k0 = 8 * c;
+    const int b = (int)(p / hw);
+    const int r = (int)(p - (I)b * hw);
+    const int oy = r / Wo, ox = r - oy * Wo;
     uint4 v = make_uint4(0u, 0u, 0u, 0u);
     if (k0 < kk) {
-      const int tap = k0 / C, ci = k0 % C;
-      const int iy = oy * stride + tap / ks - pad, ix = ox * stride + tap % ks - pad;
+      const int tap = k0 / C, ci = k0 - tap * C;
+      const int ky = tap / ks, kx = tap - ky * ks;
+      const int iy = oy * stride + ky - pad, ix = ox * stride + kx - pad;
       if (iy >= 0 && iy < Hi && ix >= 0 && ix < Wi)
         v = *reinterpret_cast<const uint4*>(x + (((size_t)b * Hi + iy) * Wi + ix) * C + ci);
     } else if (k0 == kk) {
       v.x = 0x3F80u;  // bf16 1.0 in the low half: element k0
     }
-    *reinterpret_cast<uint4*>(col + p * ldk + k0) = v;
+    *reinterpret_cast<uint4*>(col + (size_t)p * ldk + k0) = v;
   }
 }
 
@@ -399,9 +406,14 @@ extern "C" gs2d_status gs2d_im2col(const void* x, int32_t B, int32_t Hi, int32_t
   if (Ho < 1 || Wo < 1) return set_error(GS2D_ERR_INVALID_ARG, "gs2d_im2col: empty output");
   const size_t total = (size_t)B * Ho * Wo * (ldk / 8);
   if (total == 0) return set_error(GS2D_OK, "");
-  k_im2col<<<grid_for(total, 256), 256, 0, (cudaStream_t)stream>>>(
-      B, Hi, Wi, C, Ho, Wo, ks, stride, pad, ldk, static_cast<const bf16*>(x),
-      static_cast<bf16*>(col));
+  if (total < (size_t)INT32_MAX)
+    k_im2col<uint32_t><<<grid_for(total, 256), 256, 0, (cudaStream_t)stream>>>(
+        B, Hi, Wi, C, Ho, Wo, ks, stride, pad, ldk, static_cast<const bf16*>(x),
+        static_cast<bf16*>(col));
+  else
+    k_im2col<size_t><<<grid_for(total, 256), 256, 0, (cudaStream_t)stream>>>(
+        B, Hi, Wi, C, Ho, Wo, ks, stride, pad, ldk, static_cast<const bf16*>(x),
+        static_cast<bf16*>(col));
   return launched("gs2d_im2col");
 }
 
