@@ -295,17 +295,20 @@ __global__ void k_im2col(int B, int Hi, int Wi, int C, int Ho, int Wo, int ks, i
 }
 
 // One thread per (input pixel, channel): the taps that read it.
+// I: the index type, 32-bit whenever the element count fits (as k_im2col).
+template <typename I>
 __global__ void k_col2im(const float* __restrict__ dcol, int ldk, int B, int Hi, int Wi, int C,
                          int Ho, int Wo, int ks, int stride, int pad,
                          const bf16* __restrict__ act, bf16* __restrict__ dx) {
-  const size_t total = (size_t)B * Hi * Wi * C;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
-       t += (size_t)gridDim.x * blockDim.x) {
-    const int ci = (int)(t % C);
-    const size_t pin = t / C;
-    const int b = (int)(pin / ((size_t)Hi * Wi));
-    const int r = (int)(pin % ((size_t)Hi * Wi));
-    const int iy = r / Wi, ix = r % Wi;
+  const I hw = (I)Hi * (I)Wi;
+  const I total = (I)B * hw * (I)C;
+  for (I t = (I)blockIdx.x * (I)blockDim.x + (I)threadIdx.x; t < total;
+       t += (I)gridDim.x * (I)blockDim.x) {
+    const I pin = t / (I)C;
+    const int ci = (int)(t - pin * (I)C);
+    const int b = (int)(pin / hw);
+    const int r = (int)(pin - (I)b * hw);
+    const int iy = r / Wi, ix = r - iy * Wi;
     float s = 0.0f;
     for (int ky = 0; ky < ks; ky++) {
       const int ny = iy + pad - ky;
@@ -426,9 +429,14 @@ extern "C" gs2d_status gs2d_col2im(const float* dcol, int32_t ldk, int32_t B, in
   const int Ho = (Hi + 2 * pad - ks) / stride + 1, Wo = (Wi + 2 * pad - ks) / stride + 1;
   const size_t total = (size_t)B * Hi * Wi * C;
   if (total == 0) return set_error(GS2D_OK, "");
-  k_col2im<<<grid_for(total, 256), 256, 0, (cudaStream_t)stream>>>(
-      dcol, ldk, B, Hi, Wi, C, Ho, Wo, ks, stride, pad, static_cast<const bf16*>(act),
-      static_cast<bf16*>(dx));
+  if (total < (size_t)INT32_MAX)
+    k_col2im<uint32_t><<<grid_for(total, 256), 256, 0, (cudaStream_t)stream>>>(
+        dcol, ldk, B, Hi, Wi, C, Ho, Wo, ks, stride, pad, static_cast<const bf16*>(act),
+        static_cast<bf16*>(dx));
+  else
+    k_col2im<size_t><<<grid_for(total, 256), 256, 0, (cudaStream_t)stream>>>(
+        dcol, ldk, B, Hi, Wi, C, Ho, Wo, ks, stride, pad, static_cast<const bf16*>(act),
+        static_cast<bf16*>(dx));
   return launched("gs2d_col2im");
 }
 
