@@ -60,10 +60,9 @@ constexpr int kCstRegion = 8192;
 constexpr int kSmemBudget = 227 * 1024;
 
 struct RowsArgs {
-  int Hi, Wi, C, Ho, Wo;
+  int C, Ho, Wo;
   int N, ldc, relu;
-  int segs, tiles, nk, kbias;
-  int nbox;                     // boxes per A slot: 1 (C = 32) or 2 (C = 64)
+  int segs, tiles, nk;
   int sa, sb;                   // A slots; weight slots (streamed weights)
   int resident_b;
   int a_off, b_off;             // the A ring; the weight ring or the resident weights
@@ -476,8 +475,6 @@ int rows_setup(const TcConvProblem& pr, RowsArgs* g) {
   // row per unit in flight; the tap kernel of csrc/conv_tap.cu is faster there
   if (pr.C != 32 && pr.C != 64) return 0;
   if (pr.N < 1 || pr.N > 256 || pr.B <= 0 || pr.Hi <= 0) return 0;
-  g->Hi = pr.Hi;
-  g->Wi = pr.Wi;
   g->C = pr.C;
   g->Ho = (pr.Hi - 1) / 2 + 1;
   g->Wo = (pr.Wi - 1) / 2 + 1;
@@ -488,10 +485,9 @@ int rows_setup(const TcConvProblem& pr, RowsArgs* g) {
   g->segs = (g->Wo + kBM - 1) / kBM;
   g->tiles = pr.B * g->Ho * g->segs;
   g->nk = (pr.ldk + kBK - 1) / kBK;
-  g->kbias = 9 * pr.C;
-  g->nbox = pr.C == 32 ? 1 : pr.C / 32;
+  const int nbox = pr.C == 32 ? 1 : 2;  // boxes per A slot
   const int bn = tc_gemm_bn(pr.N);
-  const int smem = rows_plan(bn, g->nk, g->nbox, g);
+  const int smem = rows_plan(bn, g->nk, nbox, g);
   // the kernels are built for the weights' placement of the smallest ldk
   return g->resident_b == (rows_resident(pr.C, bn) ? 1 : 0) ? smem : 0;
 }

@@ -61,7 +61,7 @@ constexpr int kCstRegion = 8192;
 constexpr int kSmemBudget = 227 * 1024;
 
 struct TapArgs {
-  int Hi, Wi, C, Ho, Wo, ks, stride, pad;
+  int Ho, Wo, ks, stride, pad;
   int N, ldc, relu;
   int segs, tiles, nk;
   int cw, cpt, blocks_real, kbias;  // channels per block, blocks per tap, tap blocks, bias k
@@ -427,9 +427,6 @@ cudaError_t tap_conv(const TcConvProblem& pr, cudaStream_t s) {
   if (!tap_conv_supported(pr)) return cudaErrorInvalidValue;
   const int bn = tc_gemm_bn(pr.N);
   TapArgs g;
-  g.Hi = pr.Hi;
-  g.Wi = pr.Wi;
-  g.C = pr.C;
   g.Ho = Ho;
   g.Wo = Wo;
   g.ks = pr.ks;
