@@ -34,6 +34,18 @@ def test_every_declared_function_is_exported(nat):
     assert set(decl) == set(nat.EXPORTS)
 
 
+def test_every_declared_constant_is_bound(nat):
+    """Each enum constant of include/gs2d.h has the same value in the Python
+    binding (under its full name or without the GS2D_ prefix)."""
+    src = open(os.path.join(ROOT, "include", "gs2d.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    consts = re.findall(r"\b(GS2D_[A-Z0-9_]+)\s*=\s*(-?\d+)", src)
+    assert len(consts) >= 15
+    for name, value in consts:
+        bound = getattr(nat, name, getattr(nat, name[len("GS2D_"):], None))
+        assert bound == int(value), f"{name} = {value} bound as {bound}"
+
+
 def test_struct_layouts_match(nat):
     lib = nat.load()
     assert lib.gs2d_sizeof_plan() == ctypes.sizeof(nat.Plan)
