@@ -9,8 +9,11 @@ into cell-anchored Gaussians; each frame keeps the n with the largest |w|.
 About 1.3 M parameters; BF16 weights and activations, FP32 accumulation and
 FP32 master weights.
 
-Every convolution is im2col + one BF16 tensor-core GEMM (gs2d_gemm_bf16, the
-bias a weight column against a column of ones); the backward pass is one
+In training every convolution is im2col + one BF16 tensor-core GEMM
+(gs2d_gemm_bf16, the bias a weight column against a column of ones); at
+inference the convolutions run as implicit GEMMs that read their operands
+straight from the activations (gs2d_conv_bf16, gs2d_conv_frame_bf16), with
+the same sums in the same order.  The backward pass is one
 weight-gradient GEMM (dZ^T . col, split over pixels) and one input-gradient
 GEMM (dZ . W) + col2im with the ReLU mask per layer.  The optimiser is the
 library's Adam on the FP32 master weights.  Training minimises the L2 render
