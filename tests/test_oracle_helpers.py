@@ -87,3 +87,30 @@ def test_scale_step_codes_the_range_end_points(bits, lo, hi):
 def test_scale_step_of_an_empty_range():
     assert quant.scale_step(8, 1.0, 1.0) == (0.0, 0.0)
     assert quant.scale_step(8, 2.0, 1.0) == (0.0, 0.0)
+
+
+def test_head_keys_read_each_slots_weight_channel():
+    # out [B, gh gw, 9 slots]: slot s of cell c has its 9 outputs at 9 s ... 9 s + 8,
+    # the weight offset last; key = |0.25 + o8| in float32
+    B, gh, gw, slots = 2, 3, 4, 5
+    g = np.random.Generator(np.random.PCG64(6))
+    out = g.normal(size=(B, gh * gw, 9 * slots)).astype(np.float32)
+    keys = cnn.head_keys(out, gh, gw, slots)
+    assert keys.shape == (B, gh * gw * slots) and keys.dtype == np.float32
+    for b in range(B):
+        for c in range(gh * gw):
+            for s in range(slots):
+                ref = abs(np.float32(0.25) + out[b, c, 9 * s + 8])
+                assert keys[b, c * slots + s] == ref
+
+
+def test_initial_centres_take_the_seed_pixel():
+    g = np.random.Generator(np.random.PCG64(7))
+    frame = g.uniform(0, 1, size=(3, 6, 10)).astype(np.float32)
+    sxy = np.array([[0.5, 0.5], [9.99, 5.99], [3.2, 4.0], [10.0, 6.0], [-0.3, 2.5]])
+    col, xy = sp.initial_centres(frame, sxy)
+    np.testing.assert_array_equal(xy, sxy)
+    for i, (x, y) in enumerate(sxy):
+        xi = min(max(int(np.floor(x)), 0), 9)   # positions on the edge clamp to the last pixel
+        yi = min(max(int(np.floor(y)), 0), 5)
+        np.testing.assert_array_equal(col[i], frame[:, yi, xi].astype(np.float64))
